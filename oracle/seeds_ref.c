@@ -1,0 +1,741 @@
+/*
+ * seeds_ref.c -- the oracle for the SEEDS hot path: a plain, slow,
+ * single-threaded CPU statement of what the GPU library computes.
+ *
+ * TEST INFRASTRUCTURE ONLY.  The test suite, the package smoke check and the
+ * benchmark's CPU-baseline / reference leg are the only callers.  Nothing in
+ * this file is shared with the CUDA path (no header, helper, table or
+ * generator), and the CUDA path never loads it.
+ *
+ * Method: M. Van den Bergh, X. Boix, G. Roig, L. Van Gool, "SEEDS:
+ * Superpixels Extracted via Energy-Driven Sampling" (arXiv 1309.3848).
+ *
+ *   partition s : {1..N} -> {1..K}, sets A_k ........... Sec. 3, Eqs. 1-2
+ *   colour histogram c_A(j) ............................ Sec. 4.1, Eq. 4
+ *   label-patch histogram b_{N_i}(k), G(s) ............. Sec. 4.2, Eqs. 6-7
+ *   grid initialisation, block hierarchy ............... Sec. 5.1
+ *   block / pixel proposals ............................ Sec. 5.2
+ *   intersection test (Prop. 1) ........................ Sec. 5.3, App. A.1
+ *   single-lookup pixel test ........................... Sec. 5.3 (Fig. 6)
+ *   label-patch test (Prop. 2) ......................... Sec. 5.3, App. A.2
+ *   incremental histogram update ....................... Sec. 5.3 (last part)
+ *
+ * Readings taken where the paper is silent or loose (R-numbers; the same
+ * list, with reasons, is kept in the repository's design notes):
+ *   R1  colour bins from the raw RGB bytes: channel value v falls in bin
+ *       b = floor(v*B/256); bin index j = bR*B*B + bG*B + bB.
+ *   R2  colour histograms are normalised by |A| (App. A.1); label-patch
+ *       histograms by the constant Z = 9, also for patches clipped at the
+ *       image border, which keeps Prop. 2 exact.
+ *   R3  grid: gx = max(1, round(sqrt(K*W/H))), gy = max(1, round(K/gx))
+ *       (round half away from zero), K_actual = gx*gy; superpixel column
+ *       edges floor(i*W/gx); level-l block column edges
+ *       floor(i*W/(gx*2^(L-l+1))), rows likewise.  Level L blocks are a
+ *       quarter superpixel (2x2 per superpixel), each finer level splits a
+ *       block 2x2; the grids nest exactly.  Needs gx*2^L <= W, gy*2^L <= H.
+ *   R4  L block levels (L = largest) then one pixel level; every level
+ *       runs iters_per_level iterations.
+ *   R5  a unit (block or pixel) is a boundary unit when a 4-neighbour unit
+ *       of the same level has another label; its candidates are the
+ *       distinct other labels among its 4-neighbours; the best candidate is
+ *       the argmax of the score, ties to the smallest label id.
+ *   R6  schedule: each iteration has four phases (py,px) = (0,0),(0,1),
+ *       (1,0),(1,1); phase units are those with bx%2==px and by%2==py.
+ *       All decisions of a phase read the labels and histograms as they
+ *       were when the phase began; all accepted moves are applied after.
+ *   R7  validity: superpixels are 4-connected.  Unit u may leave k only if
+ *       (i) some 4-neighbour of u has label k and (ii) all k-labelled
+ *       4-neighbours lie in one 4-connected run of k-labelled cells of u's
+ *       8-ring (cells outside the grid are not k).
+ *   R8  a move is accepted only if the score strictly increases.
+ *   R9  every normalised comparison is an exact cross-multiplication
+ *       (here in 128-bit integers).
+ *   R10 pixel score: f(n) = D*c_An(j) + gamma*(G_n + |K_p|),
+ *       f_stay = D*c_{Ak\p}(j) + gamma*G_k, D = N^4 = 81, where
+ *       G_x = sum_{i in K_p} b_{N_i}(x) in counts (Prop. 2); blocks use the
+ *       intersection alone (no G, Sec. 5.3).
+ *   R13 K_p and N_i contain in-image pixels only.
+ *   R14 sequential mode (quality reference only): per iteration the units
+ *       are visited in a random permutation (SplitMix64 + Fisher-Yates),
+ *       each boundary unit proposes one uniformly drawn candidate, and an
+ *       accepted move is applied at once.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define REF_MAX_LEVELS 15
+
+typedef __int128 i128;
+
+typedef struct {
+    int32_t width, height;
+    int32_t num_superpixels;
+    int32_t block_levels;
+    int32_t bins_per_channel;
+    int32_t iters_per_level;
+    int32_t patch;      /* 0 = no boundary term, 3 = 3x3 patches */
+    int32_t gamma_num;
+    int32_t gamma_den;
+} ref_params;
+
+typedef struct {
+    ref_params p;
+    int W, H, L, B, nbins;
+    int gx, gy, K;
+    /* unit grids: level 0 = pixels, level l >= 1 = blocks */
+    int nbx[REF_MAX_LEVELS + 1], nby[REF_MAX_LEVELS + 1];
+    int *xe[REF_MAX_LEVELS + 1], *ye[REF_MAX_LEVELS + 1];
+    int *bin;        /* colour bin of every pixel */
+    int *lab;        /* s(i) for every pixel */
+    int64_t *hist;   /* K x nbins: |A_k| * c_{A_k}(j) */
+    int64_t *size;   /* |A_k| */
+    int64_t *tmp_l;  /* dense histogram of the unit being evaluated */
+    int64_t *tmp_a;  /* A_k \ L */
+    int32_t *moves;  /* (unit, k, n) triples of the current phase */
+    int64_t moves_cap;
+} ref_state;
+
+enum { REF_OK = 0, REF_EINVAL = -1, REF_EGEOM = -2, REF_ENOMEM = -4, REF_ESIZE = -7 };
+
+/* ------------------------------------------------------------------ */
+/* geometry (R3)                                                        */
+/* ------------------------------------------------------------------ */
+
+static int64_t edge_at(int64_t i, int64_t extent, int64_t count)
+{
+    return (i * extent) / count; /* floor for non-negative operands */
+}
+
+int ref_check_params(const ref_params *p)
+{
+    if (!p) return REF_EINVAL;
+    if (p->width < 1 || p->height < 1 || p->width > 32768 || p->height > 32768) return REF_EINVAL;
+    if ((int64_t)p->width * p->height > 0x7fffffffLL) return REF_EINVAL;
+    if (p->num_superpixels < 1) return REF_EINVAL;
+    if (p->block_levels < 0 || p->block_levels > REF_MAX_LEVELS) return REF_EINVAL;
+    if (p->bins_per_channel < 1 || p->bins_per_channel > 16) return REF_EINVAL;
+    if (p->iters_per_level < 1) return REF_EINVAL;
+    if (p->patch != 0 && p->patch != 3) return REF_EINVAL;
+    if (p->gamma_num < 0 || p->gamma_num > 1024) return REF_EINVAL;
+    if (p->gamma_den < 1 || p->gamma_den > 1024) return REF_EINVAL;
+    return REF_OK;
+}
+
+/* R3: superpixel grid gx x gy from the requested count. */
+int ref_grid(const ref_params *p, int32_t *gx_out, int32_t *gy_out)
+{
+    int rc = ref_check_params(p);
+    if (rc) return rc;
+    double K = p->num_superpixels, W = p->width, H = p->height;
+    long gx = lround(sqrt(K * W / H));
+    if (gx < 1) gx = 1;
+    long gy = lround(K / (double)gx);
+    if (gy < 1) gy = 1;
+    if (gx * gy > 65535) return REF_EINVAL;
+    *gx_out = (int32_t)gx;
+    *gy_out = (int32_t)gy;
+    if ((gx << p->block_levels) > p->width || (gy << p->block_levels) > p->height) return REF_EGEOM;
+    return REF_OK;
+}
+
+void ref_destroy(ref_state *st)
+{
+    if (!st) return;
+    for (int l = 0; l <= REF_MAX_LEVELS; ++l) {
+        free(st->xe[l]);
+        free(st->ye[l]);
+    }
+    free(st->bin);
+    free(st->lab);
+    free(st->hist);
+    free(st->size);
+    free(st->tmp_l);
+    free(st->tmp_a);
+    free(st->moves);
+    free(st);
+}
+
+int ref_create(const ref_params *p, ref_state **out)
+{
+    int32_t gx, gy;
+    int rc = ref_grid(p, &gx, &gy);
+    if (rc) return rc;
+    ref_state *st = (ref_state *)calloc(1, sizeof(ref_state));
+    if (!st) return REF_ENOMEM;
+    st->p = *p;
+    st->W = p->width;
+    st->H = p->height;
+    st->L = p->block_levels;
+    st->B = p->bins_per_channel;
+    st->nbins = st->B * st->B * st->B;
+    st->gx = gx;
+    st->gy = gy;
+    st->K = gx * gy;
+    int64_t N = (int64_t)st->W * st->H;
+
+    /* level 0: every pixel is its own unit */
+    st->nbx[0] = st->W;
+    st->nby[0] = st->H;
+    for (int l = 1; l <= st->L; ++l) {
+        st->nbx[l] = gx << (st->L - l + 1);
+        st->nby[l] = gy << (st->L - l + 1);
+    }
+    for (int l = 0; l <= st->L; ++l) {
+        st->xe[l] = (int *)malloc(sizeof(int) * (st->nbx[l] + 1));
+        st->ye[l] = (int *)malloc(sizeof(int) * (st->nby[l] + 1));
+        if (!st->xe[l] || !st->ye[l]) { ref_destroy(st); return REF_ENOMEM; }
+        for (int i = 0; i <= st->nbx[l]; ++i) st->xe[l][i] = (int)edge_at(i, st->W, st->nbx[l]);
+        for (int i = 0; i <= st->nby[l]; ++i) st->ye[l][i] = (int)edge_at(i, st->H, st->nby[l]);
+    }
+    st->bin = (int *)calloc((size_t)N, sizeof(int));
+    st->lab = (int *)calloc((size_t)N, sizeof(int));
+    st->hist = (int64_t *)calloc((size_t)st->K * st->nbins, sizeof(int64_t));
+    st->size = (int64_t *)calloc((size_t)st->K, sizeof(int64_t));
+    st->tmp_l = (int64_t *)calloc((size_t)st->nbins, sizeof(int64_t));
+    st->tmp_a = (int64_t *)calloc((size_t)st->nbins, sizeof(int64_t));
+    /* a phase holds at most ceil(nbx/2)*ceil(nby/2) units; level 0 is the largest grid */
+    st->moves_cap = (int64_t)((st->W + 1) / 2) * ((st->H + 1) / 2);
+    st->moves = (int32_t *)malloc(sizeof(int32_t) * 3 * st->moves_cap);
+    if (!st->bin || !st->lab || !st->hist || !st->size || !st->tmp_l || !st->tmp_a || !st->moves) {
+        ref_destroy(st);
+        return REF_ENOMEM;
+    }
+    *out = st;
+    return REF_OK;
+}
+
+int ref_info(const ref_state *st, int32_t *gx, int32_t *gy, int32_t *K, int32_t *nbins)
+{
+    *gx = st->gx;
+    *gy = st->gy;
+    *K = st->K;
+    *nbins = st->nbins;
+    return REF_OK;
+}
+
+/* unit grid and edges of one level (level 0 = pixels) */
+int ref_level_grid(const ref_state *st, int level, int32_t *nbx, int32_t *nby, int32_t *xe, int32_t *ye)
+{
+    if (level < 0 || level > st->L) return REF_EINVAL;
+    *nbx = st->nbx[level];
+    *nby = st->nby[level];
+    if (xe) for (int i = 0; i <= st->nbx[level]; ++i) xe[i] = st->xe[level][i];
+    if (ye) for (int i = 0; i <= st->nby[level]; ++i) ye[i] = st->ye[level][i];
+    return REF_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* colour bins (R1), initial grid (Sec. 5.1) and histograms (Eq. 4)      */
+/* ------------------------------------------------------------------ */
+
+static int channel_bin(int v, int B)
+{
+    /* the bin whose interval [b*256/B, (b+1)*256/B) holds v */
+    for (int b = 0; b < B; ++b)
+        if (v * B >= b * 256 && v * B < (b + 1) * 256) return b;
+    return B - 1; /* unreachable for 0 <= v <= 255 */
+}
+
+/* index of the interval [e[i], e[i+1]) that holds v */
+static int find_interval(const int *e, int n, int v)
+{
+    for (int i = 0; i < n; ++i)
+        if (v >= e[i] && v < e[i + 1]) return i;
+    return -1;
+}
+
+/* recount c_{A_k} (unnormalised) and |A_k| from the labels */
+static void recount_histograms(ref_state *st)
+{
+    int64_t N = (int64_t)st->W * st->H;
+    memset(st->hist, 0, sizeof(int64_t) * (size_t)st->K * st->nbins);
+    memset(st->size, 0, sizeof(int64_t) * (size_t)st->K);
+    for (int64_t i = 0; i < N; ++i) {
+        st->hist[(int64_t)st->lab[i] * st->nbins + st->bin[i]] += 1;
+        st->size[st->lab[i]] += 1;
+    }
+}
+
+int ref_init(ref_state *st, const uint8_t *rgb, int64_t row_stride)
+{
+    if (!rgb || row_stride < 3 * (int64_t)st->W) return REF_EINVAL;
+    int B = st->B;
+    /* superpixel edges (the level-L blocks joined 2x2) */
+    int *sxe = (int *)malloc(sizeof(int) * (st->gx + 1));
+    int *sye = (int *)malloc(sizeof(int) * (st->gy + 1));
+    if (!sxe || !sye) { free(sxe); free(sye); return REF_ENOMEM; }
+    for (int i = 0; i <= st->gx; ++i) sxe[i] = (int)edge_at(i, st->W, st->gx);
+    for (int i = 0; i <= st->gy; ++i) sye[i] = (int)edge_at(i, st->H, st->gy);
+    for (int y = 0; y < st->H; ++y) {
+        int sy = find_interval(sye, st->gy, y);
+        for (int x = 0; x < st->W; ++x) {
+            const uint8_t *px = rgb + (int64_t)y * row_stride + 3 * (int64_t)x;
+            int br = channel_bin(px[0], B), bg = channel_bin(px[1], B), bb = channel_bin(px[2], B);
+            int sx = find_interval(sxe, st->gx, x);
+            st->bin[(int64_t)y * st->W + x] = br * B * B + bg * B + bb;
+            st->lab[(int64_t)y * st->W + x] = sy * st->gx + sx;
+        }
+    }
+    free(sxe);
+    free(sye);
+    recount_histograms(st);
+    return REF_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* unit helpers                                                         */
+/* ------------------------------------------------------------------ */
+
+/* label of unit (bx,by) at a level: the label of its first pixel; units
+ * are label-homogeneous (blocks move whole, levels run coarse to fine) */
+static int unit_label(const ref_state *st, int level, int bx, int by)
+{
+    if (bx < 0 || by < 0 || bx >= st->nbx[level] || by >= st->nby[level]) return -1;
+    int x = st->xe[level][bx], y = st->ye[level][by];
+    return st->lab[(int64_t)y * st->W + x];
+}
+
+/* R7: local validity test on the 8-ring of unit (bx,by) for leaving label k.
+ * Ring order walks around the unit; odd positions are the 4-neighbours, and
+ * consecutive positions are 4-adjacent, so connected sets of ring cells are
+ * runs of consecutive positions. */
+static const int RING_DX[8] = {-1, 0, 1, 1, 1, 0, -1, -1};
+static const int RING_DY[8] = {-1, -1, -1, 0, 1, 1, 1, 0};
+
+static int leaving_keeps_connected(const ref_state *st, int level, int bx, int by, int k)
+{
+    int isk[8];
+    int nk4 = 0, nk = 0;
+    for (int r = 0; r < 8; ++r) {
+        isk[r] = unit_label(st, level, bx + RING_DX[r], by + RING_DY[r]) == k;
+        nk += isk[r];
+        if (r & 1) nk4 += isk[r];
+    }
+    if (nk4 == 0) return 0;        /* (i) no k-labelled 4-neighbour */
+    if (nk == 8) return 1;         /* whole ring is k: one run */
+    int start = 0;
+    while (isk[start]) ++start;    /* a position outside every run */
+    int runs_with_4 = 0, in_run = 0, run_has_4 = 0;
+    for (int t = 1; t <= 8; ++t) {
+        int r = (start + t) % 8;
+        if (isk[r]) {
+            if (!in_run) { in_run = 1; run_has_4 = 0; }
+            if (r & 1) run_has_4 = 1;
+        } else if (in_run) {
+            in_run = 0;
+            runs_with_4 += run_has_4;
+        }
+    }
+    /* the walk ends on `start`, which is not k, so every run was closed */
+    return runs_with_4 == 1;
+}
+
+/* R5: distinct labels != k among the 4-neighbours, ascending */
+static int candidates(const ref_state *st, int level, int bx, int by, int k, int cand[4])
+{
+    static const int DX[4] = {-1, 1, 0, 0}, DY[4] = {0, 0, -1, 1};
+    int nc = 0;
+    for (int d = 0; d < 4; ++d) {
+        int n = unit_label(st, level, bx + DX[d], by + DY[d]);
+        if (n < 0 || n == k) continue;
+        int seen = 0;
+        for (int c = 0; c < nc; ++c) seen |= cand[c] == n;
+        if (!seen) cand[nc++] = n;
+    }
+    for (int a = 1; a < nc; ++a) /* insertion sort */
+        for (int b = a; b > 0 && cand[b - 1] > cand[b]; --b) {
+            int t = cand[b]; cand[b] = cand[b - 1]; cand[b - 1] = t;
+        }
+    return nc;
+}
+
+/* dense colour histogram of the pixels of unit (bx,by); returns |L| */
+static int64_t unit_histogram(const ref_state *st, int level, int bx, int by, int64_t *h)
+{
+    memset(h, 0, sizeof(int64_t) * st->nbins);
+    int64_t m = 0;
+    for (int y = st->ye[level][by]; y < st->ye[level][by + 1]; ++y)
+        for (int x = st->xe[level][bx]; x < st->xe[level][bx + 1]; ++x) {
+            h[st->bin[(int64_t)y * st->W + x]] += 1;
+            ++m;
+        }
+    return m;
+}
+
+/* ------------------------------------------------------------------ */
+/* Prop. 1: intersection distance, scaled to integers                  */
+/* ------------------------------------------------------------------ */
+
+/* int(c_A, c_L) = sum_j min(A[j]/|A|, L[j]/|L|); multiplied by |A||L| it is
+ * S(A,L) = sum_j min(A[j]*|L|, L[j]*|A|), an integer. */
+static i128 scaled_intersection(const int64_t *A, int64_t sA, const int64_t *Lh, int64_t m, int nbins)
+{
+    i128 S = 0;
+    for (int j = 0; j < nbins; ++j) {
+        i128 a = (i128)A[j] * m, l = (i128)Lh[j] * sA;
+        S += a < l ? a : l;
+    }
+    return S;
+}
+
+/* f(n) > f_stay for a block L of |L| = m leaving k, given S_n = S(A_n, L):
+ * S_n/|A_n| > S(A_k\L, L)/(|A_k|-|L|) */
+static int block_beats_stay(ref_state *st, int k, int n, i128 S_n, const int64_t *Lh, int64_t m)
+{
+    int64_t *Ar = st->tmp_a;
+    const int64_t *Ak = st->hist + (int64_t)k * st->nbins;
+    for (int j = 0; j < st->nbins; ++j) Ar[j] = Ak[j] - Lh[j];
+    int64_t s_rest = st->size[k] - m;
+    i128 S_stay = scaled_intersection(Ar, s_rest, Lh, m, st->nbins);
+    return S_n * s_rest > S_stay * st->size[n];
+}
+
+/* Block move (Sec. 5.2-5.3, Prop. 1; no G for blocks).  Scores are
+ * f(n) = int(c_An, c_L) and f_stay = int(c_{Ak\L}, c_L); the common factor
+ * 1/|L| is dropped, so f(n) = S(A_n,L)/|A_n|. Returns the target or -1. */
+static int decide_block(ref_state *st, int level, int bx, int by)
+{
+    int k = unit_label(st, level, bx, by);
+    int cand[4];
+    int nc = candidates(st, level, bx, by, k, cand);
+    if (nc == 0) return -1;                               /* not a boundary unit */
+    if (!leaving_keeps_connected(st, level, bx, by, k)) return -1;
+    int64_t *Lh = st->tmp_l;
+    int64_t m = unit_histogram(st, level, bx, by, Lh);
+    int best = -1;
+    i128 S_best = 0;
+    for (int c = 0; c < nc; ++c) {
+        int n = cand[c];
+        i128 S = scaled_intersection(st->hist + (int64_t)n * st->nbins, st->size[n], Lh, m, st->nbins);
+        /* S/|A_n| > S_best/|A_best| */
+        if (best < 0 || S * st->size[best] > S_best * st->size[n]) { best = n; S_best = S; }
+    }
+    /* R8: strictly better than staying */
+    return block_beats_stay(st, k, best, S_best, Lh, m) ? best : -1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Prop. 2: label-patch counts                                          */
+/* ------------------------------------------------------------------ */
+
+static int in_image(const ref_state *st, int x, int y) { return x >= 0 && y >= 0 && x < st->W && y < st->H; }
+
+/* sum over the patches N_i that contain pixel p of b_{N_i}(label), in
+ * counts (Z = 9 dropped): the two sides of Prop. 2 are built from it.
+ * K_p = { i in image : p in N_i }, N_i = in-image 3x3 around i (R13). */
+static int64_t patch_label_count(const ref_state *st, int x, int y, int label, int64_t *Kp)
+{
+    int64_t G = 0, nK = 0;
+    for (int iy = y - 1; iy <= y + 1; ++iy)
+        for (int ix = x - 1; ix <= x + 1; ++ix) {
+            if (!in_image(st, ix, iy)) continue;
+            ++nK;
+            for (int qy = iy - 1; qy <= iy + 1; ++qy)
+                for (int qx = ix - 1; qx <= ix + 1; ++qx)
+                    if (in_image(st, qx, qy) && st->lab[(int64_t)qy * st->W + qx] == label) ++G;
+        }
+    if (Kp) *Kp = nK;
+    return G;
+}
+
+/* f(n) > f_stay for pixel (x,y) leaving k, times gamma_den*|A_n|*(|A_k|-1):
+ *   gamma_den*D*(A_n[j]*(|A_k|-1) - (A_k[j]-1)*|A_n|)
+ *     + gamma_num*(G_n + |K_p| - G_k)*|A_n|*(|A_k|-1) > 0 */
+static int pixel_beats_stay(const ref_state *st, int x, int y, int k, int n, int64_t a_n, int64_t s_n, int64_t G_n,
+                            int64_t G_k, int64_t Kp)
+{
+    const int use_g = st->p.patch == 3;
+    int j = st->bin[(int64_t)y * st->W + x];
+    (void)n;
+    int64_t a_k = st->hist[(int64_t)k * st->nbins + j], s_k = st->size[k];
+    i128 gain = (i128)st->p.gamma_den * 81 * ((i128)a_n * (s_k - 1) - (i128)(a_k - 1) * s_n)
+              + (use_g ? (i128)st->p.gamma_num * (G_n + Kp - G_k) * s_n * (s_k - 1) : 0);
+    return gain > 0;
+}
+
+/* Pixel move (Sec. 5.3): colour term by one histogram lookup (Fig. 6),
+ * boundary term by Prop. 2, combined as in R10:
+ *   f(n)    = D * A_n[j]/|A_n|           + gamma * (G_n + |K_p|)
+ *   f_stay  = D * (A_k[j]-1)/(|A_k|-1)   + gamma * G_k
+ * compared exactly after multiplying by gamma_den and the positive sizes. */
+static int decide_pixel(ref_state *st, int x, int y)
+{
+    int k = st->lab[(int64_t)y * st->W + x];
+    int cand[4];
+    int nc = candidates(st, 0, x, y, k, cand);
+    if (nc == 0) return -1;
+    if (!leaving_keeps_connected(st, 0, x, y, k)) return -1;
+    const int use_g = st->p.patch == 3;
+    const i128 D = 81, gn = st->p.gamma_num, gd = st->p.gamma_den;
+    int j = st->bin[(int64_t)y * st->W + x];
+    int64_t Kp = 0;
+    int64_t Gk = use_g ? patch_label_count(st, x, y, k, &Kp) : 0;
+    int best = -1;
+    int64_t a_b = 0, s_b = 1, G_b = 0;
+    for (int c = 0; c < nc; ++c) {
+        int n = cand[c];
+        int64_t a = st->hist[(int64_t)n * st->nbins + j], s = st->size[n];
+        int64_t G = use_g ? patch_label_count(st, x, y, n, NULL) : 0;
+        if (best >= 0) {
+            /* f(n) - f(best) > 0, times gamma_den*|A_n|*|A_best| */
+            i128 diff = gd * D * ((i128)a * s_b - (i128)a_b * s) + gn * (i128)(G - G_b) * s * s_b;
+            if (!(diff > 0)) continue;
+        }
+        best = n; a_b = a; s_b = s; G_b = G;
+    }
+    return pixel_beats_stay(st, x, y, k, best, a_b, s_b, G_b, Gk, Kp) ? best : -1;
+}
+
+/* move a whole unit from k to n: relabel its pixels and update the
+ * histograms incrementally (Sec. 5.3, "Updating the Color Distributions") */
+static void apply_move(ref_state *st, int level, int bx, int by, int k, int n)
+{
+    for (int y = st->ye[level][by]; y < st->ye[level][by + 1]; ++y)
+        for (int x = st->xe[level][bx]; x < st->xe[level][bx + 1]; ++x) {
+            int64_t i = (int64_t)y * st->W + x;
+            int j = st->bin[i];
+            st->lab[i] = n;
+            st->hist[(int64_t)k * st->nbins + j] -= 1;
+            st->hist[(int64_t)n * st->nbins + j] += 1;
+            st->size[k] -= 1;
+            st->size[n] += 1;
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* the parity schedule (R4, R6)                                         */
+/* ------------------------------------------------------------------ */
+
+/* One phase: every unit of the phase is judged against the state at phase
+ * start, then all accepted moves are applied.  Returns the number of moves. */
+int64_t ref_run_phase(ref_state *st, int level, int phase)
+{
+    if (level < 0 || level > st->L || phase < 0 || phase > 3) return REF_EINVAL;
+    int py = phase >> 1, px = phase & 1;
+    int64_t nm = 0;
+    for (int by = py; by < st->nby[level]; by += 2)
+        for (int bx = px; bx < st->nbx[level]; bx += 2) {
+            int n = level == 0 ? decide_pixel(st, bx, by) : decide_block(st, level, bx, by);
+            if (n < 0) continue;
+            st->moves[3 * nm + 0] = by * st->nbx[level] + bx;
+            st->moves[3 * nm + 1] = unit_label(st, level, bx, by);
+            st->moves[3 * nm + 2] = n;
+            ++nm;
+        }
+    for (int64_t t = 0; t < nm; ++t) {
+        int u = st->moves[3 * t];
+        apply_move(st, level, u % st->nbx[level], u / st->nbx[level], st->moves[3 * t + 1], st->moves[3 * t + 2]);
+    }
+    return nm;
+}
+
+/* whole schedule: levels L..1 (blocks), then level 0 (pixels) */
+int64_t ref_run(ref_state *st, const uint8_t *rgb, int64_t row_stride)
+{
+    int rc = ref_init(st, rgb, row_stride);
+    if (rc) return rc;
+    int64_t total = 0;
+    for (int level = st->L; level >= 0; --level)
+        for (int it = 0; it < st->p.iters_per_level; ++it)
+            for (int phase = 0; phase < 4; ++phase) total += ref_run_phase(st, level, phase);
+    return total;
+}
+
+/* ------------------------------------------------------------------ */
+/* state access                                                         */
+/* ------------------------------------------------------------------ */
+
+void ref_get_labels(const ref_state *st, int32_t *out)
+{
+    int64_t N = (int64_t)st->W * st->H;
+    for (int64_t i = 0; i < N; ++i) out[i] = st->lab[i];
+}
+
+void ref_get_bins(const ref_state *st, int32_t *out)
+{
+    int64_t N = (int64_t)st->W * st->H;
+    for (int64_t i = 0; i < N; ++i) out[i] = st->bin[i];
+}
+
+void ref_get_hist(const ref_state *st, int64_t *hist_out, int64_t *size_out)
+{
+    if (hist_out) memcpy(hist_out, st->hist, sizeof(int64_t) * (size_t)st->K * st->nbins);
+    if (size_out) memcpy(size_out, st->size, sizeof(int64_t) * (size_t)st->K);
+}
+
+/* replace the labels (values in [0,K)) and recount the histograms */
+int ref_set_labels(ref_state *st, const int32_t *labels)
+{
+    int64_t N = (int64_t)st->W * st->H;
+    for (int64_t i = 0; i < N; ++i)
+        if (labels[i] < 0 || labels[i] >= st->K) return REF_EINVAL;
+    for (int64_t i = 0; i < N; ++i) st->lab[i] = labels[i];
+    recount_histograms(st);
+    return REF_OK;
+}
+
+/* sum_{i in K_p} b_{N_i}(label) in counts, and |K_p| */
+int64_t ref_patch_label_count(const ref_state *st, int x, int y, int label, int64_t *Kp)
+{
+    return patch_label_count(st, x, y, label, Kp);
+}
+
+/* the parity schedule's decision for one unit against the current state
+ * (target label, or -1 for no move) */
+int ref_decide(ref_state *st, int level, int bx, int by)
+{
+    if (level < 0 || level > st->L || bx < 0 || by < 0 || bx >= st->nbx[level] || by >= st->nby[level])
+        return REF_EINVAL;
+    return level == 0 ? decide_pixel(st, bx, by) : decide_block(st, level, bx, by);
+}
+
+/* ------------------------------------------------------------------ */
+/* sequential mode (R14): the paper's proposal order, quality reference */
+/* ------------------------------------------------------------------ */
+
+/* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) */
+static uint64_t splitmix64(uint64_t *s)
+{
+    uint64_t z = (*s += 0x9e3779b97f4a7c15ULL);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+/* sum over labels of b^2 for the in-image 3x3 patch around (x,y), counts */
+static int64_t patch_sum_sq(const ref_state *st, int x, int y)
+{
+    int labs[9], cnt[9], nl = 0;
+    for (int qy = y - 1; qy <= y + 1; ++qy)
+        for (int qx = x - 1; qx <= x + 1; ++qx) {
+            if (!in_image(st, qx, qy)) continue;
+            int l = st->lab[(int64_t)qy * st->W + qx], f = -1;
+            for (int t = 0; t < nl; ++t) if (labs[t] == l) f = t;
+            if (f < 0) { labs[nl] = l; cnt[nl] = 1; ++nl; } else ++cnt[f];
+        }
+    int64_t s = 0;
+    for (int t = 0; t < nl; ++t) s += (int64_t)cnt[t] * cnt[t];
+    return s;
+}
+
+/* change of sum_i sum_k b_{N_i}(k)^2 (counts) if unit u moves k -> n */
+static int64_t delta_patch_energy(ref_state *st, int level, int bx, int by, int k, int n)
+{
+    int x0 = st->xe[level][bx], x1 = st->xe[level][bx + 1];
+    int y0 = st->ye[level][by], y1 = st->ye[level][by + 1];
+    int64_t before = 0, after = 0;
+    for (int y = y0 - 1; y <= y1; ++y)
+        for (int x = x0 - 1; x <= x1; ++x)
+            if (in_image(st, x, y)) before += patch_sum_sq(st, x, y);
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) st->lab[(int64_t)y * st->W + x] = n;
+    for (int y = y0 - 1; y <= y1; ++y)
+        for (int x = x0 - 1; x <= x1; ++x)
+            if (in_image(st, x, y)) after += patch_sum_sq(st, x, y);
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) st->lab[(int64_t)y * st->W + x] = k;
+    return after - before;
+}
+
+static i128 sum_sq(const int64_t *A, int nbins)
+{
+    i128 s = 0;
+    for (int j = 0; j < nbins; ++j) s += (i128)A[j] * A[j];
+    return s;
+}
+
+/* exact energy test: E = H + gamma*G (Eqs. 3, 5, 7) rises strictly when u
+ * moves k -> n.  H changes only in A_k and A_n; G changes only in patches
+ * touching u.  Everything is multiplied by the positive common denominator
+ * (a+m)^2 (b-m)^2 a^2 b^2 * 81 * gamma_den, with a=|A_n|, b=|A_k|, m=|L|. */
+static int exact_energy_rises(ref_state *st, int level, int bx, int by, int k, int n)
+{
+    int64_t *Lh = st->tmp_l, *T = st->tmp_a;
+    int64_t m = unit_histogram(st, level, bx, by, Lh);
+    const int64_t *An = st->hist + (int64_t)n * st->nbins, *Ak = st->hist + (int64_t)k * st->nbins;
+    i128 a = st->size[n], b = st->size[k];
+    i128 Qn = sum_sq(An, st->nbins), Qk = sum_sq(Ak, st->nbins);
+    for (int j = 0; j < st->nbins; ++j) T[j] = An[j] + Lh[j];
+    i128 Qn2 = sum_sq(T, st->nbins);
+    for (int j = 0; j < st->nbins; ++j) T[j] = Ak[j] - Lh[j];
+    i128 Qk2 = sum_sq(T, st->nbins);
+    i128 an2 = (a + m) * (a + m), bk2 = (b - m) * (b - m), a2 = a * a, b2 = b * b;
+    i128 dH = Qn2 * bk2 * a2 * b2 + Qk2 * an2 * a2 * b2 - Qn * an2 * bk2 * b2 - Qk * an2 * bk2 * a2;
+    i128 gd = st->p.gamma_den, gn = st->p.gamma_num;
+    i128 total = 81 * gd * dH;
+    if (st->p.patch == 3) {
+        i128 dG = delta_patch_energy(st, level, bx, by, k, n);
+        total += gn * dG * an2 * bk2 * a2 * b2;
+    }
+    return total > 0;
+}
+
+/* Sequential hill climbing.  accept_mode 0: the parity schedule's proxy
+ * rule (Props. 1 and 2) for the one drawn candidate; 1: exact energy rise
+ * (small images only, N <= 1024).  Accepted moves are written to `trace` as
+ * (level, unit, k, n) quadruples while room is left.  Returns the number of
+ * accepted moves, or a negative error. */
+int64_t ref_run_sequential(ref_state *st, const uint8_t *rgb, int64_t row_stride, uint64_t seed, int accept_mode,
+                           int32_t *trace, int64_t trace_cap)
+{
+    if (accept_mode != 0 && accept_mode != 1) return REF_EINVAL;
+    if (accept_mode == 1 && (int64_t)st->W * st->H > 1024) return REF_ESIZE;
+    int rc = ref_init(st, rgb, row_stride);
+    if (rc) return rc;
+    uint64_t rng = seed;
+    int64_t n_acc = 0;
+    int64_t cap_units = (int64_t)st->W * st->H;
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * cap_units);
+    if (!order) return REF_ENOMEM;
+    for (int level = st->L; level >= 0; --level) {
+        int nbx = st->nbx[level], nby = st->nby[level];
+        int64_t nu = (int64_t)nbx * nby;
+        for (int it = 0; it < st->p.iters_per_level; ++it) {
+            for (int64_t u = 0; u < nu; ++u) order[u] = (int32_t)u;
+            for (int64_t u = nu - 1; u > 0; --u) { /* Fisher-Yates */
+                int64_t v = (int64_t)(splitmix64(&rng) % (uint64_t)(u + 1));
+                int32_t t = order[u]; order[u] = order[v]; order[v] = t;
+            }
+            for (int64_t t = 0; t < nu; ++t) {
+                int bx = order[t] % nbx, by = order[t] / nbx;
+                int k = unit_label(st, level, bx, by);
+                int cand[4];
+                int nc = candidates(st, level, bx, by, k, cand);
+                if (nc == 0) continue;
+                int n = cand[splitmix64(&rng) % (uint64_t)nc];
+                if (!leaving_keeps_connected(st, level, bx, by, k)) continue;
+                int ok;
+                if (accept_mode == 1) {
+                    ok = exact_energy_rises(st, level, bx, by, k, n);
+                } else if (level == 0) {
+                    /* the pixel rule with only n on offer */
+                    const int use_g = st->p.patch == 3;
+                    int j = st->bin[(int64_t)by * st->W + bx];
+                    int64_t Kp = 0;
+                    int64_t Gk = use_g ? patch_label_count(st, bx, by, k, &Kp) : 0;
+                    int64_t Gn = use_g ? patch_label_count(st, bx, by, n, NULL) : 0;
+                    ok = pixel_beats_stay(st, bx, by, k, n, st->hist[(int64_t)n * st->nbins + j], st->size[n], Gn,
+                                          Gk, Kp);
+                } else {
+                    int64_t *Lh = st->tmp_l;
+                    int64_t m = unit_histogram(st, level, bx, by, Lh);
+                    i128 S_n = scaled_intersection(st->hist + (int64_t)n * st->nbins, st->size[n], Lh, m, st->nbins);
+                    ok = block_beats_stay(st, k, n, S_n, Lh, m);
+                }
+                if (!ok) continue;
+                apply_move(st, level, bx, by, k, n);
+                if (trace && n_acc < trace_cap) {
+                    trace[4 * n_acc + 0] = level;
+                    trace[4 * n_acc + 1] = order[t];
+                    trace[4 * n_acc + 2] = k;
+                    trace[4 * n_acc + 3] = n;
+                }
+                ++n_acc;
+            }
+        }
+    }
+    free(order);
+    return n_acc;
+}

@@ -1,0 +1,45 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case compiles a copy of seeds_ref.c with one planted mistake (a dropped
+term, a wrong sign, a transposed operand, a shifted index ...) on the CPU and
+runs the pin suite against it in a subprocess; the suite has to fail.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "seeds_ref.c")
+
+MUTANTS = {
+    "G term loses |K_p|": ("(G_n + Kp - G_k)", "(G_n - G_k)"),
+    "candidate G difference sign": ("(i128)(G - G_b)", "(i128)(G_b - G)"),
+    "block stay test transposed": ("S_n * s_rest > S_stay * st->size[n]", "S_n * st->size[n] > S_stay * s_rest"),
+    "intersection scales by the wrong size": ("(i128)Lh[j] * sA", "(i128)Lh[j] * m"),
+    "patch window one column short": ("qx <= ix + 1; ++qx)\n                    if (in_image(st, qx, qy) && st->lab",
+                                      "qx <= ix; ++qx)\n                    if (in_image(st, qx, qy) && st->lab"),
+    "ring test ignores which cells are 4-neighbours": ("if (r & 1) run_has_4 = 1;", "run_has_4 = 1;"),
+    "stay histogram keeps the moving pixel": ("(i128)(a_k - 1) * s_n", "(i128)a_k * s_n"),
+    "bin order B-major": ("br * B * B + bg * B + bb", "bb * B * B + bg * B + br"),
+    "size not decremented on a move": ("            st->size[k] -= 1;\n", "\n"),
+    "ties go to the largest label": ("if (!(diff > 0)) continue;", "if (diff < 0) continue;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, "mutation site not found: %s" % name
+    mutated = src.replace(old, new, 1)
+    c = tmp_path / "mutant.c"
+    c.write_text(mutated)
+    lib = tmp_path / "mutant.so"
+    subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(lib), str(c), "-lm"], check=True)
+    env = dict(os.environ, SEEDS_REF_LIB=str(lib))
+    res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                          os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode != 0, "pins passed with the mutant '%s'" % name

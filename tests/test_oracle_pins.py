@@ -1,0 +1,509 @@
+"""Pins for the oracle: what the paper and the mathematics fix, checked
+against the oracle's C code without trusting any of its formulas.
+
+Covered: the colour bins (equal-width intervals, R-major order), the grid
+geometry (closed-form counts, nesting, non-empty blocks), the initial grid
+and its histograms, per-phase invariants (histograms equal a recount, one
+label per pixel, every label present and 4-connected, block homogeneity),
+every decision of every phase against a brute-force restatement in exact
+fractions, Prop. 2 as an exact identity, the block test at |L| = 1 against the
+single-lookup pixel test, special cases with known answers, and the
+sequential mode's energy ascent.
+"""
+import itertools
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import brute
+from oracle import energy, ref
+from paper_1309_3848_gb300 import synth
+
+
+def rgb_noise(W, H, seed, lo=0, hi=256):
+    return np.random.default_rng(seed).integers(lo, hi, size=(H, W, 3)).astype(np.uint8)
+
+
+def recount(labels, bins, K, nbins):
+    h = np.zeros((K, nbins), np.int64)
+    np.add.at(h, (labels.ravel(), bins.ravel()), 1)
+    return h, np.bincount(labels.ravel(), minlength=K).astype(np.int64)
+
+
+def four_connected(mask):
+    """Number of 4-connected components of a boolean mask (plain BFS)."""
+    H, W = mask.shape
+    seen = np.zeros_like(mask, dtype=bool)
+    comps = 0
+    for y0, x0 in zip(*np.nonzero(mask)):
+        if seen[y0, x0]:
+            continue
+        comps += 1
+        stack = [(y0, x0)]
+        seen[y0, x0] = True
+        while stack:
+            y, x = stack.pop()
+            for ny, nx in ((y - 1, x), (y + 1, x), (y, x - 1), (y, x + 1)):
+                if 0 <= ny < H and 0 <= nx < W and mask[ny, nx] and not seen[ny, nx]:
+                    seen[ny, nx] = True
+                    stack.append((ny, nx))
+    return comps
+
+
+def assert_valid_partition(labels, K):
+    assert labels.min() >= 0 and labels.max() < K
+    present = np.unique(labels)
+    assert len(present) == K, "a superpixel vanished"
+    for k in range(K):
+        assert four_connected(labels == k) == 1, "superpixel %d is split" % k
+
+
+# --------------------------------------------------------------------------
+# colour bins (R1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("B", list(range(1, 17)))
+def test_bins_are_equal_width_and_r_major(B):
+    v = np.arange(256, dtype=np.uint8)
+    # one row per channel under test; the other two channels held at 0
+    img = np.zeros((3, 256, 3), np.uint8)
+    for c in range(3):
+        img[c, :, c] = v
+    r = ref.Ref(256, 3, 1, 0, B, 1)
+    r.init(img)
+    bins = r.bins()
+    per_channel = [bins[0] // (B * B), (bins[1] // B) % B, bins[2] % B]
+    weights = [B * B, B, 1]
+    for c in range(3):
+        b = per_channel[c]
+        # only this channel's digit moves, in place value B^2, B, 1
+        assert np.array_equal(bins[c], b * weights[c])
+        assert b[0] == 0 and b[-1] == B - 1
+        assert np.all(np.diff(b) >= 0) and np.all(np.diff(b) <= 1)
+        widths = np.bincount(b, minlength=B)
+        assert set(widths.tolist()) <= {256 // B, -(-256 // B)}
+        # bin b covers [b*256/B, (b+1)*256/B): the lowest member is ceil(b*256/B)
+        starts = [int(np.argmax(b == t)) for t in range(B)]
+        assert starts == [-(-t * 256 // B) for t in range(B)]
+    assert r.nbins == B ** 3
+
+
+# --------------------------------------------------------------------------
+# geometry (R3)
+# --------------------------------------------------------------------------
+
+def test_superpixel_counts_of_the_workloads():
+    # gx = round(sqrt(K W/H)), gy = round(K/gx)
+    assert ref.grid(481, 321, 200, 4)[1:] == (17, 12)
+    assert ref.grid(1920, 1080, 1000, 4)[1:] == (42, 24)
+    assert ref.grid(3840, 2160, 5000, 5)[1:] == (94, 53)
+    assert ref.grid(320, 240, 1500, 2) == (0, 45, 33)
+    assert ref.grid(320, 240, 1500, 3)[0] == ref.EGEOM  # 45*8 > 320
+
+
+@pytest.mark.parametrize("W,H,K,L", [(481, 321, 200, 4), (64, 48, 12, 3), (33, 17, 5, 2), (1920, 1080, 1000, 4),
+                                     (20, 20, 1, 4), (7, 5, 35, 0)])
+def test_levels_nest_and_blocks_are_non_empty(W, H, K, L):
+    r = ref.Ref(W, H, K, L, 5, 1)
+    sx = [(i * W) // r.gx for i in range(r.gx + 1)]
+    sy = [(i * H) // r.gy for i in range(r.gy + 1)]
+    prev = None
+    for level in range(L, -1, -1):
+        nbx, nby, xe, ye = r.level_grid(level)
+        assert xe[0] == 0 and xe[-1] == W and ye[0] == 0 and ye[-1] == H
+        assert np.all(np.diff(xe) >= 1) and np.all(np.diff(ye) >= 1)
+        if level == L and L > 0:
+            # level L: a superpixel is exactly 2x2 blocks
+            assert nbx == 2 * r.gx and nby == 2 * r.gy
+            assert list(xe[::2]) == sx and list(ye[::2]) == sy
+        if prev is not None and level > 0:
+            # every edge of the coarser level is an edge of this one (2x2 joining)
+            assert set(prev[0].tolist()) <= set(xe.tolist()) and nbx == 2 * (len(prev[0]) - 1)
+            assert set(prev[1].tolist()) <= set(ye.tolist()) and nby == 2 * (len(prev[1]) - 1)
+        if level == 0:
+            assert nbx == W and nby == H
+        prev = (xe, ye)
+
+
+def test_smallest_blocks_are_small():
+    # the paper's smallest blocks are 2x2 or 3x3 pixels (Sec. 5.1)
+    for (W, H, K, L) in [(481, 321, 200, 4), (1920, 1080, 1000, 4), (3840, 2160, 5000, 5)]:
+        r = ref.Ref(W, H, K, L, 5, 1)
+        _, _, xe, ye = r.level_grid(1)
+        assert np.diff(xe).max() <= 3 and np.diff(ye).max() <= 3
+
+
+def test_invalid_parameters_are_rejected():
+    with pytest.raises(ref.OracleError):
+        ref.Ref(0, 5, 1, 0, 5, 1)
+    with pytest.raises(ref.OracleError):
+        ref.Ref(16, 16, 4, 0, 17, 1)
+    with pytest.raises(ref.OracleError):
+        ref.Ref(16, 16, 4, 0, 5, 1, patch=5)
+    with pytest.raises(ref.OracleError) as e:
+        ref.Ref(16, 16, 4, 4, 5, 1)  # 2 * 2^4 > 16
+    assert e.value.code == ref.EGEOM
+
+
+# --------------------------------------------------------------------------
+# initial grid and histograms (Sec. 5.1, Eq. 4)
+# --------------------------------------------------------------------------
+
+def test_initial_partition_is_the_grid():
+    W, H, K = 53, 37, 12
+    r = ref.Ref(W, H, K, 2, 4, 1)
+    img = rgb_noise(W, H, 1)
+    r.init(img)
+    lab = r.labels()
+    sx = [(i * W) // r.gx for i in range(r.gx + 1)]
+    sy = [(i * H) // r.gy for i in range(r.gy + 1)]
+    for y in range(H):
+        for x in range(W):
+            cx = max(i for i in range(r.gx) if sx[i] <= x)
+            cy = max(i for i in range(r.gy) if sy[i] <= y)
+            assert lab[y, x] == cy * r.gx + cx
+    h, s = r.hist()
+    h2, s2 = recount(lab, r.bins(), r.K, r.nbins)
+    assert np.array_equal(h, h2) and np.array_equal(s, s2)
+
+
+# --------------------------------------------------------------------------
+# invariants after every phase
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_invariants_after_every_phase(seed):
+    jobs = synth.random_small_jobs(100 + seed, 1, max_side=40)
+    job = jobs[0]
+    W, H = job.image.width, job.image.height
+    L = job.levels
+    while L > 0 and ref.grid(W, H, job.num_superpixels, L)[0] != 0:
+        L -= 1
+    r = ref.Ref(W, H, job.num_superpixels, L, job.bins_per_channel, job.iters_per_level, job.patch, job.gamma)
+    img = synth.make_image(job.image)
+    r.init(img)
+    bins = r.bins()
+    last_level = None
+    for level, phase in r.schedule():
+        if level != last_level:
+            # at the start of a level every unit carries one label
+            nbx, nby, xe, ye = r.level_grid(level)
+            lab = r.labels()
+            for by in range(nby):
+                for bx in range(nbx):
+                    blk = lab[ye[by]:ye[by + 1], xe[bx]:xe[bx + 1]]
+                    assert np.all(blk == blk[0, 0])
+            last_level = level
+        r.run_phase(level, phase)
+        lab = r.labels()
+        h, s = r.hist()
+        h2, s2 = recount(lab, bins, r.K, r.nbins)
+        assert np.array_equal(h, h2) and np.array_equal(s, s2)
+        assert_valid_partition(lab, r.K)
+
+
+# --------------------------------------------------------------------------
+# every decision against the brute-force restatement (exact fractions)
+# --------------------------------------------------------------------------
+
+BRUTE_CASES = [
+    # W, H, K, L, B, iters, patch, gamma, image seed
+    (16, 16, 4, 2, 3, 2, 3, (1, 1), 1),
+    (17, 13, 6, 1, 4, 2, 3, (1, 1), 2),
+    (20, 14, 5, 2, 2, 1, 0, (1, 1), 3),
+    (15, 15, 9, 1, 5, 2, 3, (3, 2), 4),
+    (24, 10, 4, 2, 3, 1, 3, (0, 1), 5),
+    (12, 18, 6, 0, 4, 3, 3, (2, 1), 6),
+]
+
+
+@pytest.mark.parametrize("case", BRUTE_CASES)
+def test_every_decision_matches_brute_force(case):
+    W, H, K, L, B, iters, patch, gamma, seed = case
+    r = ref.Ref(W, H, K, L, B, iters, patch, gamma)
+    # piecewise-constant colours plus noise, so moves actually happen
+    spec = synth.ImageSpec(W, H, seed=seed, cells=5, sigma=20.0)
+    img = synth.make_image(spec)
+    r.init(img)
+    bins = r.bins()
+    total = 0
+    for level, phase in r.schedule():
+        _, _, xe, ye = r.level_grid(level)
+        before = r.labels()
+        dec = brute.phase_decisions(before, bins, r.nbins, level, phase, xe, ye, gamma, patch)
+        n = r.run_phase(level, phase)
+        assert n == len(dec)
+        assert np.array_equal(r.labels(), brute.apply_decisions(before, dec, xe, ye))
+        total += n
+    assert total > 0
+
+
+# --------------------------------------------------------------------------
+# Prop. 2 as an exact identity (App. A.2)
+# --------------------------------------------------------------------------
+
+def test_prop2_identity_on_random_labelings():
+    rng = np.random.default_rng(7)
+    for trial in range(12):
+        W, H = int(rng.integers(3, 9)), int(rng.integers(3, 9))
+        K = int(rng.integers(2, 5))
+        # any labeling works for the identity, connected or not
+        labels = rng.integers(0, K, size=(H, W)).astype(np.int32)
+        if ref.grid(W, H, K)[0] != 0:
+            continue
+        rK = ref.Ref(W, H, K, 0, 1, 1)
+        if rK.K != K:
+            continue
+        rK.init(np.zeros((H, W, 3), np.uint8))
+        rK.set_labels(labels)
+        for y, x in itertools.product(range(H), range(W)):
+            k = int(labels[y, x])
+            for n in range(K):
+                if n == k:
+                    continue
+                Gk, Kp = rK.patch_label_count(x, y, k)
+                Gn, _ = rK.patch_label_count(x, y, n)
+                before = energy.boundary_term_counts(labels)
+                moved = labels.copy()
+                moved[y, x] = n
+                after = energy.boundary_term_counts(moved)
+                # Z^2 (G(s) - G(s_t)) = 2 (G_n + |K_p| - G_k)
+                assert after - before == 2 * (Gn + Kp - Gk)
+                # |K_p| = in-image pixels of the 3x3 around p
+                assert Kp == (min(x + 1, W - 1) - max(x - 1, 0) + 1) * (min(y + 1, H - 1) - max(y - 1, 0) + 1)
+
+
+# --------------------------------------------------------------------------
+# block test at |L| = 1 equals the single-lookup pixel test (Sec. 5)
+# --------------------------------------------------------------------------
+
+def test_one_pixel_blocks_decide_like_pixels():
+    # W = gx * 2^L makes every level-1 block a single pixel
+    W = H = 16
+    for seed in range(3):
+        r = ref.Ref(W, H, 4, 3, 3, 1, patch=0)
+        assert (r.gx, r.gy) == (2, 2)
+        nbx, nby, xe, ye = r.level_grid(1)
+        assert (nbx, nby) == (W, H) and list(xe) == list(range(W + 1))
+        r.init(synth.make_image(synth.ImageSpec(W, H, seed=seed, cells=4, sigma=25.0)))
+        checked = 0
+        for level, phase in r.schedule():
+            if level == 1:
+                for y in range(H):
+                    for x in range(W):
+                        assert r.decide(1, x, y) == r.decide(0, x, y)
+                        checked += r.decide(0, x, y) >= 0
+            r.run_phase(level, phase)
+        assert checked > 0
+
+
+# --------------------------------------------------------------------------
+# special cases with known answers
+# --------------------------------------------------------------------------
+
+def grid_labels(r):
+    W, H = r.W, r.H
+    sx = np.array([(i * W) // r.gx for i in range(r.gx + 1)])
+    sy = np.array([(i * H) // r.gy for i in range(r.gy + 1)])
+    cx = np.searchsorted(sx, np.arange(W), side="right") - 1
+    cy = np.searchsorted(sy, np.arange(H), side="right") - 1
+    return (cy[:, None] * r.gx + cx[None, :]).astype(np.int32)
+
+
+@pytest.mark.parametrize("gamma", [(0, 1), (1, 1), (5, 1)])
+@pytest.mark.parametrize("B", [1, 5])
+def test_constant_image_keeps_the_grid(gamma, B):
+    r = ref.Ref(48, 40, 12, 2, B, 2, 3, gamma)
+    img = np.full((40, 48, 3), 97, np.uint8)
+    assert np.array_equal(r.run(img), grid_labels(r))
+
+
+def test_one_bin_without_boundary_term_keeps_the_grid():
+    r = ref.Ref(40, 32, 8, 2, 1, 2, 3, (0, 1))
+    assert np.array_equal(r.run(rgb_noise(40, 32, 3)), grid_labels(r))
+
+
+def test_grid_aligned_colour_edge_keeps_the_grid():
+    # two flat colours split along a superpixel column edge
+    r = ref.Ref(64, 32, 8, 2, 5, 2)
+    img = np.zeros((32, 64, 3), np.uint8)
+    img[:, :32] = (200, 30, 30)
+    img[:, 32:] = (20, 20, 220)
+    assert (r.gx, r.gy) == (4, 2)
+    assert np.array_equal(r.run(img), grid_labels(r))
+
+
+def test_boundaries_snap_to_an_off_grid_colour_edge():
+    # colour edge at x = 37 inside the superpixel column [32, 48)
+    r = ref.Ref(64, 32, 8, 2, 5, 3)
+    img = np.zeros((32, 64, 3), np.uint8)
+    img[:, :37] = (200, 30, 30)
+    img[:, 37:] = (20, 20, 220)
+    lab = r.run(img)
+    # every pair of horizontally adjacent pixels across the colour edge
+    # now belongs to two different superpixels
+    assert np.all(lab[:, 36] != lab[:, 37])
+    # and no superpixel spans both colours
+    for k in range(r.K):
+        xs = np.nonzero(lab == k)[1]
+        assert xs.max() < 37 or xs.min() >= 37
+
+
+# --------------------------------------------------------------------------
+# sequential mode (the paper's order): energy ascent
+# --------------------------------------------------------------------------
+
+def unit_pixels(r, level, unit):
+    nbx, nby, xe, ye = r.level_grid(level)
+    bx, by = unit % nbx, unit // nbx
+    return slice(ye[by], ye[by + 1]), slice(xe[bx], xe[bx + 1])
+
+
+# In the literal energy G outweighs H by about |A| (a pixel move changes G by
+# ~18/81 but H by ~1/|A|), so gamma is kept small here to leave both active.
+@pytest.mark.parametrize("seed,gamma,patch", [(1, (1, 32), 3), (2, (0, 1), 3), (3, (1, 64), 3), (4, (1, 1), 0)])
+def test_exact_sequential_mode_raises_energy_on_every_move(seed, gamma, patch):
+    W, H = 24, 20
+    r = ref.Ref(W, H, 6, 2, 3, 2, patch, gamma)
+    img = synth.make_image(synth.ImageSpec(W, H, seed=seed, cells=5, sigma=18.0))
+    final, trace, n = r.sequential(img, seed=seed, exact=True)
+    assert n == len(trace) and n > 0
+    bins = r.bins()
+    lab = grid_labels(r)
+    g = Fraction(*gamma)
+    E = energy.energy(lab, bins, g, patch)
+    for level, unit, k, nlab in trace.tolist():
+        sl = unit_pixels(r, level, unit)
+        assert np.all(lab[sl] == k)
+        lab[sl] = nlab
+        E2 = energy.energy(lab, bins, g, patch)
+        assert E2 > E
+        E = E2
+    assert np.array_equal(lab, final)
+    assert_valid_partition(final, r.K)
+
+
+def test_proxy_sequential_with_one_bin_climbs_the_boundary_term():
+    # with one colour bin the colour test always ties, so every accepted move
+    # is a pure Prop. 2 decision, which is exact: G rises on each of them
+    W, H = 24, 24
+    r = ref.Ref(W, H, 9, 2, 1, 2, 3, (1, 1))
+    img = rgb_noise(W, H, 9)
+    # start from a ragged partition so that the boundary term has work to do
+    final, trace, n = r.sequential(img, seed=5, exact=False)
+    lab = grid_labels(r)
+    G = energy.boundary_term_counts(lab)
+    for level, unit, k, nlab in trace.tolist():
+        sl = unit_pixels(r, level, unit)
+        lab[sl] = nlab
+        G2 = energy.boundary_term_counts(lab)
+        assert G2 > G
+        G = G2
+    assert np.array_equal(lab, final)
+
+
+def test_prop1_agreement_rate_is_high():
+    """Diagnostic for Prop. 1 (an approximation; the paper reports agreement
+    of 89-97%): over the parity schedule's pixel moves on a few noisy
+    images, how often does an accepted move raise the exact colour term H?
+    Loose band only: the test images are far smaller than the paper's."""
+    agree = total = 0
+    for (W, H, K, B, seed, cells, sigma) in [(32, 24, 8, 4, 11, 6, 15.0), (48, 48, 6, 5, 11, 6, 10.0),
+                                             (48, 48, 6, 5, 12, 8, 6.0), (64, 48, 6, 5, 13, 6, 8.0)]:
+        r = ref.Ref(W, H, K, 2, B, 2, 0)
+        r.init(synth.make_image(synth.ImageSpec(W, H, seed=seed, cells=cells, sigma=sigma)))
+        bins = r.bins()
+        for level, phase in r.schedule():
+            before = r.labels()
+            r.run_phase(level, phase)
+            after = r.labels()
+            if level != 0:
+                continue
+            H0 = energy.colour_term(before, bins)
+            for y, x in zip(*np.nonzero(before != after)):
+                moved = before.copy()
+                moved[y, x] = after[y, x]
+                total += 1
+                agree += energy.colour_term(moved, bins) > H0
+    print("Prop. 1 agreement on accepted pixel moves: %d / %d" % (agree, total))
+    assert total > 500
+    assert agree / total >= 0.8, (agree, total)
+
+
+# --------------------------------------------------------------------------
+# constructed configurations: candidate ties and the ring rule
+# --------------------------------------------------------------------------
+
+RED, BLUE, GREEN = (220, 20, 20), (20, 20, 220), (20, 220, 20)
+
+
+def constructed_state(labels, blue_labels, p):
+    """16x16 state with 1-pixel level-1 blocks (gx = gy = 2, L = 3): pixels of
+    `blue_labels` and the pixel p are blue, label 0 is red, the rest green."""
+    img = np.zeros((16, 16, 3), np.uint8)
+    img[:] = GREEN
+    img[labels == 0] = RED
+    for b in blue_labels:
+        img[labels == b] = BLUE
+    img[p[1], p[0]] = BLUE
+    r = ref.Ref(16, 16, 4, 3, 5, 1, patch=0)
+    r.init(img)
+    r.set_labels(labels)
+    return r
+
+
+def t_junction(left, right):
+    """p = (6,6) in label 0 (a red row above), `left` and `right` on its
+    sides, `left` below: one run of 0 in the ring, so p may leave 0."""
+    lab = np.full((16, 16), 3, np.int32)
+    x0, y0 = 6, 6
+    lab[y0 - 1, x0 - 2:x0 + 3] = 0
+    lab[y0, x0 - 2:x0] = left
+    lab[y0, x0] = 0
+    lab[y0, x0 + 1:x0 + 3] = right
+    lab[y0 + 1, x0 - 2:x0 + 1] = left
+    lab[y0 + 1, x0 + 1:x0 + 3] = right
+    return lab, (x0, y0)
+
+
+@pytest.mark.parametrize("left,right", [(1, 2), (2, 1)])
+def test_equal_candidates_go_to_the_smallest_label(left, right):
+    lab, p = t_junction(left, right)
+    r = constructed_state(lab, [1, 2], p)
+    # both neighbours are all blue like p: f(1) == f(2) > f_stay = 0
+    assert r.decide(0, *p) == 1
+    assert r.decide(1, *p) == 1
+
+
+def test_isolated_diagonal_cell_does_not_block_a_move():
+    lab = np.full((16, 16), 3, np.int32)
+    x0, y0 = 6, 6
+    lab[:y0 + 1, x0] = 0            # label 0 comes down to p from above
+    lab[y0, x0 - 1] = 1
+    lab[y0, x0 + 1] = 1
+    lab[y0 + 1, x0] = 1
+    lab[y0 + 1, x0 + 1] = 0         # a 0-cell touching p's ring only at a corner
+    lab[y0 + 1:, x0 + 1:] = 0
+    lab[y0 + 1, x0 + 1:] = 0
+    r = constructed_state(lab, [1], (x0, y0))
+    assert r.decide(0, x0, y0) == 1
+    assert r.decide(1, x0, y0) == 1
+
+
+def test_a_move_that_splits_its_superpixel_is_refused():
+    lab = np.full((16, 16), 3, np.int32)
+    x0, y0 = 6, 6
+    lab[:, x0] = 0                  # a vertical line of 0 through p
+    lab[y0, x0 - 1] = 1
+    lab[y0, x0 + 1] = 1
+    r = constructed_state(lab, [1], (x0, y0))
+    # moving p to 1 would be favourable but would cut label 0 in two
+    assert r.decide(0, x0, y0) == -1
+    assert r.decide(1, x0, y0) == -1
+    # join the upper and lower halves through the cells right of p: the ring
+    # now holds one run of 0, so the same move is allowed
+    lab[y0 - 1:y0 + 2, x0 + 1] = 0
+    r = constructed_state(lab, [1], (x0, y0))
+    assert r.decide(0, x0, y0) == 1
+    assert r.decide(1, x0, y0) == 1
