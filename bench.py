@@ -1,0 +1,432 @@
+#!/usr/bin/env python3
+"""Throughput of the SEEDS hot path on GB300 (Mpixel/s, exact labels).
+
+One step = one pass of the whole path (quantise, grid, histograms, block
+levels, pixel level, int32 labels) over one batch of synthetic images that
+already sit in device memory.  Default workload: one 1920x1080 image, 1000
+superpixels, 4 block levels, 4 iterations per level, 5 bins per channel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Under torchrun every rank runs its own replica of the workload (images are
+independent; no collective touches the data) and rank 0 prints one JSON line.
+"""
+import argparse
+import concurrent.futures
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SEEDS Mpixel/s (exact labels)"
+UNIT = "Mpixel/s"
+B_MIN_PER_PX = 7  # read 3 B of RGB, write 4 B of int32 label per pixel
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gseeds", choices=["gseeds", "reference"])
+    ap.add_argument("--workload", default="plain_1920x1080")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched comparison and the CPU baseline")
+    return ap.parse_args()
+
+
+def workload_jobs(name):
+    from paper_1309_3848_gb300 import synth
+    return synth.WORKLOADS[name]()
+
+
+def make_images(jobs):
+    from paper_1309_3848_gb300 import synth
+    with concurrent.futures.ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
+        return list(ex.map(lambda j: synth.make_image(j.image), jobs))
+
+
+def config_of(name, jobs, extra=None):
+    px = sum(j.pixels for j in jobs)
+    cfg = {"workload": name, "images": len(jobs), "pixels_per_step": px}
+    if len(jobs) == 1:
+        j = jobs[0]
+        cfg.update({"width": j.image.width, "height": j.image.height, "superpixels_requested": j.num_superpixels,
+                    "bins_per_channel": j.bins_per_channel, "block_levels": j.levels,
+                    "iters_per_level": j.iters_per_level, "patch": j.patch,
+                    "gamma": "%d/%d" % tuple(j.gamma)})
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# measured peaks and recorded DRAM traffic
+# ---------------------------------------------------------------------------
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("seeds_kernels.cu", "seeds_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1309_3848_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch of the persistent kernel from an ncu capture,
+    only while the kernel sources are unchanged since that capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(workload)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("kernel_sources") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU legs (the oracle)
+# ---------------------------------------------------------------------------
+
+def oracle_levels(job):
+    from oracle import ref
+    L = job.levels
+    if job.clamp_levels:
+        while L > 0 and ref.grid(job.image.width, job.image.height, job.num_superpixels, L)[0] == ref.EGEOM:
+            L -= 1
+    return L
+
+
+def oracle_run(job, img):
+    from oracle import ref
+    r = ref.Ref(job.image.width, job.image.height, job.num_superpixels, oracle_levels(job), job.bins_per_channel,
+                job.iters_per_level, job.patch, job.gamma)
+    return r.run(img)
+
+
+def cpu_sample(jobs, imgs, min_seconds=10.0, max_seconds=30.0):
+    """Time the oracle over copies of the workload's images on all host
+    cores (one image per thread) until about min_seconds have passed."""
+    cores = os.cpu_count() or 1
+    work = []
+    while len(work) < max(cores, len(jobs)):
+        work.extend(zip(jobs, imgs))
+    labels = {}
+    px = 0
+    t0 = time.perf_counter()
+    rounds = 0
+    with concurrent.futures.ThreadPoolExecutor(cores) as ex:
+        while True:
+            futs = [ex.submit(oracle_run, j, im) for j, im in work]
+            for i, f in enumerate(futs):
+                lab = f.result()
+                if i < len(jobs):
+                    labels[i] = lab
+            px += sum(j.pixels for j, _ in work)
+            rounds += 1
+            el = time.perf_counter() - t0
+            if el >= min_seconds or el + el / rounds > max_seconds:
+                break
+    el = time.perf_counter() - t0
+    return px / el / 1e6, cores, "%d images (%d copies of the workload's %d) in %.1f s on %d threads" % (
+        len(work) * rounds, len(work) * rounds // max(1, len(jobs)), len(jobs), el, cores), labels
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    jobs = workload_jobs(args.workload)
+    imgs = make_images(jobs)
+    cores = min(os.cpu_count() or 1, len(jobs))
+    px = sum(j.pixels for j in jobs)
+
+    def step():
+        with concurrent.futures.ThreadPoolExecutor(cores) as ex:
+            list(ex.map(lambda a: oracle_run(*a), zip(jobs, imgs)))
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = px * args.steps / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": config_of(args.workload, jobs),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "the whole workload (%d image(s)) per step, one thread per image" % len(jobs)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+
+def gpu_params(binding, job):
+    L = job.levels
+    if job.clamp_levels:
+        L = min(L, binding.feasible_levels(job.image.width, job.image.height, job.num_superpixels))
+    return binding.make_params(job.image.width, job.image.height, job.num_superpixels, L, job.bins_per_channel,
+                               job.iters_per_level, job.patch, job.gamma)
+
+
+def timed_steps(torch, fn, steps, flush, kernel_ms=None):
+    """Per-step CUDA-event time (ms) with an L2 flush before every step;
+    optionally the persistent kernel's own event time per step."""
+    s = torch.cuda.current_stream()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    kms = []
+    for i in range(steps):
+        flush.add_(1)
+        e0[i].record(s)
+        fn()
+        e1[i].record(s)
+        if kernel_ms is not None:
+            kms.append(kernel_ms())
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(e0, e1)], kms
+
+
+def batched_vs_plain(torch, binding, flush, steps=5):
+    """64 mixed images: one context and one launch for all of them against
+    one context and one launch per image, same labels required."""
+    from paper_1309_3848_gb300 import synth
+    jobs = synth.batch_64()
+    imgs = make_images(jobs)
+    params = [gpu_params(binding, j) for j in jobs]
+    d = [torch.from_numpy(im).cuda() for im in imgs]
+    outs_b = [torch.empty((j.image.height, j.image.width), dtype=torch.int32, device="cuda") for j in jobs]
+    outs_p = [torch.empty_like(o) for o in outs_b]
+    batch = binding.SeedsContext(params)
+    plain = [binding.SeedsContext([p]) for p in params]
+
+    def run_batch():
+        batch.run(d, outs_b)
+
+    def run_plain():
+        for c, x, o in zip(plain, d, outs_p):
+            c.run([x], [o])
+
+    for _ in range(2):
+        run_batch()
+        run_plain()
+    torch.cuda.synchronize()
+    tb, _ = timed_steps(torch, run_batch, steps, flush)
+    tp, _ = timed_steps(torch, run_plain, steps, flush)
+    batch.check_status()
+    for c in plain:
+        c.check_status()
+    same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_p))
+    px = sum(j.pixels for j in jobs)
+    vb = px / (statistics.mean(tb) / 1e3) / 1e6
+    vp = px / (statistics.mean(tp) / 1e3) / 1e6
+    return {"workload": "batch64_mixed", "pixels": px, "batched_mpix_s": vb, "plain_mpix_s": vp,
+            "batched_over_plain": vb / vp, "labels_identical": bool(same)}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1309_3848_gb300 import binding
+
+    jobs = workload_jobs(args.workload)
+    imgs = make_images(jobs)
+    params = [gpu_params(binding, j) for j in jobs]
+    px = sum(j.pixels for j in jobs)
+    ctx = binding.SeedsContext(params)
+    ctx.profile(True)
+    d = [torch.from_numpy(im).cuda() for im in imgs]
+    outs = [torch.empty((j.image.height, j.image.width), dtype=torch.int32, device="cuda") for j in jobs]
+    flush = torch.zeros(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB of L2
+
+    def step():
+        ctx.run(d, outs)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ctx.check_status()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = ctx.launch_count()
+    step_ms, kernel_ms = timed_steps(torch, step, args.steps, flush, ctx.last_kernel_ms)
+    launches = ctx.launch_count() - n0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ctx.check_status()
+
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms, float(launches)], device="cuda", dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms, launches = float(tmax[0]), int(t[1])
+    ms_per_step = total_ms / args.steps
+    value = world * px * args.steps / (total_ms / 1e3) / 1e6
+
+    # end to end through the public API from pinned host memory
+    h_imgs = [torch.from_numpy(im).pin_memory() for im in imgs]
+    h_outs = [torch.empty((j.image.height, j.image.width), dtype=torch.int32).pin_memory() for j in jobs]
+    e2e_steps = max(3, min(args.steps, 100))
+
+    def host_step():
+        ctx.run_host(h_imgs, h_outs)
+
+    host_step()
+    torch.cuda.synchronize()
+    e2e_ms, _ = timed_steps(torch, host_step, e2e_steps, flush)
+    ctx.check_status()
+    e2e_value = px / (statistics.mean(e2e_ms) / 1e3) / 1e6
+    e2e_identical = all(torch.equal(h, o.cpu()) for h, o in zip(h_outs, outs))
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = hbm_peak()
+    kms = statistics.mean(kernel_ms)
+    bytes_min = B_MIN_PER_PX * px
+    achieved = bytes_min / (kms / 1e3) / 1e9
+    # streaming model: per phase the label map (2 B/px) and the bins (bb B/px)
+    bb = 2 if any(j.bins_per_channel ** 3 > 256 for j in jobs) else 1
+    stream_bytes = sum(j.pixels * (B_MIN_PER_PX + bb + (p.block_levels + 1) * j.iters_per_level * (bb + 2))
+                       for j, p in zip(jobs, params))
+    traffic = recorded_traffic(args.workload)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": config_of(args.workload, jobs, {
+            "l2": "flushed before every step (256 MiB write)",
+            "superpixels_actual": ctx.num_superpixels if len(jobs) > 1 else ctx.num_superpixels[0],
+            "parallelism": "replicas" if world > 1 else "single GPU"}),
+        "roofline": {"bound": "hbm", "kernel": "seeds_persistent", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": bytes_min, "kernel_ms": kms,
+                     "stream_model_bytes_per_launch": stream_bytes,
+                     "stream_model_frac": stream_bytes / (kms / 1e3) / 1e9 / peak},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": sum(3 * j.pixels for j in jobs),
+                "d2h_bytes_per_step": sum(4 * j.pixels for j in jobs), "labels_identical": bool(e2e_identical)},
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    if world == 1 and not args.no_extras:
+        line["batched"] = batched_vs_plain(torch, binding, flush)
+        gpu_labels = [o.cpu().numpy() for o in outs]
+        v, cores, sample, ref_labels = cpu_sample(jobs, imgs)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        import numpy as np
+        line["parity"] = "bit-exact" if all(np.array_equal(gpu_labels[i], ref_labels[i])
+                                            for i in range(len(jobs))) else "MISMATCH"
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * seeds.h -- C ABI of libseeds.so: SEEDS superpixels on one GB300 (sm_103a).
+ *
+ * Method: M. Van den Bergh, X. Boix, G. Roig, L. Van Gool, "SEEDS:
+ * Superpixels Extracted via Energy-Driven Sampling", arXiv 1309.3848.
+ * The library runs the paper's hill climbing (Sec. 5): a grid start
+ * (Sec. 5.1), block moves from the largest block level down to the
+ * smallest, then pixel moves (Sec. 5.2), each judged by the histogram
+ * intersection test (Prop. 1) and, for pixels, the label-patch test
+ * (Prop. 2), with incremental histogram updates (Sec. 5.3).
+ *
+ * Fixed readings (the same ones the bundled CPU oracle follows):
+ *  - colour bins from the RGB bytes: bin(v) = floor(v*B/256) per channel,
+ *    j = bR*B*B + bG*B + bB;
+ *  - grid: gx = max(1, round(sqrt(K*W/H))), gy = max(1, round(K/gx)),
+ *    K_actual = gx*gy; level-l block edges floor(i*W/(gx*2^(L-l+1)));
+ *  - every level runs iters_per_level iterations of four parity phases
+ *    (py,px) = (0,0),(0,1),(1,0),(1,1); a phase judges all its units against
+ *    the state at phase start and applies the accepted moves together;
+ *  - a unit may leave superpixel k only if k stays 4-connected around it
+ *    (local 8-ring test); candidates are the distinct neighbour labels,
+ *    best score wins, ties to the smallest label, accept on strict gain;
+ *  - pixel score D*c_An(j) + gamma*(G_n + |K_p|) against
+ *    D*c_{Ak\p}(j) + gamma*G_k with D = 81 (Prop. 1 + Prop. 2); blocks use
+ *    the intersection alone; all compares are exact int64 products.
+ * Results are deterministic: the same image and parameters give the same
+ * labels on any stream, in any batch, at any tuning.
+ *
+ * Memory and streams.  Device pointers (d_*) are CUDA device addresses
+ * owned by the caller (e.g. torch tensor data_ptr()).  Host pointers (h_*)
+ * are ordinary host memory; pinned memory makes their copies asynchronous.
+ * `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ * Calls on one context must be issued from one host thread at a time and
+ * are ordered by the stream they are given; a context keeps its state (bin
+ * maps, label grids, histograms) resident on the device between calls.
+ *
+ * Errors.  Every entry point returns an int status: SEEDS_OK or one of the
+ * negative codes below.  No exception crosses the ABI.  Device-side faults
+ * that the kernels detect themselves (a grid-barrier wait that ran out, an
+ * index outside its buffer) are recorded in the context's error word and
+ * reported by seeds_status().
+ */
+#ifndef SEEDS_H
+#define SEEDS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEEDS_OK 0
+#define SEEDS_ERR_INVALID (-1)     /* bad argument or parameter */
+#define SEEDS_ERR_GEOMETRY (-2)    /* gx*2^L > W or gy*2^L > H */
+#define SEEDS_ERR_INT64 (-3)       /* exact int64 products could overflow */
+#define SEEDS_ERR_NO_MEMORY (-4)   /* device allocation failed */
+#define SEEDS_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+#define SEEDS_ERR_DEVICE (-6)      /* device-side timeout or bounds trip */
+
+#define SEEDS_MAX_LEVELS 12
+#define SEEDS_MAX_BATCH 4096
+
+typedef struct seeds_ctx seeds_ctx;
+
+/* Parameters of one image (Sec. 6.2 fixes gamma = 1, a 3x3 patch, 5 bins).
+ *   width, height      image size, 1..32768 each, width*height < 2^31
+ *   num_superpixels    requested K (>= 1); the grid gives gx*gy <= 65535
+ *   block_levels       L >= 0 (0 = pixel moves only)
+ *   bins_per_channel   B in 1..16; histograms have B^3 bins
+ *   iters_per_level    >= 1, for every block level and the pixel level
+ *   patch              0 (no boundary term) or 3 (3x3 patches, Prop. 2)
+ *   gamma_num/den      gamma = num/den, 0 <= num <= 1024, 1 <= den <= 1024 */
+typedef struct {
+    int32_t width, height;
+    int32_t num_superpixels;
+    int32_t block_levels;
+    int32_t bins_per_channel;
+    int32_t iters_per_level;
+    int32_t patch;
+    int32_t gamma_num, gamma_den;
+} seeds_params;
+
+/* Result-invariant launch knobs (any value gives identical labels).
+ *   threads_per_block  128, 256 or 512 (0 = default)
+ *   blocks_per_sm      resident CTAs per SM of the persistent kernel,
+ *                      0 = as many as fit
+ *   hist_layout        0: hist[k][j] (label-major), 1: hist[j][k] (bin-major)
+ *   small_block_area   blocks of at most this many pixels are judged by one
+ *                      thread, larger ones by a warp (1..16; 0 = default) */
+typedef struct {
+    int32_t threads_per_block;
+    int32_t blocks_per_sm;
+    int32_t hist_layout;
+    int32_t small_block_area;
+} seeds_tuning;
+
+/* Fill p with the paper's defaults for a W x H image and K superpixels:
+ * 4 block levels (clamped to what the grid allows), 5 bins per channel,
+ * 2 iterations, 3x3 patch, gamma = 1.  Host only. */
+int seeds_params_default(seeds_params *p, int32_t width, int32_t height, int32_t num_superpixels);
+
+/* Largest block_levels the grid geometry of *p allows (>= 0), ignoring
+ * p->block_levels itself.  Host only; SEEDS_ERR_INVALID for bad sizes. */
+int seeds_feasible_levels(const seeds_params *p, int32_t *max_levels);
+
+/* Validate *p and compute its grid without allocating: K_actual = gx*gy.
+ * Returns SEEDS_ERR_GEOMETRY / SEEDS_ERR_INT64 exactly as seeds_create would. */
+int seeds_check_params(const seeds_params *p, int32_t *gx, int32_t *gy);
+
+/* Device bytes a context for these images would hold (for admission
+ * control by footprint).  Host only. */
+int seeds_footprint(const seeds_params *p, int32_t n, int64_t *bytes);
+
+/* Create a context for one image on the current CUDA device: validates the
+ * parameters (grid geometry, int64 bound of the exact compares) and
+ * allocates all device state.  Host call, synchronous. */
+int seeds_create(const seeds_params *p, seeds_ctx **out);
+
+/* Run the whole schedule on one image: quantise, grid, histograms, block
+ * levels L..1, pixel level.  d_rgb: device, H rows of W*3 uint8 (R,G,B),
+ * row_stride_bytes >= 3*W apart.  Asynchronous on `stream`; d_rgb must stay
+ * valid until the stream reaches this work.  Re-initialises from the image
+ * on every call. */
+int seeds_iterate(seeds_ctx *c, const uint8_t *d_rgb, int64_t row_stride_bytes, void *stream);
+
+/* Write the labels of the last seeds_iterate: d_labels_out is a device
+ * int32 H x W row-major buffer (caller-owned), values in [0, K_actual).
+ * Asynchronous on `stream`. */
+int seeds_labels(seeds_ctx *c, int32_t *d_labels_out, void *stream);
+
+/* K_actual = gx*gy of image 0 of the context. */
+int seeds_num_superpixels(const seeds_ctx *c, int32_t *k_out);
+
+/* Wait for the context's last launched work and report device-side errors:
+ * SEEDS_OK, SEEDS_ERR_DEVICE (the error word was set; it is cleared), or
+ * SEEDS_ERR_CUDA. */
+int seeds_status(seeds_ctx *c);
+
+/* Free the context (waits for its work first). */
+int seeds_destroy(seeds_ctx *c);
+
+/* ---- batches: many images of any sizes in one persistent launch ------- */
+
+/* Context for n images (1..SEEDS_MAX_BATCH); p[i] are their parameters. */
+int seeds_batch_create(const seeds_params *p, int32_t n, seeds_ctx **out);
+
+/* Number of images and K_actual of image i. */
+int seeds_batch_size(const seeds_ctx *c, int32_t *n_out);
+int seeds_batch_num_superpixels(const seeds_ctx *c, int32_t i, int32_t *k_out);
+
+/* Run all images: h_rgb_ptrs[i] is the DEVICE address of image i (an array
+ * of n device pointers held in host memory), h_row_strides[i] its row
+ * stride in bytes.  One persistent kernel launch.  Asynchronous. */
+int seeds_batch_iterate(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides,
+                        void *stream);
+
+/* Write every image's labels: h_label_ptrs[i] is the device address of an
+ * int32 H_i x W_i buffer.  Asynchronous. */
+int seeds_batch_labels(seeds_ctx *c, int32_t *const *h_label_ptrs, void *stream);
+
+/* seeds_batch_iterate and seeds_batch_labels fused into one launch. */
+int seeds_batch_run(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides,
+                    int32_t *const *h_label_ptrs, void *stream);
+
+/* End to end from HOST memory: copies every image host->device into
+ * context-owned staging buffers, runs the batch, and copies the labels
+ * device->host.  h_rgb[i]: H_i rows of 3*W_i bytes, h_row_strides[i] apart;
+ * h_labels[i]: int32 H_i x W_i.  Asynchronous on `stream` (the host buffers
+ * must stay valid until the stream completes; pinned buffers overlap). */
+int seeds_run_host(seeds_ctx *c, const uint8_t *const *h_rgb, const int64_t *h_row_strides, int32_t *const *h_labels,
+                   void *stream);
+
+/* Launch knobs; see seeds_tuning. */
+int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t);
+int seeds_get_tuning(const seeds_ctx *c, seeds_tuning *t);
+
+/* ---- test hooks --------------------------------------------------------- */
+
+/* Operation list of image i: op 0 quantises and builds the grid and the
+ * histograms; then one op per phase (level L..0, iteration, phase 0..3)
+ * with one descent op after each block level; the last op is the output
+ * (only run by seeds_batch_run).  kind: 0 init, 1 phase, 2 descend,
+ * 3 output. */
+int seeds_debug_num_ops(const seeds_ctx *c, int32_t i, int32_t *n_ops);
+int seeds_debug_op_info(const seeds_ctx *c, int32_t i, int32_t op, int32_t *kind, int32_t *level, int32_t *phase);
+
+/* Run ops [op_begin, op_end) of every image (clamped to each image's list)
+ * from the current device state; inputs as seeds_batch_iterate. */
+int seeds_debug_run_ops(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides, int32_t op_begin,
+                        int32_t op_end, void *stream);
+
+/* Synchronous read of image i's state into host buffers (any may be NULL):
+ * h_labels: the label grid of `level` (level 0 = pixels, H x W; level l >=
+ * 1: its block grid), h_hist: K x B^3 int32 label-major, h_sizes: K int32,
+ * h_bins: H x W int32. */
+int seeds_debug_read_state(seeds_ctx *c, int32_t i, int32_t level, int32_t *h_labels, int32_t *h_hist, int32_t *h_sizes,
+                           int32_t *h_bins);
+
+/* Replace image i's labels at `level` (host int32 grid as above, values in
+ * [0,K)) and recount its histograms and sizes on the device from the
+ * current bin map.  Synchronous. */
+int seeds_debug_set_labels(seeds_ctx *c, int32_t i, int32_t level, const int32_t *h_labels);
+
+/* Set the context's device error word (host-side fault injection: the next
+ * seeds_status() must report SEEDS_ERR_DEVICE). */
+int seeds_debug_inject_error(seeds_ctx *c);
+
+/* Kernel launches issued by the context so far (every launch of the
+ * persistent kernel and of the small pointer-upload kernel counts one). */
+int seeds_debug_launch_count(const seeds_ctx *c, int64_t *n);
+
+/* ---- profiling ---------------------------------------------------------- */
+
+/* enable != 0: record a CUDA event pair on the launch stream around every
+ * persistent-kernel launch of this context (off by default). */
+int seeds_profile_enable(seeds_ctx *c, int32_t enable);
+
+/* Device time in ms of the context's most recent persistent-kernel launch
+ * (waits for it).  SEEDS_ERR_INVALID if profiling was off for it. */
+int seeds_profile_last_ms(seeds_ctx *c, float *ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEEDS_H */

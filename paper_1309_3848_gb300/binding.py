@@ -1,0 +1,288 @@
+"""Thin ctypes binding of libseeds.so (include/seeds.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Functions carry the C names; `SeedsContext` adds the torch
+plumbing (device memory via data_ptr(), streams via cuda_stream).  If the
+compiled library is missing this module raises on import -- there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libseeds.so")
+
+SEEDS_OK = 0
+SEEDS_ERR_INVALID = -1
+SEEDS_ERR_GEOMETRY = -2
+SEEDS_ERR_INT64 = -3
+SEEDS_ERR_NO_MEMORY = -4
+SEEDS_ERR_CUDA = -5
+SEEDS_ERR_DEVICE = -6
+SEEDS_MAX_LEVELS = 12
+SEEDS_MAX_BATCH = 4096
+
+_NAMES = {0: "SEEDS_OK", -1: "SEEDS_ERR_INVALID", -2: "SEEDS_ERR_GEOMETRY", -3: "SEEDS_ERR_INT64",
+          -4: "SEEDS_ERR_NO_MEMORY", -5: "SEEDS_ERR_CUDA", -6: "SEEDS_ERR_DEVICE"}
+
+# every entry point of include/seeds.h
+EXPORTS = [
+    "seeds_params_default", "seeds_feasible_levels", "seeds_check_params", "seeds_footprint", "seeds_create",
+    "seeds_iterate", "seeds_labels", "seeds_num_superpixels", "seeds_status", "seeds_destroy",
+    "seeds_batch_create", "seeds_batch_size", "seeds_batch_num_superpixels", "seeds_batch_iterate",
+    "seeds_batch_labels", "seeds_batch_run", "seeds_run_host", "seeds_set_tuning", "seeds_get_tuning",
+    "seeds_debug_num_ops", "seeds_debug_op_info", "seeds_debug_run_ops", "seeds_debug_read_state",
+    "seeds_debug_set_labels", "seeds_debug_inject_error", "seeds_debug_launch_count", "seeds_profile_enable",
+    "seeds_profile_last_ms",
+]
+
+
+class SeedsError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s returned %s (%d)" % (what, _NAMES.get(code, "?"), code))
+        self.code = code
+
+
+class seeds_params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("num_superpixels", ctypes.c_int32),
+                ("block_levels", ctypes.c_int32), ("bins_per_channel", ctypes.c_int32),
+                ("iters_per_level", ctypes.c_int32), ("patch", ctypes.c_int32), ("gamma_num", ctypes.c_int32),
+                ("gamma_den", ctypes.c_int32)]
+
+
+class seeds_tuning(ctypes.Structure):
+    _fields_ = [("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("hist_layout", ctypes.c_int32), ("small_block_area", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libseeds.so is not built (expected at %s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    i32, i64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    P = ctypes.POINTER
+    sig = {
+        "seeds_params_default": [P(seeds_params), i32, i32, i32],
+        "seeds_feasible_levels": [P(seeds_params), P(i32)],
+        "seeds_check_params": [P(seeds_params), P(i32), P(i32)],
+        "seeds_footprint": [P(seeds_params), i32, P(i64)],
+        "seeds_create": [P(seeds_params), P(vp)],
+        "seeds_iterate": [vp, vp, i64, vp],
+        "seeds_labels": [vp, vp, vp],
+        "seeds_num_superpixels": [vp, P(i32)],
+        "seeds_status": [vp],
+        "seeds_destroy": [vp],
+        "seeds_batch_create": [P(seeds_params), i32, P(vp)],
+        "seeds_batch_size": [vp, P(i32)],
+        "seeds_batch_num_superpixels": [vp, i32, P(i32)],
+        "seeds_batch_iterate": [vp, P(vp), P(i64), vp],
+        "seeds_batch_labels": [vp, P(vp), vp],
+        "seeds_batch_run": [vp, P(vp), P(i64), P(vp), vp],
+        "seeds_run_host": [vp, P(vp), P(i64), P(vp), vp],
+        "seeds_set_tuning": [vp, P(seeds_tuning)],
+        "seeds_get_tuning": [vp, P(seeds_tuning)],
+        "seeds_debug_num_ops": [vp, i32, P(i32)],
+        "seeds_debug_op_info": [vp, i32, i32, P(i32), P(i32), P(i32)],
+        "seeds_debug_run_ops": [vp, P(vp), P(i64), i32, i32, vp],
+        "seeds_debug_read_state": [vp, i32, i32, vp, vp, vp, vp],
+        "seeds_debug_set_labels": [vp, i32, i32, vp],
+        "seeds_debug_inject_error": [vp],
+        "seeds_debug_launch_count": [vp, P(i64)],
+        "seeds_profile_enable": [vp, i32],
+        "seeds_profile_last_ms": [vp, P(ctypes.c_float)],
+    }
+    for name in EXPORTS:
+        f = getattr(L, name)
+        f.argtypes = sig[name]
+        f.restype = ctypes.c_int
+    return L
+
+
+lib = _load()
+
+
+def check(code: int, what: str) -> int:
+    if code != SEEDS_OK:
+        raise SeedsError(code, what)
+    return code
+
+
+def make_params(width, height, num_superpixels, block_levels, bins_per_channel, iters_per_level, patch=3,
+                gamma=(1, 1)) -> seeds_params:
+    return seeds_params(int(width), int(height), int(num_superpixels), int(block_levels), int(bins_per_channel),
+                        int(iters_per_level), int(patch), int(gamma[0]), int(gamma[1]))
+
+
+def feasible_levels(width, height, num_superpixels) -> int:
+    p = make_params(width, height, num_superpixels, 0, 5, 1)
+    out = ctypes.c_int32()
+    check(lib.seeds_feasible_levels(ctypes.byref(p), ctypes.byref(out)), "seeds_feasible_levels")
+    return out.value
+
+
+def check_params(p: seeds_params):
+    gx, gy = ctypes.c_int32(), ctypes.c_int32()
+    rc = lib.seeds_check_params(ctypes.byref(p), ctypes.byref(gx), ctypes.byref(gy))
+    return rc, gx.value, gy.value
+
+
+def footprint(params: Sequence[seeds_params]) -> int:
+    arr = (seeds_params * len(params))(*params)
+    out = ctypes.c_int64()
+    check(lib.seeds_footprint(arr, len(params), ctypes.byref(out)), "seeds_footprint")
+    return out.value
+
+
+def _ptrs(values, ctype=ctypes.c_void_p):
+    return (ctype * len(values))(*values)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class SeedsContext:
+    """One library context over a list of image parameter sets.
+
+    Images and label buffers are torch tensors: uint8 (H, W, 3) on the GPU
+    (any row stride with unit channel/column strides) and int32 (H, W)."""
+
+    def __init__(self, params: Sequence[seeds_params]):
+        self.params = list(params)
+        self.n = len(self.params)
+        arr = (seeds_params * self.n)(*self.params)
+        h = ctypes.c_void_p()
+        check(lib.seeds_batch_create(arr, self.n, ctypes.byref(h)), "seeds_batch_create")
+        self._h = h
+        self.num_superpixels: List[int] = []
+        for i in range(self.n):
+            k = ctypes.c_int32()
+            check(lib.seeds_batch_num_superpixels(self._h, i, ctypes.byref(k)), "seeds_batch_num_superpixels")
+            self.num_superpixels.append(k.value)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.seeds_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- marshalling helpers
+    @staticmethod
+    def _rgb_args(images):
+        ptrs, strides = [], []
+        for t in images:
+            assert t.dtype.itemsize == 1 and t.dim() == 3 and t.shape[2] == 3 and t.is_cuda
+            assert t.stride(2) == 1 and t.stride(1) == 3
+            ptrs.append(t.data_ptr())
+            strides.append(t.stride(0))
+        return _ptrs(ptrs), _ptrs(strides, ctypes.c_int64)
+
+    def iterate(self, images, stream=None):
+        rgb, strides = self._rgb_args(images)
+        check(lib.seeds_batch_iterate(self._h, rgb, strides, _stream_handle(stream)), "seeds_batch_iterate")
+
+    def labels(self, outs, stream=None):
+        for t in outs:
+            assert t.is_contiguous() and t.is_cuda and t.element_size() == 4
+        check(lib.seeds_batch_labels(self._h, _ptrs([t.data_ptr() for t in outs]), _stream_handle(stream)),
+              "seeds_batch_labels")
+
+    def run(self, images, outs, stream=None):
+        rgb, strides = self._rgb_args(images)
+        for t in outs:
+            assert t.is_contiguous() and t.is_cuda and t.element_size() == 4
+        check(lib.seeds_batch_run(self._h, rgb, strides, _ptrs([t.data_ptr() for t in outs]),
+                                  _stream_handle(stream)), "seeds_batch_run")
+
+    def run_host(self, images, outs, stream=None):
+        """images: host uint8 (H, W, 3) tensors; outs: host int32 (H, W)."""
+        ptrs, strides = [], []
+        for t in images:
+            assert not t.is_cuda and t.stride(2) == 1 and t.stride(1) == 3
+            ptrs.append(t.data_ptr())
+            strides.append(t.stride(0))
+        for t in outs:
+            assert not t.is_cuda and t.is_contiguous() and t.element_size() == 4
+        check(lib.seeds_run_host(self._h, _ptrs(ptrs), _ptrs(strides, ctypes.c_int64),
+                                 _ptrs([t.data_ptr() for t in outs]), _stream_handle(stream)), "seeds_run_host")
+
+    def status(self) -> int:
+        return lib.seeds_status(self._h)
+
+    def check_status(self):
+        check(self.status(), "seeds_status")
+
+    def set_tuning(self, threads_per_block=0, blocks_per_sm=0, hist_layout=0, small_block_area=0):
+        t = seeds_tuning(threads_per_block, blocks_per_sm, hist_layout, small_block_area)
+        check(lib.seeds_set_tuning(self._h, ctypes.byref(t)), "seeds_set_tuning")
+
+    def get_tuning(self) -> seeds_tuning:
+        t = seeds_tuning()
+        check(lib.seeds_get_tuning(self._h, ctypes.byref(t)), "seeds_get_tuning")
+        return t
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int64()
+        check(lib.seeds_debug_launch_count(self._h, ctypes.byref(n)), "seeds_debug_launch_count")
+        return n.value
+
+    def profile(self, enable: bool = True):
+        check(lib.seeds_profile_enable(self._h, 1 if enable else 0), "seeds_profile_enable")
+
+    def last_kernel_ms(self) -> float:
+        ms = ctypes.c_float()
+        check(lib.seeds_profile_last_ms(self._h, ctypes.byref(ms)), "seeds_profile_last_ms")
+        return ms.value
+
+    # -- test hooks
+    def num_ops(self, i: int) -> int:
+        n = ctypes.c_int32()
+        check(lib.seeds_debug_num_ops(self._h, i, ctypes.byref(n)), "seeds_debug_num_ops")
+        return n.value
+
+    def op_info(self, i: int, op: int):
+        k, l, p = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib.seeds_debug_op_info(self._h, i, op, ctypes.byref(k), ctypes.byref(l), ctypes.byref(p)),
+              "seeds_debug_op_info")
+        return k.value, l.value, p.value
+
+    def run_ops(self, images, op_begin: int, op_end: int, stream=None):
+        rgb, strides = self._rgb_args(images)
+        check(lib.seeds_debug_run_ops(self._h, rgb, strides, op_begin, op_end, _stream_handle(stream)),
+              "seeds_debug_run_ops")
+
+    def read_state(self, i: int, level: int, grid_shape, nbins: int, pixels: int):
+        import numpy as np
+        K = self.num_superpixels[i]
+        lab = np.zeros(grid_shape, np.int32)
+        hist = np.zeros((K, nbins), np.int32)
+        sizes = np.zeros(K, np.int32)
+        bins = np.zeros(pixels, np.int32)
+        check(lib.seeds_debug_read_state(self._h, i, level, lab.ctypes.data, hist.ctypes.data, sizes.ctypes.data,
+                                         bins.ctypes.data), "seeds_debug_read_state")
+        return lab, hist, sizes, bins
+
+    def set_labels(self, i: int, level: int, labels):
+        import numpy as np
+        labels = np.ascontiguousarray(labels, np.int32)
+        check(lib.seeds_debug_set_labels(self._h, i, level, labels.ctypes.data), "seeds_debug_set_labels")
+
+    def inject_error(self):
+        check(lib.seeds_debug_inject_error(self._h), "seeds_debug_inject_error")

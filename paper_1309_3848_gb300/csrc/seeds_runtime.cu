@@ -1,0 +1,859 @@
+// seeds_runtime.cu -- host runtime behind the C ABI of include/seeds.h.
+//
+// Validates parameters and derives each image's grid geometry, lays out all
+// device state of a context in one allocation, builds and caches the step
+// schedules the persistent kernel walks, and issues the launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "seeds.h"
+#include "seeds_device.cuh"
+
+using namespace seeds;
+
+namespace {
+
+struct Op {
+    int kind, level, phase;
+};
+
+struct ImageHost {
+    seeds_params p{};
+    int gx = 0, gy = 0, K = 0, L = 0, B = 0, nbins = 0;
+    int64_t N = 0;
+    int nbx[kMaxLevels + 1] = {}, nby[kMaxLevels + 1] = {};
+    std::vector<int32_t> xe[kMaxLevels + 1], ye[kMaxLevels + 1];
+    int maxarea[kMaxLevels + 1] = {};
+    std::vector<Op> ops;  // full list, output op last
+    int moves_cap = 0;
+    // byte offsets inside the context's pool
+    size_t off_bins = 0, off_lab[kMaxLevels + 1] = {}, off_xe[kMaxLevels + 1] = {}, off_ye[kMaxLevels + 1] = {};
+    size_t off_hist = 0, off_size = 0, off_moves = 0, bytes = 0;
+};
+
+struct DevSchedule {
+    void *buf = nullptr;
+    Schedule s{};
+};
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+int from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return SEEDS_OK;
+    if (e == cudaErrorMemoryAllocation) return SEEDS_ERR_NO_MEMORY;
+    return SEEDS_ERR_CUDA;
+}
+
+// Validate one image's parameters and derive its grid (gx, gy) and block
+// levels: gx = max(1, round(sqrt(K*W/H))), gy = max(1, round(K/gx)), level-l
+// edges floor(i*W/(gx*2^(L-l+1))) (Sec. 5.1).  Checks the int64 bound of the
+// exact compares.  Fills the host image record when `g` is given.
+int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t *gy_out)
+{
+    if (!p) return SEEDS_ERR_INVALID;
+    if (p->width < 1 || p->height < 1 || p->width > 32768 || p->height > 32768) return SEEDS_ERR_INVALID;
+    const int64_t N = (int64_t)p->width * p->height;
+    if (N > 0x7fffffffLL) return SEEDS_ERR_INVALID;
+    if (p->num_superpixels < 1) return SEEDS_ERR_INVALID;
+    if (p->block_levels < 0 || p->block_levels > kMaxLevels) return SEEDS_ERR_INVALID;
+    if (p->bins_per_channel < 1 || p->bins_per_channel > 16) return SEEDS_ERR_INVALID;
+    if (p->iters_per_level < 1 || p->iters_per_level > 1000) return SEEDS_ERR_INVALID;
+    if (p->patch != 0 && p->patch != 3) return SEEDS_ERR_INVALID;
+    if (p->gamma_num < 0 || p->gamma_num > 1024 || p->gamma_den < 1 || p->gamma_den > 1024) return SEEDS_ERR_INVALID;
+    const double Kd = p->num_superpixels, Wd = p->width, Hd = p->height;
+    long long gx = std::llround(std::sqrt(Kd * Wd / Hd));
+    if (gx < 1) gx = 1;
+    long long gy = std::llround(Kd / (double)gx);
+    if (gy < 1) gy = 1;
+    if (gx * gy > 65535) return SEEDS_ERR_INVALID;  // labels are 16-bit
+    if (gx_out) *gx_out = (int32_t)gx;
+    if (gy_out) *gy_out = (int32_t)gy;
+    const int L = p->block_levels;
+    if ((gx << L) > p->width || (gy << L) > p->height) return SEEDS_ERR_GEOMETRY;
+
+    ImageHost local;
+    ImageHost &h = g ? *g : local;
+    h.p = *p;
+    h.gx = (int)gx;
+    h.gy = (int)gy;
+    h.K = (int)(gx * gy);
+    h.L = L;
+    h.B = p->bins_per_channel;
+    h.nbins = h.B * h.B * h.B;
+    h.N = N;
+    h.nbx[0] = p->width;
+    h.nby[0] = p->height;
+    h.maxarea[0] = 1;
+    int amax = 1;
+    for (int l = 1; l <= L; ++l) {
+        h.nbx[l] = (int)(gx << (L - l + 1));
+        h.nby[l] = (int)(gy << (L - l + 1));
+        h.xe[l].resize(h.nbx[l] + 1);
+        h.ye[l].resize(h.nby[l] + 1);
+        int mw = 0, mh = 0;
+        for (int i = 0; i <= h.nbx[l]; ++i) {
+            h.xe[l][i] = (int32_t)((int64_t)i * p->width / h.nbx[l]);
+            if (i) mw = std::max(mw, h.xe[l][i] - h.xe[l][i - 1]);
+        }
+        for (int i = 0; i <= h.nby[l]; ++i) {
+            h.ye[l][i] = (int32_t)((int64_t)i * p->height / h.nby[l]);
+            if (i) mh = std::max(mh, h.ye[l][i] - h.ye[l][i - 1]);
+        }
+        h.maxarea[l] = mw * mh;
+        amax = std::max(amax, mw * mh);
+    }
+    // exact int64 compares: block products reach |L|max*N^2, pixel products
+    // (81*gamma_den + 90*gamma_num)*N^2
+    const __int128 N2 = (__int128)N * N;
+    const __int128 lim = ((__int128)1) << 63;
+    if ((__int128)amax * N2 >= lim) return SEEDS_ERR_INT64;
+    if ((__int128)(81 * p->gamma_den + 90 * p->gamma_num) * N2 >= lim) return SEEDS_ERR_INT64;
+
+    // op list: init, block levels L..1 (phases then descent), pixel level, output
+    h.ops.clear();
+    h.ops.push_back({OP_INIT, 0, 0});
+    for (int l = L; l >= 1; --l) {
+        for (int it = 0; it < p->iters_per_level; ++it)
+            for (int ph = 0; ph < 4; ++ph) h.ops.push_back({OP_PHASE, l, ph});
+        h.ops.push_back({OP_DESCEND, l, 0});
+    }
+    for (int it = 0; it < p->iters_per_level; ++it)
+        for (int ph = 0; ph < 4; ++ph) h.ops.push_back({OP_PHASE, 0, ph});
+    h.ops.push_back({OP_OUTPUT, 0, 0});
+    h.moves_cap = (int)(((int64_t)(p->width + 1) / 2) * ((p->height + 1) / 2));
+
+    // device layout
+    size_t off = 0;
+    h.off_bins = off;
+    off = align_up(off + (size_t)N * (h.nbins > 256 ? 2 : 1));
+    for (int l = 0; l <= L; ++l) {
+        h.off_lab[l] = off;
+        off = align_up(off + (size_t)h.nbx[l] * h.nby[l] * 2);
+    }
+    for (int l = 1; l <= L; ++l) {
+        h.off_xe[l] = off;
+        off = align_up(off + (h.nbx[l] + 1) * 4);
+        h.off_ye[l] = off;
+        off = align_up(off + (h.nby[l] + 1) * 4);
+    }
+    h.off_hist = off;
+    off = align_up(off + (size_t)h.K * h.nbins * 4);
+    h.off_size = off;
+    off = align_up(off + (size_t)h.K * 4);
+    h.off_moves = off;
+    off = align_up(off + (size_t)h.moves_cap * 8);
+    h.bytes = off;
+    return SEEDS_OK;
+}
+
+int units_of(const ImageHost &h, const Op &op, int small_area, int *group)
+{
+    *group = 1;
+    switch (op.kind) {
+    case OP_INIT:
+        *group = 32;
+        return h.K;
+    case OP_PHASE: {
+        const int px = op.phase & 1, py = op.phase >> 1;
+        const int nx = h.nbx[op.level], ny = h.nby[op.level];
+        const int64_t u = (int64_t)((nx - px + 1) >> 1) * ((ny - py + 1) >> 1);
+        if (op.level > 0 && h.maxarea[op.level] > small_area) *group = 32;
+        return (int)u;
+    }
+    case OP_DESCEND:
+        return op.level - 1 >= 1 ? h.nbx[op.level - 1] * h.nby[op.level - 1] : (int)h.N;
+    case OP_OUTPUT:
+        return (int)h.N;
+    }
+    return 0;
+}
+
+}  // namespace
+
+struct seeds_ctx {
+    int device = 0;
+    int sm_count = 0;
+    std::vector<ImageHost> img;
+    std::vector<DevImage> h_imgs;
+    std::vector<IoEntry> io;
+    DevImage *d_imgs = nullptr;
+    unsigned char *pool = nullptr;
+    size_t pool_bytes = 0;
+    int32_t *d_cnt = nullptr;  // 2 per image
+    GridBarrier *d_bar = nullptr;
+    int32_t *d_err = nullptr;
+    seeds_tuning tune{256, 0, 0, 16};
+    int grid = 0;
+    size_t smem = 0;
+    int max_nbins = 1;
+    std::map<std::tuple<int, int, int>, DevSchedule> schedules;
+    cudaEvent_t done = nullptr;
+    bool launched = false;
+    bool profile = false, profiled = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int64_t launches = 0;
+    unsigned char *stage = nullptr;
+    size_t stage_bytes = 0;
+    std::vector<size_t> stage_rgb, stage_out;
+};
+
+namespace {
+
+enum { SCHED_ITERATE = 0, SCHED_FULL = 1, SCHED_OUTPUT = 2, SCHED_DEBUG = 3 };
+
+void free_schedules(seeds_ctx *c)
+{
+    for (auto &kv : c->schedules) cudaFree(kv.second.buf);
+    c->schedules.clear();
+}
+
+int configure_launch(seeds_ctx *c)
+{
+    const int threads = c->tune.threads_per_block;
+    c->smem = (size_t)(threads / 32) * warp_scratch_bytes(c->max_nbins);
+    int rc = from_cuda(prepare_persistent(c->smem));
+    if (rc) return rc;
+    int per_sm = 0;
+    rc = from_cuda(persistent_max_blocks_per_sm(threads, c->smem, &per_sm));
+    if (rc) return rc;
+    if (per_sm < 1) return SEEDS_ERR_INVALID;
+    if (c->tune.blocks_per_sm > 0) per_sm = std::min(per_sm, c->tune.blocks_per_sm);
+    c->grid = per_sm * c->sm_count;
+    return SEEDS_OK;
+}
+
+void fill_dev_images(seeds_ctx *c)
+{
+    c->h_imgs.resize(c->img.size());
+    for (size_t i = 0; i < c->img.size(); ++i) {
+        const ImageHost &h = c->img[i];
+        DevImage d;
+        std::memset(&d, 0, sizeof(d));
+        d.W = h.p.width;
+        d.H = h.p.height;
+        d.K = h.K;
+        d.gx = h.gx;
+        d.gy = h.gy;
+        d.L = h.L;
+        d.iters = h.p.iters_per_level;
+        d.B = h.B;
+        d.nbins = h.nbins;
+        d.patch = h.p.patch;
+        d.gnum = h.p.gamma_num;
+        d.gden = h.p.gamma_den;
+        d.bins16 = h.nbins > 256;
+        d.hist_jmajor = c->tune.hist_layout == 1;
+        unsigned char *base = c->pool;
+        for (size_t t = 0; t < i; ++t) base += c->img[t].bytes;
+        for (int l = 0; l <= h.L; ++l) {
+            d.nbx[l] = h.nbx[l];
+            d.nby[l] = h.nby[l];
+            d.lab[l] = (uint16_t *)(base + h.off_lab[l]);
+            d.group[l] = (l > 0 && h.maxarea[l] > c->tune.small_block_area) ? 32 : 1;
+            if (l >= 1) {
+                d.xe[l] = (const int32_t *)(base + h.off_xe[l]);
+                d.ye[l] = (const int32_t *)(base + h.off_ye[l]);
+            }
+        }
+        d.bins = base + h.off_bins;
+        d.hist = (int32_t *)(base + h.off_hist);
+        d.size = (int32_t *)(base + h.off_size);
+        d.moves = (uint32_t *)(base + h.off_moves);
+        d.moves_cap = h.moves_cap;
+        d.cnt = c->d_cnt + 2 * i;
+        d.rgb = c->io[i].rgb;
+        d.stride = c->io[i].stride;
+        d.out = c->io[i].out;
+        c->h_imgs[i] = d;
+    }
+}
+
+// per-image op ranges [b, e) for a schedule kind
+void op_range(const ImageHost &h, int kind, int ob, int oe, int *b, int *e)
+{
+    const int n = (int)h.ops.size();
+    switch (kind) {
+    case SCHED_ITERATE:
+        *b = 0;
+        *e = n - 1;
+        break;
+    case SCHED_FULL:
+        *b = 0;
+        *e = n;
+        break;
+    case SCHED_OUTPUT:
+        *b = n - 1;
+        *e = n;
+        break;
+    default:
+        *b = std::min(std::max(ob, 0), n - 1);
+        *e = std::min(std::max(oe, *b), n - 1);
+        break;
+    }
+}
+
+int get_schedule(seeds_ctx *c, int kind, int ob, int oe, const Schedule **out)
+{
+    auto key = std::make_tuple(kind, kind == SCHED_DEBUG ? ob : 0, kind == SCHED_DEBUG ? oe : 0);
+    auto it = c->schedules.find(key);
+    if (it != c->schedules.end()) {
+        *out = &it->second.s;
+        return SEEDS_OK;
+    }
+    const int n = (int)c->img.size();
+    std::vector<int> b(n), e(n);
+    int nsteps = 0;
+    for (int i = 0; i < n; ++i) {
+        op_range(c->img[i], kind, ob, oe, &b[i], &e[i]);
+        nsteps = std::max(nsteps, e[i] - b[i]);
+    }
+    std::vector<StepEntry> ent;
+    std::vector<int32_t> first, apply;
+    std::vector<int64_t> vt;
+    for (int s = 0; s < nsteps; ++s) {
+        first.push_back((int32_t)ent.size());
+        int64_t v = 0;
+        int ap = 0;
+        for (int i = 0; i < n; ++i) {
+            const int o = b[i] + s;
+            if (o >= e[i]) continue;
+            const Op &op = c->img[i].ops[o];
+            int group = 1;
+            const int units = units_of(c->img[i], op, c->tune.small_block_area, &group);
+            const int64_t count = ((int64_t)units * group + 31) / 32 * 32;
+            if (count == 0) continue;
+            StepEntry se;
+            se.img = i;
+            se.op = op.kind;
+            se.level = op.level;
+            se.phase = op.phase;
+            se.vt_begin = v;
+            se.units = units;
+            se.group = group;
+            ent.push_back(se);
+            v += count;
+            ap |= op.kind == OP_PHASE;
+        }
+        vt.push_back(v);
+        apply.push_back(ap);
+    }
+    first.push_back((int32_t)ent.size());
+    if (ent.empty()) ent.push_back(StepEntry{});  // keep the buffer non-empty
+
+    const size_t b_ent = align_up(ent.size() * sizeof(StepEntry));
+    const size_t b_first = align_up(first.size() * sizeof(int32_t));
+    const size_t b_vt = align_up(std::max<size_t>(1, vt.size()) * sizeof(int64_t));
+    const size_t b_apply = align_up(std::max<size_t>(1, apply.size()) * sizeof(int32_t));
+    DevSchedule ds;
+    int rc = from_cuda(cudaMalloc(&ds.buf, b_ent + b_first + b_vt + b_apply));
+    if (rc) return rc;
+    unsigned char *p = (unsigned char *)ds.buf;
+    std::vector<unsigned char> host(b_ent + b_first + b_vt + b_apply, 0);
+    std::memcpy(host.data(), ent.data(), ent.size() * sizeof(StepEntry));
+    std::memcpy(host.data() + b_ent, first.data(), first.size() * sizeof(int32_t));
+    if (!vt.empty()) std::memcpy(host.data() + b_ent + b_first, vt.data(), vt.size() * sizeof(int64_t));
+    if (!apply.empty())
+        std::memcpy(host.data() + b_ent + b_first + b_vt, apply.data(), apply.size() * sizeof(int32_t));
+    rc = from_cuda(cudaMemcpy(ds.buf, host.data(), host.size(), cudaMemcpyHostToDevice));
+    if (rc) {
+        cudaFree(ds.buf);
+        return rc;
+    }
+    ds.s.ent = (const StepEntry *)p;
+    ds.s.step_first = (const int32_t *)(p + b_ent);
+    ds.s.step_vt = (const int64_t *)(p + b_ent + b_first);
+    ds.s.step_apply = (const int32_t *)(p + b_ent + b_first + b_vt);
+    ds.s.nsteps = nsteps;
+    ds.s.max_nbins = c->max_nbins;
+    auto ins = c->schedules.emplace(key, ds);
+    *out = &ins.first->second.s;
+    return SEEDS_OK;
+}
+
+// push the per-call pointers of every image to the device records
+int push_io(seeds_ctx *c, cudaStream_t s)
+{
+    const int n = (int)c->img.size();
+    for (int f = 0; f < n; f += kIoChunk) {
+        IoChunk ch;
+        std::memset(&ch, 0, sizeof(ch));
+        ch.first = f;
+        ch.n = std::min(kIoChunk, n - f);
+        for (int t = 0; t < ch.n; ++t) ch.e[t] = c->io[f + t];
+        int rc = from_cuda(launch_set_io(c->d_imgs, ch, s));
+        if (rc) return rc;
+        ++c->launches;
+    }
+    return SEEDS_OK;
+}
+
+int launch(seeds_ctx *c, int kind, int ob, int oe, cudaStream_t s)
+{
+    const Schedule *sch = nullptr;
+    int rc = get_schedule(c, kind, ob, oe, &sch);
+    if (rc) return rc;
+    rc = push_io(c, s);
+    if (rc) return rc;
+    if (sch->nsteps == 0) return SEEDS_OK;
+    rc = from_cuda(cudaMemsetAsync(c->d_bar, 0, sizeof(GridBarrier), s));
+    if (!rc) rc = from_cuda(cudaMemsetAsync(c->d_cnt, 0, sizeof(int32_t) * 2 * c->img.size(), s));
+    if (rc) return rc;
+    if (c->profile) {
+        rc = from_cuda(cudaEventRecord(c->ev0, s));
+        if (rc) return rc;
+    }
+    rc = from_cuda(launch_persistent(c->d_imgs, *sch, c->d_bar, c->d_err, c->grid, c->tune.threads_per_block,
+                                     c->smem, s));
+    if (rc) return rc;
+    ++c->launches;
+    if (c->profile) {
+        rc = from_cuda(cudaEventRecord(c->ev1, s));
+        if (rc) return rc;
+    }
+    c->profiled = c->profile;
+    rc = from_cuda(cudaEventRecord(c->done, s));
+    c->launched = true;
+    return rc;
+}
+
+void destroy_ctx(seeds_ctx *c)
+{
+    if (!c) return;
+    if (c->launched) cudaEventSynchronize(c->done);
+    free_schedules(c);
+    cudaFree(c->d_imgs);
+    cudaFree(c->pool);
+    cudaFree(c->d_cnt);
+    cudaFree(c->d_bar);
+    cudaFree(c->d_err);
+    cudaFree(c->stage);
+    if (c->done) cudaEventDestroy(c->done);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+}
+
+int create_ctx(const seeds_params *p, int32_t n, seeds_ctx **out)
+{
+    if (!p || !out || n < 1 || n > SEEDS_MAX_BATCH) return SEEDS_ERR_INVALID;
+    *out = nullptr;
+    seeds_ctx *c = new (std::nothrow) seeds_ctx;
+    if (!c) return SEEDS_ERR_NO_MEMORY;
+    c->img.resize(n);
+    for (int i = 0; i < n; ++i) {
+        int rc = derive(&p[i], &c->img[i], nullptr, nullptr);
+        if (rc) {
+            delete c;
+            return rc;
+        }
+        c->max_nbins = std::max(c->max_nbins, c->img[i].nbins);
+    }
+    c->io.assign(n, IoEntry{nullptr, 0, nullptr});
+    int rc = from_cuda(cudaGetDevice(&c->device));
+    if (!rc) rc = from_cuda(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+    for (auto &h : c->img) c->pool_bytes += h.bytes;
+    if (!rc) rc = from_cuda(cudaMalloc((void **)&c->pool, c->pool_bytes));
+    if (!rc) rc = from_cuda(cudaMalloc((void **)&c->d_imgs, sizeof(DevImage) * n));
+    if (!rc) rc = from_cuda(cudaMalloc((void **)&c->d_cnt, sizeof(int32_t) * 2 * n));
+    if (!rc) rc = from_cuda(cudaMalloc((void **)&c->d_bar, sizeof(GridBarrier)));
+    if (!rc) rc = from_cuda(cudaMalloc((void **)&c->d_err, sizeof(int32_t)));
+    if (!rc) rc = from_cuda(cudaMemset(c->d_err, 0, sizeof(int32_t)));
+    if (!rc) rc = from_cuda(cudaMemset(c->d_cnt, 0, sizeof(int32_t) * 2 * n));
+    if (!rc) rc = from_cuda(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
+    if (!rc) rc = from_cuda(cudaEventCreate(&c->ev0));
+    if (!rc) rc = from_cuda(cudaEventCreate(&c->ev1));
+    if (!rc) {
+        // block edge tables are constant for the context's life
+        unsigned char *base = c->pool;
+        for (auto &h : c->img) {
+            for (int l = 1; l <= h.L && !rc; ++l) {
+                rc = from_cuda(cudaMemcpy(base + h.off_xe[l], h.xe[l].data(), h.xe[l].size() * 4,
+                                          cudaMemcpyHostToDevice));
+                if (!rc)
+                    rc = from_cuda(cudaMemcpy(base + h.off_ye[l], h.ye[l].data(), h.ye[l].size() * 4,
+                                              cudaMemcpyHostToDevice));
+            }
+            base += h.bytes;
+        }
+    }
+    if (!rc) {
+        fill_dev_images(c);
+        rc = from_cuda(cudaMemcpy(c->d_imgs, c->h_imgs.data(), sizeof(DevImage) * n, cudaMemcpyHostToDevice));
+    }
+    if (!rc) rc = configure_launch(c);
+    if (rc) {
+        destroy_ctx(c);
+        return rc;
+    }
+    *out = c;
+    return SEEDS_OK;
+}
+
+int check_io(const seeds_ctx *c, const uint8_t *const *rgb, const int64_t *strides)
+{
+    if (!rgb || !strides) return SEEDS_ERR_INVALID;
+    for (size_t i = 0; i < c->img.size(); ++i)
+        if (!rgb[i] || strides[i] < 3 * (int64_t)c->img[i].p.width) return SEEDS_ERR_INVALID;
+    return SEEDS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+int seeds_params_default(seeds_params *p, int32_t width, int32_t height, int32_t num_superpixels)
+{
+    if (!p) return SEEDS_ERR_INVALID;
+    p->width = width;
+    p->height = height;
+    p->num_superpixels = num_superpixels;
+    p->block_levels = 0;
+    p->bins_per_channel = 5;
+    p->iters_per_level = 2;
+    p->patch = 3;
+    p->gamma_num = 1;
+    p->gamma_den = 1;
+    int32_t lmax = 0;
+    int rc = seeds_feasible_levels(p, &lmax);
+    if (rc) return rc;
+    p->block_levels = std::min(4, lmax);
+    return SEEDS_OK;
+}
+
+int seeds_feasible_levels(const seeds_params *p, int32_t *max_levels)
+{
+    if (!p || !max_levels) return SEEDS_ERR_INVALID;
+    seeds_params q = *p;
+    q.block_levels = 0;
+    int32_t gx = 0, gy = 0;
+    int rc = derive(&q, nullptr, &gx, &gy);
+    if (rc) return rc;
+    int L = 0;
+    while (L < kMaxLevels && ((int64_t)gx << (L + 1)) <= p->width && ((int64_t)gy << (L + 1)) <= p->height) ++L;
+    *max_levels = L;
+    return SEEDS_OK;
+}
+
+int seeds_check_params(const seeds_params *p, int32_t *gx, int32_t *gy)
+{
+    int32_t a = 0, b = 0;
+    int rc = derive(p, nullptr, &a, &b);
+    if (gx) *gx = a;
+    if (gy) *gy = b;
+    return rc;
+}
+
+int seeds_footprint(const seeds_params *p, int32_t n, int64_t *bytes)
+{
+    if (!p || !bytes || n < 1) return SEEDS_ERR_INVALID;
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        ImageHost h;
+        int rc = derive(&p[i], &h, nullptr, nullptr);
+        if (rc) return rc;
+        total += (int64_t)h.bytes + sizeof(DevImage) + 8;
+    }
+    *bytes = total;
+    return SEEDS_OK;
+}
+
+int seeds_create(const seeds_params *p, seeds_ctx **out) { return create_ctx(p, 1, out); }
+
+int seeds_batch_create(const seeds_params *p, int32_t n, seeds_ctx **out) { return create_ctx(p, n, out); }
+
+int seeds_destroy(seeds_ctx *c)
+{
+    if (!c) return SEEDS_ERR_INVALID;
+    destroy_ctx(c);
+    return SEEDS_OK;
+}
+
+int seeds_num_superpixels(const seeds_ctx *c, int32_t *k_out) { return seeds_batch_num_superpixels(c, 0, k_out); }
+
+int seeds_batch_size(const seeds_ctx *c, int32_t *n_out)
+{
+    if (!c || !n_out) return SEEDS_ERR_INVALID;
+    *n_out = (int32_t)c->img.size();
+    return SEEDS_OK;
+}
+
+int seeds_batch_num_superpixels(const seeds_ctx *c, int32_t i, int32_t *k_out)
+{
+    if (!c || !k_out || i < 0 || i >= (int32_t)c->img.size()) return SEEDS_ERR_INVALID;
+    *k_out = c->img[i].K;
+    return SEEDS_OK;
+}
+
+int seeds_iterate(seeds_ctx *c, const uint8_t *d_rgb, int64_t row_stride_bytes, void *stream)
+{
+    if (!c || c->img.size() != 1) return SEEDS_ERR_INVALID;
+    return seeds_batch_iterate(c, &d_rgb, &row_stride_bytes, stream);
+}
+
+int seeds_labels(seeds_ctx *c, int32_t *d_labels_out, void *stream)
+{
+    if (!c || c->img.size() != 1) return SEEDS_ERR_INVALID;
+    return seeds_batch_labels(c, &d_labels_out, stream);
+}
+
+int seeds_batch_iterate(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides, void *stream)
+{
+    if (!c) return SEEDS_ERR_INVALID;
+    int rc = check_io(c, h_rgb_ptrs, h_row_strides);
+    if (rc) return rc;
+    for (size_t i = 0; i < c->img.size(); ++i) {
+        c->io[i].rgb = h_rgb_ptrs[i];
+        c->io[i].stride = h_row_strides[i];
+    }
+    return launch(c, SCHED_ITERATE, 0, 0, (cudaStream_t)stream);
+}
+
+int seeds_batch_labels(seeds_ctx *c, int32_t *const *h_label_ptrs, void *stream)
+{
+    if (!c || !h_label_ptrs) return SEEDS_ERR_INVALID;
+    for (size_t i = 0; i < c->img.size(); ++i) {
+        if (!h_label_ptrs[i]) return SEEDS_ERR_INVALID;
+        c->io[i].out = h_label_ptrs[i];
+    }
+    return launch(c, SCHED_OUTPUT, 0, 0, (cudaStream_t)stream);
+}
+
+int seeds_batch_run(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides,
+                    int32_t *const *h_label_ptrs, void *stream)
+{
+    if (!c || !h_label_ptrs) return SEEDS_ERR_INVALID;
+    int rc = check_io(c, h_rgb_ptrs, h_row_strides);
+    if (rc) return rc;
+    for (size_t i = 0; i < c->img.size(); ++i) {
+        if (!h_label_ptrs[i]) return SEEDS_ERR_INVALID;
+        c->io[i].rgb = h_rgb_ptrs[i];
+        c->io[i].stride = h_row_strides[i];
+        c->io[i].out = h_label_ptrs[i];
+    }
+    return launch(c, SCHED_FULL, 0, 0, (cudaStream_t)stream);
+}
+
+int seeds_run_host(seeds_ctx *c, const uint8_t *const *h_rgb, const int64_t *h_row_strides, int32_t *const *h_labels,
+                   void *stream)
+{
+    if (!c || !h_rgb || !h_row_strides || !h_labels) return SEEDS_ERR_INVALID;
+    const size_t n = c->img.size();
+    for (size_t i = 0; i < n; ++i)
+        if (!h_rgb[i] || !h_labels[i] || h_row_strides[i] < 3 * (int64_t)c->img[i].p.width) return SEEDS_ERR_INVALID;
+    if (!c->stage) {
+        size_t off = 0;
+        c->stage_rgb.resize(n);
+        c->stage_out.resize(n);
+        for (size_t i = 0; i < n; ++i) {
+            c->stage_rgb[i] = off;
+            off = align_up(off + (size_t)c->img[i].N * 3);
+            c->stage_out[i] = off;
+            off = align_up(off + (size_t)c->img[i].N * 4);
+        }
+        int rc = from_cuda(cudaMalloc((void **)&c->stage, off));
+        if (rc) return rc;
+        c->stage_bytes = off;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (size_t i = 0; i < n; ++i) {
+        const ImageHost &h = c->img[i];
+        const size_t row = (size_t)h.p.width * 3;
+        int rc = from_cuda(cudaMemcpy2DAsync(c->stage + c->stage_rgb[i], row, h_rgb[i], (size_t)h_row_strides[i], row,
+                                             (size_t)h.p.height, cudaMemcpyHostToDevice, s));
+        if (rc) return rc;
+        c->io[i].rgb = c->stage + c->stage_rgb[i];
+        c->io[i].stride = (int64_t)row;
+        c->io[i].out = (int32_t *)(c->stage + c->stage_out[i]);
+    }
+    int rc = launch(c, SCHED_FULL, 0, 0, s);
+    if (rc) return rc;
+    for (size_t i = 0; i < n; ++i) {
+        rc = from_cuda(cudaMemcpyAsync(h_labels[i], c->stage + c->stage_out[i], (size_t)c->img[i].N * 4,
+                                       cudaMemcpyDeviceToHost, s));
+        if (rc) return rc;
+    }
+    return from_cuda(cudaEventRecord(c->done, s));
+}
+
+int seeds_status(seeds_ctx *c)
+{
+    if (!c) return SEEDS_ERR_INVALID;
+    if (c->launched) {
+        int rc = from_cuda(cudaEventSynchronize(c->done));
+        if (rc) return rc;
+    }
+    int32_t e = 0;
+    int rc = from_cuda(cudaMemcpy(&e, c->d_err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (rc) return rc;
+    if (e != 0) {
+        cudaMemset(c->d_err, 0, sizeof(int32_t));
+        return SEEDS_ERR_DEVICE;
+    }
+    return from_cuda(cudaGetLastError());
+}
+
+int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t)
+{
+    if (!c || !t) return SEEDS_ERR_INVALID;
+    seeds_tuning n = *t;
+    if (n.threads_per_block == 0) n.threads_per_block = 256;
+    if (n.small_block_area == 0) n.small_block_area = 16;
+    if (n.threads_per_block != 128 && n.threads_per_block != 256 && n.threads_per_block != 512)
+        return SEEDS_ERR_INVALID;
+    if (n.blocks_per_sm < 0 || n.hist_layout < 0 || n.hist_layout > 1) return SEEDS_ERR_INVALID;
+    if (n.small_block_area < 1 || n.small_block_area > 16) return SEEDS_ERR_INVALID;
+    if (c->launched) cudaEventSynchronize(c->done);
+    c->tune = n;
+    free_schedules(c);
+    fill_dev_images(c);
+    int rc = from_cuda(cudaMemcpy(c->d_imgs, c->h_imgs.data(), sizeof(DevImage) * c->img.size(),
+                                  cudaMemcpyHostToDevice));
+    if (rc) return rc;
+    return configure_launch(c);
+}
+
+int seeds_get_tuning(const seeds_ctx *c, seeds_tuning *t)
+{
+    if (!c || !t) return SEEDS_ERR_INVALID;
+    *t = c->tune;
+    return SEEDS_OK;
+}
+
+int seeds_debug_num_ops(const seeds_ctx *c, int32_t i, int32_t *n_ops)
+{
+    if (!c || !n_ops || i < 0 || i >= (int32_t)c->img.size()) return SEEDS_ERR_INVALID;
+    *n_ops = (int32_t)c->img[i].ops.size();
+    return SEEDS_OK;
+}
+
+int seeds_debug_op_info(const seeds_ctx *c, int32_t i, int32_t op, int32_t *kind, int32_t *level, int32_t *phase)
+{
+    if (!c || i < 0 || i >= (int32_t)c->img.size()) return SEEDS_ERR_INVALID;
+    const auto &ops = c->img[i].ops;
+    if (op < 0 || op >= (int32_t)ops.size()) return SEEDS_ERR_INVALID;
+    if (kind) *kind = ops[op].kind;
+    if (level) *level = ops[op].level;
+    if (phase) *phase = ops[op].phase;
+    return SEEDS_OK;
+}
+
+int seeds_debug_run_ops(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides, int32_t op_begin,
+                        int32_t op_end, void *stream)
+{
+    if (!c || op_begin < 0 || op_end < op_begin) return SEEDS_ERR_INVALID;
+    int rc = check_io(c, h_rgb_ptrs, h_row_strides);
+    if (rc) return rc;
+    for (size_t i = 0; i < c->img.size(); ++i) {
+        c->io[i].rgb = h_rgb_ptrs[i];
+        c->io[i].stride = h_row_strides[i];
+    }
+    return launch(c, SCHED_DEBUG, op_begin, op_end, (cudaStream_t)stream);
+}
+
+int seeds_debug_read_state(seeds_ctx *c, int32_t i, int32_t level, int32_t *h_labels, int32_t *h_hist,
+                           int32_t *h_sizes, int32_t *h_bins)
+{
+    if (!c || i < 0 || i >= (int32_t)c->img.size()) return SEEDS_ERR_INVALID;
+    const ImageHost &h = c->img[i];
+    const DevImage &d = c->h_imgs[i];
+    if (level < 0 || level > h.L) return SEEDS_ERR_INVALID;
+    int rc = from_cuda(cudaDeviceSynchronize());
+    if (rc) return rc;
+    if (h_labels) {
+        const size_t n = (size_t)h.nbx[level] * h.nby[level];
+        std::vector<uint16_t> t(n);
+        rc = from_cuda(cudaMemcpy(t.data(), d.lab[level], n * 2, cudaMemcpyDeviceToHost));
+        if (rc) return rc;
+        for (size_t q = 0; q < n; ++q) h_labels[q] = t[q];
+    }
+    if (h_hist) {
+        const size_t n = (size_t)h.K * h.nbins;
+        std::vector<int32_t> t(n);
+        rc = from_cuda(cudaMemcpy(t.data(), d.hist, n * 4, cudaMemcpyDeviceToHost));
+        if (rc) return rc;
+        for (int k = 0; k < h.K; ++k)
+            for (int j = 0; j < h.nbins; ++j)
+                h_hist[(size_t)k * h.nbins + j] = d.hist_jmajor ? t[(size_t)j * h.K + k] : t[(size_t)k * h.nbins + j];
+    }
+    if (h_sizes) {
+        rc = from_cuda(cudaMemcpy(h_sizes, d.size, (size_t)h.K * 4, cudaMemcpyDeviceToHost));
+        if (rc) return rc;
+    }
+    if (h_bins) {
+        if (d.bins16) {
+            std::vector<uint16_t> t((size_t)h.N);
+            rc = from_cuda(cudaMemcpy(t.data(), d.bins, (size_t)h.N * 2, cudaMemcpyDeviceToHost));
+            if (rc) return rc;
+            for (int64_t q = 0; q < h.N; ++q) h_bins[q] = t[q];
+        } else {
+            std::vector<uint8_t> t((size_t)h.N);
+            rc = from_cuda(cudaMemcpy(t.data(), d.bins, (size_t)h.N, cudaMemcpyDeviceToHost));
+            if (rc) return rc;
+            for (int64_t q = 0; q < h.N; ++q) h_bins[q] = t[q];
+        }
+    }
+    return SEEDS_OK;
+}
+
+int seeds_debug_set_labels(seeds_ctx *c, int32_t i, int32_t level, const int32_t *h_labels)
+{
+    if (!c || !h_labels || i < 0 || i >= (int32_t)c->img.size()) return SEEDS_ERR_INVALID;
+    const ImageHost &h = c->img[i];
+    if (level < 0 || level > h.L) return SEEDS_ERR_INVALID;
+    const size_t n = (size_t)h.nbx[level] * h.nby[level];
+    std::vector<uint16_t> t(n);
+    for (size_t q = 0; q < n; ++q) {
+        if (h_labels[q] < 0 || h_labels[q] >= h.K) return SEEDS_ERR_INVALID;
+        t[q] = (uint16_t)h_labels[q];
+    }
+    int rc = from_cuda(cudaDeviceSynchronize());
+    if (!rc) rc = from_cuda(cudaMemcpy(c->h_imgs[i].lab[level], t.data(), n * 2, cudaMemcpyHostToDevice));
+    if (!rc) rc = from_cuda(launch_recount(c->d_imgs, i, level, h.N, 0));
+    if (!rc) rc = from_cuda(cudaDeviceSynchronize());
+    c->launches += 2;
+    return rc;
+}
+
+int seeds_debug_inject_error(seeds_ctx *c)
+{
+    if (!c) return SEEDS_ERR_INVALID;
+    const int32_t v = DERR_INJECTED;
+    return from_cuda(cudaMemcpy(c->d_err, &v, sizeof(v), cudaMemcpyHostToDevice));
+}
+
+int seeds_debug_launch_count(const seeds_ctx *c, int64_t *n)
+{
+    if (!c || !n) return SEEDS_ERR_INVALID;
+    *n = c->launches;
+    return SEEDS_OK;
+}
+
+int seeds_profile_enable(seeds_ctx *c, int32_t enable)
+{
+    if (!c) return SEEDS_ERR_INVALID;
+    c->profile = enable != 0;
+    return SEEDS_OK;
+}
+
+int seeds_profile_last_ms(seeds_ctx *c, float *ms)
+{
+    if (!c || !ms || !c->profiled) return SEEDS_ERR_INVALID;
+    int rc = from_cuda(cudaEventSynchronize(c->ev1));
+    if (rc) return rc;
+    return from_cuda(cudaEventElapsedTime(ms, c->ev0, c->ev1));
+}
+
+}  // extern "C"

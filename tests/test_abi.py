@@ -1,0 +1,94 @@
+"""C ABI checks that need no GPU: the library loads, exports every entry
+point that include/seeds.h declares, and its host-side parameter logic
+(validation, grid geometry, feasible levels, int64 bound) behaves."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "seeds.h")
+
+
+@pytest.fixture(scope="module")
+def binding():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1309_3848_gb300 import binding
+    return binding
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\bint\s+(seeds_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["seeds_create", "seeds_iterate", "seeds_labels", "seeds_num_superpixels", "seeds_destroy",
+              "seeds_batch_create", "seeds_batch_iterate", "seeds_debug_set_labels", "seeds_debug_run_ops"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(binding):
+    lib = ctypes.CDLL(binding.LIB_PATH)
+    names = declared_functions()
+    assert sorted(binding.EXPORTS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_geometry_agrees_with_the_oracle(binding):
+    from oracle import ref
+    rng = np.random.default_rng(0)
+    cases = [(481, 321, 200, 4), (1920, 1080, 1000, 4), (3840, 2160, 5000, 5), (320, 240, 1500, 2),
+             (320, 240, 1500, 3), (7, 5, 35, 0), (1, 1, 1, 0)]
+    for _ in range(300):
+        W, H = int(rng.integers(1, 400)), int(rng.integers(1, 400))
+        cases.append((W, H, int(rng.integers(1, max(2, W * H // 3))), int(rng.integers(0, 6))))
+    for W, H, K, L in cases:
+        p = binding.make_params(W, H, K, L, 5, 1)
+        rc, gx, gy = binding.check_params(p)
+        rrc, rgx, rgy = ref.grid(W, H, K, L)
+        if rrc == ref.EINVAL:
+            assert rc == binding.SEEDS_ERR_INVALID
+            continue
+        assert (gx, gy) == (rgx, rgy), (W, H, K, L)
+        assert (rc == binding.SEEDS_ERR_GEOMETRY) == (rrc == ref.EGEOM), (W, H, K, L)
+        if rc == 0:
+            Lmax = binding.feasible_levels(W, H, K)
+            assert Lmax >= L
+            assert ref.grid(W, H, K, Lmax)[0] == 0
+            assert ref.grid(W, H, K, Lmax + 1)[0] == ref.EGEOM or Lmax + 1 > 12
+
+
+def test_invalid_parameters(binding):
+    bad = [binding.make_params(0, 10, 4, 0, 5, 1), binding.make_params(10, 10, 0, 0, 5, 1),
+           binding.make_params(10, 10, 4, 0, 17, 1), binding.make_params(10, 10, 4, 0, 5, 0),
+           binding.make_params(10, 10, 4, 0, 5, 1, patch=2), binding.make_params(10, 10, 4, 0, 5, 1, gamma=(1, 0)),
+           binding.make_params(10, 10, 4, 13, 5, 1)]
+    for p in bad:
+        assert binding.check_params(p)[0] == binding.SEEDS_ERR_INVALID
+    assert binding.check_params(binding.make_params(16, 16, 4, 4, 5, 1))[0] == binding.SEEDS_ERR_GEOMETRY
+    # exact int64 compares: gamma 1024/1024 on an 8192x8192 image overflows
+    assert binding.check_params(binding.make_params(8192, 8192, 1000, 0, 5, 1, gamma=(1024, 1024)))[0] == \
+        binding.SEEDS_ERR_INT64
+
+
+def test_defaults_follow_the_paper(binding):
+    p = binding.seeds_params()
+    assert binding.lib.seeds_params_default(ctypes.byref(p), 481, 321, 200) == 0
+    assert (p.bins_per_channel, p.patch, p.gamma_num, p.gamma_den) == (5, 3, 1, 1)
+    assert p.block_levels == 4
+    assert binding.lib.seeds_params_default(ctypes.byref(p), 320, 240, 1500) == 0
+    assert p.block_levels == 2
+
+
+def test_footprint_grows_with_the_images(binding):
+    a = binding.footprint([binding.make_params(640, 480, 500, 3, 5, 2)])
+    b = binding.footprint([binding.make_params(640, 480, 500, 3, 5, 2)] * 3)
+    c = binding.footprint([binding.make_params(3840, 2160, 5000, 5, 8, 4)])
+    assert a > 640 * 480 * 5 and b >= 3 * a and c > 8 * a
