@@ -219,6 +219,12 @@ int seeds_profile_enable(seeds_ctx *c, int32_t enable);
  * (waits for it).  SEEDS_ERR_INVALID if profiling was off for it. */
 int seeds_profile_last_ms(seeds_ctx *c, float *ms);
 
+/* Step stamps of the most recent profiled persistent launch: *n = 1 +
+ * 2*steps values (ns since the kernel began, read on the device's global
+ * timer by one thread): [0] start, [1+2s] end of step s's evaluate slot,
+ * [2+2s] end of its apply slot.  Call with h_ns = NULL to get *n. */
+int seeds_profile_steps(seeds_ctx *c, int64_t *h_ns, int32_t cap, int32_t *n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,7 +36,7 @@ EXPORTS = [
     "seeds_batch_labels", "seeds_batch_run", "seeds_run_host", "seeds_set_tuning", "seeds_get_tuning",
     "seeds_debug_num_ops", "seeds_debug_op_info", "seeds_debug_run_ops", "seeds_debug_read_state",
     "seeds_debug_set_labels", "seeds_debug_inject_error", "seeds_debug_launch_count", "seeds_profile_enable",
-    "seeds_profile_last_ms",
+    "seeds_profile_last_ms", "seeds_profile_steps",
 ]
 
 
@@ -93,6 +93,7 @@ def _load():
         "seeds_debug_launch_count": [vp, P(i64)],
         "seeds_profile_enable": [vp, i32],
         "seeds_profile_last_ms": [vp, P(ctypes.c_float)],
+        "seeds_profile_steps": [vp, vp, i32, P(i32)],
     }
     for name in EXPORTS:
         f = getattr(L, name)
@@ -250,6 +251,16 @@ class SeedsContext:
         ms = ctypes.c_float()
         check(lib.seeds_profile_last_ms(self._h, ctypes.byref(ms)), "seeds_profile_last_ms")
         return ms.value
+
+    def step_stamps(self):
+        """ns stamps of the last profiled launch: start, then per step the
+        end of its evaluate slot and of its apply slot."""
+        import numpy as np
+        n = ctypes.c_int32()
+        check(lib.seeds_profile_steps(self._h, None, 0, ctypes.byref(n)), "seeds_profile_steps")
+        out = np.zeros(n.value, np.int64)
+        check(lib.seeds_profile_steps(self._h, out.ctypes.data, n.value, ctypes.byref(n)), "seeds_profile_steps")
+        return out
 
     # -- test hooks
     def num_ops(self, i: int) -> int:

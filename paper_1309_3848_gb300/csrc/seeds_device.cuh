@@ -64,6 +64,7 @@ struct Schedule {
     const int32_t *step_apply;  // step has a phase entry
     int32_t nsteps;
     int32_t max_nbins;          // largest histogram of the context (scratch size)
+    unsigned long long *trace;  // optional: 1 + 2*nsteps globaltimer stamps
 };
 
 struct GridBarrier {

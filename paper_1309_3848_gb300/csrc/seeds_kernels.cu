@@ -399,7 +399,7 @@ __device__ __forceinline__ int64_t warp_sum64(int64_t v)
 }
 
 __device__ void op_block_phase_warp(const DevImage &im, int level, int phase, int units, int s, int u, int lane,
-                                    int32_t *wsh, int32_t *err)
+                                    int32_t *wsh, int max_nbins, int32_t *err)
 {
     if (u >= units) return;
     const int px = phase & 1, py = phase >> 1;
@@ -415,9 +415,11 @@ __device__ void op_block_phase_warp(const DevImage &im, int level, int phase, in
     const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
     const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
     const int bw = x1 - x0, m = bw * (y1 - y0);
+    // the list lives past the largest histogram of the context, so that it
+    // never overlaps histogram entries another image's blocks rely on being 0
     int32_t *ndist = wsh;
     int32_t *hsh = wsh + kScratchHeader;
-    uint16_t *lst = (uint16_t *)(hsh + im.nbins);
+    uint16_t *lst = (uint16_t *)(hsh + max_nbins);
     // sparse histogram of the block: counts in shared memory, distinct bins listed
     for (int base = 0; base < m; base += 32) {
         const int t = base + lane;
@@ -581,6 +583,8 @@ __global__ void __launch_bounds__(512) seeds_persistent(const DevImage *__restri
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
 
+    const bool tracer = S.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
+    if (tracer) S.trace[0] = global_ns();
     for (int s = 0; s < S.nsteps; ++s) {
         const int e0 = S.step_first[s], e1 = S.step_first[s + 1];
         // the other move counter of every image in this step was last read
@@ -612,7 +616,8 @@ __global__ void __launch_bounds__(512) seeds_persistent(const DevImage *__restri
                 else if (E.group == 1)
                     op_block_phase_thread(im, E.level, E.phase, E.units, s, (int)(off + lane), lane, err);
                 else
-                    op_block_phase_warp(im, E.level, E.phase, E.units, s, (int)(off >> 5), lane, wsh, err);
+                    op_block_phase_warp(im, E.level, E.phase, E.units, s, (int)(off >> 5), lane, wsh, S.max_nbins,
+                                        err);
                 break;
             case OP_DESCEND:
                 op_descend(im, E.level, off + lane);
@@ -627,9 +632,11 @@ __global__ void __launch_bounds__(512) seeds_persistent(const DevImage *__restri
         const bool last = s + 1 == S.nsteps;
         if (!S.step_apply[s]) {
             if (!last && !grid_sync(bar, err)) return;
+            if (tracer) S.trace[1 + 2 * s] = S.trace[2 + 2 * s] = global_ns();
             continue;
         }
         if (!grid_sync(bar, err)) return;
+        if (tracer) S.trace[1 + 2 * s] = global_ns();
 
         // ---- apply slot
         for (int e = e0; e < e1; ++e) {
@@ -650,6 +657,7 @@ __global__ void __launch_bounds__(512) seeds_persistent(const DevImage *__restri
             }
         }
         if (!last && !grid_sync(bar, err)) return;
+        if (tracer) S.trace[2 + 2 * s] = global_ns();
     }
 }
 

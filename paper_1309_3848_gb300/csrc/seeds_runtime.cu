@@ -200,6 +200,8 @@ struct seeds_ctx {
     bool launched = false;
     bool profile = false, profiled = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    unsigned long long *d_trace = nullptr;  // step stamps while profiling
+    int trace_cap = 0, traced_steps = 0;
     int64_t launches = 0;
     unsigned char *stage = nullptr;
     size_t stage_bytes = 0;
@@ -407,11 +409,19 @@ int launch(seeds_ctx *c, int kind, int ob, int oe, cudaStream_t s)
     rc = from_cuda(cudaMemsetAsync(c->d_bar, 0, sizeof(GridBarrier), s));
     if (!rc) rc = from_cuda(cudaMemsetAsync(c->d_cnt, 0, sizeof(int32_t) * 2 * c->img.size(), s));
     if (rc) return rc;
+    Schedule run = *sch;
+    run.trace = nullptr;
     if (c->profile) {
         rc = from_cuda(cudaEventRecord(c->ev0, s));
         if (rc) return rc;
+        if (1 + 2 * run.nsteps <= c->trace_cap) {
+            run.trace = c->d_trace;
+            c->traced_steps = run.nsteps;
+        } else {
+            c->traced_steps = 0;
+        }
     }
-    rc = from_cuda(launch_persistent(c->d_imgs, *sch, c->d_bar, c->d_err, c->grid, c->tune.threads_per_block,
+    rc = from_cuda(launch_persistent(c->d_imgs, run, c->d_bar, c->d_err, c->grid, c->tune.threads_per_block,
                                      c->smem, s));
     if (rc) return rc;
     ++c->launches;
@@ -436,6 +446,7 @@ void destroy_ctx(seeds_ctx *c)
     cudaFree(c->d_bar);
     cudaFree(c->d_err);
     cudaFree(c->stage);
+    cudaFree(c->d_trace);
     if (c->done) cudaEventDestroy(c->done);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -844,7 +855,29 @@ int seeds_debug_launch_count(const seeds_ctx *c, int64_t *n)
 int seeds_profile_enable(seeds_ctx *c, int32_t enable)
 {
     if (!c) return SEEDS_ERR_INVALID;
+    if (enable && !c->d_trace) {
+        int most = 0;
+        for (auto &h : c->img) most = std::max(most, (int)h.ops.size());
+        c->trace_cap = 1 + 2 * most;
+        int rc = from_cuda(cudaMalloc((void **)&c->d_trace, sizeof(unsigned long long) * c->trace_cap));
+        if (rc) return rc;
+    }
     c->profile = enable != 0;
+    return SEEDS_OK;
+}
+
+int seeds_profile_steps(seeds_ctx *c, int64_t *h_ns, int32_t cap, int32_t *n)
+{
+    if (!c || !n || !c->profiled || c->traced_steps == 0) return SEEDS_ERR_INVALID;
+    const int m = 1 + 2 * c->traced_steps;
+    *n = m;
+    if (!h_ns || cap < m) return SEEDS_OK;
+    int rc = from_cuda(cudaEventSynchronize(c->ev1));
+    if (rc) return rc;
+    std::vector<unsigned long long> t(m);
+    rc = from_cuda(cudaMemcpy(t.data(), c->d_trace, sizeof(unsigned long long) * m, cudaMemcpyDeviceToHost));
+    if (rc) return rc;
+    for (int i = 0; i < m; ++i) h_ns[i] = (int64_t)(t[i] - t[0]);
     return SEEDS_OK;
 }
 

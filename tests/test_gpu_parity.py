@@ -74,6 +74,41 @@ def test_state_matches_after_every_op(torch, binding, job):
     assert moved_total > 0
 
 
+@pytest.mark.parametrize("tuning", [dict(small_block_area=1), dict(small_block_area=16, hist_layout=1)])
+def test_mixed_bin_batch_matches_after_every_op(torch, binding, tuning):
+    """Images with different bin counts (and so different scratch use) in
+    one batch, every block judged by a warp or by a thread: full state of
+    every image after every op."""
+    jobs = [synth.JobSpec(synth.ImageSpec(96, 64, seed=21, cells=8, sigma=12.0), 24, 8, 2, 2),
+            synth.JobSpec(synth.ImageSpec(80, 72, seed=22, cells=9, sigma=14.0), 20, 5, 2, 2),
+            synth.JobSpec(synth.ImageSpec(64, 64, seed=23, cells=6, sigma=10.0), 16, 3, 2, 2)]
+    imgs = [synth.make_image(j.image) for j in jobs]
+    refs = [ref.Ref(j.image.width, j.image.height, j.num_superpixels, 2, j.bins_per_channel, 2) for j in jobs]
+    ctx = binding.SeedsContext([gc.params_for(binding, j) for j in jobs])
+    ctx.set_tuning(**tuning)
+    d = [torch.from_numpy(im).cuda() for im in imgs]
+    nops = ctx.num_ops(0)
+    assert all(ctx.num_ops(i) == nops for i in range(len(jobs)))
+    for op in range(nops - 1):
+        kind, level, phase = ctx.op_info(0, op)
+        ctx.run_ops(d, op, op + 1)
+        ctx.check_status()
+        for i, (j, r, im) in enumerate(zip(jobs, refs, imgs)):
+            if kind == 0:
+                r.init(im)
+                show = 2
+            elif kind == 1:
+                r.run_phase(level, phase)
+                show = level
+            else:
+                show = level - 1
+            nbx, nby, _, _ = r.level_grid(show)
+            lab, hist, sizes, _ = ctx.read_state(i, show, (nby, nbx), r.nbins, j.pixels)
+            assert gc.first_mismatch(lab, r.level_labels(show)) is None, "image %d op %d" % (i, op)
+            h, s = r.hist()
+            assert np.array_equal(hist, h) and np.array_equal(sizes, s), "image %d op %d" % (i, op)
+
+
 # --------------------------------------------------------------------------
 # a single phase from injected (non-grid) states
 # --------------------------------------------------------------------------
