@@ -56,9 +56,11 @@ extern "C" {
 #define SEEDS_ERR_NO_MEMORY (-4)   /* device allocation failed */
 #define SEEDS_ERR_CUDA (-5)        /* a CUDA runtime call failed */
 #define SEEDS_ERR_DEVICE (-6)      /* device-side timeout or bounds trip */
+#define SEEDS_ERR_STATIC_SIZE (-7) /* image too large for seeds_run_static */
 
 #define SEEDS_MAX_LEVELS 12
 #define SEEDS_MAX_BATCH 4096
+#define SEEDS_STATIC_SCRATCH_BYTES (32u << 20) /* device scratch of seeds_run_static */
 
 typedef struct seeds_ctx seeds_ctx;
 
@@ -173,6 +175,41 @@ int seeds_run_host(seeds_ctx *c, const uint8_t *const *h_rgb, const int64_t *h_r
 /* Launch knobs; see seeds_tuning. */
 int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t);
 int seeds_get_tuning(const seeds_ctx *c, seeds_tuning *t);
+
+/* ---- one image without allocating ----------------------------------------
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory themselves or through a library: code
+ * that runs inside a framework which owns the whole device memory through its
+ * own pool and budget, or a latency-critical loop that cannot afford the
+ * device-wide synchronisation and unpredictable time a cudaMalloc/cudaFree
+ * can bring.  It runs the same schedule as seeds_iterate + seeds_labels on
+ * one image and gives the same labels, but keeps every byte of its device
+ * state (bin map, label grids, histograms, move lists, schedule, barrier) in
+ * one file-scope static device array of SEEDS_STATIC_SCRATCH_BYTES (32 MiB)
+ * inside libseeds.so.  Every GPU that loads the library holds that array
+ * until the process exits.  No cudaMalloc, cudaFree, host heap or other
+ * allocating routine is called.
+ *
+ *   p              image parameters, as for seeds_create
+ *   d_rgb          device, H rows of W*3 uint8, row_stride_bytes apart
+ *   d_labels_out   device int32 H x W, written with labels in [0, K_actual)
+ *   d_status       device int32 or NULL; receives the run's device error word
+ *                  (0 = no device-side timeout or bounds trip)
+ *   stream         cudaStream_t as void*; the call is asynchronous on it
+ *
+ * Returns SEEDS_ERR_STATIC_SIZE, without launching anything, when the
+ * image's state does not fit the array (about 4 Mpixel at 5 bins per
+ * channel; a 1920x1080 image with 1000 superpixels needs about 11.5 MiB),
+ * and the usual codes for bad parameters.  The first call on each device
+ * looks up the array's device address (with that device current) and
+ * caches it; make that first call before any stream capture.  All calls
+ * share the one array, which keeps the previous call's contents: each call
+ * re-initialises everything it reads, but calls whose work overlaps on the
+ * GPU (other streams, other host threads) race on it and must be serialised
+ * by the caller. */
+int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int64_t row_stride_bytes, int32_t *d_labels_out,
+                     int32_t *d_status, void *stream);
 
 /* ---- test hooks --------------------------------------------------------- */
 

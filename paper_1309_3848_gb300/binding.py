@@ -22,11 +22,13 @@ SEEDS_ERR_INT64 = -3
 SEEDS_ERR_NO_MEMORY = -4
 SEEDS_ERR_CUDA = -5
 SEEDS_ERR_DEVICE = -6
+SEEDS_ERR_STATIC_SIZE = -7
+SEEDS_STATIC_SCRATCH_BYTES = 32 << 20
 SEEDS_MAX_LEVELS = 12
 SEEDS_MAX_BATCH = 4096
 
 _NAMES = {0: "SEEDS_OK", -1: "SEEDS_ERR_INVALID", -2: "SEEDS_ERR_GEOMETRY", -3: "SEEDS_ERR_INT64",
-          -4: "SEEDS_ERR_NO_MEMORY", -5: "SEEDS_ERR_CUDA", -6: "SEEDS_ERR_DEVICE"}
+          -4: "SEEDS_ERR_NO_MEMORY", -5: "SEEDS_ERR_CUDA", -6: "SEEDS_ERR_DEVICE", -7: "SEEDS_ERR_STATIC_SIZE"}
 
 # every entry point of include/seeds.h
 EXPORTS = [
@@ -36,7 +38,7 @@ EXPORTS = [
     "seeds_batch_labels", "seeds_batch_run", "seeds_run_host", "seeds_set_tuning", "seeds_get_tuning",
     "seeds_debug_num_ops", "seeds_debug_op_info", "seeds_debug_run_ops", "seeds_debug_read_state",
     "seeds_debug_set_labels", "seeds_debug_inject_error", "seeds_debug_launch_count", "seeds_profile_enable",
-    "seeds_profile_last_ms", "seeds_profile_steps",
+    "seeds_profile_last_ms", "seeds_profile_steps", "seeds_run_static",
 ]
 
 
@@ -94,6 +96,7 @@ def _load():
         "seeds_profile_enable": [vp, i32],
         "seeds_profile_last_ms": [vp, P(ctypes.c_float)],
         "seeds_profile_steps": [vp, vp, i32, P(i32)],
+        "seeds_run_static": [P(seeds_params), vp, i64, vp, vp, vp],
     }
     for name in EXPORTS:
         f = getattr(L, name)

@@ -17,7 +17,10 @@
 // out sets the error word and every block leaves the kernel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "seeds_device.cuh"
 
@@ -734,3 +737,262 @@ cudaError_t launch_recount(const DevImage *d_imgs, int img, int level, int64_t n
 }
 
 }  // namespace seeds
+
+// ===========================================================================
+// One image with no allocation at all: every byte of device state lives in a
+// file-scope static device array.  For callers that may not allocate device
+// memory (see seeds_run_static in seeds.h).
+// ===========================================================================
+
+#include <mutex>
+
+namespace seeds {
+
+static __device__ __align__(256) unsigned char g_static_scratch[SEEDS_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned char *g_static_addr[kStaticMaxDevices] = {};
+
+// Host address stand-ins are not device addresses: ask the runtime, once per
+// device, with that device current.
+cudaError_t static_scratch_address(int dev, unsigned char **out)
+{
+    if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = (unsigned char *)p;
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
+size_t sal(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+// everything the setup kernel needs, passed by value
+struct StaticSetup {
+    DevImage img;  // pointers already inside the scratch
+    StepEntry *ent;
+    int32_t *first;
+    int64_t *vt;
+    int32_t *apply;
+    unsigned char *zero_begin;  // barrier, counters, error word
+    int32_t zero_bytes;
+    int32_t maxarea[kMaxLevels + 1];
+    int32_t small_area;
+    DevImage *img_out;
+};
+
+// Lays out one image inside the scratch: the image record, the block edge
+// tables of every level, and the op schedule (one op per step); clears the
+// barrier, the move counters and the error word.
+__global__ void static_setup_kernel(StaticSetup S)
+{
+    const DevImage &im = S.img;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (int l = 1; l <= im.L; ++l) {
+        int32_t *xe = (int32_t *)im.xe[l], *ye = (int32_t *)im.ye[l];
+        for (int i = t; i <= im.nbx[l]; i += nt) xe[i] = (int32_t)((int64_t)i * im.W / im.nbx[l]);
+        for (int i = t; i <= im.nby[l]; i += nt) ye[i] = (int32_t)((int64_t)i * im.H / im.nby[l]);
+    }
+    for (int i = t; i < S.zero_bytes; i += nt) S.zero_begin[i] = 0;
+    if (t != 0) return;
+    *S.img_out = im;
+    int s = 0, ne = 0;
+    auto emit = [&](int kind, int level, int phase, int64_t units, int group) {
+        S.first[s] = ne;
+        const int64_t count = (units * group + 31) / 32 * 32;
+        S.vt[s] = count;
+        S.apply[s] = 0;
+        if (count > 0) {
+            StepEntry e;
+            e.img = 0;
+            e.op = kind;
+            e.level = level;
+            e.phase = phase;
+            e.vt_begin = 0;
+            e.units = (int32_t)units;
+            e.group = group;
+            S.ent[ne++] = e;
+            S.apply[s] = kind == OP_PHASE;
+        }
+        ++s;
+    };
+    auto phase_units = [&](int l, int ph) {
+        return (int64_t)((im.nbx[l] - (ph & 1) + 1) >> 1) * ((im.nby[l] - (ph >> 1) + 1) >> 1);
+    };
+    emit(OP_INIT, 0, 0, im.K, 32);
+    for (int l = im.L; l >= 1; --l) {
+        const int group = S.maxarea[l] > S.small_area ? 32 : 1;
+        for (int it = 0; it < im.iters; ++it)
+            for (int ph = 0; ph < 4; ++ph) emit(OP_PHASE, l, ph, phase_units(l, ph), group);
+        emit(OP_DESCEND, l, 0, l - 1 >= 1 ? (int64_t)im.nbx[l - 1] * im.nby[l - 1] : (int64_t)im.W * im.H, 1);
+    }
+    for (int it = 0; it < im.iters; ++it)
+        for (int ph = 0; ph < 4; ++ph) emit(OP_PHASE, 0, ph, phase_units(0, ph), 1);
+    emit(OP_OUTPUT, 0, 0, (int64_t)im.W * im.H, 1);
+    S.first[s] = ne;
+}
+
+__global__ void static_status_kernel(const int32_t *err, int32_t *status) { *status = *err; }
+
+}  // namespace seeds
+
+using namespace seeds;
+
+extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int64_t row_stride_bytes,
+                                int32_t *d_labels_out, int32_t *d_status, void *stream)
+{
+    // ---- parameters and grid (Sec. 5.1), arithmetic only
+    if (!p || !d_rgb || !d_labels_out) return SEEDS_ERR_INVALID;
+    if (p->width < 1 || p->height < 1 || p->width > 32768 || p->height > 32768) return SEEDS_ERR_INVALID;
+    const int64_t N = (int64_t)p->width * p->height;
+    if (N > 0x7fffffffLL || row_stride_bytes < 3 * (int64_t)p->width) return SEEDS_ERR_INVALID;
+    if (p->num_superpixels < 1 || p->block_levels < 0 || p->block_levels > kMaxLevels) return SEEDS_ERR_INVALID;
+    if (p->bins_per_channel < 1 || p->bins_per_channel > 16) return SEEDS_ERR_INVALID;
+    if (p->iters_per_level < 1 || p->iters_per_level > 1000) return SEEDS_ERR_INVALID;
+    if (p->patch != 0 && p->patch != 3) return SEEDS_ERR_INVALID;
+    if (p->gamma_num < 0 || p->gamma_num > 1024 || p->gamma_den < 1 || p->gamma_den > 1024) return SEEDS_ERR_INVALID;
+    const double Kd = p->num_superpixels, Wd = p->width, Hd = p->height;
+    long long gx = std::llround(std::sqrt(Kd * Wd / Hd));
+    if (gx < 1) gx = 1;
+    long long gy = std::llround(Kd / (double)gx);
+    if (gy < 1) gy = 1;
+    if (gx * gy > 65535) return SEEDS_ERR_INVALID;
+    const int L = p->block_levels;
+    if ((gx << L) > p->width || (gy << L) > p->height) return SEEDS_ERR_GEOMETRY;
+    const int B = p->bins_per_channel, nbins = B * B * B, K = (int)(gx * gy);
+
+    StaticSetup S;
+    std::memset(&S, 0, sizeof(S));
+    DevImage &d = S.img;
+    d.W = p->width;
+    d.H = p->height;
+    d.K = K;
+    d.gx = (int)gx;
+    d.gy = (int)gy;
+    d.L = L;
+    d.iters = p->iters_per_level;
+    d.B = B;
+    d.nbins = nbins;
+    d.patch = p->patch;
+    d.gnum = p->gamma_num;
+    d.gden = p->gamma_den;
+    d.bins16 = nbins > 256;
+    d.hist_jmajor = 0;
+    d.nbx[0] = p->width;
+    d.nby[0] = p->height;
+    int amax = 1;
+    for (int l = 1; l <= L; ++l) {
+        d.nbx[l] = (int)(gx << (L - l + 1));
+        d.nby[l] = (int)(gy << (L - l + 1));
+        const int mw = (p->width + d.nbx[l] - 1) / d.nbx[l], mh = (p->height + d.nby[l] - 1) / d.nby[l];
+        S.maxarea[l] = mw * mh;
+        amax = std::max(amax, mw * mh);
+    }
+    const __int128 N2 = (__int128)N * N, lim = ((__int128)1) << 63;
+    if ((__int128)amax * N2 >= lim || (__int128)(81 * p->gamma_den + 90 * p->gamma_num) * N2 >= lim)
+        return SEEDS_ERR_INT64;
+    S.small_area = 16;
+    const int nops = 1 + (L + 1) * 4 * p->iters_per_level + L + 1;
+    const int moves_cap = (int)(((int64_t)(p->width + 1) / 2) * ((p->height + 1) / 2));
+
+    // ---- layout inside the scratch
+    size_t off = 0;
+    const size_t o_img = off;
+    off = sal(off + sizeof(DevImage));
+    const size_t o_zero = off;  // barrier | 2 counters | error word
+    const size_t o_bar = off, o_cnt = off + 16, o_err = off + 32;
+    off = sal(off + 64);
+    const size_t o_ent = off;
+    off = sal(off + sizeof(StepEntry) * (size_t)nops);
+    const size_t o_first = off;
+    off = sal(off + 4 * (size_t)(nops + 1));
+    const size_t o_vt = off;
+    off = sal(off + 8 * (size_t)nops);
+    const size_t o_apply = off;
+    off = sal(off + 4 * (size_t)nops);
+    size_t o_xe[kMaxLevels + 1] = {}, o_ye[kMaxLevels + 1] = {}, o_lab[kMaxLevels + 1] = {};
+    for (int l = 1; l <= L; ++l) {
+        o_xe[l] = off;
+        off = sal(off + 4 * (size_t)(d.nbx[l] + 1));
+        o_ye[l] = off;
+        off = sal(off + 4 * (size_t)(d.nby[l] + 1));
+    }
+    const size_t o_bins = off;
+    off = sal(off + (size_t)N * (d.bins16 ? 2 : 1));
+    for (int l = 0; l <= L; ++l) {
+        o_lab[l] = off;
+        off = sal(off + 2 * (size_t)d.nbx[l] * d.nby[l]);
+    }
+    const size_t o_hist = off;
+    off = sal(off + 4 * (size_t)K * nbins);
+    const size_t o_size = off;
+    off = sal(off + 4 * (size_t)K);
+    const size_t o_moves = off;
+    off = sal(off + 8 * (size_t)moves_cap);
+    if (off > (size_t)SEEDS_STATIC_SCRATCH_BYTES) return SEEDS_ERR_STATIC_SIZE;
+
+    // ---- the scratch's device address on the current device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SEEDS_ERR_CUDA;
+    unsigned char *base = nullptr;
+    if (static_scratch_address(dev, &base) != cudaSuccess) return SEEDS_ERR_CUDA;
+
+    for (int l = 0; l <= L; ++l) d.lab[l] = (uint16_t *)(base + o_lab[l]);
+    for (int l = 1; l <= L; ++l) {
+        d.xe[l] = (const int32_t *)(base + o_xe[l]);
+        d.ye[l] = (const int32_t *)(base + o_ye[l]);
+    }
+    d.bins = base + o_bins;
+    d.hist = (int32_t *)(base + o_hist);
+    d.size = (int32_t *)(base + o_size);
+    d.moves = (uint32_t *)(base + o_moves);
+    d.moves_cap = moves_cap;
+    d.cnt = (int32_t *)(base + o_cnt);
+    d.rgb = d_rgb;
+    d.stride = row_stride_bytes;
+    d.out = d_labels_out;
+    S.ent = (StepEntry *)(base + o_ent);
+    S.first = (int32_t *)(base + o_first);
+    S.vt = (int64_t *)(base + o_vt);
+    S.apply = (int32_t *)(base + o_apply);
+    S.zero_begin = base + o_zero;
+    S.zero_bytes = 64;
+    S.img_out = (DevImage *)(base + o_img);
+
+    // ---- launch configuration of the persistent kernel (as a context would)
+    const int threads = 256;
+    const size_t smem = (size_t)(threads / 32) * warp_scratch_bytes(nbins);
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SEEDS_ERR_CUDA;
+    if (prepare_persistent(smem) != cudaSuccess) return SEEDS_ERR_CUDA;
+    if (persistent_max_blocks_per_sm(threads, smem, &per_sm) != cudaSuccess || per_sm < 1) return SEEDS_ERR_CUDA;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    static_setup_kernel<<<8, 256, 0, s>>>(S);
+    if (cudaGetLastError() != cudaSuccess) return SEEDS_ERR_CUDA;
+    Schedule sch;
+    sch.ent = S.ent;
+    sch.step_first = S.first;
+    sch.step_vt = S.vt;
+    sch.step_apply = S.apply;
+    sch.nsteps = nops;
+    sch.max_nbins = nbins;
+    sch.trace = nullptr;
+    if (launch_persistent(S.img_out, sch, (GridBarrier *)(base + o_bar), (int32_t *)(base + o_err), per_sm * sms,
+                          threads, smem, s) != cudaSuccess)
+        return SEEDS_ERR_CUDA;
+    if (d_status) {
+        static_status_kernel<<<1, 1, 0, s>>>((const int32_t *)(base + o_err), d_status);
+        if (cudaGetLastError() != cudaSuccess) return SEEDS_ERR_CUDA;
+    }
+    return SEEDS_OK;
+}
