@@ -1,12 +1,18 @@
-// seeds_device.cuh -- device-side data layout of the SEEDS GB300 path.
+// seeds_device.cuh -- device-side data layout and op schedule of the SEEDS
+// GB300 path.
 //
-// One DevImage per image of a context, resident in device memory.  The
-// persistent kernel walks a host-built schedule: a list of steps, each step
-// a list of (image, op) entries whose work is flattened into one range of
-// "virtual threads" (every entry padded to a multiple of 32 so that a warp
-// never straddles two entries).  A step is an evaluate slot, a grid
-// barrier, and -- when the step holds a phase -- an apply slot and another
-// barrier.
+// One DevImage per image, resident in device memory.  The persistent kernel
+// walks a schedule: a list of steps, each step a list of entries whose work
+// is flattened into one range of "virtual threads" (every entry padded to a
+// multiple of 32 so that a warp never straddles two entries), followed by
+// one grid barrier.
+//
+// State is double-buffered.  Op number o of an image reads buffer o&1 of its
+// labels, histograms and sizes, and writes the other buffer: its own accepted
+// moves go there at once, and so do (a "catch-up" entry of the same step) the
+// moves of op o-1, which were applied to buffer o&1 one step earlier.  So
+// after ops [0, e) the complete state is in buffer e&1, decisions of a phase
+// only ever see the state at phase start, and one barrier per step suffices.
 #pragma once
 
 #include <cstdint>
@@ -16,10 +22,11 @@
 namespace seeds {
 
 constexpr int kMaxLevels = SEEDS_MAX_LEVELS;
-constexpr uint16_t kNoLabel = 0xFFFF;  // labels are < 65535
+constexpr uint16_t kNoLabel = 0xFFFF;   // labels are < 65535
+constexpr uint32_t kNoMove = 0xFFFFFFFFu;
 
-// op kinds (same numbering as the debug hooks of seeds.h)
-enum : int32_t { OP_INIT = 0, OP_PHASE = 1, OP_DESCEND = 2, OP_OUTPUT = 3 };
+// op kinds (0..3 as in the debug hooks of seeds.h)
+enum : int32_t { OP_INIT = 0, OP_PHASE = 1, OP_DESCEND = 2, OP_OUTPUT = 3, OP_CATCHUP = 4 };
 
 // device error word bits
 enum : int32_t { DERR_TIMEOUT = 1, DERR_BOUNDS = 2, DERR_INJECTED = 4 };
@@ -29,18 +36,19 @@ struct DevImage {
     int32_t W, H, K, gx, gy, L, iters, B, nbins, patch, gnum, gden;
     int32_t bins16;       // bin map stored as uint16 (B^3 > 256)
     int32_t hist_jmajor;  // hist[j*K + k] instead of hist[k*nbins + j]
+    int32_t hist_sk, hist_sj;  // hist index = k*hist_sk + j*hist_sj (either layout)
+    int32_t small_area;   // blocks up to this many pixels are judged by one thread
     int32_t nbx[kMaxLevels + 1], nby[kMaxLevels + 1];  // level 0 = W, H
-    int32_t group[kMaxLevels + 1];                     // lanes per unit (1 or 32)
+    int32_t maxarea[kMaxLevels + 1];                   // largest block of a level
     const int32_t *xe[kMaxLevels + 1];                 // block column edges, level >= 1
     const int32_t *ye[kMaxLevels + 1];                 // block row edges, level >= 1
     // state
-    void *bins;                      // colour bin per pixel
-    uint16_t *lab[kMaxLevels + 1];   // lab[0]: pixel labels; lab[l]: level-l block grid
-    int32_t *hist;                   // K x nbins counts
-    int32_t *size;                   // |A_k|
-    uint32_t *moves;                 // 2 words per accepted move of the current phase
-    int32_t moves_cap;
-    int32_t *cnt;                    // 2 move counters (step parity)
+    void *bins;                         // colour bin per pixel
+    uint16_t *lab[kMaxLevels + 1][2];   // [0]: pixel labels, [l]: level-l block grid; 2 buffers
+    int32_t *hist[2];                   // K x nbins counts, 2 buffers
+    int32_t *size[2];                   // |A_k|, 2 buffers
+    uint32_t *dec[2];                   // per unit of a phase: (k << 16 | n) or kNoMove
+    int32_t units_cap;                  // entries of each dec buffer
     // per call
     const uint8_t *rgb;
     int64_t stride;
@@ -49,22 +57,24 @@ struct DevImage {
 
 struct StepEntry {
     int32_t img;
-    int32_t op;
-    int32_t level;
+    int32_t op;        // OP_*; OP_CATCHUP replays the moves of op `opidx - 1`
+    int32_t level;     // of the op (for a catch-up: of the previous op)
     int32_t phase;
+    int32_t opidx;     // the image's op number: selects the buffers
+    int32_t units;     // units of work
     int64_t vt_begin;  // first virtual thread of the entry inside its step
-    int32_t units;     // units of work (threads or warps, see group)
     int32_t group;     // 1: one thread per unit, 32: one warp per unit
+    int32_t cphase;    // OP_PHASE: the previous phase of the same level, whose
+                       // moves the same units replay first; -1 for none
 };
 
 struct Schedule {
     const StepEntry *ent;
     const int32_t *step_first;  // nsteps + 1
     const int64_t *step_vt;     // virtual threads of each step
-    const int32_t *step_apply;  // step has a phase entry
     int32_t nsteps;
     int32_t max_nbins;          // largest histogram of the context (scratch size)
-    unsigned long long *trace;  // optional: 1 + 2*nsteps globaltimer stamps
+    unsigned long long *trace;  // optional: 1 + nsteps globaltimer stamps
 };
 
 struct GridBarrier {
@@ -89,10 +99,156 @@ struct IoChunk {
 //   int32[nbins]   histogram (kept all-zero between uses)
 //   uint16[nbins]  the distinct bins seen
 constexpr int kScratchHeader = 4;
-__host__ __device__ inline int warp_scratch_bytes(int nbins)
+__host__ __device__ inline int warp_hist_scratch_bytes(int nbins)
 {
     int b = kScratchHeader * 4 + nbins * 4 + nbins * 2;
     return (b + 15) & ~15;
+}
+
+// The pixel phase works on warp tiles of kTileUX x kTileUY units of one
+// parity class (a unit per lane and tile row); the warp stages the labels of
+// the tile plus a 2-pixel halo in shared memory, behind the histogram scratch.
+constexpr int kTileUX = 32, kTileUY = 4;
+constexpr int kTileW = 2 * kTileUX + 4;  // pixel columns staged
+constexpr int kTileH = 2 * kTileUY + 3;  // pixel rows staged
+// staged labels, the units' bins, the list of the tile's boundary units
+constexpr int kTileBytes = (kTileW * kTileH * 2 + kTileUY * kTileUX * 2 + kTileUY * kTileUX + 15) & ~15;
+// the pixel catch-up replays kCatchupPerLane units per lane
+constexpr int kCatchupPerLane = 4;
+
+__host__ __device__ inline int warp_scratch_bytes(int nbins) { return warp_hist_scratch_bytes(nbins) + kTileBytes; }
+
+// ---------------------------------------------------------------------------
+// the op list of one image (shared by the host scheduler and the device-side
+// setup of the allocation-free entry point)
+// ---------------------------------------------------------------------------
+
+struct OpDesc {
+    int32_t kind, level, phase;
+};
+
+// init, block levels L..1 (iters*4 phases, then a descent), the pixel level
+// (iters*4 phases), output
+__host__ __device__ inline int num_ops(int L, int iters) { return 1 + L * (4 * iters + 1) + 4 * iters + 1; }
+
+__host__ __device__ inline OpDesc op_at(int L, int iters, int o)
+{
+    OpDesc d{OP_OUTPUT, 0, 0};
+    const int per = 4 * iters + 1, P = 1 + L * per;
+    if (o == 0) {
+        d.kind = OP_INIT;
+    } else if (o < P) {
+        const int i = (o - 1) / per, r = (o - 1) % per;
+        d.level = L - i;
+        if (r < 4 * iters) {
+            d.kind = OP_PHASE;
+            d.phase = r & 3;
+        } else {
+            d.kind = OP_DESCEND;
+        }
+    } else if (o < P + 4 * iters) {
+        d.kind = OP_PHASE;
+        d.phase = (o - P) & 3;
+    }
+    return d;
+}
+
+__host__ __device__ inline int64_t phase_units(const DevImage &im, int level, int phase)
+{
+    return (int64_t)((im.nbx[level] - (phase & 1) + 1) >> 1) * ((im.nby[level] - (phase >> 1) + 1) >> 1);
+}
+
+__host__ __device__ inline int level_group(const DevImage &im, int level)
+{
+    return (level > 0 && im.maxarea[level] > im.small_area) ? 32 : 1;
+}
+
+// The unit lattice of a phase on a grid nx x ny: unit (ux,uy) is cell
+// (2ux + px, 2uy + py).  A phase entry that also replays the previous phase
+// (cphase >= 0) walks the union of both lattices, so that one thread or warp
+// handles unit (ux,uy) of both.
+__host__ __device__ inline void lattice(int nx, int ny, int phase, int cphase, int *cols, int *rows)
+{
+    *cols = (nx - (phase & 1) + 1) >> 1;
+    *rows = (ny - (phase >> 1) + 1) >> 1;
+    if (cphase >= 0) {
+        const int c2 = (nx - (cphase & 1) + 1) >> 1, r2 = (ny - (cphase >> 1) + 1) >> 1;
+        *cols = *cols > c2 ? *cols : c2;
+        *rows = *rows > r2 ? *rows : r2;
+    }
+}
+
+// warp tiles of a pixel phase
+__host__ __device__ inline int64_t pixel_tiles(const DevImage &im, int phase, int cphase)
+{
+    int cols, rows;
+    lattice(im.W, im.H, phase, cphase, &cols, &rows);
+    return (int64_t)((cols + kTileUX - 1) / kTileUX) * ((rows + kTileUY - 1) / kTileUY);
+}
+
+// Entries of image `img` for its op `o`.  When the moves of op o-1 (a phase)
+// are pending, a phase of the same level replays them unit by unit before
+// judging its own units (one fused entry); any other op gets a catch-up
+// entry of its own first.  Returns the number of entries written; `vt`
+// advances by their padded thread counts.
+__host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, bool catchup, StepEntry *out,
+                                            int64_t *vt)
+{
+    int n = 0;
+    const OpDesc op = op_at(im.L, im.iters, o);
+    int cphase = -1;
+    if (catchup && o > 0) {
+        const OpDesc pv = op_at(im.L, im.iters, o - 1);
+        if (pv.kind == OP_PHASE && op.kind == OP_PHASE && pv.level == op.level) {
+            cphase = pv.phase;
+        } else if (pv.kind == OP_PHASE) {
+            // large blocks are replayed by a warp each, small blocks by a
+            // thread each, pixels kCatchupPerLane to a thread
+            int64_t units = phase_units(im, pv.level, pv.phase);
+            const int group = level_group(im, pv.level);
+            if (pv.level == 0) units = (units + kCatchupPerLane - 1) / kCatchupPerLane;
+            const int64_t count = (units * group + 31) / 32 * 32;
+            if (count > 0) {
+                StepEntry e{img, OP_CATCHUP, pv.level, pv.phase, o, (int32_t)units, *vt, group, -1};
+                out[n++] = e;
+                *vt += count;
+            }
+        }
+    }
+    int64_t units = 0;
+    int group = 1;
+    switch (op.kind) {
+    case OP_INIT:
+        units = im.K;
+        group = 32;
+        break;
+    case OP_PHASE:
+        if (op.level == 0) {  // warp tiles
+            units = pixel_tiles(im, op.phase, cphase);
+            group = 32;
+        } else {
+            int cols, rows;
+            lattice(im.nbx[op.level], im.nby[op.level], op.phase, cphase, &cols, &rows);
+            units = (int64_t)cols * rows;
+            group = level_group(im, op.level);
+        }
+        break;
+    case OP_DESCEND:
+        // a thread per cell of the finer grid, or per 4 pixels of a row
+        units = op.level - 1 >= 1 ? (int64_t)im.nbx[op.level - 1] * im.nby[op.level - 1]
+                                  : (int64_t)im.H * ((im.W + 3) / 4);
+        break;
+    default:  // OP_OUTPUT: a thread per 4 pixels of a row
+        units = (int64_t)im.H * ((im.W + 3) / 4);
+        break;
+    }
+    const int64_t count = (units * group + 31) / 32 * 32;
+    if (count > 0) {
+        StepEntry e{img, op.kind, op.level, op.phase, o, (int32_t)units, *vt, group, cphase};
+        out[n++] = e;
+        *vt += count;
+    }
+    return n;
 }
 
 // launch helpers (seeds_kernels.cu)

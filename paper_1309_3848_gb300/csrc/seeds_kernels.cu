@@ -6,21 +6,23 @@
 //                  warp-aggregated shared-memory atomics, write the grid
 //                  labels (Sec. 5.1, Eq. 4)
 //   op_*_phase     judge every unit of one parity phase against the state
-//                  at phase start and append accepted moves (Sec. 5.2-5.3:
-//                  Prop. 1 for blocks, Prop. 1 + Prop. 2 for pixels)
-//   apply slot     apply the phase's moves: labels and incremental histogram
-//                  updates (Sec. 5.3, "Updating the Color Distributions")
-//   op_descend     copy block labels to the next finer grid (Sec. 5.1-5.2,
-//                  coarse to fine)
+//                  at phase start (Sec. 5.2-5.3: Prop. 1 for blocks, Prop. 1 +
+//                  Prop. 2 for pixels); accepted moves update the other state
+//                  buffer at once (Sec. 5.3, "Updating the Color
+//                  Distributions")
+//   op_catchup     replay the previous phase's moves into the buffer that
+//                  phase read, so both buffers stay one step apart
+//   op_descend     copy block labels to the next finer grid (coarse to fine)
 //   op_output      int32 labels for the caller
-// Grid barriers between slots spin with a time limit; a barrier that runs
-// out sets the error word and every block leaves the kernel.
+// Every step ends in a grid barrier that spins with a time limit; a barrier
+// that runs out sets the error word and every block leaves the kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "seeds_device.cuh"
 
@@ -57,26 +59,28 @@ __device__ bool grid_sync(GridBarrier *bar, int32_t *err)
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned g = ld_acquire_u32(&bar->gen);
+        const unsigned g = ld_acquire_u32(&bar->gen);
         __threadfence();
-        unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
+        const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
         if (arrived == gridDim.x) {
             atomicExch(&bar->count, 0u);
             __threadfence();
             atomicAdd(&bar->gen, 1u);
         } else {
-            uint64_t t0 = global_ns();
-            while (ld_acquire_u32(&bar->gen) == g) {
-                if (ld_relaxed_i32(err) != 0) {
-                    ok = 0;
-                    break;
+            const uint64_t t0 = global_ns();
+            for (unsigned it = 1; ld_acquire_u32(&bar->gen) == g; ++it) {
+                if ((it & 31u) == 0) {
+                    if (ld_relaxed_i32(err) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    if (global_ns() - t0 > kBarrierTimeoutNs) {
+                        atomicOr(err, DERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(40);
-                if (global_ns() - t0 > kBarrierTimeoutNs) {
-                    atomicOr(err, DERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -90,10 +94,7 @@ __device__ bool grid_sync(GridBarrier *bar, int32_t *err)
 // small helpers
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ int hidx(const DevImage &im, int k, int j)
-{
-    return im.hist_jmajor ? j * im.K + k : k * im.nbins + j;
-}
+__device__ __forceinline__ int hidx(const DevImage &im, int k, int j) { return k * im.hist_sk + j * im.hist_sj; }
 
 __device__ __forceinline__ int bin_at(const DevImage &im, int p)
 {
@@ -109,10 +110,10 @@ __device__ __forceinline__ bool ring_allows_leaving(unsigned m)
 {
     if ((m & 0xAAu) == 0) return false;
     if (m == 0xFFu) return true;
-    unsigned prev = ((m << 1) | (m >> 7)) & 0xFFu;  // bit r = bit r-1 of m
-    unsigned next = ((m >> 1) | (m << 7)) & 0xFFu;  // bit r = bit r+1 of m
-    unsigned starts = m & ~prev;
-    unsigned lone_corners = m & ~prev & ~next & 0x55u;
+    const unsigned prev = ((m << 1) | (m >> 7)) & 0xFFu;  // bit r = bit r-1 of m
+    const unsigned next = ((m >> 1) | (m << 7)) & 0xFFu;  // bit r = bit r+1 of m
+    const unsigned starts = m & ~prev;
+    const unsigned lone_corners = m & ~prev & ~next & 0x55u;
     return __popc(starts) - __popc(lone_corners) == 1;
 }
 
@@ -122,27 +123,31 @@ __device__ __forceinline__ int cell(const uint16_t *lab, int nx, int ny, int x, 
     return (x < 0 || y < 0 || x >= nx || y >= ny) ? (int)kNoLabel : (int)lab[y * nx + x];
 }
 
-// Shared unit logic: boundary test, ring validity, sorted distinct
+// Shared unit logic over a fetch function for the 8-ring (cells outside the
+// grid read kNoLabel): boundary test, ring validity, sorted distinct
 // candidates.  Returns the candidate count (0 = no move possible).
-__device__ __forceinline__ int unit_candidates(const uint16_t *lab, int nx, int ny, int x, int y, int k, int cand[4])
+template <class Fetch>
+__device__ __forceinline__ int candidates_from(Fetch at, int k, int cand[4])
 {
-    const int lf = cell(lab, nx, ny, x - 1, y), rt = cell(lab, nx, ny, x + 1, y);
-    const int up = cell(lab, nx, ny, x, y - 1), dn = cell(lab, nx, ny, x, y + 1);
+    const int lf = at(-1, 0), rt = at(1, 0);
+    const int up = at(0, -1), dn = at(0, 1);
     const bool boundary = (lf != k && lf != kNoLabel) || (rt != k && rt != kNoLabel) ||
                           (up != k && up != kNoLabel) || (dn != k && dn != kNoLabel);
     if (!boundary) return 0;
     unsigned m = 0;
-    m |= (cell(lab, nx, ny, x - 1, y - 1) == k) << 0;
+    m |= (at(-1, -1) == k) << 0;
     m |= (up == k) << 1;
-    m |= (cell(lab, nx, ny, x + 1, y - 1) == k) << 2;
+    m |= (at(1, -1) == k) << 2;
     m |= (rt == k) << 3;
-    m |= (cell(lab, nx, ny, x + 1, y + 1) == k) << 4;
+    m |= (at(1, 1) == k) << 4;
     m |= (dn == k) << 5;
-    m |= (cell(lab, nx, ny, x - 1, y + 1) == k) << 6;
+    m |= (at(-1, 1) == k) << 6;
     m |= (lf == k) << 7;
     if (!ring_allows_leaving(m)) return 0;
-    // sort the four neighbour labels (kNoLabel sorts last), then keep the
-    // distinct ones other than k
+    // sort the four neighbour labels (kNoLabel sorts last); equal labels are
+    // then adjacent.  The candidates keep fixed slots in ascending order, a
+    // slot holding kNoLabel when its label is k, a repeat or no label, so all
+    // later loops index them with constants.
     int a = lf, b = rt, c = up, d = dn, t;
 #define SEEDS_CSWAP(p, q) \
     if (p > q) {          \
@@ -152,47 +157,94 @@ __device__ __forceinline__ int unit_candidates(const uint16_t *lab, int nx, int 
     }
     SEEDS_CSWAP(a, b) SEEDS_CSWAP(c, d) SEEDS_CSWAP(a, c) SEEDS_CSWAP(b, d) SEEDS_CSWAP(b, c)
 #undef SEEDS_CSWAP
-    int nc = 0, last = -1;
-    const int v[4] = {a, b, c, d};
+    cand[0] = (a != k) ? a : (int)kNoLabel;
+    cand[1] = (b != k && b != a) ? b : (int)kNoLabel;
+    cand[2] = (c != k && c != b) ? c : (int)kNoLabel;
+    cand[3] = (d != k && d != c) ? d : (int)kNoLabel;
+    return (cand[0] != kNoLabel) + (cand[1] != kNoLabel) + (cand[2] != kNoLabel) + (cand[3] != kNoLabel);
+}
+
+__device__ __forceinline__ int unit_candidates(const uint16_t *lab, int nx, int ny, int x, int y, int k, int cand[4])
+{
+    return candidates_from([&](int dx, int dy) { return cell(lab, nx, ny, x + dx, y + dy); }, k, cand);
+}
+
+// position of unit u of a parity phase on a grid nx wide
+__device__ __forceinline__ void unit_pos(int u, int phase, int nx, int *x, int *y)
+{
+    const int px = phase & 1, py = phase >> 1;
+    const int ncols = (nx - px + 1) >> 1;
+    const int uy = u / ncols, ux = u - uy * ncols;
+    *x = 2 * ux + px;
+    *y = 2 * uy + py;
+}
+
+__device__ __forceinline__ void move_counts(const DevImage &im, int buf, int k, int n, int j, int cnt)
+{
+    atomicSub(&im.hist[buf][hidx(im, k, j)], cnt);
+    atomicAdd(&im.hist[buf][hidx(im, n, j)], cnt);
+}
+
+__device__ __forceinline__ void move_size(const DevImage &im, int buf, int k, int n, int cnt)
+{
+    atomicSub(&im.size[buf][k], cnt);
+    atomicAdd(&im.size[buf][n], cnt);
+}
+
+// Sparse colour histogram of block (bx,by) of a level in the warp's shared
+// scratch: counts in hsh[j], distinct bins listed in lst[0..nd).  Whole warp;
+// returns nd.  Loads of four rounds are issued before any is used.
+__device__ int block_sparse_hist(const DevImage &im, int level, int bx, int by, int lane, int32_t *wsh, int max_nbins,
+                                 int *m_out)
+{
+    int32_t *ndist = wsh;
+    int32_t *hsh = wsh + kScratchHeader;
+    // the list lives past the largest histogram of the context, so that it
+    // never overlaps histogram entries another image's blocks rely on being 0
+    uint16_t *lst = (uint16_t *)(hsh + max_nbins);
+    const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
+    const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
+    const int bw = x1 - x0, m = bw * (y1 - y0);
+    for (int base = 0; base < m; base += 128) {
+        int j[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-        if (v[i] != kNoLabel && v[i] != k && v[i] != last) {
-            cand[nc++] = v[i];
-            last = v[i];
+        for (int q = 0; q < 4; ++q) {
+            const int t = base + 32 * q + lane;
+            j[q] = -1;
+            if (t < m) {
+                const int dy = t / bw;
+                j[q] = bin_at(im, (y0 + dy) * im.W + x0 + (t - dy * bw));
+            }
         }
-    return nc;
-}
-
-// append one move per lane that has one (whole warp calls this)
-__device__ __forceinline__ void append_moves_warp(const DevImage &im, int s, bool has, uint32_t w0, uint32_t w1,
-                                                  int lane, int32_t *err)
-{
-    unsigned ballot = __ballot_sync(0xffffffffu, has);
-    if (!ballot) return;
-    int leader = __ffs(ballot) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(&im.cnt[s & 1], __popc(ballot));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (has) {
-        int idx = base + __popc(ballot & ((1u << lane) - 1u));
-        if (idx < im.moves_cap) {
-            im.moves[2 * idx] = w0;
-            im.moves[2 * idx + 1] = w1;
-        } else {
-            atomicOr(err, DERR_BOUNDS);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const unsigned peers = __match_any_sync(0xffffffffu, j[q]);
+            if (j[q] >= 0 && lane == __ffs(peers) - 1) {
+                const int old = atomicAdd(&hsh[j[q]], __popc(peers));
+                if (old == 0) lst[atomicAdd(ndist, 1)] = (uint16_t)j[q];
+            }
         }
     }
+    __syncwarp();
+    *m_out = m;
+    return *(volatile int32_t *)ndist;
 }
 
-__device__ __forceinline__ void append_move_single(const DevImage &im, int s, uint32_t w0, uint32_t w1, int32_t *err)
+// after block_sparse_hist: apply (if k >= 0) the block's counts as a move
+// k -> n to buffer `buf`, and clear the scratch for the next use
+__device__ void block_sparse_apply_clear(const DevImage &im, int buf, int k, int n, int nd, int lane, int32_t *wsh,
+                                         int max_nbins)
 {
-    int idx = atomicAdd(&im.cnt[s & 1], 1);
-    if (idx < im.moves_cap) {
-        im.moves[2 * idx] = w0;
-        im.moves[2 * idx + 1] = w1;
-    } else {
-        atomicOr(err, DERR_BOUNDS);
+    int32_t *hsh = wsh + kScratchHeader;
+    const uint16_t *lst = (const uint16_t *)(hsh + max_nbins);
+    for (int t = lane; t < nd; t += 32) {
+        const int j = lst[t];
+        if (k >= 0) move_counts(im, buf, k, n, j, hsh[j]);
+        hsh[j] = 0;
     }
+    __syncwarp();
+    if (lane == 0) wsh[0] = 0;
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -202,121 +254,229 @@ __device__ __forceinline__ void append_move_single(const DevImage &im, int s, ui
 __device__ void op_init(const DevImage &im, int k, int lane, int32_t *wsh)
 {
     if (k >= im.K) return;
+    int32_t *hsh = wsh + kScratchHeader;
     const int sx = k % im.gx, sy = k / im.gx;
     const int x0 = (int)((int64_t)sx * im.W / im.gx), x1 = (int)((int64_t)(sx + 1) * im.W / im.gx);
     const int y0 = (int)((int64_t)sy * im.H / im.gy), y1 = (int)((int64_t)(sy + 1) * im.H / im.gy);
-    const int rw = x1 - x0, area = rw * (y1 - y0);
+    const int area = (x1 - x0) * (y1 - y0);
     const int B = im.B;
-    for (int base = 0; base < area; base += 32) {
-        const int t = base + lane;
-        const bool act = t < area;
-        int j = -1;
-        if (act) {
-            const int dy = t / rw, x = x0 + (t - dy * rw), y = y0 + dy;
-            const uint8_t *px = im.rgb + (int64_t)y * im.stride + 3 * (int64_t)x;
-            const int r = px[0], g = px[1], b = px[2];
-            j = ((r * B) >> 8) * B * B + ((g * B) >> 8) * B + ((b * B) >> 8);
-            const int p = y * im.W + x;
-            if (im.bins16)
-                ((uint16_t *)im.bins)[p] = (uint16_t)j;
-            else
-                ((uint8_t *)im.bins)[p] = (uint8_t)j;
-            if (im.L == 0) im.lab[0][p] = (uint16_t)k;
+    // rounds of 8 rows x 32 columns: lanes walk a row, rows are unrolled
+    for (int yb = y0; yb < y1; yb += 8)
+        for (int xb = x0; xb < x1; xb += 32) {
+        int j[8], p[8];
+        const int x = xb + lane;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int y = yb + q;
+            j[q] = -1;
+            p[q] = 0;
+            if (y < y1 && x < x1) {
+                const uint8_t *px = im.rgb + (int64_t)y * im.stride + 3 * (int64_t)x;
+                const int r = px[0], g = px[1], b = px[2];
+                j[q] = ((r * B) >> 8) * B * B + ((g * B) >> 8) * B + ((b * B) >> 8);
+                p[q] = y * im.W + x;
+            }
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, j);
-        if (act && lane == __ffs(peers) - 1) atomicAdd(&wsh[j], __popc(peers));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (j[q] >= 0) {
+                if (im.bins16)
+                    ((uint16_t *)im.bins)[p[q]] = (uint16_t)j[q];
+                else
+                    ((uint8_t *)im.bins)[p[q]] = (uint8_t)j[q];
+                if (im.L == 0) im.lab[0][0][p[q]] = im.lab[0][1][p[q]] = (uint16_t)k;
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, j[q]);
+            if (j[q] >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hsh[j[q]], __popc(peers));
+        }
     }
     __syncwarp();
     for (int j = lane; j < im.nbins; j += 32) {
-        im.hist[hidx(im, k, j)] = wsh[j];
-        wsh[j] = 0;
+        const int v = hsh[j];
+        im.hist[0][hidx(im, k, j)] = v;
+        im.hist[1][hidx(im, k, j)] = v;
+        hsh[j] = 0;
     }
     __syncwarp();
-    if (lane == 0) im.size[k] = area;
+    if (lane == 0) im.size[0][k] = im.size[1][k] = area;
     if (im.L >= 1 && lane < 4) {
         const int L = im.L;
         const int bx = 2 * sx + (lane & 1), by = 2 * sy + (lane >> 1);
-        im.lab[L][by * im.nbx[L] + bx] = (uint16_t)k;
+        im.lab[L][0][by * im.nbx[L] + bx] = im.lab[L][1][by * im.nbx[L] + bx] = (uint16_t)k;
     }
 }
 
 // ---------------------------------------------------------------------------
-// pixel phase: one thread per pixel of the parity class
+// pixel phase: warp tiles
 // ---------------------------------------------------------------------------
 
-__device__ void op_pixel_phase(const DevImage &im, int phase, int units, int s, int u, int lane, int32_t *err)
+// Replay one move k -> n of pixel p into buffer `buf`.
+__device__ __forceinline__ void replay_pixel(const DevImage &im, int buf, int p, uint32_t d)
 {
-    bool has = false;
-    uint32_t w0 = 0, w1 = 0;
-    if (u < units) {
-        const int px = phase & 1, py = phase >> 1;
-        const int W = im.W, H = im.H;
-        const int ncols = (W - px + 1) >> 1;
-        const int uy = u / ncols, ux = u - uy * ncols;
-        const int x = 2 * ux + px, y = 2 * uy + py;
-        const uint16_t *lab = im.lab[0];
-        const int p = y * W + x;
-        const int k = lab[p];
-        int cand[4];
-        const int nc = unit_candidates(lab, W, H, x, y, k, cand);
-        if (nc > 0) {
-            const int j = bin_at(im, p);
-            // Prop. 2 sums G_x = sum_{i in K_p} b_{N_i}(x) as a weighted count
-            // over the 5x5 window: w(p,q) = #{i in image: |i-p|,|i-q| <= 1}
-            int Gk = 0, Gc[4] = {0, 0, 0, 0}, Kp = 0;
-            if (im.patch != 0 && im.gnum != 0) {
-                int wx[5], wy[5];
+    const int k = (int)(d >> 16), n = (int)(d & 0xFFFFu);
+    im.lab[0][buf][p] = (uint16_t)n;
+    move_counts(im, buf, k, n, bin_at(im, p), 1);
+    move_size(im, buf, k, n, 1);
+}
+
+// One warp-tile of a pixel phase: units (ux, uy) with ux in a 32-wide column
+// range (one per lane) and uy in a kTileUY-row range.  The warp first
+// replays the moves of the previous phase (cphase >= 0) for the same unit
+// range, then judges its own units.  The labels of the tile and a 2-pixel
+// halo are staged in shared memory (kNoLabel outside the image) with
+// independent coalesced loads, with the units' colour bins; a cheap pass
+// finds the units that sit on a boundary and may leave, and the warp judges
+// only those, compacted so that every lane works.
+__device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, int tiles, int tile, int lane,
+                              uint16_t *tsh)
+{
+    if (tile >= tiles) return;
+    const int b = o & 1, nb = b ^ 1;
+    const int W = im.W, H = im.H;
+    const int px = phase & 1, py = phase >> 1;
+    const int ncols = (W - px + 1) >> 1, nrows = (H - py + 1) >> 1;
+    int mcols, mrows;
+    lattice(W, H, phase, cphase, &mcols, &mrows);
+    const int tiles_x = (mcols + kTileUX - 1) / kTileUX;
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const int ux = tx * kTileUX + lane, uy0 = ty * kTileUY;
+
+    // the previous phase's decisions for the same units (loads issued first)
+    uint32_t cd[kTileUY];
+    int ccols = 0, crows = 0, cpx = 0, cpy = 0;
+    if (cphase >= 0) {
+        cpx = cphase & 1;
+        cpy = cphase >> 1;
+        ccols = (W - cpx + 1) >> 1;
+        crows = (H - cpy + 1) >> 1;
+    }
 #pragma unroll
-                for (int d = 0; d < 5; ++d) {
-                    const int qx = x + d - 2, qy = y + d - 2;
-                    const int lox = max(max(x, qx) - 1, 0), hix = min(min(x, qx) + 1, W - 1);
-                    const int loy = max(max(y, qy) - 1, 0), hiy = min(min(y, qy) + 1, H - 1);
-                    wx[d] = (qx < 0 || qx >= W) ? 0 : max(0, hix - lox + 1);
-                    wy[d] = (qy < 0 || qy >= H) ? 0 : max(0, hiy - loy + 1);
-                }
-                Kp = wx[2] * wy[2];
+    for (int r = 0; r < kTileUY; ++r) {
+        const int uy = uy0 + r;
+        cd[r] = (ux < ccols && uy < crows) ? im.dec[nb][uy * ccols + ux] : kNoMove;
+    }
+
+    // stage the labels of buffer b and the units' bins
+    const int X0 = 2 * tx * kTileUX + px - 2, Y0 = 2 * uy0 + py - 2;
+    const uint16_t *lab = im.lab[0][b];
 #pragma unroll
-                for (int dy = 0; dy < 5; ++dy) {
-                    if (wy[dy] == 0) continue;
-                    const uint16_t *row = lab + (y + dy - 2) * W + (x - 2);
+    for (int r = 0; r < kTileH; ++r) {
+        const int yy = Y0 + r;
+        const bool rowin = yy >= 0 && yy < H;
 #pragma unroll
-                    for (int dx = 0; dx < 5; ++dx) {
-                        const int w = wx[dx] * wy[dy];
-                        if (w == 0) continue;
-                        const int l = row[dx];
-                        if (l == k) Gk += w;
-#pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            if (c < nc && l == cand[c]) Gc[c] += w;
-                    }
-                }
-            }
-            const int64_t gd81 = 81ll * im.gden, gn = im.gnum;
-            int best = cand[0];
-            int64_t a_b = im.hist[hidx(im, best, j)], s_b = im.size[best];
-            int G_b = Gc[0];
-            for (int c = 1; c < nc; ++c) {
-                const int n = cand[c];
-                const int64_t a = im.hist[hidx(im, n, j)], sz = im.size[n];
-                const int64_t diff = gd81 * (a * s_b - a_b * sz) + gn * (int64_t)(Gc[c] - G_b) * sz * s_b;
-                if (diff > 0) {
-                    best = n;
-                    a_b = a;
-                    s_b = sz;
-                    G_b = Gc[c];
-                }
-            }
-            const int64_t a_k = im.hist[hidx(im, k, j)], s_k = im.size[k];
-            const int64_t gain =
-                gd81 * (a_b * (s_k - 1) - (a_k - 1) * s_b) + gn * (int64_t)(G_b + Kp - Gk) * s_b * (s_k - 1);
-            if (gain > 0) {
-                has = true;
-                w0 = (uint32_t)p;
-                w1 = ((uint32_t)k << 16) | (uint32_t)best;
-            }
+        for (int c = lane; c < kTileW; c += 32) {
+            const int xx = X0 + c;
+            tsh[r * kTileW + c] = (rowin && xx >= 0 && xx < W) ? lab[yy * W + xx] : kNoLabel;
         }
     }
-    append_moves_warp(im, s, has, w0, w1, lane, err);
+    uint16_t *jsh = tsh + kTileW * kTileH;
+    uint8_t *lst = (uint8_t *)(jsh + kTileUY * kTileUX);
+#pragma unroll
+    for (int r = 0; r < kTileUY; ++r) {
+        const int uy = uy0 + r;
+        jsh[r * 32 + lane] = (ux < ncols && uy < nrows) ? bin_at(im, (2 * uy + py) * W + 2 * ux + px) : 0;
+    }
+
+    // replay the previous phase's moves into buffer nb
+#pragma unroll
+    for (int r = 0; r < kTileUY; ++r)
+        if (cd[r] != kNoMove) replay_pixel(im, nb, (2 * (uy0 + r) + cpy) * W + 2 * ux + cpx, cd[r]);
+    __syncwarp();
+
+    // pass 1: boundary units that may leave; the others decide "stay" here
+    unsigned mine = 0;
+#pragma unroll
+    for (int r = 0; r < kTileUY; ++r) {
+        const int uy = uy0 + r;
+        if (ux < ncols && uy < nrows) {
+            const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * lane + 2);
+            int cand[4];
+            if (candidates_from([&](int dx, int dy) { return (int)T[dy * kTileW + dx]; }, (int)T[0], cand) > 0)
+                mine |= 1u << r;
+            else
+                im.dec[b][uy * ncols + ux] = kNoMove;
+        }
+    }
+    int nbd = 0;
+#pragma unroll
+    for (int r = 0; r < kTileUY; ++r) {
+        const unsigned bal = __ballot_sync(0xffffffffu, (mine >> r) & 1u);
+        if ((mine >> r) & 1u) lst[nbd + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(r * 32 + lane);
+        nbd += __popc(bal);
+    }
+    __syncwarp();
+
+    // pass 2: judge the boundary units, every lane busy
+    const int32_t *hist = im.hist[b], *size = im.size[b];
+    const int64_t gd81 = 81ll * im.gden, gn = im.gnum;
+    const bool use_g = im.patch != 0 && im.gnum != 0;
+    for (int i = lane; i < nbd; i += 32) {
+        const int e = lst[i], r = e >> 5, l = e & 31;
+        const int uxe = tx * kTileUX + l, uy = uy0 + r;
+        const int x = 2 * uxe + px, y = 2 * uy + py, p = y * W + x;
+        const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * l + 2);  // the unit's cell in the tile
+        const int k = T[0];
+        int cand[4];
+        candidates_from([&](int dx, int dy) { return (int)T[dy * kTileW + dx]; }, k, cand);
+        const int j = jsh[r * 32 + l];
+        // Prop. 2 sums G_x = sum_{i in K_p} b_{N_i}(x) as a weighted count
+        // over the 5x5 window: w(p,q) = #{i in image: |i-p|,|i-q| <= 1}
+        int Gk = 0, Gc[4] = {0, 0, 0, 0}, Kp = 0;
+        if (use_g) {
+            int wx[5], wy[5];
+#pragma unroll
+            for (int d = 0; d < 5; ++d) {
+                const int qx = x + d - 2, qy = y + d - 2;
+                const int lox = max(max(x, qx) - 1, 0), hix = min(min(x, qx) + 1, W - 1);
+                const int loy = max(max(y, qy) - 1, 0), hiy = min(min(y, qy) + 1, H - 1);
+                wx[d] = (qx < 0 || qx >= W) ? 0 : max(0, hix - lox + 1);
+                wy[d] = (qy < 0 || qy >= H) ? 0 : max(0, hiy - loy + 1);
+            }
+            Kp = wx[2] * wy[2];
+#pragma unroll
+            for (int dy = 0; dy < 5; ++dy) {
+                const uint16_t *row = T + (dy - 2) * kTileW - 2;
+#pragma unroll
+                for (int dx = 0; dx < 5; ++dx) {
+                    const int w = wx[dx] * wy[dy];
+                    const int lq = row[dx];
+                    if (lq == k) Gk += w;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (lq == cand[c]) Gc[c] += w;  // empty slots only meet w = 0 cells
+                }
+            }
+        }
+        // candidates in ascending label order; a later one wins only if
+        // strictly better, so ties go to the smallest label
+        int best = kNoLabel;
+        int64_t a_b = 0, s_b = 1;
+        int G_b = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int n = cand[c];
+            if (n == kNoLabel) continue;
+            const int64_t a = hist[hidx(im, n, j)], sz = size[n];
+            if (best == kNoLabel || gd81 * (a * s_b - a_b * sz) + gn * (int64_t)(Gc[c] - G_b) * sz * s_b > 0) {
+                best = n;
+                a_b = a;
+                s_b = sz;
+                G_b = Gc[c];
+            }
+        }
+        const int64_t a_k = hist[hidx(im, k, j)], s_k = size[k];
+        const int64_t gain =
+            gd81 * (a_b * (s_k - 1) - (a_k - 1) * s_b) + gn * (int64_t)(G_b + Kp - Gk) * s_b * (s_k - 1);
+        uint32_t dec = kNoMove;
+        if (gain > 0) {
+            dec = ((uint32_t)k << 16) | (uint32_t)best;
+            im.lab[0][nb][p] = (uint16_t)best;
+            move_counts(im, nb, k, best, j, 1);
+            move_size(im, nb, k, best, 1);
+        }
+        im.dec[b][uy * ncols + uxe] = dec;
+    }
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -325,69 +485,109 @@ __device__ void op_pixel_phase(const DevImage &im, int phase, int units, int s, 
 
 constexpr int kSmallMax = 16;
 
-__device__ void op_block_phase_thread(const DevImage &im, int level, int phase, int units, int s, int u, int lane,
-                                      int32_t *err)
+// Replay a small block's move into buffer `buf` (one thread).
+__device__ void replay_small_block(const DevImage &im, int buf, int level, int bx, int by, uint32_t d)
 {
-    bool has = false;
-    uint32_t w0 = 0, w1 = 0;
-    if (u < units) {
-        const int px = phase & 1, py = phase >> 1;
-        const int nx = im.nbx[level], ny = im.nby[level];
-        const int ncols = (nx - px + 1) >> 1;
-        const int uy = u / ncols, ux = u - uy * ncols;
-        const int bx = 2 * ux + px, by = 2 * uy + py;
-        const uint16_t *lab = im.lab[level];
-        const int k = lab[by * nx + bx];
-        int cand[4];
-        const int nc = unit_candidates(lab, nx, ny, bx, by, k, cand);
-        if (nc > 0) {
-            const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
-            const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
-            const int bw = x1 - x0, m = bw * (y1 - y0);
-            int jj[kSmallMax];
+    const int k = (int)(d >> 16), n = (int)(d & 0xFFFFu);
+    const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
+    const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
+    for (int yy = y0; yy < y1; ++yy)
+        for (int xx = x0; xx < x1; ++xx) move_counts(im, buf, k, n, bin_at(im, yy * im.W + xx), 1);
+    move_size(im, buf, k, n, (x1 - x0) * (y1 - y0));
+    im.lab[level][buf][by * im.nbx[level] + bx] = (uint16_t)n;
+}
+
+// Judge small block (bx,by); SM bounds its pixel count, so the dedupe of its
+// bins unrolls to SM*SM compares.
+template <int SM>
+__device__ uint32_t judge_small_block(const DevImage &im, int b, int nb, int level, int bx, int by)
+{
+    const int nx = im.nbx[level], ny = im.nby[level];
+    const uint16_t *lab = im.lab[level][b];
+    const int k = lab[by * nx + bx];
+    int cand[4];
+    if (unit_candidates(lab, nx, ny, bx, by, k, cand) == 0) return kNoMove;
+    const int32_t *hist = im.hist[b], *size = im.size[b];
+    const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
+    const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
+    const int bw = x1 - x0, m = bw * (y1 - y0);
+    int jj[SM];
 #pragma unroll
-            for (int t = 0; t < kSmallMax; ++t) {
-                jj[t] = -1;
-                if (t < m) {
-                    const int dy = t / bw;
-                    jj[t] = bin_at(im, (y0 + dy) * im.W + x0 + (t - dy * bw));
-                }
-            }
-            int64_t S[4] = {0, 0, 0, 0}, S_st = 0;
-            int64_t sz[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) sz[c] = c < nc ? im.size[cand[c]] : 1;
-            const int64_t s_k = im.size[k], s_rest = s_k - m;
-            // S(A, L) = sum over the distinct bins j of L of min(A[j]*|L|, L_j*|A|)
-#pragma unroll
-            for (int t = 0; t < kSmallMax; ++t) {
-                if (t >= m) break;
-                const int j = jj[t];
-                bool first = true;
-                int Lj = 0;
-#pragma unroll
-                for (int q = 0; q < kSmallMax; ++q) {
-                    if (q < t && jj[q] == j) first = false;
-                    if (q >= t && jj[q] == j) ++Lj;
-                }
-                if (!first) continue;
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (c < nc) S[c] += min((int64_t)im.hist[hidx(im, cand[c], j)] * m, (int64_t)Lj * sz[c]);
-                S_st += min((int64_t)(im.hist[hidx(im, k, j)] - Lj) * m, (int64_t)Lj * s_rest);
-            }
-            int bi = 0;
-#pragma unroll
-            for (int c = 1; c < 4; ++c)
-                if (c < nc && S[c] * sz[bi] > S[bi] * sz[c]) bi = c;
-            if (S[bi] * s_rest > S_st * sz[bi]) {
-                has = true;
-                w0 = (uint32_t)(by * nx + bx);
-                w1 = ((uint32_t)k << 16) | (uint32_t)cand[bi];
-            }
+    for (int t = 0; t < SM; ++t) {
+        jj[t] = -1;
+        if (t < m) {
+            const int dy = t / bw;
+            jj[t] = bin_at(im, (y0 + dy) * im.W + x0 + (t - dy * bw));
         }
     }
-    append_moves_warp(im, s, has, w0, w1, lane, err);
+    int64_t S[4] = {0, 0, 0, 0}, S_st = 0;
+    int64_t sz[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sz[c] = cand[c] != kNoLabel ? size[cand[c]] : 1;
+    const int64_t s_k = size[k], s_rest = s_k - m;
+    // S(A, L) = sum over the distinct bins j of L of min(A[j]*|L|, L_j*|A|)
+#pragma unroll
+    for (int t = 0; t < SM; ++t) {
+        if (t >= m) break;
+        const int j = jj[t];
+        bool first = true;
+        int Lj = 0;
+#pragma unroll
+        for (int q = 0; q < SM; ++q) {
+            if (q < t && jj[q] == j) first = false;
+            if (q >= t && jj[q] == j) ++Lj;
+        }
+        if (!first) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (cand[c] != kNoLabel) S[c] += min((int64_t)hist[hidx(im, cand[c], j)] * m, (int64_t)Lj * sz[c]);
+        S_st += min((int64_t)(hist[hidx(im, k, j)] - Lj) * m, (int64_t)Lj * s_rest);
+    }
+    // ascending candidates, strictly better replaces: ties to the smallest label
+    int n = kNoLabel;
+    int64_t Sb = 0, zb = 1;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (cand[c] != kNoLabel && (n == kNoLabel || S[c] * zb > Sb * sz[c])) {
+            n = cand[c];
+            Sb = S[c];
+            zb = sz[c];
+        }
+    if (!(Sb * s_rest > S_st * zb)) return kNoMove;
+    im.lab[level][nb][by * nx + bx] = (uint16_t)n;
+#pragma unroll
+    for (int t = 0; t < SM; ++t)
+        if (t < m) move_counts(im, nb, k, n, jj[t], 1);
+    move_size(im, nb, k, n, m);
+    return ((uint32_t)k << 16) | (uint32_t)n;
+}
+
+// Unit (ux,uy) of the union lattice: replay the previous phase's move of that
+// unit (cphase >= 0), then judge this phase's unit.
+__device__ void op_block_phase_thread(const DevImage &im, int o, int level, int phase, int cphase, int units, int u)
+{
+    if (u >= units) return;
+    const int b = o & 1, nb = b ^ 1;
+    const int nx = im.nbx[level], ny = im.nby[level];
+    int mcols, mrows, ncols, nrows;
+    lattice(nx, ny, phase, cphase, &mcols, &mrows);
+    lattice(nx, ny, phase, -1, &ncols, &nrows);
+    const int uy = u / mcols, ux = u - uy * mcols;
+    if (cphase >= 0) {
+        int ccols, crows;
+        lattice(nx, ny, cphase, -1, &ccols, &crows);
+        if (ux < ccols && uy < crows) {
+            const uint32_t d = im.dec[nb][uy * ccols + ux];
+            if (d != kNoMove) replay_small_block(im, nb, level, 2 * ux + (cphase & 1), 2 * uy + (cphase >> 1), d);
+        }
+    }
+    if (ux >= ncols || uy >= nrows) return;
+    const int bx = 2 * ux + (phase & 1), by = 2 * uy + (phase >> 1);
+    const int ma = im.maxarea[level];
+    const uint32_t dec = ma <= 4   ? judge_small_block<4>(im, b, nb, level, bx, by)
+                         : ma <= 9 ? judge_small_block<9>(im, b, nb, level, bx, by)
+                                   : judge_small_block<kSmallMax>(im, b, nb, level, bx, by);
+    im.dec[b][uy * ncols + ux] = dec;
 }
 
 // ---------------------------------------------------------------------------
@@ -401,173 +601,202 @@ __device__ __forceinline__ int64_t warp_sum64(int64_t v)
     return v;
 }
 
-__device__ void op_block_phase_warp(const DevImage &im, int level, int phase, int units, int s, int u, int lane,
-                                    int32_t *wsh, int max_nbins, int32_t *err)
+// Replay a large block's move into buffer `buf` (whole warp).
+__device__ void replay_large_block(const DevImage &im, int buf, int level, int bx, int by, uint32_t d, int lane,
+                                   int32_t *wsh, int max_nbins)
+{
+    const int k = (int)(d >> 16), n = (int)(d & 0xFFFFu);
+    int m;
+    const int nd = block_sparse_hist(im, level, bx, by, lane, wsh, max_nbins, &m);
+    block_sparse_apply_clear(im, buf, k, n, nd, lane, wsh, max_nbins);
+    if (lane == 0) {
+        im.lab[level][buf][by * im.nbx[level] + bx] = (uint16_t)n;
+        move_size(im, buf, k, n, m);
+    }
+}
+
+// Unit (ux,uy) of the union lattice, one warp: replay the previous phase's
+// move of that unit (cphase >= 0), then judge this phase's unit.
+__device__ void op_block_phase_warp(const DevImage &im, int o, int level, int phase, int cphase, int units, int u,
+                                    int lane, int32_t *wsh, int max_nbins)
 {
     if (u >= units) return;
-    const int px = phase & 1, py = phase >> 1;
+    const int b = o & 1, nb = b ^ 1;
     const int nx = im.nbx[level], ny = im.nby[level];
-    const int ncols = (nx - px + 1) >> 1;
-    const int uy = u / ncols, ux = u - uy * ncols;
-    const int bx = 2 * ux + px, by = 2 * uy + py;
-    const uint16_t *lab = im.lab[level];
+    int mcols, mrows, ncols, nrows;
+    lattice(nx, ny, phase, cphase, &mcols, &mrows);
+    lattice(nx, ny, phase, -1, &ncols, &nrows);
+    const int uy = u / mcols, ux = u - uy * mcols;
+    if (cphase >= 0) {
+        int ccols, crows;
+        lattice(nx, ny, cphase, -1, &ccols, &crows);
+        if (ux < ccols && uy < crows) {
+            const uint32_t d = im.dec[nb][uy * ccols + ux];
+            if (d != kNoMove)
+                replay_large_block(im, nb, level, 2 * ux + (cphase & 1), 2 * uy + (cphase >> 1), d, lane, wsh,
+                                   max_nbins);
+        }
+    }
+    if (ux >= ncols || uy >= nrows) return;
+    const int uu = uy * ncols + ux;
+    const int bx = 2 * ux + (phase & 1), by = 2 * uy + (phase >> 1);
+    const uint16_t *lab = im.lab[level][b];
     const int k = lab[by * nx + bx];
     int cand[4];
     const int nc = unit_candidates(lab, nx, ny, bx, by, k, cand);
-    if (nc == 0) return;
-    const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
-    const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
-    const int bw = x1 - x0, m = bw * (y1 - y0);
-    // the list lives past the largest histogram of the context, so that it
-    // never overlaps histogram entries another image's blocks rely on being 0
-    int32_t *ndist = wsh;
-    int32_t *hsh = wsh + kScratchHeader;
-    uint16_t *lst = (uint16_t *)(hsh + max_nbins);
-    // sparse histogram of the block: counts in shared memory, distinct bins listed
-    for (int base = 0; base < m; base += 32) {
-        const int t = base + lane;
-        const bool act = t < m;
-        int j = -1;
-        if (act) {
-            const int dy = t / bw;
-            j = bin_at(im, (y0 + dy) * im.W + x0 + (t - dy * bw));
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, j);
-        if (act && lane == __ffs(peers) - 1) {
-            const int old = atomicAdd(&hsh[j], __popc(peers));
-            if (old == 0) lst[atomicAdd(ndist, 1)] = (uint16_t)j;
-        }
+    if (nc == 0) {
+        if (lane == 0) im.dec[b][uu] = kNoMove;
+        return;
     }
-    __syncwarp();
-    const int nd = *(volatile int32_t *)ndist;
+    const int32_t *hist = im.hist[b], *size = im.size[b];
+    int m;
+    const int nd = block_sparse_hist(im, level, bx, by, lane, wsh, max_nbins, &m);
+    const int32_t *hsh = wsh + kScratchHeader;
+    const uint16_t *lst = (const uint16_t *)(hsh + max_nbins);
     int64_t sz[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) sz[c] = c < nc ? im.size[cand[c]] : 1;
-    const int64_t s_k = im.size[k], s_rest = s_k - m;
+    for (int c = 0; c < 4; ++c) sz[c] = cand[c] != kNoLabel ? size[cand[c]] : 1;
+    const int64_t s_k = size[k], s_rest = s_k - m;
     int64_t S[4] = {0, 0, 0, 0}, S_st = 0;
     for (int t = lane; t < nd; t += 32) {
         const int j = lst[t];
         const int Lj = hsh[j];
-        hsh[j] = 0;
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            if (c < nc) S[c] += min((int64_t)im.hist[hidx(im, cand[c], j)] * m, (int64_t)Lj * sz[c]);
-        S_st += min((int64_t)(im.hist[hidx(im, k, j)] - Lj) * m, (int64_t)Lj * s_rest);
+            if (cand[c] != kNoLabel) S[c] += min((int64_t)hist[hidx(im, cand[c], j)] * m, (int64_t)Lj * sz[c]);
+        S_st += min((int64_t)(hist[hidx(im, k, j)] - Lj) * m, (int64_t)Lj * s_rest);
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) S[c] = warp_sum64(S[c]);
     S_st = warp_sum64(S_st);
-    __syncwarp();
+    // every lane holds the same sums, so every lane takes the same decision;
+    // ascending candidates, strictly better replaces: ties to the smallest label
+    int n = kNoLabel;
+    int64_t Sb = 0, zb = 1;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (cand[c] != kNoLabel && (n == kNoLabel || S[c] * zb > Sb * sz[c])) {
+            n = cand[c];
+            Sb = S[c];
+            zb = sz[c];
+        }
+    const bool moves = Sb * s_rest > S_st * zb;
+    block_sparse_apply_clear(im, nb, moves ? k : -1, n, nd, lane, wsh, max_nbins);
     if (lane == 0) {
-        *ndist = 0;
-        int bi = 0;
-        for (int c = 1; c < nc; ++c)
-            if (S[c] * sz[bi] > S[bi] * sz[c]) bi = c;
-        if (S[bi] * s_rest > S_st * sz[bi])
-            append_move_single(im, s, (uint32_t)(by * nx + bx), ((uint32_t)k << 16) | (uint32_t)cand[bi], err);
+        im.dec[b][uu] = moves ? (((uint32_t)k << 16) | (uint32_t)n) : kNoMove;
+        if (moves) {
+            im.lab[level][nb][by * nx + bx] = (uint16_t)n;
+            move_size(im, nb, k, n, m);
+        }
     }
-    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// catch-up: replay op o-1's moves into the buffer that op read
+// ---------------------------------------------------------------------------
+
+// A catch-up entry of its own (before a descent or the output): replay op
+// o-1's moves into the buffer that op read.
+__device__ void op_catchup(const DevImage &im, int o, int level, int phase, int units, int group, int off, int lane,
+                           int32_t *wsh, int max_nbins)
+{
+    const int nb = (o & 1) ^ 1;  // = (o-1) & 1: the buffer op o-1 read and decided into
+    const int nx = im.nbx[level];
+    if (group == 32) {  // large blocks: one warp per unit
+        const int u = off >> 5;
+        if (u >= units) return;
+        const uint32_t d = im.dec[nb][u];
+        if (d == kNoMove) return;
+        int bx, by;
+        unit_pos(u, phase, nx, &bx, &by);
+        replay_large_block(im, nb, level, bx, by, d, lane, wsh, max_nbins);
+        return;
+    }
+    if (level == 0) {  // pixels: kCatchupPerLane units per lane, coalesced rows
+        const int chunk = off >> 5;
+        uint32_t d[kCatchupPerLane];
+#pragma unroll
+        for (int r = 0; r < kCatchupPerLane; ++r) {
+            const int u = chunk * 32 * kCatchupPerLane + 32 * r + lane;
+            d[r] = u < units ? im.dec[nb][u] : kNoMove;
+        }
+#pragma unroll
+        for (int r = 0; r < kCatchupPerLane; ++r) {
+            if (d[r] == kNoMove) continue;
+            int x, y;
+            unit_pos(chunk * 32 * kCatchupPerLane + 32 * r + lane, phase, im.W, &x, &y);
+            replay_pixel(im, nb, y * im.W + x, d[r]);
+        }
+        return;
+    }
+    const int u = off + lane;  // small blocks: one thread per unit
+    if (u >= units) return;
+    const uint32_t d = im.dec[nb][u];
+    if (d == kNoMove) return;
+    int bx, by;
+    unit_pos(u, phase, nx, &bx, &by);
+    replay_small_block(im, nb, level, bx, by, d);
 }
 
 // ---------------------------------------------------------------------------
 // descent, output
 // ---------------------------------------------------------------------------
 
-// level `level` -> level-1; the finer grid splits each block 2x2
-__device__ void op_descend(const DevImage &im, int level, int64_t c)
+// level `level` -> level-1 (both buffers); the finer grid splits each block
+// 2x2; at the pixel level a thread writes 4 pixels of a row
+__device__ void op_descend(const DevImage &im, int o, int level, int units, int c)
 {
-    const int t = level - 1;
+    if (c >= units) return;
+    const int b = o & 1, t = level - 1;
+    const uint16_t *src = im.lab[level][b];
     if (t >= 1) {
         const int nx = im.nbx[t];
-        if (c >= (int64_t)nx * im.nby[t]) return;
-        const int cy = (int)(c / nx), cx = (int)(c - (int64_t)cy * nx);
-        im.lab[t][c] = im.lab[level][(cy >> 1) * im.nbx[level] + (cx >> 1)];
+        const int cy = c / nx, cx = c - cy * nx;
+        const uint16_t v = src[(cy >> 1) * im.nbx[level] + (cx >> 1)];
+        im.lab[t][0][c] = v;
+        im.lab[t][1][c] = v;
     } else {
-        const int W = im.W;
-        if (c >= (int64_t)W * im.H) return;
-        const int y = (int)(c / W), x = (int)(c - (int64_t)y * W);
+        const int W = im.W, cw = (W + 3) >> 2;
+        const int y = c / cw, x0 = 4 * (c - y * cw);
         const int n1x = im.nbx[1], n1y = im.nby[1];
         // block b holds x iff floor(b*W/n) <= x < floor((b+1)*W/n)
-        const int bx = (int)(((int64_t)(x + 1) * n1x - 1) / W);
         const int by = (int)(((int64_t)(y + 1) * n1y - 1) / im.H);
-        im.lab[0][c] = im.lab[1][by * n1x + bx];
-    }
-}
-
-__device__ void op_output(const DevImage &im, int64_t c)
-{
-    if (c < (int64_t)im.W * im.H) im.out[c] = im.lab[0][c];
-}
-
-// ---------------------------------------------------------------------------
-// apply slot
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ void move_hist(const DevImage &im, int k, int n, int j, int cnt)
-{
-    atomicSub(&im.hist[hidx(im, k, j)], cnt);
-    atomicAdd(&im.hist[hidx(im, n, j)], cnt);
-}
-
-__device__ void apply_pixel(const DevImage &im, int m)
-{
-    const uint32_t p = im.moves[2 * m], w = im.moves[2 * m + 1];
-    const int k = (int)(w >> 16), n = (int)(w & 0xFFFFu);
-    const int j = bin_at(im, (int)p);
-    im.lab[0][p] = (uint16_t)n;
-    move_hist(im, k, n, j, 1);
-    atomicSub(&im.size[k], 1);
-    atomicAdd(&im.size[n], 1);
-}
-
-__device__ void apply_block_thread(const DevImage &im, int level, int m)
-{
-    const uint32_t u = im.moves[2 * m], w = im.moves[2 * m + 1];
-    const int k = (int)(w >> 16), n = (int)(w & 0xFFFFu);
-    const int nx = im.nbx[level];
-    const int by = (int)(u / (uint32_t)nx), bx = (int)(u - (uint32_t)by * nx);
-    im.lab[level][u] = (uint16_t)n;
-    const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
-    const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
-    for (int y = y0; y < y1; ++y)
-        for (int x = x0; x < x1; ++x) move_hist(im, k, n, bin_at(im, y * im.W + x), 1);
-    const int area = (x1 - x0) * (y1 - y0);
-    atomicSub(&im.size[k], area);
-    atomicAdd(&im.size[n], area);
-}
-
-__device__ void apply_block_warp(const DevImage &im, int level, int m, int lane)
-{
-    const uint32_t u = im.moves[2 * m], w = im.moves[2 * m + 1];
-    const int k = (int)(w >> 16), n = (int)(w & 0xFFFFu);
-    const int nx = im.nbx[level];
-    const int by = (int)(u / (uint32_t)nx), bx = (int)(u - (uint32_t)by * nx);
-    const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
-    const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
-    const int bw = x1 - x0, area = bw * (y1 - y0);
-    for (int base = 0; base < area; base += 32) {
-        const int t = base + lane;
-        const bool act = t < area;
-        int j = -1;
-        if (act) {
-            const int dy = t / bw;
-            j = bin_at(im, (y0 + dy) * im.W + x0 + (t - dy * bw));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int x = x0 + q;
+            if (x < W) {
+                const int bx = (int)(((int64_t)(x + 1) * n1x - 1) / W);
+                const uint16_t v = src[by * n1x + bx];
+                im.lab[0][0][y * W + x] = v;
+                im.lab[0][1][y * W + x] = v;
+            }
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, j);
-        if (act && lane == __ffs(peers) - 1) move_hist(im, k, n, j, __popc(peers));
     }
-    if (lane == 0) {
-        im.lab[level][u] = (uint16_t)n;
-        atomicSub(&im.size[k], area);
-        atomicAdd(&im.size[n], area);
-    }
+}
+
+__device__ void op_output(const DevImage &im, int o, int units, int c)
+{
+    if (c >= units) return;
+    const int W = im.W, cw = (W + 3) >> 2;
+    const int y = c / cw, x0 = 4 * (c - y * cw);
+    const uint16_t *lab = im.lab[0][o & 1] + y * W;
+    int32_t *out = im.out + (int64_t)y * W;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (x0 + q < W) out[x0 + q] = lab[x0 + q];
 }
 
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(512) seeds_persistent(const DevImage *__restrict__ imgs, Schedule S,
+// Resident 512-thread blocks per SM the register budget must allow (2 caps
+// registers at 64 per thread); a build-time knob.
+#ifndef SEEDS_MIN_BLOCKS
+#define SEEDS_MIN_BLOCKS 2
+#endif
+
+__global__ void __launch_bounds__(512, SEEDS_MIN_BLOCKS) seeds_persistent(const DevImage *__restrict__ imgs, Schedule S,
                                                         GridBarrier *bar, int32_t *err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -578,24 +807,17 @@ __global__ void __launch_bounds__(512) seeds_persistent(const DevImage *__restri
     // per-warp scratch sized for the largest histogram of the context
     const int wbytes = warp_scratch_bytes(S.max_nbins);
     int32_t *wsh = (int32_t *)(smem + (size_t)warp * wbytes);
+    uint16_t *tsh = (uint16_t *)(smem + (size_t)warp * wbytes + warp_hist_scratch_bytes(S.max_nbins));
     for (int i = lane; i < wbytes / 4; i += 32) wsh[i] = 0;
     __syncwarp();
 
     const int64_t gwarp = (int64_t)blockIdx.x * nwarps_blk + warp;
     const int64_t nwarps = (int64_t)gridDim.x * nwarps_blk;
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-
     const bool tracer = S.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
     if (tracer) S.trace[0] = global_ns();
+
     for (int s = 0; s < S.nsteps; ++s) {
         const int e0 = S.step_first[s], e1 = S.step_first[s + 1];
-        // the other move counter of every image in this step was last read
-        // by the previous apply slot; clear it for the next step
-        if (blockIdx.x == 0)
-            for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) imgs[S.ent[e].img].cnt[(s + 1) & 1] = 0;
-
-        // ---- evaluate slot
         const int64_t total = S.step_vt[s];
         for (int64_t base = gwarp * 32; base < total; base += nwarps * 32) {
             int lo = e0, hi = e1 - 1;
@@ -608,59 +830,36 @@ __global__ void __launch_bounds__(512) seeds_persistent(const DevImage *__restri
             }
             const StepEntry E = S.ent[lo];
             const DevImage &im = imgs[E.img];
-            const int64_t off = base - E.vt_begin;
+            const int off = (int)(base - E.vt_begin);
             switch (E.op) {
             case OP_INIT:
-                op_init(im, (int)(off >> 5), lane, wsh + kScratchHeader);
+                op_init(im, off >> 5, lane, wsh);
                 break;
             case OP_PHASE:
                 if (E.level == 0)
-                    op_pixel_phase(im, E.phase, E.units, s, (int)(off + lane), lane, err);
+                    op_pixel_tile(im, E.opidx, E.phase, E.cphase, E.units, off >> 5, lane, tsh);
                 else if (E.group == 1)
-                    op_block_phase_thread(im, E.level, E.phase, E.units, s, (int)(off + lane), lane, err);
+                    op_block_phase_thread(im, E.opidx, E.level, E.phase, E.cphase, E.units, off + lane);
                 else
-                    op_block_phase_warp(im, E.level, E.phase, E.units, s, (int)(off >> 5), lane, wsh, S.max_nbins,
-                                        err);
+                    op_block_phase_warp(im, E.opidx, E.level, E.phase, E.cphase, E.units, off >> 5, lane, wsh,
+                                        S.max_nbins);
+                break;
+            case OP_CATCHUP:
+                op_catchup(im, E.opidx, E.level, E.phase, (int)phase_units(im, E.level, E.phase), E.group, off,
+                           lane, wsh, S.max_nbins);
                 break;
             case OP_DESCEND:
-                op_descend(im, E.level, off + lane);
+                op_descend(im, E.opidx, E.level, E.units, off + lane);
                 break;
             case OP_OUTPUT:
-                op_output(im, off + lane);
+                op_output(im, E.opidx, E.units, off + lane);
                 break;
             default:
                 break;
             }
         }
-        const bool last = s + 1 == S.nsteps;
-        if (!S.step_apply[s]) {
-            if (!last && !grid_sync(bar, err)) return;
-            if (tracer) S.trace[1 + 2 * s] = S.trace[2 + 2 * s] = global_ns();
-            continue;
-        }
-        if (!grid_sync(bar, err)) return;
-        if (tracer) S.trace[1 + 2 * s] = global_ns();
-
-        // ---- apply slot
-        for (int e = e0; e < e1; ++e) {
-            const StepEntry E = S.ent[e];
-            if (E.op != OP_PHASE) continue;
-            const DevImage &im = imgs[E.img];
-            int count = ld_relaxed_i32(&im.cnt[s & 1]);
-            if (count > im.moves_cap) {
-                if (gtid == 0) atomicOr(err, DERR_BOUNDS);
-                count = im.moves_cap;
-            }
-            if (E.level > 0 && E.group == 32) {
-                for (int64_t m = gwarp; m < count; m += nwarps) apply_block_warp(im, E.level, (int)m, lane);
-            } else if (E.level > 0) {
-                for (int64_t m = gtid; m < count; m += nthreads) apply_block_thread(im, E.level, (int)m);
-            } else {
-                for (int64_t m = gtid; m < count; m += nthreads) apply_pixel(im, (int)m);
-            }
-        }
-        if (!last && !grid_sync(bar, err)) return;
-        if (tracer) S.trace[2 + 2 * s] = global_ns();
+        if (s + 1 < S.nsteps && !grid_sync(bar, err)) return;
+        if (tracer) S.trace[1 + s] = global_ns();
     }
 }
 
@@ -675,30 +874,35 @@ __global__ void set_io_kernel(DevImage *imgs, IoChunk chunk)
     }
 }
 
-// recount an image's histograms from the labels of one level (test hook)
-__global__ void recount_kernel(const DevImage *imgs, int img, int level, int64_t npix, int phase_zero)
+// recount an image's histograms (both buffers) from the labels of one level
+// of buffer 0 (test hook)
+__global__ void recount_kernel(const DevImage *imgs, int img, int level, int64_t npix, int zero_pass)
 {
     const DevImage &im = imgs[img];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (phase_zero) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (zero_pass) {
         const int64_t nh = (int64_t)im.K * im.nbins;
-        for (int64_t t = i; t < nh; t += (int64_t)gridDim.x * blockDim.x) im.hist[t] = 0;
-        for (int64_t t = i; t < im.K; t += (int64_t)gridDim.x * blockDim.x) im.size[t] = 0;
+        for (int64_t t = i; t < nh; t += stride) im.hist[0][t] = im.hist[1][t] = 0;
+        for (int64_t t = i; t < im.K; t += stride) im.size[0][t] = im.size[1][t] = 0;
         return;
     }
     if (i >= npix) return;
     const int y = (int)(i / im.W), x = (int)(i - (int64_t)y * im.W);
     int k;
     if (level == 0) {
-        k = im.lab[0][i];
+        k = im.lab[0][0][i];
     } else {
         const int nx = im.nbx[level], ny = im.nby[level];
         const int bx = (int)(((int64_t)(x + 1) * nx - 1) / im.W);
         const int by = (int)(((int64_t)(y + 1) * ny - 1) / im.H);
-        k = im.lab[level][by * nx + bx];
+        k = im.lab[level][0][by * nx + bx];
     }
-    atomicAdd(&im.hist[hidx(im, k, bin_at(im, (int)i))], 1);
-    atomicAdd(&im.size[k], 1);
+    const int j = bin_at(im, (int)i);
+    atomicAdd(&im.hist[0][hidx(im, k, j)], 1);
+    atomicAdd(&im.hist[1][hidx(im, k, j)], 1);
+    atomicAdd(&im.size[0][k], 1);
+    atomicAdd(&im.size[1][k], 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -736,17 +940,11 @@ cudaError_t launch_recount(const DevImage *d_imgs, int img, int level, int64_t n
     return cudaGetLastError();
 }
 
-}  // namespace seeds
-
 // ===========================================================================
 // One image with no allocation at all: every byte of device state lives in a
 // file-scope static device array.  For callers that may not allocate device
 // memory (see seeds_run_static in seeds.h).
 // ===========================================================================
-
-#include <mutex>
-
-namespace seeds {
 
 static __device__ __align__(256) unsigned char g_static_scratch[SEEDS_STATIC_SCRATCH_BYTES];
 
@@ -782,17 +980,15 @@ struct StaticSetup {
     StepEntry *ent;
     int32_t *first;
     int64_t *vt;
-    int32_t *apply;
-    unsigned char *zero_begin;  // barrier, counters, error word
+    unsigned char *zero_begin;  // barrier and error word
     int32_t zero_bytes;
-    int32_t maxarea[kMaxLevels + 1];
-    int32_t small_area;
+    int32_t nops;
     DevImage *img_out;
 };
 
 // Lays out one image inside the scratch: the image record, the block edge
-// tables of every level, and the op schedule (one op per step); clears the
-// barrier, the move counters and the error word.
+// tables of every level, and the op schedule (one op per step, with the
+// catch-up of the previous phase); clears the barrier and the error word.
 __global__ void static_setup_kernel(StaticSetup S)
 {
     const DevImage &im = S.img;
@@ -805,40 +1001,15 @@ __global__ void static_setup_kernel(StaticSetup S)
     for (int i = t; i < S.zero_bytes; i += nt) S.zero_begin[i] = 0;
     if (t != 0) return;
     *S.img_out = im;
-    int s = 0, ne = 0;
-    auto emit = [&](int kind, int level, int phase, int64_t units, int group) {
-        S.first[s] = ne;
-        const int64_t count = (units * group + 31) / 32 * 32;
-        S.vt[s] = count;
-        S.apply[s] = 0;
-        if (count > 0) {
-            StepEntry e;
-            e.img = 0;
-            e.op = kind;
-            e.level = level;
-            e.phase = phase;
-            e.vt_begin = 0;
-            e.units = (int32_t)units;
-            e.group = group;
-            S.ent[ne++] = e;
-            S.apply[s] = kind == OP_PHASE;
-        }
-        ++s;
-    };
-    auto phase_units = [&](int l, int ph) {
-        return (int64_t)((im.nbx[l] - (ph & 1) + 1) >> 1) * ((im.nby[l] - (ph >> 1) + 1) >> 1);
-    };
-    emit(OP_INIT, 0, 0, im.K, 32);
-    for (int l = im.L; l >= 1; --l) {
-        const int group = S.maxarea[l] > S.small_area ? 32 : 1;
-        for (int it = 0; it < im.iters; ++it)
-            for (int ph = 0; ph < 4; ++ph) emit(OP_PHASE, l, ph, phase_units(l, ph), group);
-        emit(OP_DESCEND, l, 0, l - 1 >= 1 ? (int64_t)im.nbx[l - 1] * im.nby[l - 1] : (int64_t)im.W * im.H, 1);
+    int ne = 0;
+    for (int o = 0; o < S.nops; ++o) {
+        S.first[o] = ne;
+        int64_t vt = 0;
+        const bool catchup = o > 0 && op_at(im.L, im.iters, o - 1).kind == OP_PHASE;
+        ne += emit_entries(im, 0, o, catchup, S.ent + ne, &vt);
+        S.vt[o] = vt;
     }
-    for (int it = 0; it < im.iters; ++it)
-        for (int ph = 0; ph < 4; ++ph) emit(OP_PHASE, 0, ph, phase_units(0, ph), 1);
-    emit(OP_OUTPUT, 0, 0, (int64_t)im.W * im.H, 1);
-    S.first[s] = ne;
+    S.first[S.nops] = ne;
 }
 
 __global__ void static_status_kernel(const int32_t *err, int32_t *status) { *status = *err; }
@@ -887,39 +1058,40 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     d.gden = p->gamma_den;
     d.bins16 = nbins > 256;
     d.hist_jmajor = 0;
+    d.hist_sk = nbins;
+    d.hist_sj = 1;
+    d.small_area = 16;
     d.nbx[0] = p->width;
     d.nby[0] = p->height;
+    d.maxarea[0] = 1;
     int amax = 1;
     for (int l = 1; l <= L; ++l) {
         d.nbx[l] = (int)(gx << (L - l + 1));
         d.nby[l] = (int)(gy << (L - l + 1));
+        // the widest block of a level spans ceil(W/n) columns (floor edges)
         const int mw = (p->width + d.nbx[l] - 1) / d.nbx[l], mh = (p->height + d.nby[l] - 1) / d.nby[l];
-        S.maxarea[l] = mw * mh;
+        d.maxarea[l] = mw * mh;
         amax = std::max(amax, mw * mh);
     }
     const __int128 N2 = (__int128)N * N, lim = ((__int128)1) << 63;
     if ((__int128)amax * N2 >= lim || (__int128)(81 * p->gamma_den + 90 * p->gamma_num) * N2 >= lim)
         return SEEDS_ERR_INT64;
-    S.small_area = 16;
-    const int nops = 1 + (L + 1) * 4 * p->iters_per_level + L + 1;
-    const int moves_cap = (int)(((int64_t)(p->width + 1) / 2) * ((p->height + 1) / 2));
+    const int nops = num_ops(L, p->iters_per_level);
+    const int units_cap = (int)(((int64_t)(p->width + 1) / 2) * ((p->height + 1) / 2));
 
     // ---- layout inside the scratch
     size_t off = 0;
     const size_t o_img = off;
     off = sal(off + sizeof(DevImage));
-    const size_t o_zero = off;  // barrier | 2 counters | error word
-    const size_t o_bar = off, o_cnt = off + 16, o_err = off + 32;
-    off = sal(off + 64);
+    const size_t o_zero = off, o_bar = off, o_err = off + 16;  // barrier | error word
+    off = sal(off + 32);
     const size_t o_ent = off;
-    off = sal(off + sizeof(StepEntry) * (size_t)nops);
+    off = sal(off + sizeof(StepEntry) * 2 * (size_t)nops);
     const size_t o_first = off;
     off = sal(off + 4 * (size_t)(nops + 1));
     const size_t o_vt = off;
     off = sal(off + 8 * (size_t)nops);
-    const size_t o_apply = off;
-    off = sal(off + 4 * (size_t)nops);
-    size_t o_xe[kMaxLevels + 1] = {}, o_ye[kMaxLevels + 1] = {}, o_lab[kMaxLevels + 1] = {};
+    size_t o_xe[kMaxLevels + 1] = {}, o_ye[kMaxLevels + 1] = {}, o_lab[kMaxLevels + 1][2] = {};
     for (int l = 1; l <= L; ++l) {
         o_xe[l] = off;
         off = sal(off + 4 * (size_t)(d.nbx[l] + 1));
@@ -928,16 +1100,20 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     }
     const size_t o_bins = off;
     off = sal(off + (size_t)N * (d.bins16 ? 2 : 1));
-    for (int l = 0; l <= L; ++l) {
-        o_lab[l] = off;
-        off = sal(off + 2 * (size_t)d.nbx[l] * d.nby[l]);
+    for (int l = 0; l <= L; ++l)
+        for (int q = 0; q < 2; ++q) {
+            o_lab[l][q] = off;
+            off = sal(off + 2 * (size_t)d.nbx[l] * d.nby[l]);
+        }
+    size_t o_hist[2], o_size[2], o_dec[2];
+    for (int q = 0; q < 2; ++q) {
+        o_hist[q] = off;
+        off = sal(off + 4 * (size_t)K * nbins);
+        o_size[q] = off;
+        off = sal(off + 4 * (size_t)K);
+        o_dec[q] = off;
+        off = sal(off + 4 * (size_t)units_cap);
     }
-    const size_t o_hist = off;
-    off = sal(off + 4 * (size_t)K * nbins);
-    const size_t o_size = off;
-    off = sal(off + 4 * (size_t)K);
-    const size_t o_moves = off;
-    off = sal(off + 8 * (size_t)moves_cap);
     if (off > (size_t)SEEDS_STATIC_SCRATCH_BYTES) return SEEDS_ERR_STATIC_SIZE;
 
     // ---- the scratch's device address on the current device
@@ -946,26 +1122,28 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     unsigned char *base = nullptr;
     if (static_scratch_address(dev, &base) != cudaSuccess) return SEEDS_ERR_CUDA;
 
-    for (int l = 0; l <= L; ++l) d.lab[l] = (uint16_t *)(base + o_lab[l]);
+    for (int l = 0; l <= L; ++l)
+        for (int q = 0; q < 2; ++q) d.lab[l][q] = (uint16_t *)(base + o_lab[l][q]);
     for (int l = 1; l <= L; ++l) {
         d.xe[l] = (const int32_t *)(base + o_xe[l]);
         d.ye[l] = (const int32_t *)(base + o_ye[l]);
     }
     d.bins = base + o_bins;
-    d.hist = (int32_t *)(base + o_hist);
-    d.size = (int32_t *)(base + o_size);
-    d.moves = (uint32_t *)(base + o_moves);
-    d.moves_cap = moves_cap;
-    d.cnt = (int32_t *)(base + o_cnt);
+    for (int q = 0; q < 2; ++q) {
+        d.hist[q] = (int32_t *)(base + o_hist[q]);
+        d.size[q] = (int32_t *)(base + o_size[q]);
+        d.dec[q] = (uint32_t *)(base + o_dec[q]);
+    }
+    d.units_cap = units_cap;
     d.rgb = d_rgb;
     d.stride = row_stride_bytes;
     d.out = d_labels_out;
     S.ent = (StepEntry *)(base + o_ent);
     S.first = (int32_t *)(base + o_first);
     S.vt = (int64_t *)(base + o_vt);
-    S.apply = (int32_t *)(base + o_apply);
     S.zero_begin = base + o_zero;
-    S.zero_bytes = 64;
+    S.zero_bytes = 32;
+    S.nops = nops;
     S.img_out = (DevImage *)(base + o_img);
 
     // ---- launch configuration of the persistent kernel (as a context would)
@@ -983,7 +1161,6 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     sch.ent = S.ent;
     sch.step_first = S.first;
     sch.step_vt = S.vt;
-    sch.step_apply = S.apply;
     sch.nsteps = nops;
     sch.max_nbins = nbins;
     sch.trace = nullptr;

@@ -10,7 +10,7 @@
 #include <cstring>
 #include <map>
 #include <new>
-#include <tuple>
+#include <string>
 #include <vector>
 
 #include "seeds.h"
@@ -32,10 +32,10 @@ struct ImageHost {
     std::vector<int32_t> xe[kMaxLevels + 1], ye[kMaxLevels + 1];
     int maxarea[kMaxLevels + 1] = {};
     std::vector<Op> ops;  // full list, output op last
-    int moves_cap = 0;
+    int units_cap = 0;
     // byte offsets inside the context's pool
-    size_t off_bins = 0, off_lab[kMaxLevels + 1] = {}, off_xe[kMaxLevels + 1] = {}, off_ye[kMaxLevels + 1] = {};
-    size_t off_hist = 0, off_size = 0, off_moves = 0, bytes = 0;
+    size_t off_bins = 0, off_lab[kMaxLevels + 1][2] = {}, off_xe[kMaxLevels + 1] = {}, off_ye[kMaxLevels + 1] = {};
+    size_t off_hist[2] = {}, off_size[2] = {}, off_dec[2] = {}, bytes = 0;
 };
 
 struct DevSchedule {
@@ -118,63 +118,41 @@ int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t *gy_out
     if ((__int128)amax * N2 >= lim) return SEEDS_ERR_INT64;
     if ((__int128)(81 * p->gamma_den + 90 * p->gamma_num) * N2 >= lim) return SEEDS_ERR_INT64;
 
-    // op list: init, block levels L..1 (phases then descent), pixel level, output
+    // op list (the same one the kernels derive with op_at)
     h.ops.clear();
-    h.ops.push_back({OP_INIT, 0, 0});
-    for (int l = L; l >= 1; --l) {
-        for (int it = 0; it < p->iters_per_level; ++it)
-            for (int ph = 0; ph < 4; ++ph) h.ops.push_back({OP_PHASE, l, ph});
-        h.ops.push_back({OP_DESCEND, l, 0});
+    const int nops = num_ops(L, p->iters_per_level);
+    for (int o = 0; o < nops; ++o) {
+        const OpDesc d = op_at(L, p->iters_per_level, o);
+        h.ops.push_back({d.kind, d.level, d.phase});
     }
-    for (int it = 0; it < p->iters_per_level; ++it)
-        for (int ph = 0; ph < 4; ++ph) h.ops.push_back({OP_PHASE, 0, ph});
-    h.ops.push_back({OP_OUTPUT, 0, 0});
-    h.moves_cap = (int)(((int64_t)(p->width + 1) / 2) * ((p->height + 1) / 2));
+    h.units_cap = (int)(((int64_t)(p->width + 1) / 2) * ((p->height + 1) / 2));
 
-    // device layout
+    // device layout: bins, then two buffers of every label grid, histogram,
+    // size vector and decision array
     size_t off = 0;
     h.off_bins = off;
     off = align_up(off + (size_t)N * (h.nbins > 256 ? 2 : 1));
-    for (int l = 0; l <= L; ++l) {
-        h.off_lab[l] = off;
-        off = align_up(off + (size_t)h.nbx[l] * h.nby[l] * 2);
-    }
+    for (int l = 0; l <= L; ++l)
+        for (int q = 0; q < 2; ++q) {
+            h.off_lab[l][q] = off;
+            off = align_up(off + (size_t)h.nbx[l] * h.nby[l] * 2);
+        }
     for (int l = 1; l <= L; ++l) {
         h.off_xe[l] = off;
         off = align_up(off + (h.nbx[l] + 1) * 4);
         h.off_ye[l] = off;
         off = align_up(off + (h.nby[l] + 1) * 4);
     }
-    h.off_hist = off;
-    off = align_up(off + (size_t)h.K * h.nbins * 4);
-    h.off_size = off;
-    off = align_up(off + (size_t)h.K * 4);
-    h.off_moves = off;
-    off = align_up(off + (size_t)h.moves_cap * 8);
+    for (int q = 0; q < 2; ++q) {
+        h.off_hist[q] = off;
+        off = align_up(off + (size_t)h.K * h.nbins * 4);
+        h.off_size[q] = off;
+        off = align_up(off + (size_t)h.K * 4);
+        h.off_dec[q] = off;
+        off = align_up(off + (size_t)h.units_cap * 4);
+    }
     h.bytes = off;
     return SEEDS_OK;
-}
-
-int units_of(const ImageHost &h, const Op &op, int small_area, int *group)
-{
-    *group = 1;
-    switch (op.kind) {
-    case OP_INIT:
-        *group = 32;
-        return h.K;
-    case OP_PHASE: {
-        const int px = op.phase & 1, py = op.phase >> 1;
-        const int nx = h.nbx[op.level], ny = h.nby[op.level];
-        const int64_t u = (int64_t)((nx - px + 1) >> 1) * ((ny - py + 1) >> 1);
-        if (op.level > 0 && h.maxarea[op.level] > small_area) *group = 32;
-        return (int)u;
-    }
-    case OP_DESCEND:
-        return op.level - 1 >= 1 ? h.nbx[op.level - 1] * h.nby[op.level - 1] : (int)h.N;
-    case OP_OUTPUT:
-        return (int)h.N;
-    }
-    return 0;
 }
 
 }  // namespace
@@ -188,14 +166,15 @@ struct seeds_ctx {
     DevImage *d_imgs = nullptr;
     unsigned char *pool = nullptr;
     size_t pool_bytes = 0;
-    int32_t *d_cnt = nullptr;  // 2 per image
+    std::vector<int> cur;      // per image: ops done in the current chain (state in buffer cur & 1)
+    std::vector<int> pending;  // per image: op whose moves await catch-up, or -1
     GridBarrier *d_bar = nullptr;
     int32_t *d_err = nullptr;
     seeds_tuning tune{256, 0, 0, 16};
     int grid = 0;
     size_t smem = 0;
     int max_nbins = 1;
-    std::map<std::tuple<int, int, int>, DevSchedule> schedules;
+    std::map<std::string, DevSchedule> schedules;
     cudaEvent_t done = nullptr;
     bool launched = false;
     bool profile = false, profiled = false;
@@ -254,24 +233,28 @@ void fill_dev_images(seeds_ctx *c)
         d.gden = h.p.gamma_den;
         d.bins16 = h.nbins > 256;
         d.hist_jmajor = c->tune.hist_layout == 1;
+        d.hist_sk = d.hist_jmajor ? 1 : h.nbins;
+        d.hist_sj = d.hist_jmajor ? h.K : 1;
+        d.small_area = c->tune.small_block_area;
         unsigned char *base = c->pool;
         for (size_t t = 0; t < i; ++t) base += c->img[t].bytes;
         for (int l = 0; l <= h.L; ++l) {
             d.nbx[l] = h.nbx[l];
             d.nby[l] = h.nby[l];
-            d.lab[l] = (uint16_t *)(base + h.off_lab[l]);
-            d.group[l] = (l > 0 && h.maxarea[l] > c->tune.small_block_area) ? 32 : 1;
+            d.maxarea[l] = h.maxarea[l];
+            for (int q = 0; q < 2; ++q) d.lab[l][q] = (uint16_t *)(base + h.off_lab[l][q]);
             if (l >= 1) {
                 d.xe[l] = (const int32_t *)(base + h.off_xe[l]);
                 d.ye[l] = (const int32_t *)(base + h.off_ye[l]);
             }
         }
         d.bins = base + h.off_bins;
-        d.hist = (int32_t *)(base + h.off_hist);
-        d.size = (int32_t *)(base + h.off_size);
-        d.moves = (uint32_t *)(base + h.off_moves);
-        d.moves_cap = h.moves_cap;
-        d.cnt = c->d_cnt + 2 * i;
+        for (int q = 0; q < 2; ++q) {
+            d.hist[q] = (int32_t *)(base + h.off_hist[q]);
+            d.size[q] = (int32_t *)(base + h.off_size[q]);
+            d.dec[q] = (uint32_t *)(base + h.off_dec[q]);
+        }
+        d.units_cap = h.units_cap;
         d.rgb = c->io[i].rgb;
         d.stride = c->io[i].stride;
         d.out = c->io[i].out;
@@ -303,50 +286,40 @@ void op_range(const ImageHost &h, int kind, int ob, int oe, int *b, int *e)
     }
 }
 
+// Build (or reuse) the schedule running ops [b_i, e_i) of every image i, one
+// op per step; the first op of an image catches up the moves of the op
+// before it when those are still pending from an earlier launch.
 int get_schedule(seeds_ctx *c, int kind, int ob, int oe, const Schedule **out)
 {
-    auto key = std::make_tuple(kind, kind == SCHED_DEBUG ? ob : 0, kind == SCHED_DEBUG ? oe : 0);
+    const int n = (int)c->img.size();
+    std::vector<int> b(n), e(n);
+    std::string key = std::to_string(kind) + ":" + std::to_string(ob) + ":" + std::to_string(oe) + ":";
+    int nsteps = 0;
+    for (int i = 0; i < n; ++i) {
+        op_range(c->img[i], kind, ob, oe, &b[i], &e[i]);
+        nsteps = std::max(nsteps, e[i] - b[i]);
+        key += (b[i] > 0 && c->pending[i] == b[i] - 1) ? '1' : '0';
+    }
     auto it = c->schedules.find(key);
     if (it != c->schedules.end()) {
         *out = &it->second.s;
         return SEEDS_OK;
     }
-    const int n = (int)c->img.size();
-    std::vector<int> b(n), e(n);
-    int nsteps = 0;
-    for (int i = 0; i < n; ++i) {
-        op_range(c->img[i], kind, ob, oe, &b[i], &e[i]);
-        nsteps = std::max(nsteps, e[i] - b[i]);
-    }
     std::vector<StepEntry> ent;
-    std::vector<int32_t> first, apply;
+    std::vector<int32_t> first;
     std::vector<int64_t> vt;
+    StepEntry two[2];
     for (int s = 0; s < nsteps; ++s) {
         first.push_back((int32_t)ent.size());
         int64_t v = 0;
-        int ap = 0;
         for (int i = 0; i < n; ++i) {
             const int o = b[i] + s;
             if (o >= e[i]) continue;
-            const Op &op = c->img[i].ops[o];
-            int group = 1;
-            const int units = units_of(c->img[i], op, c->tune.small_block_area, &group);
-            const int64_t count = ((int64_t)units * group + 31) / 32 * 32;
-            if (count == 0) continue;
-            StepEntry se;
-            se.img = i;
-            se.op = op.kind;
-            se.level = op.level;
-            se.phase = op.phase;
-            se.vt_begin = v;
-            se.units = units;
-            se.group = group;
-            ent.push_back(se);
-            v += count;
-            ap |= op.kind == OP_PHASE;
+            const bool catchup = s == 0 ? (o > 0 && c->pending[i] == o - 1) : c->img[i].ops[o - 1].kind == OP_PHASE;
+            const int m = emit_entries(c->h_imgs[i], i, o, catchup, two, &v);
+            for (int q = 0; q < m; ++q) ent.push_back(two[q]);
         }
         vt.push_back(v);
-        apply.push_back(ap);
     }
     first.push_back((int32_t)ent.size());
     if (ent.empty()) ent.push_back(StepEntry{});  // keep the buffer non-empty
@@ -354,17 +327,14 @@ int get_schedule(seeds_ctx *c, int kind, int ob, int oe, const Schedule **out)
     const size_t b_ent = align_up(ent.size() * sizeof(StepEntry));
     const size_t b_first = align_up(first.size() * sizeof(int32_t));
     const size_t b_vt = align_up(std::max<size_t>(1, vt.size()) * sizeof(int64_t));
-    const size_t b_apply = align_up(std::max<size_t>(1, apply.size()) * sizeof(int32_t));
     DevSchedule ds;
-    int rc = from_cuda(cudaMalloc(&ds.buf, b_ent + b_first + b_vt + b_apply));
+    int rc = from_cuda(cudaMalloc(&ds.buf, b_ent + b_first + b_vt));
     if (rc) return rc;
     unsigned char *p = (unsigned char *)ds.buf;
-    std::vector<unsigned char> host(b_ent + b_first + b_vt + b_apply, 0);
+    std::vector<unsigned char> host(b_ent + b_first + b_vt, 0);
     std::memcpy(host.data(), ent.data(), ent.size() * sizeof(StepEntry));
     std::memcpy(host.data() + b_ent, first.data(), first.size() * sizeof(int32_t));
     if (!vt.empty()) std::memcpy(host.data() + b_ent + b_first, vt.data(), vt.size() * sizeof(int64_t));
-    if (!apply.empty())
-        std::memcpy(host.data() + b_ent + b_first + b_vt, apply.data(), apply.size() * sizeof(int32_t));
     rc = from_cuda(cudaMemcpy(ds.buf, host.data(), host.size(), cudaMemcpyHostToDevice));
     if (rc) {
         cudaFree(ds.buf);
@@ -373,9 +343,9 @@ int get_schedule(seeds_ctx *c, int kind, int ob, int oe, const Schedule **out)
     ds.s.ent = (const StepEntry *)p;
     ds.s.step_first = (const int32_t *)(p + b_ent);
     ds.s.step_vt = (const int64_t *)(p + b_ent + b_first);
-    ds.s.step_apply = (const int32_t *)(p + b_ent + b_first + b_vt);
     ds.s.nsteps = nsteps;
     ds.s.max_nbins = c->max_nbins;
+    ds.s.trace = nullptr;
     auto ins = c->schedules.emplace(key, ds);
     *out = &ins.first->second.s;
     return SEEDS_OK;
@@ -407,14 +377,13 @@ int launch(seeds_ctx *c, int kind, int ob, int oe, cudaStream_t s)
     if (rc) return rc;
     if (sch->nsteps == 0) return SEEDS_OK;
     rc = from_cuda(cudaMemsetAsync(c->d_bar, 0, sizeof(GridBarrier), s));
-    if (!rc) rc = from_cuda(cudaMemsetAsync(c->d_cnt, 0, sizeof(int32_t) * 2 * c->img.size(), s));
     if (rc) return rc;
     Schedule run = *sch;
     run.trace = nullptr;
     if (c->profile) {
         rc = from_cuda(cudaEventRecord(c->ev0, s));
         if (rc) return rc;
-        if (1 + 2 * run.nsteps <= c->trace_cap) {
+        if (1 + run.nsteps <= c->trace_cap) {
             run.trace = c->d_trace;
             c->traced_steps = run.nsteps;
         } else {
@@ -432,6 +401,14 @@ int launch(seeds_ctx *c, int kind, int ob, int oe, cudaStream_t s)
     c->profiled = c->profile;
     rc = from_cuda(cudaEventRecord(c->done, s));
     c->launched = true;
+    // where every image's state now lives, and which moves await catch-up
+    for (size_t i = 0; i < c->img.size(); ++i) {
+        int b = 0, e = 0;
+        op_range(c->img[i], kind, ob, oe, &b, &e);
+        if (e <= b) continue;
+        c->cur[i] = e;
+        c->pending[i] = c->img[i].ops[e - 1].kind == OP_PHASE ? e - 1 : -1;
+    }
     return rc;
 }
 
@@ -442,7 +419,6 @@ void destroy_ctx(seeds_ctx *c)
     free_schedules(c);
     cudaFree(c->d_imgs);
     cudaFree(c->pool);
-    cudaFree(c->d_cnt);
     cudaFree(c->d_bar);
     cudaFree(c->d_err);
     cudaFree(c->stage);
@@ -469,16 +445,16 @@ int create_ctx(const seeds_params *p, int32_t n, seeds_ctx **out)
         c->max_nbins = std::max(c->max_nbins, c->img[i].nbins);
     }
     c->io.assign(n, IoEntry{nullptr, 0, nullptr});
+    c->cur.assign(n, 0);
+    c->pending.assign(n, -1);
     int rc = from_cuda(cudaGetDevice(&c->device));
     if (!rc) rc = from_cuda(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
     for (auto &h : c->img) c->pool_bytes += h.bytes;
     if (!rc) rc = from_cuda(cudaMalloc((void **)&c->pool, c->pool_bytes));
     if (!rc) rc = from_cuda(cudaMalloc((void **)&c->d_imgs, sizeof(DevImage) * n));
-    if (!rc) rc = from_cuda(cudaMalloc((void **)&c->d_cnt, sizeof(int32_t) * 2 * n));
     if (!rc) rc = from_cuda(cudaMalloc((void **)&c->d_bar, sizeof(GridBarrier)));
     if (!rc) rc = from_cuda(cudaMalloc((void **)&c->d_err, sizeof(int32_t)));
     if (!rc) rc = from_cuda(cudaMemset(c->d_err, 0, sizeof(int32_t)));
-    if (!rc) rc = from_cuda(cudaMemset(c->d_cnt, 0, sizeof(int32_t) * 2 * n));
     if (!rc) rc = from_cuda(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
     if (!rc) rc = from_cuda(cudaEventCreate(&c->ev0));
     if (!rc) rc = from_cuda(cudaEventCreate(&c->ev1));
@@ -783,24 +759,25 @@ int seeds_debug_read_state(seeds_ctx *c, int32_t i, int32_t level, int32_t *h_la
     if (level < 0 || level > h.L) return SEEDS_ERR_INVALID;
     int rc = from_cuda(cudaDeviceSynchronize());
     if (rc) return rc;
+    const int q = c->cur[i] & 1;  // buffer holding the complete state
     if (h_labels) {
         const size_t n = (size_t)h.nbx[level] * h.nby[level];
         std::vector<uint16_t> t(n);
-        rc = from_cuda(cudaMemcpy(t.data(), d.lab[level], n * 2, cudaMemcpyDeviceToHost));
+        rc = from_cuda(cudaMemcpy(t.data(), d.lab[level][q], n * 2, cudaMemcpyDeviceToHost));
         if (rc) return rc;
         for (size_t q = 0; q < n; ++q) h_labels[q] = t[q];
     }
     if (h_hist) {
         const size_t n = (size_t)h.K * h.nbins;
         std::vector<int32_t> t(n);
-        rc = from_cuda(cudaMemcpy(t.data(), d.hist, n * 4, cudaMemcpyDeviceToHost));
+        rc = from_cuda(cudaMemcpy(t.data(), d.hist[q], n * 4, cudaMemcpyDeviceToHost));
         if (rc) return rc;
         for (int k = 0; k < h.K; ++k)
             for (int j = 0; j < h.nbins; ++j)
                 h_hist[(size_t)k * h.nbins + j] = d.hist_jmajor ? t[(size_t)j * h.K + k] : t[(size_t)k * h.nbins + j];
     }
     if (h_sizes) {
-        rc = from_cuda(cudaMemcpy(h_sizes, d.size, (size_t)h.K * 4, cudaMemcpyDeviceToHost));
+        rc = from_cuda(cudaMemcpy(h_sizes, d.size[q], (size_t)h.K * 4, cudaMemcpyDeviceToHost));
         if (rc) return rc;
     }
     if (h_bins) {
@@ -831,10 +808,12 @@ int seeds_debug_set_labels(seeds_ctx *c, int32_t i, int32_t level, const int32_t
         t[q] = (uint16_t)h_labels[q];
     }
     int rc = from_cuda(cudaDeviceSynchronize());
-    if (!rc) rc = from_cuda(cudaMemcpy(c->h_imgs[i].lab[level], t.data(), n * 2, cudaMemcpyHostToDevice));
+    for (int q = 0; q < 2 && !rc; ++q)
+        rc = from_cuda(cudaMemcpy(c->h_imgs[i].lab[level][q], t.data(), n * 2, cudaMemcpyHostToDevice));
     if (!rc) rc = from_cuda(launch_recount(c->d_imgs, i, level, h.N, 0));
     if (!rc) rc = from_cuda(cudaDeviceSynchronize());
     c->launches += 2;
+    c->pending[i] = -1;  // the injected state replaces any moves awaiting catch-up
     return rc;
 }
 
@@ -858,7 +837,7 @@ int seeds_profile_enable(seeds_ctx *c, int32_t enable)
     if (enable && !c->d_trace) {
         int most = 0;
         for (auto &h : c->img) most = std::max(most, (int)h.ops.size());
-        c->trace_cap = 1 + 2 * most;
+        c->trace_cap = 1 + most;
         int rc = from_cuda(cudaMalloc((void **)&c->d_trace, sizeof(unsigned long long) * c->trace_cap));
         if (rc) return rc;
     }
@@ -869,7 +848,7 @@ int seeds_profile_enable(seeds_ctx *c, int32_t enable)
 int seeds_profile_steps(seeds_ctx *c, int64_t *h_ns, int32_t cap, int32_t *n)
 {
     if (!c || !n || !c->profiled || c->traced_steps == 0) return SEEDS_ERR_INVALID;
-    const int m = 1 + 2 * c->traced_steps;
+    const int m = 1 + c->traced_steps;
     *n = m;
     if (!h_ns || cap < m) return SEEDS_OK;
     int rc = from_cuda(cudaEventSynchronize(c->ev1));
