@@ -176,6 +176,66 @@ int seeds_run_host(seeds_ctx *c, const uint8_t *const *h_rgb, const int64_t *h_r
 int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t);
 int seeds_get_tuning(const seeds_ctx *c, seeds_tuning *t);
 
+/* Pick the fastest result-invariant knobs for this context's images by
+ * timing candidate settings on them (the labels do not depend on the
+ * choice), apply them, and return them in *best (may be NULL).  Runs
+ * `reps` timed batches per candidate on `stream` and synchronises.  The
+ * inputs are as for seeds_batch_run (device images and label buffers). */
+int seeds_autotune(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides,
+                   int32_t *const *h_label_ptrs, int32_t reps, void *stream, seeds_tuning *best);
+
+/* ---- serving: continuous batching over a device arena ------------------
+ *
+ * The server keeps images resident in slots of one device arena and runs
+ * them in epochs: one persistent launch advances every resident image by up
+ * to epoch_steps of its ops (a step = one parity phase, a descent, the init
+ * or the output of Sec. 5), so an image admitted while others run joins them
+ * at the next epoch.  Requests are admitted first come first served when a
+ * slot is free and their footprint (seeds_footprint plus 7 bytes per pixel
+ * of image and label staging) fits the arena.  Each image's labels are the
+ * same alone or in any mix.  All work runs on the server's own stream. */
+typedef struct seeds_server seeds_server;
+
+typedef struct {
+    int64_t arena_bytes;           /* device memory for resident images (>= 1 MiB) */
+    int32_t max_slots;             /* images resident at once, 1..128 */
+    int32_t epoch_steps;           /* ops per image per launch, 1..1024 */
+    int32_t max_bins_per_channel;  /* largest B a request may use, 1..16 */
+} seeds_server_config;
+
+typedef struct {
+    int32_t queued, resident;
+    int64_t arena_free_bytes;
+    int64_t epochs, launches, admitted;
+    double host_ms;  /* host time since creation, on the clock done_ms uses */
+} seeds_server_stats_t;
+
+int seeds_server_create(const seeds_server_config *cfg, seeds_server **out);
+int seeds_server_destroy(seeds_server *s);
+
+/* Queue one request.  h_rgb: host, H rows of 3*W bytes, row_stride_bytes
+ * apart; h_labels: host int32 H x W that receives the labels.  Both must stay
+ * valid until the request is reported done by seeds_server_poll (pinned
+ * memory makes the copies asynchronous).  *id receives the request id.
+ * SEEDS_ERR_NO_MEMORY if the image could never fit the arena. */
+int seeds_server_submit(seeds_server *s, const seeds_params *p, const uint8_t *h_rgb, int64_t row_stride_bytes,
+                        int32_t *h_labels, int64_t *id);
+
+/* Admit what fits, then launch one epoch over the resident images
+ * (asynchronous; blocks only while two epochs are already queued).
+ * *resident receives the number of images in the epoch (0: nothing to do). */
+int seeds_server_step(seeds_server *s, int32_t *resident);
+
+/* Requests finished since the last call (non-blocking): ids[i] and the
+ * device-side completion time done_ms[i] in ms since the server was created,
+ * for i < *n <= cap. */
+int seeds_server_poll(seeds_server *s, int64_t *ids, float *done_ms, int32_t cap, int32_t *n);
+
+/* Wait for all launched work; report device-side errors as seeds_status. */
+int seeds_server_drain(seeds_server *s);
+
+int seeds_server_stats(const seeds_server *s, seeds_server_stats_t *out);
+
 /* ---- one image without allocating ----------------------------------------
  *
  * The paper has no counterpart to this entry point; it exists for callers

@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libseeds.so")
-SOURCES = ["seeds_kernels.cu", "seeds_runtime.cu"]
+SOURCES = ["seeds_kernels.cu", "seeds_runtime.cu", "seeds_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -38,7 +38,9 @@ EXPORTS = [
     "seeds_batch_labels", "seeds_batch_run", "seeds_run_host", "seeds_set_tuning", "seeds_get_tuning",
     "seeds_debug_num_ops", "seeds_debug_op_info", "seeds_debug_run_ops", "seeds_debug_read_state",
     "seeds_debug_set_labels", "seeds_debug_inject_error", "seeds_debug_launch_count", "seeds_profile_enable",
-    "seeds_profile_last_ms", "seeds_profile_steps", "seeds_run_static",
+    "seeds_profile_last_ms", "seeds_profile_steps", "seeds_run_static", "seeds_autotune",
+    "seeds_server_create", "seeds_server_destroy", "seeds_server_submit", "seeds_server_step", "seeds_server_poll",
+    "seeds_server_drain", "seeds_server_stats",
 ]
 
 
@@ -53,6 +55,17 @@ class seeds_params(ctypes.Structure):
                 ("block_levels", ctypes.c_int32), ("bins_per_channel", ctypes.c_int32),
                 ("iters_per_level", ctypes.c_int32), ("patch", ctypes.c_int32), ("gamma_num", ctypes.c_int32),
                 ("gamma_den", ctypes.c_int32)]
+
+
+class seeds_server_config(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("epoch_steps", ctypes.c_int32),
+                ("max_bins_per_channel", ctypes.c_int32)]
+
+
+class seeds_server_stats_t(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int32), ("resident", ctypes.c_int32), ("arena_free_bytes", ctypes.c_int64),
+                ("epochs", ctypes.c_int64), ("launches", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("host_ms", ctypes.c_double)]
 
 
 class seeds_tuning(ctypes.Structure):
@@ -97,6 +110,14 @@ def _load():
         "seeds_profile_last_ms": [vp, P(ctypes.c_float)],
         "seeds_profile_steps": [vp, vp, i32, P(i32)],
         "seeds_run_static": [P(seeds_params), vp, i64, vp, vp, vp],
+        "seeds_autotune": [vp, P(vp), P(i64), P(vp), i32, vp, P(seeds_tuning)],
+        "seeds_server_create": [P(seeds_server_config), P(vp)],
+        "seeds_server_destroy": [vp],
+        "seeds_server_submit": [vp, P(seeds_params), vp, i64, vp, P(i64)],
+        "seeds_server_step": [vp, P(i32)],
+        "seeds_server_poll": [vp, P(i64), P(ctypes.c_float), i32, P(i32)],
+        "seeds_server_drain": [vp],
+        "seeds_server_stats": [vp, P(seeds_server_stats_t)],
     }
     for name in EXPORTS:
         f = getattr(L, name)
@@ -237,6 +258,14 @@ class SeedsContext:
         t = seeds_tuning(threads_per_block, blocks_per_sm, hist_layout, small_block_area)
         check(lib.seeds_set_tuning(self._h, ctypes.byref(t)), "seeds_set_tuning")
 
+    def autotune(self, images, outs, reps=3, stream=None) -> seeds_tuning:
+        """Time the result-invariant knobs on these inputs and keep the fastest."""
+        rgb, strides = self._rgb_args(images)
+        best = seeds_tuning()
+        check(lib.seeds_autotune(self._h, rgb, strides, _ptrs([t.data_ptr() for t in outs]), reps,
+                                 _stream_handle(stream), ctypes.byref(best)), "seeds_autotune")
+        return best
+
     def get_tuning(self) -> seeds_tuning:
         t = seeds_tuning()
         check(lib.seeds_get_tuning(self._h, ctypes.byref(t)), "seeds_get_tuning")
@@ -300,3 +329,61 @@ class SeedsContext:
 
     def inject_error(self):
         check(lib.seeds_debug_inject_error(self._h), "seeds_debug_inject_error")
+
+
+class Server:
+    """Continuous-batching server (seeds_server_*): host images in, host labels out."""
+
+    def __init__(self, arena_bytes, max_slots=64, epoch_steps=8, max_bins_per_channel=8):
+        cfg = seeds_server_config(int(arena_bytes), int(max_slots), int(epoch_steps), int(max_bins_per_channel))
+        h = ctypes.c_void_p()
+        check(lib.seeds_server_create(ctypes.byref(cfg), ctypes.byref(h)), "seeds_server_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.seeds_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, params: seeds_params, h_rgb, h_labels) -> int:
+        """h_rgb: host uint8 (H, W, 3) tensor or array; h_labels: host int32 (H, W)."""
+        ptr_rgb, stride = _host_ptr_stride(h_rgb)
+        ptr_out, _ = _host_ptr_stride(h_labels)
+        rid = ctypes.c_int64()
+        check(lib.seeds_server_submit(self._h, ctypes.byref(params), ptr_rgb, stride, ptr_out, ctypes.byref(rid)),
+              "seeds_server_submit")
+        return rid.value
+
+    def step(self) -> int:
+        n = ctypes.c_int32()
+        check(lib.seeds_server_step(self._h, ctypes.byref(n)), "seeds_server_step")
+        return n.value
+
+    def poll(self, cap=4096):
+        ids = (ctypes.c_int64 * cap)()
+        ms = (ctypes.c_float * cap)()
+        n = ctypes.c_int32()
+        check(lib.seeds_server_poll(self._h, ids, ms, cap, ctypes.byref(n)), "seeds_server_poll")
+        return [(ids[i], ms[i]) for i in range(n.value)]
+
+    def drain(self):
+        check(lib.seeds_server_drain(self._h), "seeds_server_drain")
+
+    def stats(self) -> seeds_server_stats_t:
+        st = seeds_server_stats_t()
+        check(lib.seeds_server_stats(self._h, ctypes.byref(st)), "seeds_server_stats")
+        return st
+
+
+def _host_ptr_stride(a):
+    """(address, row stride in bytes) of a host tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        assert not a.is_cuda
+        return a.data_ptr(), a.stride(0) * a.element_size()
+    return a.ctypes.data, a.strides[0]

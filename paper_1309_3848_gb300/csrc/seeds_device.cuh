@@ -251,7 +251,24 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
     return n;
 }
 
+// An epoch of the serving runtime: for each resident slot, the range of its
+// ops to run; the device builds the step schedule from it.
+constexpr int kMaxEpochSlots = 128;
+struct EpochSlot {
+    int32_t slot;
+    int32_t begin, end;  // ops [begin, end) of the slot's image
+    int32_t catchup;     // op begin-1's moves are pending
+};
+struct EpochPlan {
+    int32_t n;       // slots in the epoch
+    int32_t nsteps;  // max over slots of end - begin (<= 1024)
+    EpochSlot s[kMaxEpochSlots];
+};
+
 // launch helpers (seeds_kernels.cu)
+cudaError_t launch_admit(DevImage *d_imgs, int slot, const DevImage &rec, cudaStream_t s);
+cudaError_t launch_epoch_schedule(const DevImage *d_imgs, const EpochPlan &plan, StepEntry *ent, int32_t *first,
+                                  int64_t *vt, cudaStream_t s);
 cudaError_t launch_set_io(DevImage *d_imgs, const IoChunk &chunk, cudaStream_t s);
 cudaError_t launch_persistent(const DevImage *d_imgs, const Schedule &sch, GridBarrier *bar, int32_t *err,
                               int grid, int threads, size_t smem, cudaStream_t s);

@@ -906,8 +906,83 @@ __global__ void recount_kernel(const DevImage *imgs, int img, int level, int64_t
 }
 
 // ---------------------------------------------------------------------------
+// serving: install an admitted image, build an epoch's schedule
+// ---------------------------------------------------------------------------
+
+// the slot's record, and the block edge tables of every level
+__global__ void admit_kernel(DevImage *imgs, int slot, DevImage rec)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) imgs[slot] = rec;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (int l = 1; l <= rec.L; ++l) {
+        int32_t *xe = (int32_t *)rec.xe[l], *ye = (int32_t *)rec.ye[l];
+        for (int i = t; i <= rec.nbx[l]; i += nt) xe[i] = (int32_t)((int64_t)i * rec.W / rec.nbx[l]);
+        for (int i = t; i <= rec.nby[l]; i += nt) ye[i] = (int32_t)((int64_t)i * rec.H / rec.nby[l]);
+    }
+}
+
+// One block, a thread per step: count the step's entries, scan, write them.
+__global__ void epoch_schedule_kernel(const DevImage *imgs, EpochPlan plan, StepEntry *ent, int32_t *first,
+                                      int64_t *vt)
+{
+    __shared__ int32_t cnt[1024];
+    const int s = threadIdx.x;
+    StepEntry tmp[2];
+    int c = 0;
+    if (s < plan.nsteps)
+        for (int i = 0; i < plan.n; ++i) {
+            const EpochSlot &q = plan.s[i];
+            const int o = q.begin + s;
+            if (o >= q.end) continue;
+            const DevImage &im = imgs[q.slot];
+            const bool cu = s == 0 ? q.catchup != 0 : op_at(im.L, im.iters, o - 1).kind == OP_PHASE;
+            int64_t v = 0;
+            c += emit_entries(im, q.slot, o, cu, tmp, &v);
+        }
+    cnt[s] = c;
+    __syncthreads();
+    if (s == 0) {  // exclusive scan over the steps (at most 1024)
+        int acc = 0;
+        for (int t = 0; t < plan.nsteps; ++t) {
+            const int v = cnt[t];
+            cnt[t] = acc;
+            acc += v;
+        }
+        first[plan.nsteps] = acc;
+    }
+    __syncthreads();
+    if (s >= plan.nsteps) return;
+    int e = cnt[s];
+    first[s] = e;
+    int64_t v = 0;
+    for (int i = 0; i < plan.n; ++i) {
+        const EpochSlot &q = plan.s[i];
+        const int o = q.begin + s;
+        if (o >= q.end) continue;
+        const DevImage &im = imgs[q.slot];
+        const bool cu = s == 0 ? q.catchup != 0 : op_at(im.L, im.iters, o - 1).kind == OP_PHASE;
+        e += emit_entries(im, q.slot, o, cu, ent + e, &v);
+    }
+    vt[s] = v;
+}
+
+// ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
+
+cudaError_t launch_admit(DevImage *d_imgs, int slot, const DevImage &rec, cudaStream_t s)
+{
+    admit_kernel<<<4, 256, 0, s>>>(d_imgs, slot, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_epoch_schedule(const DevImage *d_imgs, const EpochPlan &plan, StepEntry *ent, int32_t *first,
+                                  int64_t *vt, cudaStream_t s)
+{
+    if (plan.nsteps < 1 || plan.nsteps > 1024) return cudaErrorInvalidValue;
+    epoch_schedule_kernel<<<1, 1024, 0, s>>>(d_imgs, plan, ent, first, vt);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_set_io(DevImage *d_imgs, const IoChunk &chunk, cudaStream_t s)
 {

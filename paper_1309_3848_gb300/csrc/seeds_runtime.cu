@@ -15,145 +15,18 @@
 
 #include "seeds.h"
 #include "seeds_device.cuh"
+#include "seeds_host.h"
 
 using namespace seeds;
 
+using namespace seeds::host;
+
 namespace {
-
-struct Op {
-    int kind, level, phase;
-};
-
-struct ImageHost {
-    seeds_params p{};
-    int gx = 0, gy = 0, K = 0, L = 0, B = 0, nbins = 0;
-    int64_t N = 0;
-    int nbx[kMaxLevels + 1] = {}, nby[kMaxLevels + 1] = {};
-    std::vector<int32_t> xe[kMaxLevels + 1], ye[kMaxLevels + 1];
-    int maxarea[kMaxLevels + 1] = {};
-    std::vector<Op> ops;  // full list, output op last
-    int units_cap = 0;
-    // byte offsets inside the context's pool
-    size_t off_bins = 0, off_lab[kMaxLevels + 1][2] = {}, off_xe[kMaxLevels + 1] = {}, off_ye[kMaxLevels + 1] = {};
-    size_t off_hist[2] = {}, off_size[2] = {}, off_dec[2] = {}, bytes = 0;
-};
 
 struct DevSchedule {
     void *buf = nullptr;
     Schedule s{};
 };
-
-constexpr size_t kAlign = 256;
-size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
-
-int from_cuda(cudaError_t e)
-{
-    if (e == cudaSuccess) return SEEDS_OK;
-    if (e == cudaErrorMemoryAllocation) return SEEDS_ERR_NO_MEMORY;
-    return SEEDS_ERR_CUDA;
-}
-
-// Validate one image's parameters and derive its grid (gx, gy) and block
-// levels: gx = max(1, round(sqrt(K*W/H))), gy = max(1, round(K/gx)), level-l
-// edges floor(i*W/(gx*2^(L-l+1))) (Sec. 5.1).  Checks the int64 bound of the
-// exact compares.  Fills the host image record when `g` is given.
-int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t *gy_out)
-{
-    if (!p) return SEEDS_ERR_INVALID;
-    if (p->width < 1 || p->height < 1 || p->width > 32768 || p->height > 32768) return SEEDS_ERR_INVALID;
-    const int64_t N = (int64_t)p->width * p->height;
-    if (N > 0x7fffffffLL) return SEEDS_ERR_INVALID;
-    if (p->num_superpixels < 1) return SEEDS_ERR_INVALID;
-    if (p->block_levels < 0 || p->block_levels > kMaxLevels) return SEEDS_ERR_INVALID;
-    if (p->bins_per_channel < 1 || p->bins_per_channel > 16) return SEEDS_ERR_INVALID;
-    if (p->iters_per_level < 1 || p->iters_per_level > 1000) return SEEDS_ERR_INVALID;
-    if (p->patch != 0 && p->patch != 3) return SEEDS_ERR_INVALID;
-    if (p->gamma_num < 0 || p->gamma_num > 1024 || p->gamma_den < 1 || p->gamma_den > 1024) return SEEDS_ERR_INVALID;
-    const double Kd = p->num_superpixels, Wd = p->width, Hd = p->height;
-    long long gx = std::llround(std::sqrt(Kd * Wd / Hd));
-    if (gx < 1) gx = 1;
-    long long gy = std::llround(Kd / (double)gx);
-    if (gy < 1) gy = 1;
-    if (gx * gy > 65535) return SEEDS_ERR_INVALID;  // labels are 16-bit
-    if (gx_out) *gx_out = (int32_t)gx;
-    if (gy_out) *gy_out = (int32_t)gy;
-    const int L = p->block_levels;
-    if ((gx << L) > p->width || (gy << L) > p->height) return SEEDS_ERR_GEOMETRY;
-
-    ImageHost local;
-    ImageHost &h = g ? *g : local;
-    h.p = *p;
-    h.gx = (int)gx;
-    h.gy = (int)gy;
-    h.K = (int)(gx * gy);
-    h.L = L;
-    h.B = p->bins_per_channel;
-    h.nbins = h.B * h.B * h.B;
-    h.N = N;
-    h.nbx[0] = p->width;
-    h.nby[0] = p->height;
-    h.maxarea[0] = 1;
-    int amax = 1;
-    for (int l = 1; l <= L; ++l) {
-        h.nbx[l] = (int)(gx << (L - l + 1));
-        h.nby[l] = (int)(gy << (L - l + 1));
-        h.xe[l].resize(h.nbx[l] + 1);
-        h.ye[l].resize(h.nby[l] + 1);
-        int mw = 0, mh = 0;
-        for (int i = 0; i <= h.nbx[l]; ++i) {
-            h.xe[l][i] = (int32_t)((int64_t)i * p->width / h.nbx[l]);
-            if (i) mw = std::max(mw, h.xe[l][i] - h.xe[l][i - 1]);
-        }
-        for (int i = 0; i <= h.nby[l]; ++i) {
-            h.ye[l][i] = (int32_t)((int64_t)i * p->height / h.nby[l]);
-            if (i) mh = std::max(mh, h.ye[l][i] - h.ye[l][i - 1]);
-        }
-        h.maxarea[l] = mw * mh;
-        amax = std::max(amax, mw * mh);
-    }
-    // exact int64 compares: block products reach |L|max*N^2, pixel products
-    // (81*gamma_den + 90*gamma_num)*N^2
-    const __int128 N2 = (__int128)N * N;
-    const __int128 lim = ((__int128)1) << 63;
-    if ((__int128)amax * N2 >= lim) return SEEDS_ERR_INT64;
-    if ((__int128)(81 * p->gamma_den + 90 * p->gamma_num) * N2 >= lim) return SEEDS_ERR_INT64;
-
-    // op list (the same one the kernels derive with op_at)
-    h.ops.clear();
-    const int nops = num_ops(L, p->iters_per_level);
-    for (int o = 0; o < nops; ++o) {
-        const OpDesc d = op_at(L, p->iters_per_level, o);
-        h.ops.push_back({d.kind, d.level, d.phase});
-    }
-    h.units_cap = (int)(((int64_t)(p->width + 1) / 2) * ((p->height + 1) / 2));
-
-    // device layout: bins, then two buffers of every label grid, histogram,
-    // size vector and decision array
-    size_t off = 0;
-    h.off_bins = off;
-    off = align_up(off + (size_t)N * (h.nbins > 256 ? 2 : 1));
-    for (int l = 0; l <= L; ++l)
-        for (int q = 0; q < 2; ++q) {
-            h.off_lab[l][q] = off;
-            off = align_up(off + (size_t)h.nbx[l] * h.nby[l] * 2);
-        }
-    for (int l = 1; l <= L; ++l) {
-        h.off_xe[l] = off;
-        off = align_up(off + (h.nbx[l] + 1) * 4);
-        h.off_ye[l] = off;
-        off = align_up(off + (h.nby[l] + 1) * 4);
-    }
-    for (int q = 0; q < 2; ++q) {
-        h.off_hist[q] = off;
-        off = align_up(off + (size_t)h.K * h.nbins * 4);
-        h.off_size[q] = off;
-        off = align_up(off + (size_t)h.K * 4);
-        h.off_dec[q] = off;
-        off = align_up(off + (size_t)h.units_cap * 4);
-    }
-    h.bytes = off;
-    return SEEDS_OK;
-}
 
 }  // namespace
 
@@ -215,50 +88,10 @@ int configure_launch(seeds_ctx *c)
 void fill_dev_images(seeds_ctx *c)
 {
     c->h_imgs.resize(c->img.size());
+    unsigned char *base = c->pool;
     for (size_t i = 0; i < c->img.size(); ++i) {
-        const ImageHost &h = c->img[i];
-        DevImage d;
-        std::memset(&d, 0, sizeof(d));
-        d.W = h.p.width;
-        d.H = h.p.height;
-        d.K = h.K;
-        d.gx = h.gx;
-        d.gy = h.gy;
-        d.L = h.L;
-        d.iters = h.p.iters_per_level;
-        d.B = h.B;
-        d.nbins = h.nbins;
-        d.patch = h.p.patch;
-        d.gnum = h.p.gamma_num;
-        d.gden = h.p.gamma_den;
-        d.bins16 = h.nbins > 256;
-        d.hist_jmajor = c->tune.hist_layout == 1;
-        d.hist_sk = d.hist_jmajor ? 1 : h.nbins;
-        d.hist_sj = d.hist_jmajor ? h.K : 1;
-        d.small_area = c->tune.small_block_area;
-        unsigned char *base = c->pool;
-        for (size_t t = 0; t < i; ++t) base += c->img[t].bytes;
-        for (int l = 0; l <= h.L; ++l) {
-            d.nbx[l] = h.nbx[l];
-            d.nby[l] = h.nby[l];
-            d.maxarea[l] = h.maxarea[l];
-            for (int q = 0; q < 2; ++q) d.lab[l][q] = (uint16_t *)(base + h.off_lab[l][q]);
-            if (l >= 1) {
-                d.xe[l] = (const int32_t *)(base + h.off_xe[l]);
-                d.ye[l] = (const int32_t *)(base + h.off_ye[l]);
-            }
-        }
-        d.bins = base + h.off_bins;
-        for (int q = 0; q < 2; ++q) {
-            d.hist[q] = (int32_t *)(base + h.off_hist[q]);
-            d.size[q] = (int32_t *)(base + h.off_size[q]);
-            d.dec[q] = (uint32_t *)(base + h.off_dec[q]);
-        }
-        d.units_cap = h.units_cap;
-        d.rgb = c->io[i].rgb;
-        d.stride = c->io[i].stride;
-        d.out = c->io[i].out;
-        c->h_imgs[i] = d;
+        c->h_imgs[i] = make_dev_image(c->img[i], base, c->tune, c->io[i]);
+        base += c->img[i].bytes;
     }
 }
 
@@ -703,13 +536,73 @@ int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t)
     if (n.blocks_per_sm < 0 || n.hist_layout < 0 || n.hist_layout > 1) return SEEDS_ERR_INVALID;
     if (n.small_block_area < 1 || n.small_block_area > 16) return SEEDS_ERR_INVALID;
     if (c->launched) cudaEventSynchronize(c->done);
-    c->tune = n;
-    free_schedules(c);
-    fill_dev_images(c);
-    int rc = from_cuda(cudaMemcpy(c->d_imgs, c->h_imgs.data(), sizeof(DevImage) * c->img.size(),
-                                  cudaMemcpyHostToDevice));
-    if (rc) return rc;
-    return configure_launch(c);
+    const seeds_tuning old = c->tune;
+    auto apply = [&](const seeds_tuning &v) {
+        c->tune = v;
+        free_schedules(c);
+        fill_dev_images(c);
+        int rc = from_cuda(cudaMemcpy(c->d_imgs, c->h_imgs.data(), sizeof(DevImage) * c->img.size(),
+                                      cudaMemcpyHostToDevice));
+        return rc ? rc : configure_launch(c);
+    };
+    const int rc = apply(n);
+    if (rc) apply(old);  // a setting that cannot launch leaves the context as it was
+    return rc;
+}
+
+int seeds_autotune(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides,
+                   int32_t *const *h_label_ptrs, int32_t reps, void *stream, seeds_tuning *best)
+{
+    if (!c || reps < 1) return SEEDS_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    int rc = from_cuda(cudaEventCreate(&a));
+    if (!rc) rc = from_cuda(cudaEventCreate(&b));
+    // best-of-reps time of one batch under a setting; +inf if it cannot run
+    auto time_it = [&](const seeds_tuning &t, float *ms) -> int {
+        *ms = 1e30f;
+        if (seeds_set_tuning(c, &t) != SEEDS_OK) return SEEDS_OK;
+        int r = seeds_batch_run(c, h_rgb_ptrs, h_row_strides, h_label_ptrs, stream);
+        for (int i = 0; i < reps && !r; ++i) {
+            r = from_cuda(cudaEventRecord(a, st));
+            if (!r) r = seeds_batch_run(c, h_rgb_ptrs, h_row_strides, h_label_ptrs, stream);
+            if (!r) r = from_cuda(cudaEventRecord(b, st));
+            if (!r) r = from_cuda(cudaEventSynchronize(b));
+            float e = 0.f;
+            if (!r) r = from_cuda(cudaEventElapsedTime(&e, a, b));
+            if (!r) *ms = std::min(*ms, e);
+        }
+        return r;
+    };
+    seeds_tuning cur = c->tune;
+    float cur_ms = 0.f;
+    if (!rc) rc = time_it(cur, &cur_ms);
+    // coordinate descent, one pass over the knobs; a change must win by 2%
+    const int threads[] = {128, 256, 512}, blocks[] = {0, 1, 2, 3}, layouts[] = {0, 1}, areas[] = {4, 9, 16};
+    for (int knob = 0; knob < 4 && !rc; ++knob) {
+        const int *vals = knob == 0 ? threads : knob == 1 ? blocks : knob == 2 ? layouts : areas;
+        const int nv = knob == 0 ? 3 : knob == 1 ? 4 : knob == 2 ? 2 : 3;
+        for (int v = 0; v < nv && !rc; ++v) {
+            seeds_tuning t = cur;
+            int *field = knob == 0 ? &t.threads_per_block
+                         : knob == 1 ? &t.blocks_per_sm
+                         : knob == 2 ? &t.hist_layout
+                                     : &t.small_block_area;
+            if (*field == vals[v]) continue;
+            *field = vals[v];
+            float ms = 0.f;
+            rc = time_it(t, &ms);
+            if (!rc && ms < 0.98f * cur_ms) {
+                cur = t;
+                cur_ms = ms;
+            }
+        }
+    }
+    if (!rc) rc = seeds_set_tuning(c, &cur);
+    if (!rc && best) *best = cur;
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return rc;
 }
 
 int seeds_get_tuning(const seeds_ctx *c, seeds_tuning *t)

@@ -1,0 +1,113 @@
+"""Serving driver: a timed request stream through the continuous-batching
+server of libseeds.so (seeds_server_*).
+
+The server (native code) owns the device arena, the admission queue and the
+epoch launches; this module only releases requests at their arrival times,
+calls the server, and turns its completion times into latencies.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from typing import Dict, List, Sequence, Tuple
+
+import numpy as np
+
+from . import binding, synth
+
+
+@dataclasses.dataclass
+class StreamResult:
+    latency_ms: np.ndarray      # per request, completion - scheduled arrival
+    makespan_ms: float          # first arrival to last completion
+    pixels: int
+    labels: List[np.ndarray]    # per request, as returned by the server
+    max_resident: int
+    epochs: int
+
+    @property
+    def mpix_per_s(self) -> float:
+        return self.pixels / (self.makespan_ms / 1e3) / 1e6
+
+    def percentile(self, q: float) -> float:
+        return float(np.percentile(self.latency_ms, q))
+
+
+def job_params(job: synth.JobSpec) -> binding.seeds_params:
+    """Parameters of a job, its levels clamped to what its grid allows."""
+    L = job.levels
+    if job.clamp_levels:
+        L = min(L, binding.feasible_levels(job.image.width, job.image.height, job.num_superpixels))
+    return binding.make_params(job.image.width, job.image.height, job.num_superpixels, L, job.bins_per_channel,
+                               job.iters_per_level, job.patch, job.gamma)
+
+
+def run_stream(requests: Sequence[Tuple[float, synth.JobSpec]], images: Sequence, arena_bytes: int,
+               max_slots: int = 64, epoch_steps: int = 8, max_bins_per_channel: int = 8,
+               pinned: bool = True) -> StreamResult:
+    """Serve `requests` (arrival time in s, job) whose host images are
+    `images` (uint8 HxWx3, one per request).  Arrivals are released in real
+    time on the server's clock."""
+    import torch  # pinned host buffers
+
+    srv = binding.Server(arena_bytes, max_slots, epoch_steps, max_bins_per_channel)
+    n = len(requests)
+    outs, srcs = [], []
+    for (_, job), img in zip(requests, images):
+        t = torch.from_numpy(np.ascontiguousarray(img))
+        o = torch.empty((job.image.height, job.image.width), dtype=torch.int32)
+        if pinned:
+            t, o = t.pin_memory(), o.pin_memory()
+        srcs.append(t)
+        outs.append(o)
+    params = [job_params(job) for _, job in requests]
+    start = srv.stats().host_ms
+    arrival = np.array([start + 1e3 * a for a, _ in requests])
+    id_to_req: Dict[int, int] = {}
+    done_ms = np.full(n, np.nan)
+    submitted = finished = 0
+    max_res = 0
+    while finished < n:
+        now = srv.stats().host_ms
+        while submitted < n and arrival[submitted] <= now:
+            rid = srv.submit(params[submitted], srcs[submitted], outs[submitted])
+            id_to_req[rid] = submitted
+            submitted += 1
+        resident = srv.step()
+        max_res = max(max_res, resident)
+        for rid, ms in srv.poll():
+            done_ms[id_to_req[rid]] = ms
+            finished += 1
+        if resident == 0 and submitted < n and finished == submitted:
+            # idle until the next arrival
+            wait = (arrival[submitted] - srv.stats().host_ms) / 1e3
+            if wait > 0:
+                time.sleep(min(wait, 0.002))
+    srv.drain()
+    st = srv.stats()
+    srv.close()
+    lat = done_ms - arrival
+    return StreamResult(latency_ms=lat, makespan_ms=float(np.nanmax(done_ms) - arrival[0]),
+                        pixels=sum(job.pixels for _, job in requests), labels=[o.numpy() for o in outs],
+                        max_resident=max_res, epochs=int(st.epochs))
+
+
+def image_pool(sizes: Sequence[Tuple[int, int]], per_size: int, seed: int) -> Dict[Tuple[int, int], List[np.ndarray]]:
+    """Seeded Voronoi+noise images (cells = pixels/2000, sigma 8), a few per
+    size; serving requests draw their content from this pool."""
+    rng = np.random.default_rng(seed)
+    pool = {}
+    for (W, H) in sizes:
+        pool[(W, H)] = [synth.make_image(synth.ImageSpec(W, H, seed=int(rng.integers(0, 2**31)),
+                                                         cells=max(1, W * H // 2000), sigma=8.0))
+                        for _ in range(per_size)]
+    return pool
+
+
+def stream_images(requests, pool) -> List[np.ndarray]:
+    """The pool image each request's seed selects."""
+    out = []
+    for _, job in requests:
+        imgs = pool[(job.image.width, job.image.height)]
+        out.append(imgs[job.image.seed % len(imgs)])
+    return out

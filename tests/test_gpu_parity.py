@@ -295,3 +295,36 @@ def test_launch_count(torch, binding):
     ctx.run([img], [out])
     ctx.check_status()
     assert ctx.launch_count() - n0 == 2  # pointer upload + one persistent kernel
+
+
+def test_autotune_keeps_labels(torch, binding):
+    jobs = synth.plain_481() + synth.random_small_jobs(31, 5, max_side=120)
+    imgs = gc.make_images(jobs)
+    ctx = binding.SeedsContext([gc.params_for(binding, j) for j in jobs])
+    d = [torch.from_numpy(im).cuda() for im in imgs]
+    outs = [torch.empty((j.image.height, j.image.width), dtype=torch.int32, device="cuda") for j in jobs]
+    best = ctx.autotune(d, outs, reps=2)
+    assert best.threads_per_block in (128, 256, 512)
+    t = ctx.get_tuning()
+    assert (t.threads_per_block, t.blocks_per_sm, t.hist_layout, t.small_block_area) == \
+        (best.threads_per_block, best.blocks_per_sm, best.hist_layout, best.small_block_area)
+    for o in outs:
+        o.fill_(-1)
+    ctx.run(d, outs)
+    ctx.check_status()
+    want = gc.oracle_many(jobs, imgs)
+    for o, w in zip(outs, want):
+        assert np.array_equal(o.cpu().numpy(), w)
+
+
+def test_set_tuning_that_cannot_launch_leaves_context_usable(torch, binding):
+    # 4096 bins: 512-thread blocks need more shared memory than a block may have
+    job = synth.JobSpec(synth.ImageSpec(64, 64, seed=6, cells=6, sigma=20.0), 4, 16, 2, 2)
+    ctx = binding.SeedsContext([gc.params_for(binding, job)])
+    before = ctx.get_tuning()
+    with pytest.raises(binding.SeedsError):
+        ctx.set_tuning(threads_per_block=512)
+    after = ctx.get_tuning()
+    assert after.threads_per_block == before.threads_per_block
+    got, _ = gc.gpu_run(binding, torch, [job], [synth.make_image(job.image)])
+    assert np.array_equal(got[0], gc.oracle_run(job, synth.make_image(job.image)))

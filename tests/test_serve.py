@@ -1,0 +1,81 @@
+"""Serving (continuous batching): requests of different sizes arrive while
+others run; each one's labels must equal the same request run alone and the
+oracle's (integer labels: tolerance 0)."""
+import numpy as np
+import pytest
+
+import gpu_cases as gc
+from paper_1309_3848_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def serve(torch):
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1309_3848_gb300 import serve as s
+    return s
+
+
+def mixed_requests(seed, n, rate):
+    rng = np.random.default_rng(seed)
+    sizes = [(64, 48), (97, 61), (160, 120), (320, 240), (200, 33)]
+    out, t = [], 0.0
+    for i in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        W, H = sizes[int(rng.integers(0, len(sizes)))]
+        K = int(rng.integers(8, max(9, W * H // 150)))
+        B = int(rng.choice([3, 5, 8]))
+        img = synth.ImageSpec(W, H, seed=int(rng.integers(0, 2**31)), cells=max(2, W * H // 800), sigma=8.0)
+        out.append((t, synth.JobSpec(img, K, B, 3, int(rng.integers(1, 3)), clamp_levels=True)))
+    return out
+
+
+def test_served_labels_equal_alone_and_oracle(torch, serve):
+    from paper_1309_3848_gb300 import binding
+    reqs = mixed_requests(5, 24, rate=2000.0)
+    imgs = [synth.make_image(j.image) for _, j in reqs]
+    # a small arena and few slots: requests queue, overlap and reuse memory
+    res = serve.run_stream(reqs, imgs, arena_bytes=8 << 20, max_slots=4, epoch_steps=4)
+    assert res.max_resident > 1
+    assert res.epochs > 1
+    want = gc.oracle_many([j for _, j in reqs], imgs)
+    for i, ((_, job), img) in enumerate(zip(reqs, imgs)):
+        assert gc.first_mismatch(res.labels[i], want[i]) is None, "request %d" % i
+        alone, _ = gc.gpu_run(binding, torch, [job], [img])
+        assert np.array_equal(alone[0], res.labels[i])
+    assert np.all(np.isfinite(res.latency_ms)) and np.all(res.latency_ms >= 0)
+
+
+def test_arena_bounds_residency(torch, serve):
+    from paper_1309_3848_gb300 import binding
+    # one 320x240 request's footprint plus a little: only one fits at a time
+    job = synth.JobSpec(synth.ImageSpec(320, 240, seed=9, cells=40, sigma=8.0), 300, 5, 3, 1)
+    one = binding.footprint([serve.job_params(job)]) + 320 * 240 * 7 + (1 << 16)
+    reqs = [(0.0, job)] * 3
+    img = synth.make_image(job.image)
+    res = serve.run_stream(reqs, [img] * 3, arena_bytes=max(one, 1 << 20), max_slots=8, epoch_steps=64)
+    assert res.max_resident == 1
+    for lab in res.labels[1:]:
+        assert np.array_equal(lab, res.labels[0])
+
+
+def test_request_too_large_for_the_arena_is_refused(torch, serve):
+    from paper_1309_3848_gb300 import binding
+    srv = binding.Server(1 << 20, 2, 4, 5)
+    job = synth.JobSpec(synth.ImageSpec(640, 480, seed=1, cells=10, sigma=8.0), 100, 5, 2, 1)
+    img = np.zeros((480, 640, 3), np.uint8)
+    out = np.zeros((480, 640), np.int32)
+    with pytest.raises(binding.SeedsError) as e:
+        srv.submit(serve.job_params(job), img, out)
+    assert e.value.code == binding.SEEDS_ERR_NO_MEMORY
+    srv.close()
