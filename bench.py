@@ -38,8 +38,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gseeds", choices=["gseeds", "reference"])
-    ap.add_argument("--workload", default="plain_1920x1080")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched comparison and the CPU baseline")
+    ap.add_argument("--workload", default="plain_1920x1080",
+                    help="plain_481x321 | plain_1920x1080 | batch64_mixed | batch16_3840x2160 | serve_poisson")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window per rate (serve_poisson)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched comparison, the serving sample and the CPU baseline")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch knobs")
     return ap.parse_args()
 
 
@@ -300,6 +304,55 @@ def batched_vs_plain(torch, binding, flush, steps=5):
             "batched_over_plain": vb / vp, "labels_identical": bool(same)}
 
 
+def serve_requests(rate, seconds, seed, max_requests=4000):
+    from paper_1309_3848_gb300 import synth
+    return synth.serve_requests(rate, seconds, seed, max_requests=max_requests)
+
+
+def serve_sample(rates, seconds, per_size=3, arena_gib=8, epoch_steps=16):
+    """Poisson request streams (sizes 320x240..3840x2160, 200..5000
+    superpixels) through the continuous-batching server: latency
+    percentiles from each request's scheduled arrival to its completion,
+    and throughput over the stream."""
+    from paper_1309_3848_gb300 import serve, synth
+    pool = serve.image_pool(synth.IMAGE_SIZES_SERVE, per_size, seed=4)
+    out = []
+    for i, rate in enumerate(rates):
+        reqs = serve_requests(rate, seconds, seed=40 + i)
+        if not reqs:
+            continue
+        res = serve.run_stream(reqs, serve.stream_images(reqs, pool), arena_bytes=arena_gib << 30, max_slots=128,
+                               epoch_steps=epoch_steps, max_bins_per_channel=5)
+        out.append({"rate_req_s": rate, "requests": len(reqs), "mpix_s": res.mpix_per_s,
+                    "p50_ms": res.percentile(50), "p99_ms": res.percentile(99), "max_resident": res.max_resident,
+                    "epochs": res.epochs, "arrival_window_s": seconds})
+    return out
+
+
+def run_serve(args):
+    """The serving workload: Poisson streams at 100..2000 req/s."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import __graft_entry__
+    __graft_entry__.build_library()
+    rates = (100.0, 250.0, 500.0, 1000.0, 2000.0)
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    served = serve_sample(rates, seconds=args.serve_seconds)
+    clocks = sampler.stop()
+    top = served[-1]
+    line = {"metric": METRIC, "value": top["mpix_s"], "unit": UNIT, "n_gpus": 1, "steps": len(served),
+            "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "serve_poisson", "rates_req_s": list(rates),
+                       "arrival_window_s": args.serve_seconds, "sizes": "320x240..3840x2160",
+                       "superpixels": "200..5000", "bins_per_channel": 5, "iters_per_level": 2},
+            "served": served, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -328,6 +381,11 @@ def run_gpu(args):
     def step():
         ctx.run(d, outs)
 
+    tuned = None
+    if not args.no_autotune:  # result-invariant knobs, picked before the timed region
+        t = ctx.autotune(d, outs, reps=3)
+        tuned = {"threads_per_block": t.threads_per_block, "blocks_per_sm": t.blocks_per_sm,
+                 "hist_layout": t.hist_layout, "small_block_area": t.small_block_area}
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -395,7 +453,7 @@ def run_gpu(args):
         "config": config_of(args.workload, jobs, {
             "l2": "flushed before every step (256 MiB write)",
             "superpixels_actual": ctx.num_superpixels if len(jobs) > 1 else ctx.num_superpixels[0],
-            "parallelism": "replicas" if world > 1 else "single GPU"}),
+            "parallelism": "replicas" if world > 1 else "single GPU", "tuning": tuned}),
         "roofline": {"bound": "hbm", "kernel": "seeds_persistent", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": bytes_min, "kernel_ms": kms,
@@ -408,6 +466,7 @@ def run_gpu(args):
     }
     if world == 1 and not args.no_extras:
         line["batched"] = batched_vs_plain(torch, binding, flush)
+        line["served"] = serve_sample(rates=(500.0, 2000.0), seconds=1.0)
         gpu_labels = [o.cpu().numpy() for o in outs]
         v, cores, sample, ref_labels = cpu_sample(jobs, imgs)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -424,6 +483,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve_poisson":
+        run_serve(args)
     else:
         run_gpu(args)
 
