@@ -211,8 +211,16 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    jobs = workload_jobs(args.workload)
-    imgs = make_images(jobs)
+    if args.workload == "serve_poisson":
+        # a bounded sample of the request stream (about 25 requests)
+        from paper_1309_3848_gb300 import serve, synth
+        reqs = synth.serve_requests(500.0, 0.05, seed=40)
+        pool = serve.image_pool(synth.IMAGE_SIZES_SERVE, 3, seed=4)
+        jobs = [j for _, j in reqs]
+        imgs = serve.stream_images(reqs, pool)
+    else:
+        jobs = workload_jobs(args.workload)
+        imgs = make_images(jobs)
     cores = min(os.cpu_count() or 1, len(jobs))
     px = sum(j.pixels for j in jobs)
 
@@ -353,6 +361,18 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def reduce_over_ranks(total_ms, launches, device):
+    """Replicas share nothing but this: the slowest rank's timed region
+    (the job's time) and the kernel launches of all ranks."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms, float(launches)], device=device, dtype=torch.float64)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), int(t[1])
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -408,11 +428,7 @@ def run_gpu(args):
 
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms, float(launches)], device="cuda", dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms, launches = float(tmax[0]), int(t[1])
+        total_ms, launches = reduce_over_ranks(total_ms, launches, "cuda")
     ms_per_step = total_ms / args.steps
     value = world * px * args.steps / (total_ms / 1e3) / 1e6
 

@@ -260,7 +260,7 @@ int seeds_server_stats(const seeds_server *s, seeds_server_stats_t *out);
  *
  * Returns SEEDS_ERR_STATIC_SIZE, without launching anything, when the
  * image's state does not fit the array (about 4 Mpixel at 5 bins per
- * channel; a 1920x1080 image with 1000 superpixels needs about 11.5 MiB),
+ * channel; a 1920x1080 image with 1000 superpixels needs about 17 MiB),
  * and the usual codes for bad parameters.  The first call on each device
  * looks up the array's device address (with that device current) and
  * caches it; make that first call before any stream capture.  All calls
