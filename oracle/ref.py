@@ -54,6 +54,10 @@ def lib():
             L.ref_run_phase.restype = i64
             L.ref_run.argtypes = [vp, vp, i64]
             L.ref_run.restype = i64
+            L.ref_run_ops.argtypes = [vp, vp, i64, i32]
+            L.ref_run_ops.restype = i64
+            L.ref_num_ops.argtypes = [vp]
+            L.ref_num_ops.restype = i32
             L.ref_get_labels.argtypes = [vp, vp]
             L.ref_get_labels.restype = None
             L.ref_get_bins.argtypes = [vp, vp]
@@ -156,6 +160,20 @@ class Ref:
         n = lib().ref_run(self._h, rgb.ctypes.data, stride)
         if n < 0:
             raise OracleError(n, "ref_run")
+        self.total_moves = n
+        return self.labels()
+
+    def num_ops(self):
+        """Ops of the schedule: init, per block level 4*iters phases and a
+        descent, 4*iters pixel phases, the output (Sec. 5.4 reading R15)."""
+        return int(lib().ref_num_ops(self._h))
+
+    def run_ops(self, rgb, nops):
+        """Anytime termination: the partition after the first nops ops."""
+        rgb, stride = _rgb_arg(rgb)
+        n = lib().ref_run_ops(self._h, rgb.ctypes.data, stride, int(nops))
+        if n < 0:
+            raise OracleError(n, "ref_run_ops")
         self.total_moves = n
         return self.labels()
 

@@ -55,6 +55,10 @@
  *       G_x = sum_{i in K_p} b_{N_i}(x) in counts (Prop. 2); blocks use the
  *       intersection alone (no G, Sec. 5.3).
  *   R13 K_p and N_i contain in-image pixels only.
+ *   R15 anytime termination (Sec. 5.4): stopping after the first n ops of
+ *       the schedule (init; per block level its phases and a descent; the
+ *       pixel phases; the output) yields the partition as it stands, each
+ *       pixel labelled by its unit at the current level.
  *   R14 sequential mode (quality reference only): per iteration the units
  *       are visited in a random permutation (SplitMix64 + Fisher-Yates),
  *       each boundary unit proposes one uniformly drawn candidate, and an
@@ -542,6 +546,35 @@ int64_t ref_run(ref_state *st, const uint8_t *rgb, int64_t row_stride)
             for (int phase = 0; phase < 4; ++phase) total += ref_run_phase(st, level, phase);
     return total;
 }
+
+/* R15 anytime termination (Sec. 5.4): the schedule as a list of ops -- the
+ * initialisation, then for each level L..1 its 4*iters phases and the
+ * descent to the next finer level, then the 4*iters pixel phases, then the
+ * output -- run only up to its first `nops` ops (nops >= 1).  Blocks move
+ * their pixels whole here, so descents and the output leave the pixel
+ * labels as they are, and the partition after any prefix is the pixel
+ * labels.  Returns the number of accepted moves. */
+int64_t ref_run_ops(ref_state *st, const uint8_t *rgb, int64_t row_stride, int32_t nops)
+{
+    if (nops < 1) return REF_EINVAL;
+    int rc = ref_init(st, rgb, row_stride);
+    if (rc) return rc;
+    int64_t total = 0;
+    int32_t done = 1; /* the initialisation */
+    for (int level = st->L; level >= 0; --level) {
+        for (int it = 0; it < st->p.iters_per_level; ++it)
+            for (int phase = 0; phase < 4; ++phase) {
+                if (done >= nops) return total;
+                total += ref_run_phase(st, level, phase);
+                ++done;
+            }
+        ++done; /* the descent to level-1, or after level 0 the output */
+    }
+    return total;
+}
+
+/* number of ops in the schedule of R15 */
+int32_t ref_num_ops(const ref_state *st) { return 1 + (st->L + 1) * (4 * st->p.iters_per_level + 1); }
 
 /* ------------------------------------------------------------------ */
 /* state access                                                         */

@@ -25,6 +25,8 @@ MUTANTS = {
     "bin order B-major": ("br * B * B + bg * B + bb", "bb * B * B + bg * B + br"),
     "size not decremented on a move": ("            st->size[k] -= 1;\n", "\n"),
     "ties go to the largest label": ("if (!(diff > 0)) continue;", "if (diff < 0) continue;"),
+    "anytime prefix skips the descent op": ("        ++done; /* the descent", "        /* the descent"),
+    "anytime prefix runs one phase too many": ("if (done >= nops) return total;", "if (done > nops) return total;"),
 }
 
 

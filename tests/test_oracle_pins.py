@@ -507,3 +507,69 @@ def test_a_move_that_splits_its_superpixel_is_refused():
     r = constructed_state(lab, [1], (x0, y0))
     assert r.decide(0, x0, y0) == 1
     assert r.decide(1, x0, y0) == 1
+
+
+# --------------------------------------------------------------------------
+# anytime termination (Sec. 5.4, reading R15)
+# --------------------------------------------------------------------------
+
+def paper_op_list(L, iters):
+    """The schedule as ops, written out from Sec. 5: the initialisation;
+    for each block level L..1 its iterations of four parity phases, then the
+    descent; the pixel level's phases; the output."""
+    ops = [("init",)]
+    for level in range(L, -1, -1):
+        for _ in range(iters):
+            for phase in range(4):
+                ops.append(("phase", level, phase))
+        ops.append(("descend",) if level > 0 else ("output",))
+    return ops
+
+
+ANYTIME_CASES = [
+    # W, H, K, L, B, iters, image seed
+    (37, 29, 6, 2, 4, 1, 11),
+    (24, 40, 5, 1, 3, 2, 12),
+    (30, 22, 4, 0, 5, 2, 13),
+]
+
+
+@pytest.mark.parametrize("case", ANYTIME_CASES)
+def test_anytime_prefixes_follow_the_op_list(case):
+    W, H, K, L, B, iters, seed = case
+    img = rgb_noise(W, H, seed)
+    ops = paper_op_list(L, iters)
+    r = ref.Ref(W, H, K, L, B, iters)
+    assert r.num_ops() == len(ops)
+    for n in range(1, len(ops) + 2):
+        got = r.run_ops(img, n)
+        want = ref.Ref(W, H, K, L, B, iters)
+        want.init(img)
+        for op in ops[1:n]:
+            if op[0] == "phase":
+                want.run_phase(op[1], op[2])
+        assert np.array_equal(got, want.labels()), "prefix of %d ops" % n
+        # Sec. 5.4: stopping at any point leaves a valid partition
+        assert_valid_partition(got, r.K)
+        h, s = r.hist()
+        h2, s2 = recount(got, r.bins(), r.K, r.nbins)
+        assert np.array_equal(h, h2) and np.array_equal(s, s2)
+
+
+def test_anytime_one_op_is_the_grid_and_all_ops_the_full_run():
+    W, H, K = 45, 31, 9
+    img = rgb_noise(W, H, 21)
+    r = ref.Ref(W, H, K, 2, 4, 2)
+    lab = r.run_ops(img, 1)
+    sx = [(i * W) // r.gx for i in range(r.gx + 1)]
+    sy = [(i * H) // r.gy for i in range(r.gy + 1)]
+    for y in range(H):
+        for x in range(W):
+            cx = max(i for i in range(r.gx) if sx[i] <= x)
+            cy = max(i for i in range(r.gy) if sy[i] <= y)
+            assert lab[y, x] == cy * r.gx + cx
+    full = ref.Ref(W, H, K, 2, 4, 2).run(img)
+    assert np.array_equal(r.run_ops(img, r.num_ops()), full)
+    assert np.array_equal(r.run_ops(img, r.num_ops() + 5), full)
+    with pytest.raises(ref.OracleError):
+        r.run_ops(img, 0)
