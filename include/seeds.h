@@ -164,6 +164,28 @@ int seeds_batch_labels(seeds_ctx *c, int32_t *const *h_label_ptrs, void *stream)
 int seeds_batch_run(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides,
                     int32_t *const *h_label_ptrs, void *stream);
 
+/* Anytime termination (Sec. 5.4).  As seeds_batch_run, but the launch may
+ * stop early: at the first step boundary where max_steps steps have run
+ * (max_steps > 0) or budget_ns nanoseconds of device time have passed since
+ * the launch began (budget_ns > 0), whichever comes first; 0 for both runs
+ * every step.  A step is one op of every image, and image i's ops are, in
+ * order: the initialisation; for each block level L..1 its 4*iters parity
+ * phases and the descent to the next finer level; the 4*iters pixel phases;
+ * the output.  An image whose output op has not run when the launch stops
+ * gets the partition after its ops done so far, each pixel labelled by the
+ * unit that holds it at the level the image stands at; it is a valid
+ * partition (every superpixel non-empty and 4-connected).  Asynchronous;
+ * seeds_anytime_steps tells how many steps ran.  The context's state is then
+ * that of the stop, so seeds_batch_labels / seeds_labels return
+ * SEEDS_ERR_INVALID until the next seeds_batch_iterate or run.
+ * Errors: SEEDS_ERR_INVALID for a negative limit or a null pointer. */
+int seeds_batch_run_anytime(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides,
+                            int32_t *const *h_label_ptrs, int32_t max_steps, int64_t budget_ns, void *stream);
+
+/* Steps the last seeds_batch_run_anytime launch ran (waits for it); 0 if
+ * there was none. */
+int seeds_anytime_steps(seeds_ctx *c, int32_t *steps);
+
 /* End to end from HOST memory: copies every image host->device into
  * context-owned staging buffers, runs the batch, and copies the labels
  * device->host.  h_rgb[i]: H_i rows of 3*W_i bytes, h_row_strides[i] apart;

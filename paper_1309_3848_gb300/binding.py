@@ -35,7 +35,7 @@ EXPORTS = [
     "seeds_params_default", "seeds_feasible_levels", "seeds_check_params", "seeds_footprint", "seeds_create",
     "seeds_iterate", "seeds_labels", "seeds_num_superpixels", "seeds_status", "seeds_destroy",
     "seeds_batch_create", "seeds_batch_size", "seeds_batch_num_superpixels", "seeds_batch_iterate",
-    "seeds_batch_labels", "seeds_batch_run", "seeds_run_host", "seeds_set_tuning", "seeds_get_tuning",
+    "seeds_batch_labels", "seeds_batch_run", "seeds_batch_run_anytime", "seeds_anytime_steps", "seeds_run_host", "seeds_set_tuning", "seeds_get_tuning",
     "seeds_debug_num_ops", "seeds_debug_op_info", "seeds_debug_run_ops", "seeds_debug_read_state",
     "seeds_debug_set_labels", "seeds_debug_inject_error", "seeds_debug_launch_count", "seeds_profile_enable",
     "seeds_profile_last_ms", "seeds_profile_steps", "seeds_run_static", "seeds_autotune",
@@ -96,6 +96,8 @@ def _load():
         "seeds_batch_iterate": [vp, P(vp), P(i64), vp],
         "seeds_batch_labels": [vp, P(vp), vp],
         "seeds_batch_run": [vp, P(vp), P(i64), P(vp), vp],
+        "seeds_batch_run_anytime": [vp, P(vp), P(i64), P(vp), i32, i64, vp],
+        "seeds_anytime_steps": [vp, P(i32)],
         "seeds_run_host": [vp, P(vp), P(i64), P(vp), vp],
         "seeds_set_tuning": [vp, P(seeds_tuning)],
         "seeds_get_tuning": [vp, P(seeds_tuning)],
@@ -235,6 +237,23 @@ class SeedsContext:
             assert t.is_contiguous() and t.is_cuda and t.element_size() == 4
         check(lib.seeds_batch_run(self._h, rgb, strides, _ptrs([t.data_ptr() for t in outs]),
                                   _stream_handle(stream)), "seeds_batch_run")
+
+    def run_anytime(self, images, outs, max_steps=0, budget_ns=0, stream=None):
+        """Anytime termination (Sec. 5.4): run, stopping after max_steps
+        steps or budget_ns of device time (0 = no limit); asynchronous, see
+        anytime_steps()."""
+        rgb, strides = self._rgb_args(images)
+        for t in outs:
+            assert t.is_contiguous() and t.is_cuda and t.element_size() == 4
+        check(lib.seeds_batch_run_anytime(self._h, rgb, strides, _ptrs([t.data_ptr() for t in outs]),
+                                          int(max_steps), int(budget_ns), _stream_handle(stream)),
+              "seeds_batch_run_anytime")
+
+    def anytime_steps(self) -> int:
+        """Steps the last run_anytime launch ran (waits for it)."""
+        n = ctypes.c_int32()
+        check(lib.seeds_anytime_steps(self._h, ctypes.byref(n)), "seeds_anytime_steps")
+        return n.value
 
     def run_host(self, images, outs, stream=None):
         """images: host uint8 (H, W, 3) tensors; outs: host int32 (H, W)."""

@@ -75,6 +75,13 @@ struct Schedule {
     int32_t nsteps;
     int32_t max_nbins;          // largest histogram of the context (scratch size)
     unsigned long long *trace;  // optional: 1 + nsteps globaltimer stamps
+    // anytime termination (Sec. 5.4): stop at the first step boundary after
+    // stop_steps steps (> 0) or budget_ns of device time (> 0), write every
+    // unfinished image's partition, and store the steps run in *steps_out
+    int32_t stop_steps;
+    int32_t nimg;
+    unsigned long long budget_ns;
+    int32_t *steps_out;
 };
 
 struct GridBarrier {

@@ -51,9 +51,13 @@ __device__ __forceinline__ int ld_relaxed_i32(const int32_t *p)
     return v;
 }
 
+constexpr unsigned kGenStop = 0x80000000u;  // generation bit: the grid stops here
+
 // Grid-wide barrier for a persistent launch whose blocks are all resident.
-// Returns false when the wait ran out or another block reported an error.
-__device__ bool grid_sync(GridBarrier *bar, int32_t *err)
+// Returns 0 when the wait ran out or another block reported an error, 1 to
+// go on, 2 to stop: the last block to arrive decides (its thread 0 passes
+// want_stop) and publishes the decision in the generation word it bumps.
+__device__ int grid_sync(GridBarrier *bar, int32_t *err, bool want_stop = false)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -65,10 +69,12 @@ __device__ bool grid_sync(GridBarrier *bar, int32_t *err)
         if (arrived == gridDim.x) {
             atomicExch(&bar->count, 0u);
             __threadfence();
-            atomicAdd(&bar->gen, 1u);
+            atomicAdd(&bar->gen, want_stop ? kGenStop + 1u : 1u);
+            if (want_stop) ok = 2;
         } else {
             const uint64_t t0 = global_ns();
-            for (unsigned it = 1; ld_acquire_u32(&bar->gen) == g; ++it) {
+            unsigned cur;
+            for (unsigned it = 1; (cur = ld_acquire_u32(&bar->gen)) == g; ++it) {
                 if ((it & 31u) == 0) {
                     if (ld_relaxed_i32(err) != 0) {
                         ok = 0;
@@ -82,12 +88,13 @@ __device__ bool grid_sync(GridBarrier *bar, int32_t *err)
                 }
                 __nanosleep(32);
             }
+            if (ok && ((cur ^ g) & kGenStop)) ok = 2;
         }
         __threadfence();
         s_ok = ok;
     }
     __syncthreads();
-    return s_ok != 0;
+    return s_ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -786,6 +793,42 @@ __device__ void op_output(const DevImage &im, int o, int units, int c)
         if (x0 + q < W) out[x0 + q] = lab[x0 + q];
 }
 
+// Anytime termination (Sec. 5.4): every image whose output op has not run
+// gets its partition after op o, the last op the grid completed.  Its labels
+// live on the grid of the level it stands at (a phase: that level; a
+// descent from l: level l-1; the init: level L), in buffer (o+1)&1, and each
+// pixel takes the label of the unit that holds it: unit column
+// bx = ((x+1)*nbx - 1) / W inverts the edges floor(i*W/nbx), rows likewise.
+// Few images: every thread walks each image; many: a block per image.
+__device__ void anytime_output(const DevImage *imgs, int nimg, int o)
+{
+    const bool per_block = nimg >= (int)gridDim.x;
+    const int i0 = per_block ? blockIdx.x : 0, istep = per_block ? gridDim.x : 1;
+    const int64_t t0 = per_block ? threadIdx.x : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tstep = per_block ? blockDim.x : (int64_t)gridDim.x * blockDim.x;
+    for (int i = i0; i < nimg; i += istep) {
+        const DevImage &im = imgs[i];
+        if (o >= num_ops(im.L, im.iters) - 1) continue;  // finished: its output ran
+        const OpDesc d = op_at(im.L, im.iters, o);
+        const int level = d.kind == OP_PHASE ? d.level : d.kind == OP_DESCEND ? d.level - 1 : im.L;
+        const uint16_t *lab = im.lab[level][(o + 1) & 1];
+        const int W = im.W, nx = im.nbx[level], ny = im.nby[level];
+        const int64_t npx = (int64_t)W * im.H;
+        for (int64_t p = t0; p < npx; p += tstep) {
+            const int y = (int)(p / W), x = (int)(p - (int64_t)y * W);
+            int v;
+            if (level == 0) {
+                v = lab[p];
+            } else {
+                const int bx = (int)(((int64_t)(x + 1) * nx - 1) / W);
+                const int by = (int)(((int64_t)(y + 1) * ny - 1) / im.H);
+                v = lab[by * nx + bx];
+            }
+            im.out[p] = v;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
@@ -815,6 +858,8 @@ __global__ void __launch_bounds__(512, SEEDS_MIN_BLOCKS) seeds_persistent(const 
     const int64_t nwarps = (int64_t)gridDim.x * nwarps_blk;
     const bool tracer = S.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
     if (tracer) S.trace[0] = global_ns();
+    const bool anytime = S.stop_steps > 0 || S.budget_ns > 0;
+    const uint64_t t_start = anytime ? global_ns() : 0;
 
     for (int s = 0; s < S.nsteps; ++s) {
         const int e0 = S.step_first[s], e1 = S.step_first[s + 1];
@@ -858,9 +903,21 @@ __global__ void __launch_bounds__(512, SEEDS_MIN_BLOCKS) seeds_persistent(const 
                 break;
             }
         }
-        if (s + 1 < S.nsteps && !grid_sync(bar, err)) return;
+        if (s + 1 < S.nsteps) {
+            const bool want_stop = anytime && threadIdx.x == 0 &&
+                                   ((S.stop_steps > 0 && s + 1 >= S.stop_steps) ||
+                                    (S.budget_ns > 0 && global_ns() - t_start >= S.budget_ns));
+            const int go = grid_sync(bar, err, want_stop);
+            if (go == 0) return;
+            if (go == 2) {
+                anytime_output(imgs, S.nimg, s);
+                if (blockIdx.x == 0 && threadIdx.x == 0 && S.steps_out) *S.steps_out = s + 1;
+                return;
+            }
+        }
         if (tracer) S.trace[1 + s] = global_ns();
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && S.steps_out) *S.steps_out = S.nsteps;
 }
 
 __global__ void set_io_kernel(DevImage *imgs, IoChunk chunk)
@@ -1232,7 +1289,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     cudaStream_t s = (cudaStream_t)stream;
     static_setup_kernel<<<8, 256, 0, s>>>(S);
     if (cudaGetLastError() != cudaSuccess) return SEEDS_ERR_CUDA;
-    Schedule sch;
+    Schedule sch{};
     sch.ent = S.ent;
     sch.step_first = S.first;
     sch.step_vt = S.vt;

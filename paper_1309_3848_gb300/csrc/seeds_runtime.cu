@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <new>
@@ -43,6 +44,8 @@ struct seeds_ctx {
     std::vector<int> pending;  // per image: op whose moves await catch-up, or -1
     GridBarrier *d_bar = nullptr;
     int32_t *d_err = nullptr;
+    int32_t *d_steps = nullptr;  // steps run by the last anytime launch
+    bool stopped_state = false;  // the last launch was an anytime run: no final state to output
     seeds_tuning tune{256, 0, 0, 16};
     int grid = 0;
     size_t smem = 0;
@@ -179,6 +182,7 @@ int get_schedule(seeds_ctx *c, int kind, int ob, int oe, const Schedule **out)
     ds.s.nsteps = nsteps;
     ds.s.max_nbins = c->max_nbins;
     ds.s.trace = nullptr;
+    ds.s.nimg = n;
     auto ins = c->schedules.emplace(key, ds);
     *out = &ins.first->second.s;
     return SEEDS_OK;
@@ -201,7 +205,9 @@ int push_io(seeds_ctx *c, cudaStream_t s)
     return SEEDS_OK;
 }
 
-int launch(seeds_ctx *c, int kind, int ob, int oe, cudaStream_t s)
+// Launch the schedule of `kind`; stop_steps / budget_ns > 0 make it an
+// anytime run (full schedules only).
+int launch(seeds_ctx *c, int kind, int ob, int oe, cudaStream_t s, int32_t stop_steps = 0, int64_t budget_ns = 0)
 {
     const Schedule *sch = nullptr;
     int rc = get_schedule(c, kind, ob, oe, &sch);
@@ -213,6 +219,10 @@ int launch(seeds_ctx *c, int kind, int ob, int oe, cudaStream_t s)
     if (rc) return rc;
     Schedule run = *sch;
     run.trace = nullptr;
+    const bool anytime = stop_steps > 0 || budget_ns > 0;
+    run.stop_steps = stop_steps;
+    run.budget_ns = (unsigned long long)budget_ns;
+    run.steps_out = anytime ? c->d_steps : nullptr;
     if (c->profile) {
         rc = from_cuda(cudaEventRecord(c->ev0, s));
         if (rc) return rc;
@@ -235,7 +245,13 @@ int launch(seeds_ctx *c, int kind, int ob, int oe, cudaStream_t s)
     rc = from_cuda(cudaEventRecord(c->done, s));
     c->launched = true;
     // where every image's state now lives, and which moves await catch-up
+    c->stopped_state = anytime;
     for (size_t i = 0; i < c->img.size(); ++i) {
+        if (anytime) {  // the state is that of wherever the launch stopped
+            c->cur[i] = 0;
+            c->pending[i] = -1;
+            continue;
+        }
         int b = 0, e = 0;
         op_range(c->img[i], kind, ob, oe, &b, &e);
         if (e <= b) continue;
@@ -254,6 +270,7 @@ void destroy_ctx(seeds_ctx *c)
     cudaFree(c->pool);
     cudaFree(c->d_bar);
     cudaFree(c->d_err);
+    cudaFree(c->d_steps);
     cudaFree(c->stage);
     cudaFree(c->d_trace);
     if (c->done) cudaEventDestroy(c->done);
@@ -288,6 +305,8 @@ int create_ctx(const seeds_params *p, int32_t n, seeds_ctx **out)
     if (!rc) rc = from_cuda(cudaMalloc((void **)&c->d_bar, sizeof(GridBarrier)));
     if (!rc) rc = from_cuda(cudaMalloc((void **)&c->d_err, sizeof(int32_t)));
     if (!rc) rc = from_cuda(cudaMemset(c->d_err, 0, sizeof(int32_t)));
+    if (!rc) rc = from_cuda(cudaMalloc((void **)&c->d_steps, sizeof(int32_t)));
+    if (!rc) rc = from_cuda(cudaMemset(c->d_steps, 0, sizeof(int32_t)));
     if (!rc) rc = from_cuda(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
     if (!rc) rc = from_cuda(cudaEventCreate(&c->ev0));
     if (!rc) rc = from_cuda(cudaEventCreate(&c->ev1));
@@ -443,7 +462,7 @@ int seeds_batch_iterate(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const in
 
 int seeds_batch_labels(seeds_ctx *c, int32_t *const *h_label_ptrs, void *stream)
 {
-    if (!c || !h_label_ptrs) return SEEDS_ERR_INVALID;
+    if (!c || !h_label_ptrs || c->stopped_state) return SEEDS_ERR_INVALID;
     for (size_t i = 0; i < c->img.size(); ++i) {
         if (!h_label_ptrs[i]) return SEEDS_ERR_INVALID;
         c->io[i].out = h_label_ptrs[i];
@@ -464,6 +483,33 @@ int seeds_batch_run(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_
         c->io[i].out = h_label_ptrs[i];
     }
     return launch(c, SCHED_FULL, 0, 0, (cudaStream_t)stream);
+}
+
+int seeds_batch_run_anytime(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides,
+                            int32_t *const *h_label_ptrs, int32_t max_steps, int64_t budget_ns, void *stream)
+{
+    if (!c || !h_label_ptrs || max_steps < 0 || budget_ns < 0) return SEEDS_ERR_INVALID;
+    int rc = check_io(c, h_rgb_ptrs, h_row_strides);
+    if (rc) return rc;
+    for (size_t i = 0; i < c->img.size(); ++i) {
+        if (!h_label_ptrs[i]) return SEEDS_ERR_INVALID;
+        c->io[i].rgb = h_rgb_ptrs[i];
+        c->io[i].stride = h_row_strides[i];
+        c->io[i].out = h_label_ptrs[i];
+    }
+    // no limit at all runs every step (and still counts them)
+    if (max_steps == 0 && budget_ns == 0) max_steps = INT32_MAX;
+    return launch(c, SCHED_FULL, 0, 0, (cudaStream_t)stream, max_steps, budget_ns);
+}
+
+int seeds_anytime_steps(seeds_ctx *c, int32_t *steps)
+{
+    if (!c || !steps) return SEEDS_ERR_INVALID;
+    if (c->launched) {
+        int rc = from_cuda(cudaEventSynchronize(c->done));
+        if (rc) return rc;
+    }
+    return from_cuda(cudaMemcpy(steps, c->d_steps, sizeof(int32_t), cudaMemcpyDeviceToHost));
 }
 
 int seeds_run_host(seeds_ctx *c, const uint8_t *const *h_rgb, const int64_t *h_row_strides, int32_t *const *h_labels,

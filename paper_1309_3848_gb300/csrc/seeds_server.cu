@@ -323,7 +323,7 @@ int seeds_server_step(seeds_server *s, int32_t *resident_out)
     if (plan.n == 0) return SEEDS_OK;
     rc = from_cuda(launch_epoch_schedule(s->d_imgs, plan, s->d_ent, s->d_first, s->d_vt, st));
     if (!rc) rc = from_cuda(cudaMemsetAsync(s->d_bar, 0, sizeof(GridBarrier), st));
-    Schedule sch;
+    Schedule sch{};
     sch.ent = s->d_ent;
     sch.step_first = s->d_first;
     sch.step_vt = s->d_vt;
