@@ -28,6 +28,7 @@ class RefParams(ctypes.Structure):
         ("patch", ctypes.c_int32),
         ("gamma_num", ctypes.c_int32),
         ("gamma_den", ctypes.c_int32),
+        ("color_space", ctypes.c_int32),
     ]
 
 
@@ -58,6 +59,8 @@ def lib():
             L.ref_run_ops.restype = i64
             L.ref_num_ops.argtypes = [vp]
             L.ref_num_ops.restype = i32
+            L.ref_lab8.argtypes = [vp, vp, i64, vp]
+            L.ref_lab8.restype = None
             L.ref_get_labels.argtypes = [vp, vp]
             L.ref_get_labels.restype = None
             L.ref_get_bins.argtypes = [vp, vp]
@@ -81,9 +84,9 @@ class OracleError(RuntimeError):
 
 
 def make_params(width, height, num_superpixels, block_levels, bins_per_channel, iters_per_level,
-                patch=3, gamma=(1, 1)):
+                patch=3, gamma=(1, 1), color_space=0):
     return RefParams(int(width), int(height), int(num_superpixels), int(block_levels), int(bins_per_channel),
-                     int(iters_per_level), int(patch), int(gamma[0]), int(gamma[1]))
+                     int(iters_per_level), int(patch), int(gamma[0]), int(gamma[1]), int(color_space))
 
 
 def grid(width, height, num_superpixels, block_levels=0, bins_per_channel=5, iters_per_level=1, patch=3,
@@ -105,9 +108,9 @@ class Ref:
     """One image's oracle state."""
 
     def __init__(self, width, height, num_superpixels, block_levels, bins_per_channel, iters_per_level,
-                 patch=3, gamma=(1, 1)):
+                 patch=3, gamma=(1, 1), color_space=0):
         self.params = make_params(width, height, num_superpixels, block_levels, bins_per_channel,
-                                  iters_per_level, patch, gamma)
+                                  iters_per_level, patch, gamma, color_space)
         self._h = ctypes.c_void_p()
         rc = lib().ref_create(ctypes.byref(self.params), ctypes.byref(self._h))
         if rc:
@@ -200,6 +203,14 @@ class Ref:
     def labels(self):
         out = np.zeros((self.H, self.W), np.int32)
         lib().ref_get_labels(self._h, out.ctypes.data)
+        return out
+
+    def lab8(self, rgb):
+        """The 8-bit CIE L*a*b* codes (reading R16) of an (..., 3) uint8 array."""
+        rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+        assert rgb.shape[-1] == 3
+        out = np.zeros(rgb.shape, np.uint8)
+        lib().ref_lab8(self._h, rgb.ctypes.data, rgb.size // 3, out.ctypes.data)
         return out
 
     def bins(self):

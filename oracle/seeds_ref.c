@@ -55,6 +55,11 @@
  *       G_x = sum_{i in K_p} b_{N_i}(x) in counts (Prop. 2); blocks use the
  *       intersection alone (no G, Sec. 5.3).
  *   R13 K_p and N_i contain in-image pixels only.
+ *   R16 colour space LAB (Sec. 6.2), optional: the bins of R1 taken over
+ *       the 8-bit CIE L*a*b* code of each pixel (sRGB, D65; L* scaled by
+ *       255/100, a* and b* offset by 128), computed in exact integer fixed
+ *       point from two small tables of the published curves (see
+ *       rgb_to_lab8).
  *   R15 anytime termination (Sec. 5.4): stopping after the first n ops of
  *       the schedule (init; per block level its phases and a descent; the
  *       pixel phases; the output) yields the partition as it stands, each
@@ -82,6 +87,7 @@ typedef struct {
     int32_t patch;      /* 0 = no boundary term, 3 = 3x3 patches */
     int32_t gamma_num;
     int32_t gamma_den;
+    int32_t color_space; /* 0 = RGB bytes (R1), 1 = CIE L*a*b* (R16) */
 } ref_params;
 
 typedef struct {
@@ -99,6 +105,8 @@ typedef struct {
     int64_t *tmp_a;  /* A_k \ L */
     int32_t *moves;  /* (unit, k, n) triples of the current phase */
     int64_t moves_cap;
+    int64_t lab_lin[256];  /* R16: sRGB byte -> linear light * 2^24 */
+    int64_t lab_m[3][3];   /* R16: linear RGB -> XYZ / white, * 2^20 */
 } ref_state;
 
 enum { REF_OK = 0, REF_EINVAL = -1, REF_EGEOM = -2, REF_ENOMEM = -4, REF_ESIZE = -7 };
@@ -124,6 +132,7 @@ int ref_check_params(const ref_params *p)
     if (p->patch != 0 && p->patch != 3) return REF_EINVAL;
     if (p->gamma_num < 0 || p->gamma_num > 1024) return REF_EINVAL;
     if (p->gamma_den < 1 || p->gamma_den > 1024) return REF_EINVAL;
+    if (p->color_space != 0 && p->color_space != 1) return REF_EINVAL;
     return REF_OK;
 }
 
@@ -160,6 +169,8 @@ void ref_destroy(ref_state *st)
     free(st->moves);
     free(st);
 }
+
+static void lab_tables(ref_state *st);
 
 int ref_create(const ref_params *p, ref_state **out)
 {
@@ -206,6 +217,7 @@ int ref_create(const ref_params *p, ref_state **out)
         ref_destroy(st);
         return REF_ENOMEM;
     }
+    lab_tables(st);
     *out = st;
     return REF_OK;
 }
@@ -242,6 +254,87 @@ static int channel_bin(int v, int B)
     return B - 1; /* unreachable for 0 <= v <= 255 */
 }
 
+/* R16: CIE 1976 L*a*b* of sRGB under D65 (Sec. 6.2 reports LAB as the
+ * best colour space), in exact integer fixed point.  Two tables come from
+ * the published definitions in double precision, rounded to integers: the
+ * sRGB decoding curve (IEC 61966-2-1) as linear light * 2^24, and the sRGB
+ * to XYZ matrix with each row divided by its sum (the D65 white) * 2^20.
+ * The rest is integer arithmetic: t = T / 2^44 per channel, f(t) * 2^20
+ * (floor), and the 8-bit code of each coordinate -- L* * 255/100, a* + 128,
+ * b* + 128, each rounded half up and clamped to [0, 255]. */
+static const double SRGB_TO_XYZ[3][3] = {
+    {0.4124, 0.3576, 0.1805}, {0.2126, 0.7152, 0.0722}, {0.0193, 0.1192, 0.9505}};
+
+static double srgb_decode(int v)
+{
+    double c = v / 255.0;
+    return c <= 0.04045 ? c / 12.92 : pow((c + 0.055) / 1.055, 2.4);
+}
+
+static void lab_tables(ref_state *st)
+{
+    for (int v = 0; v < 256; ++v) st->lab_lin[v] = llround(srgb_decode(v) * 16777216.0);
+    for (int i = 0; i < 3; ++i) {
+        double white = SRGB_TO_XYZ[i][0] + SRGB_TO_XYZ[i][1] + SRGB_TO_XYZ[i][2];
+        for (int j = 0; j < 3; ++j) st->lab_m[i][j] = llround(SRGB_TO_XYZ[i][j] / white * 1048576.0);
+    }
+}
+
+/* floor(cbrt(n)) for 0 <= n < 2^60.2, by bisection */
+static int64_t icbrt_floor(int64_t n)
+{
+    int64_t lo = 0, hi = ((int64_t)1 << 20) + ((int64_t)1 << 16);
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) / 2;
+        if (mid * mid * mid <= n)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+/* floor(f(t) * 2^20) for t = T / 2^44, where f(t) = t^(1/3) above
+ * (6/29)^3 = 216/24389 and the line t / (3 (6/29)^2) + 4/29 =
+ * (24389 t + 432) / 3132 below */
+static int64_t lab_f_q20(int64_t T)
+{
+    if (T * 24389 > ((int64_t)216 << 44)) return icbrt_floor(T << 16); /* cbrt(t * 2^60) */
+    return (24389 * T + ((int64_t)432 << 44)) / ((int64_t)3132 << 24);
+}
+
+static int64_t floor_div(int64_t a, int64_t b)
+{
+    int64_t q = a / b;
+    return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+static int clamp_byte(int64_t v) { return v < 0 ? 0 : v > 255 ? 255 : (int)v; }
+
+static void rgb_to_lab8(const ref_state *st, int r, int g, int b, int out[3])
+{
+    int64_t f[3];
+    for (int i = 0; i < 3; ++i) {
+        int64_t T = st->lab_m[i][0] * st->lab_lin[r] + st->lab_m[i][1] * st->lab_lin[g] +
+                    st->lab_m[i][2] * st->lab_lin[b];
+        f[i] = lab_f_q20(T);
+    }
+    int64_t Lq = 116 * f[1] - ((int64_t)16 << 20); /* L* * 2^20 */
+    out[0] = clamp_byte(floor_div(Lq * 255 + ((int64_t)50 << 20), (int64_t)100 << 20));
+    out[1] = clamp_byte(floor_div(500 * (f[0] - f[1]) + ((int64_t)128 << 20) + (1 << 19), (int64_t)1 << 20));
+    out[2] = clamp_byte(floor_div(200 * (f[1] - f[2]) + ((int64_t)128 << 20) + (1 << 19), (int64_t)1 << 20));
+}
+
+/* the 8-bit L*a*b* codes of n RGB triples (test hook) */
+void ref_lab8(const ref_state *st, const uint8_t *rgb, int64_t n, uint8_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int c[3];
+        rgb_to_lab8(st, rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2], c);
+        for (int q = 0; q < 3; ++q) out[3 * i + q] = (uint8_t)c[q];
+    }
+}
+
 /* index of the interval [e[i], e[i+1]) that holds v */
 static int find_interval(const int *e, int n, int v)
 {
@@ -276,7 +369,9 @@ int ref_init(ref_state *st, const uint8_t *rgb, int64_t row_stride)
         int sy = find_interval(sye, st->gy, y);
         for (int x = 0; x < st->W; ++x) {
             const uint8_t *px = rgb + (int64_t)y * row_stride + 3 * (int64_t)x;
-            int br = channel_bin(px[0], B), bg = channel_bin(px[1], B), bb = channel_bin(px[2], B);
+            int c[3] = {px[0], px[1], px[2]};
+            if (st->p.color_space == 1) rgb_to_lab8(st, px[0], px[1], px[2], c);
+            int br = channel_bin(c[0], B), bg = channel_bin(c[1], B), bb = channel_bin(c[2], B);
             int sx = find_interval(sxe, st->gx, x);
             st->bin[(int64_t)y * st->W + x] = br * B * B + bg * B + bb;
             st->lab[(int64_t)y * st->W + x] = sy * st->gx + sx;

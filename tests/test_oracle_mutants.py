@@ -25,6 +25,10 @@ MUTANTS = {
     "bin order B-major": ("br * B * B + bg * B + bb", "bb * B * B + bg * B + br"),
     "size not decremented on a move": ("            st->size[k] -= 1;\n", "\n"),
     "ties go to the largest label": ("if (!(diff > 0)) continue;", "if (diff < 0) continue;"),
+    "LAB line segment loses its offset": ("(24389 * T + ((int64_t)432 << 44))", "(24389 * T)"),
+    "LAB a* from the wrong channel pair": ("500 * (f[0] - f[1])", "500 * (f[0] - f[2])"),
+    "LAB without the sRGB decoding curve": ("pow((c + 0.055) / 1.055, 2.4)", "c"),
+    "LAB bins from the RGB bytes": ("if (st->p.color_space == 1) rgb_to_lab8", "if (0) rgb_to_lab8"),
     "anytime prefix skips the descent op": ("        ++done; /* the descent", "        /* the descent"),
     "anytime prefix runs one phase too many": ("if (done >= nops) return total;", "if (done > nops) return total;"),
 }

@@ -11,6 +11,7 @@ single-lookup pixel test, special cases with known answers, and the
 sequential mode's energy ascent.
 """
 import itertools
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -573,3 +574,73 @@ def test_anytime_one_op_is_the_grid_and_all_ops_the_full_run():
     assert np.array_equal(r.run_ops(img, r.num_ops() + 5), full)
     with pytest.raises(ref.OracleError):
         r.run_ops(img, 0)
+
+
+# --------------------------------------------------------------------------
+# LAB colour bins (Sec. 6.2, reading R16)
+# --------------------------------------------------------------------------
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def real_lab8(rgb):
+    """Real-valued 8-bit L*a*b* codes of uint8 triples: the CIE 1976
+    formulas over the sRGB decoding curve and the D65 matrix in float64,
+    without the oracle's fixed point."""
+    c = rgb.astype(np.float64) / 255.0
+    lin = np.where(c <= 0.04045, c / 12.92, ((c + 0.055) / 1.055) ** 2.4)
+    m = np.array([[0.4124, 0.3576, 0.1805], [0.2126, 0.7152, 0.0722], [0.0193, 0.1192, 0.9505]])
+    t = lin @ (m / m.sum(axis=1, keepdims=True)).T
+    d = 6.0 / 29.0
+    f = np.where(t > d ** 3, np.cbrt(t), t / (3 * d * d) + 4.0 / 29.0)
+    L = 116 * f[..., 1] - 16
+    a = 500 * (f[..., 0] - f[..., 1])
+    b = 200 * (f[..., 1] - f[..., 2])
+    code = np.stack([L * 255 / 100, a + 128, b + 128], axis=-1)
+    return np.clip(np.floor(code + 0.5), 0, 255)
+
+
+def lab_ref():
+    return ref.Ref(8, 8, 1, 0, 5, 1, color_space=1)
+
+
+def test_lab_codes_of_the_textbook_colours():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "lab_srgb_d65.txt")) if l.strip() and l[0] != "#"]
+    rgb = np.array([[int(v) for v in r[:3]] for r in rows], np.uint8)
+    lab = np.array([[float(v) for v in r[3:]] for r in rows])
+    want = np.stack([lab[:, 0] * 255 / 100, lab[:, 1] + 128, lab[:, 2] + 128], axis=1)
+    got = lab_ref().lab8(rgb).astype(np.float64)
+    assert np.all(np.abs(got - np.clip(np.floor(want + 0.5), 0, 255)) <= 1), got
+    assert got[0].tolist() == [255, 128, 128] and got[1].tolist() == [0, 128, 128]
+
+
+def test_lab_codes_match_the_real_valued_formulas():
+    v = np.arange(0, 256, 3)
+    rgb = np.stack(np.meshgrid(v, v, v, indexing="ij"), axis=-1).reshape(-1, 3).astype(np.uint8)
+    got = lab_ref().lab8(rgb).astype(np.float64)
+    want = real_lab8(rgb)
+    diff = np.abs(got - want)
+    assert diff.max() <= 1
+    assert (diff == 0).mean() > 0.999
+
+
+def test_lab_greys_are_neutral_and_ordered():
+    g = np.repeat(np.arange(256, dtype=np.uint8)[:, None], 3, axis=1)
+    got = lab_ref().lab8(g).astype(int)
+    assert np.all(got[:, 1] == 128) and np.all(got[:, 2] == 128)
+    assert np.all(np.diff(got[:, 0]) >= 0) and got[0, 0] == 0 and got[255, 0] == 255
+
+
+@pytest.mark.parametrize("B", [1, 4, 5, 8])
+def test_lab_bins_are_r1_bins_of_the_lab_codes(B):
+    W, H = 41, 23
+    img = rgb_noise(W, H, 40 + B)
+    r = ref.Ref(W, H, 6, 1, B, 1, color_space=1)
+    r.init(img)
+    code = r.lab8(img).astype(np.int64)
+    q = code * B // 256
+    assert np.array_equal(r.bins(), q[..., 0] * B * B + q[..., 1] * B + q[..., 2])
+    rgb_bins = ref.Ref(W, H, 6, 1, B, 1)
+    rgb_bins.init(img)
+    qq = img.astype(np.int64) * B // 256
+    assert np.array_equal(rgb_bins.bins(), qq[..., 0] * B * B + qq[..., 1] * B + qq[..., 2])
