@@ -175,7 +175,7 @@ def oracle_levels(job):
 def oracle_run(job, img):
     from oracle import ref
     r = ref.Ref(job.image.width, job.image.height, job.num_superpixels, oracle_levels(job), job.bins_per_channel,
-                job.iters_per_level, job.patch, job.gamma)
+                job.iters_per_level, job.patch, job.gamma, job.color_space)
     return r.run(img)
 
 
@@ -254,7 +254,7 @@ def gpu_params(binding, job):
     if job.clamp_levels:
         L = min(L, binding.feasible_levels(job.image.width, job.image.height, job.num_superpixels))
     return binding.make_params(job.image.width, job.image.height, job.num_superpixels, L, job.bins_per_channel,
-                               job.iters_per_level, job.patch, job.gamma)
+                               job.iters_per_level, job.patch, job.gamma, job.color_space)
 
 
 def timed_steps(torch, fn, steps, flush, kernel_ms=None):

@@ -64,14 +64,22 @@ extern "C" {
 
 typedef struct seeds_ctx seeds_ctx;
 
-/* Parameters of one image (Sec. 6.2 fixes gamma = 1, a 3x3 patch, 5 bins).
+/* Parameters of one image (Sec. 6.2 fixes gamma = 1, a 3x3 patch, 5 bins,
+ * and LAB colour).
  *   width, height      image size, 1..32768 each, width*height < 2^31
  *   num_superpixels    requested K (>= 1); the grid gives gx*gy <= 65535
  *   block_levels       L >= 0 (0 = pixel moves only)
  *   bins_per_channel   B in 1..16; histograms have B^3 bins
  *   iters_per_level    >= 1, for every block level and the pixel level
  *   patch              0 (no boundary term) or 3 (3x3 patches, Prop. 2)
- *   gamma_num/den      gamma = num/den, 0 <= num <= 1024, 1 <= den <= 1024 */
+ *   gamma_num/den      gamma = num/den, 0 <= num <= 1024, 1 <= den <= 1024
+ *   color_space        0: bins of the RGB bytes; 1: bins of the 8-bit CIE
+ *                      L*a*b* code of each pixel (sRGB under D65; L* scaled
+ *                      by 255/100, a* and b* offset by 128, rounded half up),
+ *                      computed in exact integer fixed point: the sRGB
+ *                      decoding curve as linear light * 2^24, the sRGB to
+ *                      XYZ matrix rows divided by the D65 white * 2^20,
+ *                      f(t) * 2^20 by an exact integer cube root */
 typedef struct {
     int32_t width, height;
     int32_t num_superpixels;
@@ -80,6 +88,7 @@ typedef struct {
     int32_t iters_per_level;
     int32_t patch;
     int32_t gamma_num, gamma_den;
+    int32_t color_space;
 } seeds_params;
 
 /* Result-invariant launch knobs (any value gives identical labels).
@@ -285,7 +294,9 @@ int seeds_server_stats(const seeds_server *s, seeds_server_stats_t *out);
  * channel; a 1920x1080 image with 1000 superpixels needs about 17 MiB),
  * and the usual codes for bad parameters.  The first call on each device
  * looks up the array's device address (with that device current) and
- * caches it; make that first call before any stream capture.  All calls
+ * caches it, and the first call with color_space = 1 on each device also
+ * copies the 1 KB LAB tables into a static device array (a synchronous copy,
+ * no allocation); make those first calls before any stream capture.  All calls
  * share the one array, which keeps the previous call's contents: each call
  * re-initialises everything it reads, but calls whose work overlaps on the
  * GPU (other streams, other host threads) race on it and must be serialised

@@ -54,7 +54,7 @@ class seeds_params(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("num_superpixels", ctypes.c_int32),
                 ("block_levels", ctypes.c_int32), ("bins_per_channel", ctypes.c_int32),
                 ("iters_per_level", ctypes.c_int32), ("patch", ctypes.c_int32), ("gamma_num", ctypes.c_int32),
-                ("gamma_den", ctypes.c_int32)]
+                ("gamma_den", ctypes.c_int32), ("color_space", ctypes.c_int32)]
 
 
 class seeds_server_config(ctypes.Structure):
@@ -138,9 +138,10 @@ def check(code: int, what: str) -> int:
 
 
 def make_params(width, height, num_superpixels, block_levels, bins_per_channel, iters_per_level, patch=3,
-                gamma=(1, 1)) -> seeds_params:
+                gamma=(1, 1), color_space=0) -> seeds_params:
+    """color_space: 0 = RGB bytes, 1 = 8-bit CIE L*a*b* codes (Sec. 6.2)."""
     return seeds_params(int(width), int(height), int(num_superpixels), int(block_levels), int(bins_per_channel),
-                        int(iters_per_level), int(patch), int(gamma[0]), int(gamma[1]))
+                        int(iters_per_level), int(patch), int(gamma[0]), int(gamma[1]), int(color_space))
 
 
 def feasible_levels(width, height, num_superpixels) -> int:

@@ -38,6 +38,7 @@ struct DevImage {
     int32_t hist_jmajor;  // hist[j*K + k] instead of hist[k*nbins + j]
     int32_t hist_sk, hist_sj;  // hist index = k*hist_sk + j*hist_sj (either layout)
     int32_t small_area;   // blocks up to this many pixels are judged by one thread
+    int32_t color;        // 0: RGB bytes, 1: 8-bit CIE L*a*b* codes (Sec. 6.2)
     int32_t nbx[kMaxLevels + 1], nby[kMaxLevels + 1];  // level 0 = W, H
     int32_t maxarea[kMaxLevels + 1];                   // largest block of a level
     const int32_t *xe[kMaxLevels + 1];                 // block column edges, level >= 1
@@ -281,6 +282,9 @@ cudaError_t launch_persistent(const DevImage *d_imgs, const Schedule &sch, GridB
                               int grid, int threads, size_t smem, cudaStream_t s);
 cudaError_t persistent_max_blocks_per_sm(int threads, size_t smem, int *n);
 cudaError_t prepare_persistent(size_t smem);
+// The LAB conversion tables on the current device (once per device; a
+// synchronous copy of 1 KB the first time).
+cudaError_t upload_lab_tables();
 cudaError_t launch_recount(const DevImage *d_imgs, int img, int level, int64_t npix, cudaStream_t s);
 
 }  // namespace seeds

@@ -59,6 +59,7 @@ inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t 
     if (p->bins_per_channel < 1 || p->bins_per_channel > 16) return SEEDS_ERR_INVALID;
     if (p->iters_per_level < 1 || p->iters_per_level > 1000) return SEEDS_ERR_INVALID;
     if (p->patch != 0 && p->patch != 3) return SEEDS_ERR_INVALID;
+    if (p->color_space != 0 && p->color_space != 1) return SEEDS_ERR_INVALID;
     if (p->gamma_num < 0 || p->gamma_num > 1024 || p->gamma_den < 1 || p->gamma_den > 1024) return SEEDS_ERR_INVALID;
     const double Kd = p->num_superpixels, Wd = p->width, Hd = p->height;
     long long gx = std::llround(std::sqrt(Kd * Wd / Hd));
@@ -163,6 +164,7 @@ inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const se
     d.B = h.B;
     d.nbins = h.nbins;
     d.patch = h.p.patch;
+    d.color = h.p.color_space;
     d.gnum = h.p.gamma_num;
     d.gden = h.p.gamma_den;
     d.bins16 = h.nbins > 256;

@@ -255,6 +255,50 @@ __device__ void block_sparse_apply_clear(const DevImage &im, int buf, int k, int
 }
 
 // ---------------------------------------------------------------------------
+// CIE L*a*b* colour codes (Sec. 6.2), exact integer fixed point
+// ---------------------------------------------------------------------------
+
+// sRGB byte -> linear light * 2^24; sRGB->XYZ matrix rows over the D65 white
+// (the row sums) * 2^20.  Built on the host from the published definitions.
+__device__ int32_t g_lab_lin[256];
+__device__ int32_t g_lab_m[9];
+
+// floor(cbrt(n)) for 0 <= n < 2^61: a single-precision estimate is within
+// one of the answer; integer cubes settle it exactly
+__device__ __forceinline__ int64_t icbrt_floor(int64_t n)
+{
+    int64_t r = (int64_t)cbrtf((float)n);
+    while (r > 0 && r * r * r > n) --r;
+    while ((r + 1) * (r + 1) * (r + 1) <= n) ++r;
+    return r;
+}
+
+// floor(f(t) * 2^20), t = T / 2^44: t^(1/3) above (6/29)^3 = 216/24389, the
+// line (24389 t + 432) / 3132 below
+__device__ __forceinline__ int64_t lab_f_q20(int64_t T)
+{
+    if (T * 24389 > ((int64_t)216 << 44)) return icbrt_floor(T << 16);
+    return (24389 * T + ((int64_t)432 << 44)) / ((int64_t)3132 << 24);
+}
+
+__device__ __forceinline__ int clamp_byte(int64_t v) { return v < 0 ? 0 : v > 255 ? 255 : (int)v; }
+
+// 8-bit L*a*b* code of one pixel: L* * 255/100, a* + 128, b* + 128, each
+// rounded half up (the numerators are >= 0 for every sRGB byte triple)
+__device__ __forceinline__ void lab8(int r, int g, int b, int &c0, int &c1, int &c2)
+{
+    const int64_t lr = __ldg(&g_lab_lin[r]), lg = __ldg(&g_lab_lin[g]), lb = __ldg(&g_lab_lin[b]);
+    int64_t f[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        f[i] = lab_f_q20(__ldg(&g_lab_m[3 * i]) * lr + __ldg(&g_lab_m[3 * i + 1]) * lg + __ldg(&g_lab_m[3 * i + 2]) * lb);
+    const int64_t Lq = 116 * f[1] - ((int64_t)16 << 20);
+    c0 = clamp_byte((Lq * 255 + ((int64_t)50 << 20)) / ((int64_t)100 << 20));
+    c1 = clamp_byte((500 * (f[0] - f[1]) + ((int64_t)128 << 20) + (1 << 19)) >> 20);
+    c2 = clamp_byte((200 * (f[1] - f[2]) + ((int64_t)128 << 20) + (1 << 19)) >> 20);
+}
+
+// ---------------------------------------------------------------------------
 // op_init: one warp per initial superpixel rectangle
 // ---------------------------------------------------------------------------
 
@@ -279,7 +323,8 @@ __device__ void op_init(const DevImage &im, int k, int lane, int32_t *wsh)
             p[q] = 0;
             if (y < y1 && x < x1) {
                 const uint8_t *px = im.rgb + (int64_t)y * im.stride + 3 * (int64_t)x;
-                const int r = px[0], g = px[1], b = px[2];
+                int r = px[0], g = px[1], b = px[2];
+                if (im.color) lab8(r, g, b, r, g, b);
                 j[q] = ((r * B) >> 8) * B * B + ((g * B) >> 8) * B + ((b * B) >> 8);
                 p[q] = y * im.W + x;
             }
@@ -1057,6 +1102,34 @@ cudaError_t persistent_max_blocks_per_sm(int threads, size_t smem, int *n)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, seeds_persistent, threads, smem);
 }
 
+cudaError_t upload_lab_tables()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    // sRGB decoding curve (IEC 61966-2-1) and the sRGB -> XYZ (D65) matrix
+    static const double m[3][3] = {{0.4124, 0.3576, 0.1805}, {0.2126, 0.7152, 0.0722}, {0.0193, 0.1192, 0.9505}};
+    int32_t lin[256], mq[9];
+    for (int v = 0; v < 256; ++v) {
+        const double c = v / 255.0;
+        const double l = c <= 0.04045 ? c / 12.92 : std::pow((c + 0.055) / 1.055, 2.4);
+        lin[v] = (int32_t)std::llround(l * 16777216.0);
+    }
+    for (int i = 0; i < 3; ++i) {
+        const double white = m[i][0] + m[i][1] + m[i][2];
+        for (int j = 0; j < 3; ++j) mq[3 * i + j] = (int32_t)std::llround(m[i][j] / white * 1048576.0);
+    }
+    e = cudaMemcpyToSymbol(g_lab_lin, lin, sizeof(lin));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_lab_m, mq, sizeof(mq));
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
 cudaError_t launch_persistent(const DevImage *d_imgs, const Schedule &sch, GridBarrier *bar, int32_t *err, int grid,
                               int threads, size_t smem, cudaStream_t s)
 {
@@ -1163,6 +1236,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     if (p->iters_per_level < 1 || p->iters_per_level > 1000) return SEEDS_ERR_INVALID;
     if (p->patch != 0 && p->patch != 3) return SEEDS_ERR_INVALID;
     if (p->gamma_num < 0 || p->gamma_num > 1024 || p->gamma_den < 1 || p->gamma_den > 1024) return SEEDS_ERR_INVALID;
+    if (p->color_space != 0 && p->color_space != 1) return SEEDS_ERR_INVALID;
     const double Kd = p->num_superpixels, Wd = p->width, Hd = p->height;
     long long gx = std::llround(std::sqrt(Kd * Wd / Hd));
     if (gx < 1) gx = 1;
@@ -1188,6 +1262,8 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     d.patch = p->patch;
     d.gnum = p->gamma_num;
     d.gden = p->gamma_den;
+    d.color = p->color_space;
+    if (d.color == 1 && upload_lab_tables() != cudaSuccess) return SEEDS_ERR_CUDA;
     d.bins16 = nbins > 256;
     d.hist_jmajor = 0;
     d.hist_sk = nbins;

@@ -310,6 +310,11 @@ int create_ctx(const seeds_params *p, int32_t n, seeds_ctx **out)
     if (!rc) rc = from_cuda(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
     if (!rc) rc = from_cuda(cudaEventCreate(&c->ev0));
     if (!rc) rc = from_cuda(cudaEventCreate(&c->ev1));
+    for (int i = 0; i < n && !rc; ++i)
+        if (c->img[i].p.color_space == 1) {
+            rc = from_cuda(upload_lab_tables());
+            break;
+        }
     if (!rc) {
         // block edge tables are constant for the context's life
         unsigned char *base = c->pool;

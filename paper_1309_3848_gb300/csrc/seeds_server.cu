@@ -215,6 +215,7 @@ int seeds_server_create(const seeds_server_config *cfg, seeds_server **out)
     if (!rc) rc = from_cuda(cudaMalloc((void **)&s->d_ent, sizeof(StepEntry) * max_ent));
     if (!rc) rc = from_cuda(cudaMalloc((void **)&s->d_first, sizeof(int32_t) * (cfg->epoch_steps + 1)));
     if (!rc) rc = from_cuda(cudaMalloc((void **)&s->d_vt, sizeof(int64_t) * cfg->epoch_steps));
+    if (!rc) rc = from_cuda(upload_lab_tables());
     if (!rc) {
         const int threads = s->tune.threads_per_block;
         s->smem = (size_t)(threads / 32) * warp_scratch_bytes(s->max_nbins);

@@ -50,6 +50,7 @@ class JobSpec:
     patch: int = 3
     gamma: Tuple[int, int] = (1, 1)
     clamp_levels: bool = False
+    color_space: int = 0  # 0 = RGB bytes, 1 = CIE L*a*b* codes
 
     @property
     def pixels(self) -> int:

@@ -69,7 +69,8 @@ def test_invalid_parameters(binding):
     bad = [binding.make_params(0, 10, 4, 0, 5, 1), binding.make_params(10, 10, 0, 0, 5, 1),
            binding.make_params(10, 10, 4, 0, 17, 1), binding.make_params(10, 10, 4, 0, 5, 0),
            binding.make_params(10, 10, 4, 0, 5, 1, patch=2), binding.make_params(10, 10, 4, 0, 5, 1, gamma=(1, 0)),
-           binding.make_params(10, 10, 4, 13, 5, 1)]
+           binding.make_params(10, 10, 4, 13, 5, 1), binding.make_params(10, 10, 4, 0, 5, 1, color_space=2),
+           binding.make_params(10, 10, 4, 0, 5, 1, color_space=-1)]
     for p in bad:
         assert binding.check_params(p)[0] == binding.SEEDS_ERR_INVALID
     assert binding.check_params(binding.make_params(16, 16, 4, 4, 5, 1))[0] == binding.SEEDS_ERR_GEOMETRY
