@@ -312,6 +312,39 @@ def batched_vs_plain(torch, binding, flush, steps=5):
             "batched_over_plain": vb / vp, "labels_identical": bool(same)}
 
 
+def next_rows(torch, binding, flush, jobs, imgs, rgb_value, steps=5):
+    """The widened rows on the bench workload: LAB colour bins (Sec. 6.2) in
+    Mpixel/s beside the RGB run, and anytime termination (Sec. 5.4) -- the
+    steps a launch reaches within device-time budgets of a quarter, half and
+    three quarters of a full run, and the time the stopped call takes."""
+    import dataclasses
+    px = sum(j.pixels for j in jobs)
+    d = [torch.from_numpy(im).cuda() for im in imgs]
+    outs = [torch.empty((j.image.height, j.image.width), dtype=torch.int32, device="cuda") for j in jobs]
+
+    lab_ctx = binding.SeedsContext([gpu_params(binding, dataclasses.replace(j, color_space=1)) for j in jobs])
+    for _ in range(3):
+        lab_ctx.run(d, outs)
+    t_lab, _ = timed_steps(torch, lambda: lab_ctx.run(d, outs), steps, flush)
+    lab_ctx.check_status()
+    lab_value = px / (statistics.mean(t_lab) / 1e3) / 1e6
+
+    ctx = binding.SeedsContext([gpu_params(binding, j) for j in jobs])
+    for _ in range(3):
+        ctx.run_anytime(d, outs)
+    t_full, _ = timed_steps(torch, lambda: ctx.run_anytime(d, outs), steps, flush)
+    full_steps = ctx.anytime_steps()
+    full_ms = statistics.mean(t_full)
+    budgets = []
+    for frac in (0.25, 0.5, 0.75):
+        budget_ns = int(frac * full_ms * 1e6)
+        t, _ = timed_steps(torch, lambda: ctx.run_anytime(d, outs, budget_ns=budget_ns), steps, flush)
+        budgets.append({"budget_us": budget_ns / 1e3, "steps": ctx.anytime_steps(), "ms": statistics.mean(t)})
+    ctx.check_status()
+    return {"lab": {"mpix_s": lab_value, "over_rgb": lab_value / rgb_value},
+            "anytime": {"full_steps": full_steps, "full_ms": full_ms, "budgets": budgets}}
+
+
 def serve_requests(rate, seconds, seed, max_requests=4000):
     from paper_1309_3848_gb300 import synth
     return synth.serve_requests(rate, seconds, seed, max_requests=max_requests)
@@ -483,6 +516,7 @@ def run_gpu(args):
     if world == 1 and not args.no_extras:
         line["batched"] = batched_vs_plain(torch, binding, flush)
         line["served"] = serve_sample(rates=(500.0, 2000.0), seconds=1.0)
+        line["next_rows"] = next_rows(torch, binding, flush, jobs, imgs, value)
         gpu_labels = [o.cpu().numpy() for o in outs]
         v, cores, sample, ref_labels = cpu_sample(jobs, imgs)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}

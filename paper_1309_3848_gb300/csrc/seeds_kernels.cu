@@ -130,17 +130,17 @@ __device__ __forceinline__ int cell(const uint16_t *lab, int nx, int ny, int x, 
     return (x < 0 || y < 0 || x >= nx || y >= ny) ? (int)kNoLabel : (int)lab[y * nx + x];
 }
 
-// Shared unit logic over a fetch function for the 8-ring (cells outside the
-// grid read kNoLabel): boundary test, ring validity, sorted distinct
-// candidates.  Returns the candidate count (0 = no move possible).
+// Boundary test and ring validity of a unit over a fetch function for its
+// 8-ring (cells outside the grid read kNoLabel): true when some 4-neighbour
+// has another label and leaving label k keeps k 4-connected (R5, R7).
 template <class Fetch>
-__device__ __forceinline__ int candidates_from(Fetch at, int k, int cand[4])
+__device__ __forceinline__ bool may_leave(Fetch at, int k)
 {
     const int lf = at(-1, 0), rt = at(1, 0);
     const int up = at(0, -1), dn = at(0, 1);
     const bool boundary = (lf != k && lf != kNoLabel) || (rt != k && rt != kNoLabel) ||
                           (up != k && up != kNoLabel) || (dn != k && dn != kNoLabel);
-    if (!boundary) return 0;
+    if (!boundary) return false;
     unsigned m = 0;
     m |= (at(-1, -1) == k) << 0;
     m |= (up == k) << 1;
@@ -150,12 +150,16 @@ __device__ __forceinline__ int candidates_from(Fetch at, int k, int cand[4])
     m |= (dn == k) << 5;
     m |= (at(-1, 1) == k) << 6;
     m |= (lf == k) << 7;
-    if (!ring_allows_leaving(m)) return 0;
-    // sort the four neighbour labels (kNoLabel sorts last); equal labels are
-    // then adjacent.  The candidates keep fixed slots in ascending order, a
-    // slot holding kNoLabel when its label is k, a repeat or no label, so all
-    // later loops index them with constants.
-    int a = lf, b = rt, c = up, d = dn, t;
+    return ring_allows_leaving(m);
+}
+
+// The distinct labels other than k among the four neighbours, in fixed
+// slots in ascending order; a slot holds kNoLabel when its label is k, a
+// repeat or no label, so later loops index them with constants.  Returns
+// how many there are.
+__device__ __forceinline__ int sorted_candidates(int a, int b, int c, int d, int k, int cand[4])
+{
+    int t;
 #define SEEDS_CSWAP(p, q) \
     if (p > q) {          \
         t = p;            \
@@ -169,6 +173,15 @@ __device__ __forceinline__ int candidates_from(Fetch at, int k, int cand[4])
     cand[2] = (c != k && c != b) ? c : (int)kNoLabel;
     cand[3] = (d != k && d != c) ? d : (int)kNoLabel;
     return (cand[0] != kNoLabel) + (cand[1] != kNoLabel) + (cand[2] != kNoLabel) + (cand[3] != kNoLabel);
+}
+
+// Shared unit logic: boundary test, ring validity, sorted distinct
+// candidates.  Returns the candidate count (0 = no move possible).
+template <class Fetch>
+__device__ __forceinline__ int candidates_from(Fetch at, int k, int cand[4])
+{
+    if (!may_leave(at, k)) return 0;
+    return sorted_candidates(at(-1, 0), at(1, 0), at(0, -1), at(0, 1), k, cand);
 }
 
 __device__ __forceinline__ int unit_candidates(const uint16_t *lab, int nx, int ny, int x, int y, int k, int cand[4])
@@ -442,8 +455,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         const int uy = uy0 + r;
         if (ux < ncols && uy < nrows) {
             const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * lane + 2);
-            int cand[4];
-            if (candidates_from([&](int dx, int dy) { return (int)T[dy * kTileW + dx]; }, (int)T[0], cand) > 0)
+            if (may_leave([&](int dx, int dy) { return (int)T[dy * kTileW + dx]; }, (int)T[0]))
                 mine |= 1u << r;
             else
                 im.dec[b][uy * ncols + ux] = kNoMove;
@@ -469,12 +481,31 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * l + 2);  // the unit's cell in the tile
         const int k = T[0];
         int cand[4];
-        candidates_from([&](int dx, int dy) { return (int)T[dy * kTileW + dx]; }, k, cand);
+        // pass 1 found that it may leave
+        const int nc = sorted_candidates(T[-1], T[1], T[-kTileW], T[kTileW], k, cand);
         const int j = jsh[r * 32 + l];
         // Prop. 2 sums G_x = sum_{i in K_p} b_{N_i}(x) as a weighted count
         // over the 5x5 window: w(p,q) = #{i in image: |i-p|,|i-q| <= 1}
         int Gk = 0, Gc[4] = {0, 0, 0, 0}, Kp = 0;
-        if (use_g) {
+        if (use_g && nc == 1 && x >= 2 && y >= 2 && x + 2 < W && y + 2 < H) {
+            // away from the border w(p,q) = (3-|dx|)(3-|dy|) and |K_p| = 9;
+            // with one candidate (the smallest slot value: empty slots hold
+            // kNoLabel) only two labels are counted
+            Kp = 9;
+            const int c0 = min(min(cand[0], cand[1]), min(cand[2], cand[3]));
+            int G0 = 0;
+#pragma unroll
+            for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+                for (int dx = -2; dx <= 2; ++dx) {
+                    const int w = (3 - (dx < 0 ? -dx : dx)) * (3 - (dy < 0 ? -dy : dy));
+                    const int lq = T[dy * kTileW + dx];
+                    Gk += lq == k ? w : 0;
+                    G0 += lq == c0 ? w : 0;
+                }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) Gc[c] = G0;  // read only for the slot holding c0
+        } else if (use_g) {
             int wx[5], wy[5];
 #pragma unroll
             for (int d = 0; d < 5; ++d) {
