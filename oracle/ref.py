@@ -29,6 +29,8 @@ class RefParams(ctypes.Structure):
         ("gamma_num", ctypes.c_int32),
         ("gamma_den", ctypes.c_int32),
         ("color_space", ctypes.c_int32),
+        ("means_iters", ctypes.c_int32),
+        ("compactness", ctypes.c_int32),
     ]
 
 
@@ -59,6 +61,9 @@ def lib():
             L.ref_run_ops.restype = i64
             L.ref_num_ops.argtypes = [vp]
             L.ref_num_ops.restype = i32
+            L.ref_run_means_phase.argtypes = [vp, ctypes.c_int]
+            L.ref_run_means_phase.restype = i64
+            L.ref_decide_means.argtypes = [vp, ctypes.c_int, ctypes.c_int]
             L.ref_lab8.argtypes = [vp, vp, i64, vp]
             L.ref_lab8.restype = None
             L.ref_get_labels.argtypes = [vp, vp]
@@ -84,9 +89,10 @@ class OracleError(RuntimeError):
 
 
 def make_params(width, height, num_superpixels, block_levels, bins_per_channel, iters_per_level,
-                patch=3, gamma=(1, 1), color_space=0):
+                patch=3, gamma=(1, 1), color_space=0, means_iters=0, compactness=0):
     return RefParams(int(width), int(height), int(num_superpixels), int(block_levels), int(bins_per_channel),
-                     int(iters_per_level), int(patch), int(gamma[0]), int(gamma[1]), int(color_space))
+                     int(iters_per_level), int(patch), int(gamma[0]), int(gamma[1]), int(color_space),
+                     int(means_iters), int(compactness))
 
 
 def grid(width, height, num_superpixels, block_levels=0, bins_per_channel=5, iters_per_level=1, patch=3,
@@ -108,9 +114,10 @@ class Ref:
     """One image's oracle state."""
 
     def __init__(self, width, height, num_superpixels, block_levels, bins_per_channel, iters_per_level,
-                 patch=3, gamma=(1, 1), color_space=0):
+                 patch=3, gamma=(1, 1), color_space=0, means_iters=0, compactness=0):
         self.params = make_params(width, height, num_superpixels, block_levels, bins_per_channel,
-                                  iters_per_level, patch, gamma, color_space)
+                                  iters_per_level, patch, gamma, color_space, means_iters, compactness)
+        self.means_iters = int(means_iters)
         self._h = ctypes.c_void_p()
         rc = lib().ref_create(ctypes.byref(self.params), ctypes.byref(self._h))
         if rc:
@@ -150,6 +157,16 @@ class Ref:
         rc = lib().ref_init(self._h, rgb.ctypes.data, stride)
         if rc:
             raise OracleError(rc, "ref_init")
+
+    def run_means_phase(self, phase):
+        n = lib().ref_run_means_phase(self._h, phase)
+        if n < 0:
+            raise OracleError(n, "ref_run_means_phase")
+        return n
+
+    def decide_means(self, x, y):
+        """Means-based decision (R17) for pixel (x, y) against the current labels."""
+        return lib().ref_decide_means(self._h, x, y)
 
     def run_phase(self, level, phase):
         n = lib().ref_run_phase(self._h, level, phase)

@@ -64,6 +64,16 @@
  *       the schedule (init; per block level its phases and a descent; the
  *       pixel phases; the output) yields the partition as it stands, each
  *       pixel labelled by its unit at the current level.
+ *   R17 means-based pixel updates (SPM, Sec. 6.3, run as the last pixel
+ *       iterations, Sec. 6.5), optional: means_iters more pixel iterations
+ *       of four parity phases in which a boundary pixel that may leave
+ *       (R5, R7) moves to the candidate whose mean is nearest in SLIC's
+ *       distance, colour codes plus (m/S)^2 times the squared distance to
+ *       the superpixel's centroid (S^2 = N/K, m = compactness), if strictly
+ *       nearer than its own superpixel's mean taken with the pixel in it;
+ *       means from the phase-start state; no boundary term; evaluated in
+ *       IEEE double in the order written in means_distance, so that any
+ *       implementation doing the same operations decides the same way.
  *   R14 sequential mode (quality reference only): per iteration the units
  *       are visited in a random permutation (SplitMix64 + Fisher-Yates),
  *       each boundary unit proposes one uniformly drawn candidate, and an
@@ -88,6 +98,8 @@ typedef struct {
     int32_t gamma_num;
     int32_t gamma_den;
     int32_t color_space; /* 0 = RGB bytes (R1), 1 = CIE L*a*b* (R16) */
+    int32_t means_iters; /* R17: means-based pixel iterations after the histogram ones */
+    int32_t compactness; /* R17: SLIC's m, weight of the spatial distance */
 } ref_params;
 
 typedef struct {
@@ -105,6 +117,9 @@ typedef struct {
     int64_t *tmp_a;  /* A_k \ L */
     int32_t *moves;  /* (unit, k, n) triples of the current phase */
     int64_t moves_cap;
+    uint8_t *code;         /* colour code (the channels the bins are taken from) of every pixel */
+    int64_t *msum;         /* R17: per superpixel: sums of the 3 codes, of x and of y */
+    double means_w;        /* R17: m^2 K / N, the spatial weight (m/S)^2 with S^2 = N/K */
     int64_t lab_lin[256];  /* R16: sRGB byte -> linear light * 2^24 */
     int64_t lab_m[3][3];   /* R16: linear RGB -> XYZ / white, * 2^20 */
 } ref_state;
@@ -133,6 +148,8 @@ int ref_check_params(const ref_params *p)
     if (p->gamma_num < 0 || p->gamma_num > 1024) return REF_EINVAL;
     if (p->gamma_den < 1 || p->gamma_den > 1024) return REF_EINVAL;
     if (p->color_space != 0 && p->color_space != 1) return REF_EINVAL;
+    if (p->means_iters < 0 || p->means_iters > 1000) return REF_EINVAL;
+    if (p->compactness < 0 || p->compactness > 1024) return REF_EINVAL;
     return REF_OK;
 }
 
@@ -167,6 +184,8 @@ void ref_destroy(ref_state *st)
     free(st->tmp_l);
     free(st->tmp_a);
     free(st->moves);
+    free(st->code);
+    free(st->msum);
     free(st);
 }
 
@@ -204,6 +223,9 @@ int ref_create(const ref_params *p, ref_state **out)
         for (int i = 0; i <= st->nbx[l]; ++i) st->xe[l][i] = (int)edge_at(i, st->W, st->nbx[l]);
         for (int i = 0; i <= st->nby[l]; ++i) st->ye[l][i] = (int)edge_at(i, st->H, st->nby[l]);
     }
+    st->code = (uint8_t *)calloc((size_t)N * 3, 1);
+    st->msum = (int64_t *)calloc((size_t)st->K * 5, sizeof(int64_t));
+    st->means_w = (double)((int64_t)p->compactness * p->compactness * st->K) / (double)N;
     st->bin = (int *)calloc((size_t)N, sizeof(int));
     st->lab = (int *)calloc((size_t)N, sizeof(int));
     st->hist = (int64_t *)calloc((size_t)st->K * st->nbins, sizeof(int64_t));
@@ -213,7 +235,8 @@ int ref_create(const ref_params *p, ref_state **out)
     /* a phase holds at most ceil(nbx/2)*ceil(nby/2) units; level 0 is the largest grid */
     st->moves_cap = (int64_t)((st->W + 1) / 2) * ((st->H + 1) / 2);
     st->moves = (int32_t *)malloc(sizeof(int32_t) * 3 * st->moves_cap);
-    if (!st->bin || !st->lab || !st->hist || !st->size || !st->tmp_l || !st->tmp_a || !st->moves) {
+    if (!st->bin || !st->lab || !st->hist || !st->size || !st->tmp_l || !st->tmp_a || !st->moves || !st->code ||
+        !st->msum) {
         ref_destroy(st);
         return REF_ENOMEM;
     }
@@ -371,6 +394,7 @@ int ref_init(ref_state *st, const uint8_t *rgb, int64_t row_stride)
             const uint8_t *px = rgb + (int64_t)y * row_stride + 3 * (int64_t)x;
             int c[3] = {px[0], px[1], px[2]};
             if (st->p.color_space == 1) rgb_to_lab8(st, px[0], px[1], px[2], c);
+            for (int q = 0; q < 3; ++q) st->code[3 * ((int64_t)y * st->W + x) + q] = (uint8_t)c[q];
             int br = channel_bin(c[0], B), bg = channel_bin(c[1], B), bb = channel_bin(c[2], B);
             int sx = find_interval(sxe, st->gx, x);
             st->bin[(int64_t)y * st->W + x] = br * B * B + bg * B + bb;
@@ -604,6 +628,68 @@ static void apply_move(ref_state *st, int level, int bx, int by, int k, int n)
 }
 
 /* ------------------------------------------------------------------ */
+/* means-based pixel updates (R17)                                      */
+/* ------------------------------------------------------------------ */
+
+/* sums of the colour codes and of the coordinates of every superpixel */
+static void means_recount(ref_state *st)
+{
+    memset(st->msum, 0, sizeof(int64_t) * (size_t)st->K * 5);
+    for (int y = 0; y < st->H; ++y)
+        for (int x = 0; x < st->W; ++x) {
+            int64_t i = (int64_t)y * st->W + x;
+            int64_t *m = st->msum + (int64_t)st->lab[i] * 5;
+            m[0] += st->code[3 * i];
+            m[1] += st->code[3 * i + 1];
+            m[2] += st->code[3 * i + 2];
+            m[3] += x;
+            m[4] += y;
+        }
+}
+
+/* SLIC's squared distance of pixel (x,y) to the mean of superpixel `label`
+ * (colour codes, then coordinates weighted by (m/S)^2), in IEEE double in
+ * this order of operations */
+static double means_distance(const ref_state *st, int x, int y, int label)
+{
+    const int64_t *m = st->msum + (int64_t)label * 5;
+    const uint8_t *c = st->code + 3 * ((int64_t)y * st->W + x);
+    double n = (double)st->size[label];
+    double dc = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        double t = (double)c[q] - (double)m[q] / n;
+        dc = dc + t * t;
+    }
+    double gx = (double)x - (double)m[3] / n;
+    double gy = (double)y - (double)m[4] / n;
+    double ds = gx * gx + gy * gy;
+    return dc + st->means_w * ds;
+}
+
+/* a boundary pixel that may leave (R5, R7) moves to the candidate with the
+ * nearest mean when that is strictly nearer than its own superpixel's mean
+ * (which includes the pixel, as SLIC assigns to the nearest centre); ties
+ * to the smallest label */
+static int decide_pixel_means(ref_state *st, int x, int y)
+{
+    int k = st->lab[(int64_t)y * st->W + x];
+    int cand[4];
+    int nc = candidates(st, 0, x, y, k, cand);
+    if (nc == 0) return -1;
+    if (!leaving_keeps_connected(st, 0, x, y, k)) return -1;
+    int best = -1;
+    double db = 0.0;
+    for (int c = 0; c < nc; ++c) {
+        double d = means_distance(st, x, y, cand[c]);
+        if (best < 0 || d < db) {
+            best = cand[c];
+            db = d;
+        }
+    }
+    return db < means_distance(st, x, y, k) ? best : -1;
+}
+
+/* ------------------------------------------------------------------ */
 /* the parity schedule (R4, R6)                                         */
 /* ------------------------------------------------------------------ */
 
@@ -630,7 +716,33 @@ int64_t ref_run_phase(ref_state *st, int level, int phase)
     return nm;
 }
 
-/* whole schedule: levels L..1 (blocks), then level 0 (pixels) */
+/* One means-based pixel phase (R17): the superpixel means are taken at the
+ * phase start, every pixel of the phase is judged against them, then all
+ * accepted moves are applied.  Returns the number of moves. */
+int64_t ref_run_means_phase(ref_state *st, int phase)
+{
+    if (phase < 0 || phase > 3) return REF_EINVAL;
+    int py = phase >> 1, px = phase & 1;
+    int64_t nm = 0;
+    means_recount(st);
+    for (int y = py; y < st->H; y += 2)
+        for (int x = px; x < st->W; x += 2) {
+            int n = decide_pixel_means(st, x, y);
+            if (n < 0) continue;
+            st->moves[3 * nm + 0] = y * st->W + x;
+            st->moves[3 * nm + 1] = st->lab[(int64_t)y * st->W + x];
+            st->moves[3 * nm + 2] = n;
+            ++nm;
+        }
+    for (int64_t t = 0; t < nm; ++t) {
+        int u = st->moves[3 * t];
+        apply_move(st, 0, u % st->W, u / st->W, st->moves[3 * t + 1], st->moves[3 * t + 2]);
+    }
+    return nm;
+}
+
+/* whole schedule: levels L..1 (blocks), then level 0 (pixels), then the
+ * means-based pixel iterations (R17) */
 int64_t ref_run(ref_state *st, const uint8_t *rgb, int64_t row_stride)
 {
     int rc = ref_init(st, rgb, row_stride);
@@ -639,13 +751,17 @@ int64_t ref_run(ref_state *st, const uint8_t *rgb, int64_t row_stride)
     for (int level = st->L; level >= 0; --level)
         for (int it = 0; it < st->p.iters_per_level; ++it)
             for (int phase = 0; phase < 4; ++phase) total += ref_run_phase(st, level, phase);
+    for (int it = 0; it < st->p.means_iters; ++it)
+        for (int phase = 0; phase < 4; ++phase) total += ref_run_means_phase(st, phase);
     return total;
 }
 
 /* R15 anytime termination (Sec. 5.4): the schedule as a list of ops -- the
  * initialisation, then for each level L..1 its 4*iters phases and the
  * descent to the next finer level, then the 4*iters pixel phases, then the
- * output -- run only up to its first `nops` ops (nops >= 1).  Blocks move
+ * output -- run only up to its first `nops` ops (nops >= 1).  With means
+ * iterations (R17) the op list has, before the output, one op that starts
+ * them and their 4*means_iters phases.  Blocks move
  * their pixels whole here, so descents and the output leave the pixel
  * labels as they are, and the partition after any prefix is the pixel
  * labels.  Returns the number of accepted moves. */
@@ -663,13 +779,36 @@ int64_t ref_run_ops(ref_state *st, const uint8_t *rgb, int64_t row_stride, int32
                 total += ref_run_phase(st, level, phase);
                 ++done;
             }
-        ++done; /* the descent to level-1, or after level 0 the output */
+        if (level > 0) ++done; /* the descent to level-1 */
     }
-    return total;
+    if (st->p.means_iters > 0) {
+        ++done; /* the start of the means iterations (R17) */
+        for (int it = 0; it < st->p.means_iters; ++it)
+            for (int phase = 0; phase < 4; ++phase) {
+                if (done >= nops) return total;
+                total += ref_run_means_phase(st, phase);
+                ++done;
+            }
+    }
+    return total; /* the output follows */
 }
 
 /* number of ops in the schedule of R15 */
-int32_t ref_num_ops(const ref_state *st) { return 1 + (st->L + 1) * (4 * st->p.iters_per_level + 1); }
+int32_t ref_num_ops(const ref_state *st)
+{
+    int32_t n = 1 + (st->L + 1) * (4 * st->p.iters_per_level + 1);
+    if (st->p.means_iters > 0) n += 1 + 4 * st->p.means_iters;
+    return n;
+}
+
+/* the means-based decision for one pixel against the current labels
+ * (target label, or -1 for no move; test hook) */
+int ref_decide_means(ref_state *st, int x, int y)
+{
+    if (x < 0 || y < 0 || x >= st->W || y >= st->H) return REF_EINVAL;
+    means_recount(st);
+    return decide_pixel_means(st, x, y);
+}
 
 /* ------------------------------------------------------------------ */
 /* state access                                                         */

@@ -29,7 +29,11 @@ MUTANTS = {
     "LAB a* from the wrong channel pair": ("500 * (f[0] - f[1])", "500 * (f[0] - f[2])"),
     "LAB without the sRGB decoding curve": ("pow((c + 0.055) / 1.055, 2.4)", "c"),
     "LAB bins from the RGB bytes": ("if (st->p.color_space == 1) rgb_to_lab8", "if (0) rgb_to_lab8"),
-    "anytime prefix skips the descent op": ("        ++done; /* the descent", "        /* the descent"),
+    "means distance drops the spatial term": ("return dc + st->means_w * ds;", "return dc;"),
+    "means ties go to the largest label": ("if (best < 0 || d < db) {", "if (best < 0 || d <= db) {"),
+    "means sums the bins, not the colour codes": ("m[0] += st->code[3 * i];", "m[0] += st->bin[i];"),
+    "means centroid row from x": ("m[4] += y;", "m[4] += x;"),
+    "anytime prefix skips the descent op": ("        if (level > 0) ++done; /* the descent", "        /* the descent"),
     "anytime prefix runs one phase too many": ("if (done >= nops) return total;", "if (done > nops) return total;"),
 }
 

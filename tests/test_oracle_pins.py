@@ -514,41 +514,52 @@ def test_a_move_that_splits_its_superpixel_is_refused():
 # anytime termination (Sec. 5.4, reading R15)
 # --------------------------------------------------------------------------
 
-def paper_op_list(L, iters):
+def paper_op_list(L, iters, means_iters=0):
     """The schedule as ops, written out from Sec. 5: the initialisation;
     for each block level L..1 its iterations of four parity phases, then the
-    descent; the pixel level's phases; the output."""
+    descent; the pixel level's phases; with means iterations (Sec. 6.5) an op
+    that starts them and their phases; the output."""
     ops = [("init",)]
     for level in range(L, -1, -1):
         for _ in range(iters):
             for phase in range(4):
                 ops.append(("phase", level, phase))
-        ops.append(("descend",) if level > 0 else ("output",))
+        if level > 0:
+            ops.append(("descend",))
+    if means_iters:
+        ops.append(("means",))
+        for _ in range(means_iters):
+            for phase in range(4):
+                ops.append(("mphase", phase))
+    ops.append(("output",))
     return ops
 
 
 ANYTIME_CASES = [
-    # W, H, K, L, B, iters, image seed
-    (37, 29, 6, 2, 4, 1, 11),
-    (24, 40, 5, 1, 3, 2, 12),
-    (30, 22, 4, 0, 5, 2, 13),
+    # W, H, K, L, B, iters, image seed, means iterations, compactness
+    (37, 29, 6, 2, 4, 1, 11, 0, 0),
+    (24, 40, 5, 1, 3, 2, 12, 0, 0),
+    (30, 22, 4, 0, 5, 2, 13, 0, 0),
+    (33, 25, 5, 1, 4, 1, 14, 2, 10),
 ]
 
 
 @pytest.mark.parametrize("case", ANYTIME_CASES)
 def test_anytime_prefixes_follow_the_op_list(case):
-    W, H, K, L, B, iters, seed = case
+    W, H, K, L, B, iters, seed, mi, m = case
     img = rgb_noise(W, H, seed)
-    ops = paper_op_list(L, iters)
-    r = ref.Ref(W, H, K, L, B, iters)
+    ops = paper_op_list(L, iters, mi)
+    r = ref.Ref(W, H, K, L, B, iters, means_iters=mi, compactness=m)
     assert r.num_ops() == len(ops)
     for n in range(1, len(ops) + 2):
         got = r.run_ops(img, n)
-        want = ref.Ref(W, H, K, L, B, iters)
+        want = ref.Ref(W, H, K, L, B, iters, means_iters=mi, compactness=m)
         want.init(img)
         for op in ops[1:n]:
             if op[0] == "phase":
                 want.run_phase(op[1], op[2])
+            elif op[0] == "mphase":
+                want.run_means_phase(op[1])
         assert np.array_equal(got, want.labels()), "prefix of %d ops" % n
         # Sec. 5.4: stopping at any point leaves a valid partition
         assert_valid_partition(got, r.K)
@@ -644,3 +655,120 @@ def test_lab_bins_are_r1_bins_of_the_lab_codes(B):
     rgb_bins.init(img)
     qq = img.astype(np.int64) * B // 256
     assert np.array_equal(rgb_bins.bins(), qq[..., 0] * B * B + qq[..., 1] * B + qq[..., 2])
+
+
+# --------------------------------------------------------------------------
+# means-based pixel updates (SPM, Sec. 6.3 and 6.5; reading R17)
+# --------------------------------------------------------------------------
+
+def exact_means_decision(labels, codes, K, m, x, y):
+    """The means rule in exact fractions: sums recounted from the labels,
+    SLIC's distance with (m/S)^2 = m^2 K / N; returns (target or -1, the
+    smallest relative gap between the winner and the runner-up or stay)."""
+    H, W = labels.shape
+    k = int(labels[y, x])
+    cand = brute.candidates(labels, x, y)
+    if not cand or not brute.ring_connected(labels, x, y, k):
+        return -1, None
+    w = Fraction(m * m * K, W * H)
+
+    def dist(lbl):
+        ys, xs = np.nonzero(labels == lbl)
+        n = len(xs)
+        d = Fraction(0)
+        for q in range(3):
+            d += (Fraction(int(codes[y, x, q])) - Fraction(int(codes[ys, xs, q].sum()), n)) ** 2
+        d += w * ((x - Fraction(int(xs.sum()), n)) ** 2 + (y - Fraction(int(ys.sum()), n)) ** 2)
+        return d
+
+    dk = dist(k)
+    ds = sorted((dist(c), c) for c in cand)
+    best_d, best = ds[0]
+    gaps = [abs(dk - best_d)] + ([abs(ds[1][0] - best_d)] if len(ds) > 1 and ds[1][0] != best_d else [])
+    scale = max(dk, Fraction(1))
+    return (best if best_d < dk else -1), min(g / scale for g in gaps)
+
+
+@pytest.mark.parametrize("seed,m,color", [(1, 0, 0), (2, 10, 0), (3, 40, 1), (4, 3, 1)])
+def test_means_decisions_match_exact_fractions(seed, m, color):
+    W, H, K = 26, 20, 6
+    img = rgb_noise(W, H, 60 + seed, 40, 220)
+    r = ref.Ref(W, H, K, 1, 4, 1, color_space=color, means_iters=1, compactness=m)
+    r.run_ops(img, 1 + 2 * (4 + 1))  # grid, the block level and the histogram pixel phases
+    labels = r.labels()
+    codes = r.lab8(img) if color else img
+    checked = 0
+    for y in range(H):
+        for x in range(W):
+            want, gap = exact_means_decision(labels, codes, r.K, m, x, y)
+            if gap is not None and gap < Fraction(1, 10 ** 9):
+                continue  # a near tie: double rounding may decide either way
+            assert r.decide_means(x, y) == want, (x, y)
+            checked += want >= 0
+    assert checked > 0, "no pixel wanted to move"
+
+
+def two_region_state(m):
+    """8 x 4 image, K = 2 (left and right halves); column x = 3 of the left
+    superpixel has the right superpixel's colour."""
+    img = np.zeros((4, 8, 3), np.uint8)
+    img[:, 3:] = 200
+    r = ref.Ref(8, 4, 2, 0, 4, 1, patch=0, means_iters=1, compactness=m)
+    r.init(img)
+    assert r.gx == 2 and r.gy == 1
+    return r
+
+
+def test_means_move_to_the_nearer_colour_mean():
+    r = two_region_state(0)
+    assert r.decide_means(3, 0) == 1 and r.decide_means(3, 1) == 1
+    assert r.decide_means(2, 1) == -1  # already nearest to its own mean
+    r.run_means_phase(1)  # phase (py, px) = (0, 1): x odd, y even
+    assert r.labels()[0, 3] == 1 and r.labels()[2, 3] == 1
+
+
+def test_means_compactness_keeps_pixels_near_their_centroid():
+    r = two_region_state(1024)  # (m/S)^2 = 1024^2 * 2 / 32: the spatial term dominates
+    assert r.decide_means(3, 0) == -1 and r.decide_means(3, 1) == -1
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_invariants_after_every_means_phase(seed):
+    W, H = 31, 23
+    img = rgb_noise(W, H, 80 + seed)
+    r = ref.Ref(W, H, 7, 1, 3, 1, means_iters=2, compactness=5 * seed)
+    r.run_ops(img, r.num_ops() - 1 - 8)  # up to the start of the means iterations
+    bins = r.bins()
+    moved = 0
+    for _ in range(2):
+        for phase in range(4):
+            moved += r.run_means_phase(phase)
+            lab = r.labels()
+            h, s = r.hist()
+            h2, s2 = recount(lab, bins, r.K, r.nbins)
+            assert np.array_equal(h, h2) and np.array_equal(s, s2)
+            assert_valid_partition(lab, r.K)
+    assert moved > 0
+
+
+def test_zero_means_iterations_leave_the_run_unchanged():
+    W, H = 35, 27
+    img = rgb_noise(W, H, 90)
+    a = ref.Ref(W, H, 6, 1, 4, 2).run(img)
+    b = ref.Ref(W, H, 6, 1, 4, 2, means_iters=0, compactness=30).run(img)
+    c = ref.Ref(W, H, 6, 1, 4, 2, means_iters=1).run(img)
+    assert np.array_equal(a, b)
+    assert not np.array_equal(a, c)
+
+
+def test_means_equal_candidates_go_to_the_smallest_label():
+    # p = (4, 1) is bright in a dark superpixel 0; its neighbours 1 and 2 are
+    # both entirely bright, so their means tie exactly
+    labels = np.array([[0] * 9, [1, 1, 1, 1, 0, 2, 2, 2, 2], [1, 1, 1, 1, 1, 2, 2, 2, 2]], np.int32)
+    img = np.repeat(np.where(labels == 0, 0, 200)[..., None], 3, axis=2).astype(np.uint8)
+    img[1, 4] = 200
+    r = ref.Ref(9, 3, 3, 0, 4, 1, patch=0, means_iters=1)
+    r.init(img)
+    assert r.K == 3
+    r.set_labels(labels)
+    assert r.decide_means(4, 1) == 1
