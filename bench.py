@@ -175,7 +175,7 @@ def oracle_levels(job):
 def oracle_run(job, img):
     from oracle import ref
     r = ref.Ref(job.image.width, job.image.height, job.num_superpixels, oracle_levels(job), job.bins_per_channel,
-                job.iters_per_level, job.patch, job.gamma, job.color_space)
+                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters, job.compactness)
     return r.run(img)
 
 
@@ -254,7 +254,8 @@ def gpu_params(binding, job):
     if job.clamp_levels:
         L = min(L, binding.feasible_levels(job.image.width, job.image.height, job.num_superpixels))
     return binding.make_params(job.image.width, job.image.height, job.num_superpixels, L, job.bins_per_channel,
-                               job.iters_per_level, job.patch, job.gamma, job.color_space)
+                               job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters,
+                               job.compactness)
 
 
 def timed_steps(torch, fn, steps, flush, kernel_ms=None):
@@ -313,8 +314,10 @@ def batched_vs_plain(torch, binding, flush, steps=5):
 
 
 def next_rows(torch, binding, flush, jobs, imgs, rgb_value, steps=5):
-    """The widened rows on the bench workload: LAB colour bins (Sec. 6.2) in
-    Mpixel/s beside the RGB run, and anytime termination (Sec. 5.4) -- the
+    """The widened rows on the bench workload: LAB colour bins (Sec. 6.2) and
+    two means-based pixel iterations after the histogram ones (Sec. 6.3,
+    6.5) in Mpixel/s beside the plain run, and anytime termination (Sec.
+    5.4) -- the
     steps a launch reaches within device-time budgets of a quarter, half and
     three quarters of a full run, and the time the stopped call takes."""
     import dataclasses
@@ -322,12 +325,16 @@ def next_rows(torch, binding, flush, jobs, imgs, rgb_value, steps=5):
     d = [torch.from_numpy(im).cuda() for im in imgs]
     outs = [torch.empty((j.image.height, j.image.width), dtype=torch.int32, device="cuda") for j in jobs]
 
-    lab_ctx = binding.SeedsContext([gpu_params(binding, dataclasses.replace(j, color_space=1)) for j in jobs])
-    for _ in range(3):
-        lab_ctx.run(d, outs)
-    t_lab, _ = timed_steps(torch, lambda: lab_ctx.run(d, outs), steps, flush)
-    lab_ctx.check_status()
-    lab_value = px / (statistics.mean(t_lab) / 1e3) / 1e6
+    def variant(**kw):
+        vctx = binding.SeedsContext([gpu_params(binding, dataclasses.replace(j, **kw)) for j in jobs])
+        for _ in range(3):
+            vctx.run(d, outs)
+        t, _ = timed_steps(torch, lambda: vctx.run(d, outs), steps, flush)
+        vctx.check_status()
+        return px / (statistics.mean(t) / 1e3) / 1e6
+
+    lab_value = variant(color_space=1)
+    means_value = variant(means_iters=2, compactness=10)
 
     ctx = binding.SeedsContext([gpu_params(binding, j) for j in jobs])
     for _ in range(3):
@@ -342,6 +349,8 @@ def next_rows(torch, binding, flush, jobs, imgs, rgb_value, steps=5):
         budgets.append({"budget_us": budget_ns / 1e3, "steps": ctx.anytime_steps(), "ms": statistics.mean(t)})
     ctx.check_status()
     return {"lab": {"mpix_s": lab_value, "over_rgb": lab_value / rgb_value},
+            "means_post": {"means_iters": 2, "compactness": 10, "mpix_s": means_value,
+                           "over_histogram_only": means_value / rgb_value},
             "anytime": {"full_steps": full_steps, "full_ms": full_ms, "budgets": budgets}}
 
 

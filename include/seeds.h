@@ -79,7 +79,17 @@ typedef struct seeds_ctx seeds_ctx;
  *                      computed in exact integer fixed point: the sRGB
  *                      decoding curve as linear light * 2^24, the sRGB to
  *                      XYZ matrix rows divided by the D65 white * 2^20,
- *                      f(t) * 2^20 by an exact integer cube root */
+ *                      f(t) * 2^20 by an exact integer cube root
+ *   means_iters        0..1000 more pixel-level iterations after the
+ *                      histogram ones in which a pixel moves to the neighbour
+ *                      superpixel whose mean is nearest in SLIC's distance
+ *                      (Sec. 6.3 SPM, run as post-processing, Sec. 6.5): the
+ *                      squared distance of its colour code to the mean code
+ *                      plus (m/S)^2 times the squared distance to the
+ *                      centroid, S^2 = W*H/K; strictly nearer than its own
+ *                      superpixel's mean (with the pixel in it), ties to the
+ *                      smallest label, IEEE double without fused operations
+ *   compactness        m in 0..1024 (0 = colour only) */
 typedef struct {
     int32_t width, height;
     int32_t num_superpixels;
@@ -89,6 +99,8 @@ typedef struct {
     int32_t patch;
     int32_t gamma_num, gamma_den;
     int32_t color_space;
+    int32_t means_iters;
+    int32_t compactness;
 } seeds_params;
 
 /* Result-invariant launch knobs (any value gives identical labels).
@@ -308,9 +320,11 @@ int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int64_t row_st
 
 /* Operation list of image i: op 0 quantises and builds the grid and the
  * histograms; then one op per phase (level L..0, iteration, phase 0..3)
- * with one descent op after each block level; the last op is the output
- * (only run by seeds_batch_run).  kind: 0 init, 1 phase, 2 descend,
- * 3 output. */
+ * with one descent op after each block level; with means_iters > 0 an op
+ * that sums every superpixel's colour codes and coordinates, then one op per
+ * means-based pixel phase; the last op is the output (only run by
+ * seeds_batch_run).  kind: 0 init, 1 phase, 2 descend, 3 output, 5 start of
+ * the means iterations, 6 means-based phase. */
 int seeds_debug_num_ops(const seeds_ctx *c, int32_t i, int32_t *n_ops);
 int seeds_debug_op_info(const seeds_ctx *c, int32_t i, int32_t op, int32_t *kind, int32_t *level, int32_t *phase);
 

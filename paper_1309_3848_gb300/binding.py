@@ -54,7 +54,8 @@ class seeds_params(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("num_superpixels", ctypes.c_int32),
                 ("block_levels", ctypes.c_int32), ("bins_per_channel", ctypes.c_int32),
                 ("iters_per_level", ctypes.c_int32), ("patch", ctypes.c_int32), ("gamma_num", ctypes.c_int32),
-                ("gamma_den", ctypes.c_int32), ("color_space", ctypes.c_int32)]
+                ("gamma_den", ctypes.c_int32), ("color_space", ctypes.c_int32), ("means_iters", ctypes.c_int32),
+                ("compactness", ctypes.c_int32)]
 
 
 class seeds_server_config(ctypes.Structure):
@@ -138,10 +139,13 @@ def check(code: int, what: str) -> int:
 
 
 def make_params(width, height, num_superpixels, block_levels, bins_per_channel, iters_per_level, patch=3,
-                gamma=(1, 1), color_space=0) -> seeds_params:
-    """color_space: 0 = RGB bytes, 1 = 8-bit CIE L*a*b* codes (Sec. 6.2)."""
+                gamma=(1, 1), color_space=0, means_iters=0, compactness=0) -> seeds_params:
+    """color_space: 0 = RGB bytes, 1 = 8-bit CIE L*a*b* codes (Sec. 6.2);
+    means_iters / compactness: means-based pixel iterations with SLIC's m
+    (Sec. 6.3, 6.5)."""
     return seeds_params(int(width), int(height), int(num_superpixels), int(block_levels), int(bins_per_channel),
-                        int(iters_per_level), int(patch), int(gamma[0]), int(gamma[1]), int(color_space))
+                        int(iters_per_level), int(patch), int(gamma[0]), int(gamma[1]), int(color_space),
+                        int(means_iters), int(compactness))
 
 
 def feasible_levels(width, height, num_superpixels) -> int:

@@ -25,8 +25,11 @@ constexpr int kMaxLevels = SEEDS_MAX_LEVELS;
 constexpr uint16_t kNoLabel = 0xFFFF;   // labels are < 65535
 constexpr uint32_t kNoMove = 0xFFFFFFFFu;
 
-// op kinds (0..3 as in the debug hooks of seeds.h)
-enum : int32_t { OP_INIT = 0, OP_PHASE = 1, OP_DESCEND = 2, OP_OUTPUT = 3, OP_CATCHUP = 4 };
+// op kinds (as in the debug hooks of seeds.h); OP_MINIT and OP_MPHASE are
+// the start and the phases of the means-based pixel iterations (Sec. 6.5)
+enum : int32_t { OP_INIT = 0, OP_PHASE = 1, OP_DESCEND = 2, OP_OUTPUT = 3, OP_CATCHUP = 4, OP_MINIT = 5, OP_MPHASE = 6 };
+
+__host__ __device__ inline bool is_phase(int kind) { return kind == OP_PHASE || kind == OP_MPHASE; }
 
 // device error word bits
 enum : int32_t { DERR_TIMEOUT = 1, DERR_BOUNDS = 2, DERR_INJECTED = 4 };
@@ -39,6 +42,8 @@ struct DevImage {
     int32_t hist_sk, hist_sj;  // hist index = k*hist_sk + j*hist_sj (either layout)
     int32_t small_area;   // blocks up to this many pixels are judged by one thread
     int32_t color;        // 0: RGB bytes, 1: 8-bit CIE L*a*b* codes (Sec. 6.2)
+    int32_t means_iters;  // means-based pixel iterations after the histogram ones
+    double means_w;       // (m/S)^2 = m^2 K / N, the spatial weight of SLIC's distance
     int32_t nbx[kMaxLevels + 1], nby[kMaxLevels + 1];  // level 0 = W, H
     int32_t maxarea[kMaxLevels + 1];                   // largest block of a level
     const int32_t *xe[kMaxLevels + 1];                 // block column edges, level >= 1
@@ -49,6 +54,7 @@ struct DevImage {
     int32_t *hist[2];                   // K x nbins counts, 2 buffers
     int32_t *size[2];                   // |A_k|, 2 buffers
     uint32_t *dec[2];                   // per unit of a phase: (k << 16 | n) or kNoMove
+    unsigned long long *msum[2];        // K x 5: sums of the 3 colour codes, of x, of y (means iterations)
     int32_t units_cap;                  // entries of each dec buffer
     // per call
     const uint8_t *rgb;
@@ -136,10 +142,14 @@ struct OpDesc {
 };
 
 // init, block levels L..1 (iters*4 phases, then a descent), the pixel level
-// (iters*4 phases), output
-__host__ __device__ inline int num_ops(int L, int iters) { return 1 + L * (4 * iters + 1) + 4 * iters + 1; }
+// (iters*4 phases), with means iterations mi > 0 their start and mi*4
+// phases, output
+__host__ __device__ inline int num_ops(int L, int iters, int mi)
+{
+    return 1 + L * (4 * iters + 1) + 4 * iters + (mi > 0 ? 1 + 4 * mi : 0) + 1;
+}
 
-__host__ __device__ inline OpDesc op_at(int L, int iters, int o)
+__host__ __device__ inline OpDesc op_at(int L, int iters, int mi, int o)
 {
     OpDesc d{OP_OUTPUT, 0, 0};
     const int per = 4 * iters + 1, P = 1 + L * per;
@@ -157,6 +167,11 @@ __host__ __device__ inline OpDesc op_at(int L, int iters, int o)
     } else if (o < P + 4 * iters) {
         d.kind = OP_PHASE;
         d.phase = (o - P) & 3;
+    } else if (mi > 0 && o == P + 4 * iters) {
+        d.kind = OP_MINIT;
+    } else if (mi > 0 && o < P + 4 * iters + 1 + 4 * mi) {
+        d.kind = OP_MPHASE;
+        d.phase = (o - P - 4 * iters - 1) & 3;
     }
     return d;
 }
@@ -203,13 +218,13 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
                                             int64_t *vt)
 {
     int n = 0;
-    const OpDesc op = op_at(im.L, im.iters, o);
+    const OpDesc op = op_at(im.L, im.iters, im.means_iters, o);
     int cphase = -1;
     if (catchup && o > 0) {
-        const OpDesc pv = op_at(im.L, im.iters, o - 1);
-        if (pv.kind == OP_PHASE && op.kind == OP_PHASE && pv.level == op.level) {
+        const OpDesc pv = op_at(im.L, im.iters, im.means_iters, o - 1);
+        if (is_phase(pv.kind) && op.kind == pv.kind && pv.level == op.level) {
             cphase = pv.phase;
-        } else if (pv.kind == OP_PHASE) {
+        } else if (is_phase(pv.kind)) {
             // large blocks are replayed by a warp each, small blocks by a
             // thread each, pixels kCatchupPerLane to a thread
             int64_t units = phase_units(im, pv.level, pv.phase);
@@ -230,6 +245,7 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
         units = im.K;
         group = 32;
         break;
+    case OP_MPHASE:
     case OP_PHASE:
         if (op.level == 0) {  // warp tiles
             units = pixel_tiles(im, op.phase, cphase);
@@ -240,6 +256,9 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
             units = (int64_t)cols * rows;
             group = level_group(im, op.level);
         }
+        break;
+    case OP_MINIT:  // a thread per pixel
+        units = (int64_t)im.W * im.H;
         break;
     case OP_DESCEND:
         // a thread per cell of the finer grid, or per 4 pixels of a row

@@ -31,7 +31,7 @@ struct ImageHost {
     int units_cap = 0;
     // byte offsets inside the context's pool
     size_t off_bins = 0, off_lab[kMaxLevels + 1][2] = {}, off_xe[kMaxLevels + 1] = {}, off_ye[kMaxLevels + 1] = {};
-    size_t off_hist[2] = {}, off_size[2] = {}, off_dec[2] = {}, bytes = 0;
+    size_t off_hist[2] = {}, off_size[2] = {}, off_dec[2] = {}, off_msum[2] = {}, bytes = 0;
 };
 
 constexpr size_t kAlign = 256;
@@ -60,6 +60,8 @@ inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t 
     if (p->iters_per_level < 1 || p->iters_per_level > 1000) return SEEDS_ERR_INVALID;
     if (p->patch != 0 && p->patch != 3) return SEEDS_ERR_INVALID;
     if (p->color_space != 0 && p->color_space != 1) return SEEDS_ERR_INVALID;
+    if (p->means_iters < 0 || p->means_iters > 1000) return SEEDS_ERR_INVALID;
+    if (p->compactness < 0 || p->compactness > 1024) return SEEDS_ERR_INVALID;
     if (p->gamma_num < 0 || p->gamma_num > 1024 || p->gamma_den < 1 || p->gamma_den > 1024) return SEEDS_ERR_INVALID;
     const double Kd = p->num_superpixels, Wd = p->width, Hd = p->height;
     long long gx = std::llround(std::sqrt(Kd * Wd / Hd));
@@ -112,9 +114,9 @@ inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t 
 
     // op list (the same one the kernels derive with op_at)
     h.ops.clear();
-    const int nops = num_ops(L, p->iters_per_level);
+    const int nops = num_ops(L, p->iters_per_level, p->means_iters);
     for (int o = 0; o < nops; ++o) {
-        const OpDesc d = op_at(L, p->iters_per_level, o);
+        const OpDesc d = op_at(L, p->iters_per_level, p->means_iters, o);
         h.ops.push_back({d.kind, d.level, d.phase});
     }
     h.units_cap = (int)(((int64_t)(p->width + 1) / 2) * ((p->height + 1) / 2));
@@ -142,6 +144,8 @@ inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t 
         off = align_up(off + (size_t)h.K * 4);
         h.off_dec[q] = off;
         off = align_up(off + (size_t)h.units_cap * 4);
+        h.off_msum[q] = off;  // per superpixel sums for the means iterations
+        if (p->means_iters > 0) off = align_up(off + (size_t)h.K * 5 * 8);
     }
     h.bytes = off;
     return SEEDS_OK;
@@ -165,6 +169,9 @@ inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const se
     d.nbins = h.nbins;
     d.patch = h.p.patch;
     d.color = h.p.color_space;
+    d.means_iters = h.p.means_iters;
+    // SLIC's (m/S)^2 with S^2 = N/K
+    d.means_w = (double)((int64_t)h.p.compactness * h.p.compactness * h.K) / (double)h.N;
     d.gnum = h.p.gamma_num;
     d.gden = h.p.gamma_den;
     d.bins16 = h.nbins > 256;
@@ -187,6 +194,7 @@ inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const se
         d.hist[q] = (int32_t *)(base + h.off_hist[q]);
         d.size[q] = (int32_t *)(base + h.off_size[q]);
         d.dec[q] = (uint32_t *)(base + h.off_dec[q]);
+        d.msum[q] = h.p.means_iters > 0 ? (unsigned long long *)(base + h.off_msum[q]) : nullptr;
     }
     d.units_cap = h.units_cap;
     d.rgb = io.rgb;

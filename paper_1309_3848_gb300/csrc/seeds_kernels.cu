@@ -364,11 +364,126 @@ __device__ void op_init(const DevImage &im, int k, int lane, int32_t *wsh)
     }
     __syncwarp();
     if (lane == 0) im.size[0][k] = im.size[1][k] = area;
+    if (im.means_iters > 0 && lane < 10) im.msum[lane / 5][(int64_t)k * 5 + lane % 5] = 0;
     if (im.L >= 1 && lane < 4) {
         const int L = im.L;
         const int bx = 2 * sx + (lane & 1), by = 2 * sy + (lane >> 1);
         im.lab[L][0][by * im.nbx[L] + bx] = im.lab[L][1][by * im.nbx[L] + bx] = (uint16_t)k;
     }
+}
+
+// ---------------------------------------------------------------------------
+// means-based pixel iterations (SPM, Sec. 6.3; the last pixel iterations,
+// Sec. 6.5): per superpixel sums of the colour codes and coordinates
+// ---------------------------------------------------------------------------
+
+// colour code of pixel (x, y): its RGB bytes or their 8-bit L*a*b* code
+__device__ __noinline__ void pixel_code(const DevImage &im, int x, int y, int &c0, int &c1, int &c2)
+{
+    const uint8_t *px = im.rgb + (int64_t)y * im.stride + 3 * (int64_t)x;
+    c0 = px[0];
+    c1 = px[1];
+    c2 = px[2];
+    if (im.color) lab8(c0, c1, c2, c0, c1, c2);
+}
+
+// move pixel (x, y) from k to n in the sums of buffer `buf`
+__device__ __noinline__ void move_sums(const DevImage &im, int buf, int k, int n, int x, int y)
+{
+    int c0, c1, c2;
+    pixel_code(im, x, y, c0, c1, c2);
+    const unsigned long long v[5] = {(unsigned long long)c0, (unsigned long long)c1, (unsigned long long)c2,
+                                     (unsigned long long)x, (unsigned long long)y};
+    unsigned long long *mk = im.msum[buf] + (int64_t)k * 5, *mn = im.msum[buf] + (int64_t)n * 5;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        atomicAdd(mk + q, 0ull - v[q]);
+        atomicAdd(mn + q, v[q]);
+    }
+}
+
+// OP_MINIT: the sums from the labels of buffer o&1, into both buffers (zeroed
+// by the init op).  A thread per pixel; the warp adds up each label's lanes
+// and one lane per label adds them to memory.  The whole warp calls this.
+__device__ __noinline__ void op_means_init(const DevImage &im, int o, int64_t units, int64_t t, int lane)
+{
+    int k = -1;
+    unsigned v[5] = {0, 0, 0, 0, 0};
+    if (t < units) {
+        const int y = (int)(t / im.W), x = (int)(t - (int64_t)y * im.W);
+        k = im.lab[0][o & 1][t];
+        int c0, c1, c2;
+        pixel_code(im, x, y, c0, c1, c2);
+        v[0] = c0;
+        v[1] = c1;
+        v[2] = c2;
+        v[3] = x;
+        v[4] = y;
+    }
+    unsigned todo = 0xffffffffu;  // the same on every lane
+    while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int kl = __shfl_sync(0xffffffffu, k, leader);
+        const unsigned grp = __ballot_sync(0xffffffffu, k == kl);
+        unsigned s[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) s[q] = __reduce_add_sync(0xffffffffu, k == kl ? v[q] : 0u);
+        if (lane == leader && kl >= 0)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                atomicAdd(&im.msum[0][(int64_t)kl * 5 + q], (unsigned long long)s[q]);
+                atomicAdd(&im.msum[1][(int64_t)kl * 5 + q], (unsigned long long)s[q]);
+            }
+        todo &= ~grp;
+    }
+}
+
+// SLIC's squared distance of a pixel (codes c, position x, y) to the mean of
+// superpixel `label` in buffer b: colour, plus (m/S)^2 times the squared
+// distance to the centroid, in IEEE double, one rounding per operation in
+// this order (no fused multiply-add)
+__device__ __noinline__ double means_distance(const DevImage &im, int b, int label, const int c[3], int x, int y)
+{
+    const unsigned long long *m = im.msum[b] + (int64_t)label * 5;
+    const double n = (double)im.size[b][label];
+    double dc = 0.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double t = __dsub_rn((double)c[q], __ddiv_rn((double)(long long)m[q], n));
+        dc = __dadd_rn(dc, __dmul_rn(t, t));
+    }
+    const double gx = __dsub_rn((double)x, __ddiv_rn((double)(long long)m[3], n));
+    const double gy = __dsub_rn((double)y, __ddiv_rn((double)(long long)m[4], n));
+    const double ds = __dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy));
+    return __dadd_rn(dc, __dmul_rn(im.means_w, ds));
+}
+
+// The means rule for boundary pixel p = (x, y) of label k that may leave:
+// the candidate (ascending, empty slots kNoLabel) whose mean is nearest,
+// ties to the smallest label, if strictly nearer than k's mean (p
+// included).  A move is applied to buffer nb at once.
+__device__ __noinline__ uint32_t means_pixel(const DevImage &im, int b, int nb, int x, int y, int k, int j,
+                                             const int cand[4])
+{
+    int c[3];
+    pixel_code(im, x, y, c[0], c[1], c[2]);
+    int best = kNoLabel;
+    double db = 0.0;
+    for (int q = 0; q < 4; ++q) {
+        const int n = cand[q];
+        if (n == kNoLabel) continue;
+        const double d = means_distance(im, b, n, c, x, y);
+        if (best == kNoLabel || d < db) {
+            best = n;
+            db = d;
+        }
+    }
+    if (!(db < means_distance(im, b, k, c, x, y))) return kNoMove;
+    im.lab[0][nb][y * im.W + x] = (uint16_t)best;
+    move_counts(im, nb, k, best, j, 1);
+    move_size(im, nb, k, best, 1);
+    move_sums(im, nb, k, best, x, y);
+    return ((uint32_t)k << 16) | (uint32_t)best;
 }
 
 // ---------------------------------------------------------------------------
@@ -392,6 +507,10 @@ __device__ __forceinline__ void replay_pixel(const DevImage &im, int buf, int p,
 // independent coalesced loads, with the units' colour bins; a cheap pass
 // finds the units that sit on a boundary and may leave, and the warp judges
 // only those, compacted so that every lane works.
+//
+// MEANS: a means-based phase (OP_MPHASE), whose moves also carry the
+// superpixel sums and whose units are judged by means_pixel.
+template <bool MEANS>
 __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, int tiles, int tile, int lane,
                               uint16_t *tsh)
 {
@@ -445,7 +564,11 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
     // replay the previous phase's moves into buffer nb
 #pragma unroll
     for (int r = 0; r < kTileUY; ++r)
-        if (cd[r] != kNoMove) replay_pixel(im, nb, (2 * (uy0 + r) + cpy) * W + 2 * ux + cpx, cd[r]);
+        if (cd[r] != kNoMove) {
+            const int cx = 2 * ux + cpx, cy = 2 * (uy0 + r) + cpy;
+            replay_pixel(im, nb, cy * W + cx, cd[r]);
+            if constexpr (MEANS) move_sums(im, nb, (int)(cd[r] >> 16), (int)(cd[r] & 0xFFFFu), cx, cy);
+        }
     __syncwarp();
 
     // pass 1: boundary units that may leave; the others decide "stay" here
@@ -484,6 +607,10 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         // pass 1 found that it may leave
         const int nc = sorted_candidates(T[-1], T[1], T[-kTileW], T[kTileW], k, cand);
         const int j = jsh[r * 32 + l];
+        if constexpr (MEANS) {
+            im.dec[b][uy * ncols + uxe] = means_pixel(im, b, nb, x, y, k, j, cand);
+            continue;
+        }
         // Prop. 2 sums G_x = sum_{i in K_p} b_{N_i}(x) as a weighted count
         // over the 5x5 window: w(p,q) = #{i in image: |i-p|,|i-q| <= 1}
         int Gk = 0, Gc[4] = {0, 0, 0, 0}, Kp = 0;
@@ -560,6 +687,14 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         im.dec[b][uy * ncols + uxe] = dec;
     }
     __syncwarp();
+}
+
+// A means-based phase's tile, out of line: the means iterations are rare, and
+// the persistent kernel's other ops keep their code compact without it.
+__device__ __noinline__ void op_means_tile(const DevImage &im, int o, int phase, int cphase, int tiles, int tile,
+                                           int lane, uint16_t *tsh)
+{
+    op_pixel_tile<true>(im, o, phase, cphase, tiles, tile, lane, tsh);
 }
 
 // ---------------------------------------------------------------------------
@@ -803,12 +938,14 @@ __device__ void op_catchup(const DevImage &im, int o, int level, int phase, int 
             const int u = chunk * 32 * kCatchupPerLane + 32 * r + lane;
             d[r] = u < units ? im.dec[nb][u] : kNoMove;
         }
+        const bool means = op_at(im.L, im.iters, im.means_iters, o - 1).kind == OP_MPHASE;
 #pragma unroll
         for (int r = 0; r < kCatchupPerLane; ++r) {
             if (d[r] == kNoMove) continue;
             int x, y;
             unit_pos(chunk * 32 * kCatchupPerLane + 32 * r + lane, phase, im.W, &x, &y);
             replay_pixel(im, nb, y * im.W + x, d[r]);
+            if (means) move_sums(im, nb, (int)(d[r] >> 16), (int)(d[r] & 0xFFFFu), x, y);
         }
         return;
     }
@@ -876,7 +1013,7 @@ __device__ void op_output(const DevImage &im, int o, int units, int c)
 // pixel takes the label of the unit that holds it: unit column
 // bx = ((x+1)*nbx - 1) / W inverts the edges floor(i*W/nbx), rows likewise.
 // Few images: every thread walks each image; many: a block per image.
-__device__ void anytime_output(const DevImage *imgs, int nimg, int o)
+__device__ __noinline__ void anytime_output(const DevImage *imgs, int nimg, int o)
 {
     const bool per_block = nimg >= (int)gridDim.x;
     const int i0 = per_block ? blockIdx.x : 0, istep = per_block ? gridDim.x : 1;
@@ -884,9 +1021,12 @@ __device__ void anytime_output(const DevImage *imgs, int nimg, int o)
     const int64_t tstep = per_block ? blockDim.x : (int64_t)gridDim.x * blockDim.x;
     for (int i = i0; i < nimg; i += istep) {
         const DevImage &im = imgs[i];
-        if (o >= num_ops(im.L, im.iters) - 1) continue;  // finished: its output ran
-        const OpDesc d = op_at(im.L, im.iters, o);
-        const int level = d.kind == OP_PHASE ? d.level : d.kind == OP_DESCEND ? d.level - 1 : im.L;
+        if (o >= num_ops(im.L, im.iters, im.means_iters) - 1) continue;  // finished: its output ran
+        const OpDesc d = op_at(im.L, im.iters, im.means_iters, o);
+        const int level = d.kind == OP_PHASE      ? d.level
+                          : d.kind == OP_DESCEND  ? d.level - 1
+                          : d.kind == OP_INIT     ? im.L
+                                                  : 0;  // the means iterations run on pixels
         const uint16_t *lab = im.lab[level][(o + 1) & 1];
         const int W = im.W, nx = im.nbx[level], ny = im.nby[level];
         const int64_t npx = (int64_t)W * im.H;
@@ -958,12 +1098,18 @@ __global__ void __launch_bounds__(512, SEEDS_MIN_BLOCKS) seeds_persistent(const 
                 break;
             case OP_PHASE:
                 if (E.level == 0)
-                    op_pixel_tile(im, E.opidx, E.phase, E.cphase, E.units, off >> 5, lane, tsh);
+                    op_pixel_tile<false>(im, E.opidx, E.phase, E.cphase, E.units, off >> 5, lane, tsh);
                 else if (E.group == 1)
                     op_block_phase_thread(im, E.opidx, E.level, E.phase, E.cphase, E.units, off + lane);
                 else
                     op_block_phase_warp(im, E.opidx, E.level, E.phase, E.cphase, E.units, off >> 5, lane, wsh,
                                         S.max_nbins);
+                break;
+            case OP_MPHASE:
+                op_means_tile(im, E.opidx, E.phase, E.cphase, E.units, off >> 5, lane, tsh);
+                break;
+            case OP_MINIT:
+                op_means_init(im, E.opidx, E.units, off + lane, lane);
                 break;
             case OP_CATCHUP:
                 op_catchup(im, E.opidx, E.level, E.phase, (int)phase_units(im, E.level, E.phase), E.group, off,
@@ -1068,7 +1214,7 @@ __global__ void epoch_schedule_kernel(const DevImage *imgs, EpochPlan plan, Step
             const int o = q.begin + s;
             if (o >= q.end) continue;
             const DevImage &im = imgs[q.slot];
-            const bool cu = s == 0 ? q.catchup != 0 : op_at(im.L, im.iters, o - 1).kind == OP_PHASE;
+            const bool cu = s == 0 ? q.catchup != 0 : is_phase(op_at(im.L, im.iters, im.means_iters, o - 1).kind);
             int64_t v = 0;
             c += emit_entries(im, q.slot, o, cu, tmp, &v);
         }
@@ -1093,7 +1239,7 @@ __global__ void epoch_schedule_kernel(const DevImage *imgs, EpochPlan plan, Step
         const int o = q.begin + s;
         if (o >= q.end) continue;
         const DevImage &im = imgs[q.slot];
-        const bool cu = s == 0 ? q.catchup != 0 : op_at(im.L, im.iters, o - 1).kind == OP_PHASE;
+        const bool cu = s == 0 ? q.catchup != 0 : is_phase(op_at(im.L, im.iters, im.means_iters, o - 1).kind);
         e += emit_entries(im, q.slot, o, cu, ent + e, &v);
     }
     vt[s] = v;
@@ -1241,7 +1387,7 @@ __global__ void static_setup_kernel(StaticSetup S)
     for (int o = 0; o < S.nops; ++o) {
         S.first[o] = ne;
         int64_t vt = 0;
-        const bool catchup = o > 0 && op_at(im.L, im.iters, o - 1).kind == OP_PHASE;
+        const bool catchup = o > 0 && is_phase(op_at(im.L, im.iters, im.means_iters, o - 1).kind);
         ne += emit_entries(im, 0, o, catchup, S.ent + ne, &vt);
         S.vt[o] = vt;
     }
@@ -1268,6 +1414,8 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     if (p->patch != 0 && p->patch != 3) return SEEDS_ERR_INVALID;
     if (p->gamma_num < 0 || p->gamma_num > 1024 || p->gamma_den < 1 || p->gamma_den > 1024) return SEEDS_ERR_INVALID;
     if (p->color_space != 0 && p->color_space != 1) return SEEDS_ERR_INVALID;
+    if (p->means_iters < 0 || p->means_iters > 1000 || p->compactness < 0 || p->compactness > 1024)
+        return SEEDS_ERR_INVALID;
     const double Kd = p->num_superpixels, Wd = p->width, Hd = p->height;
     long long gx = std::llround(std::sqrt(Kd * Wd / Hd));
     if (gx < 1) gx = 1;
@@ -1295,6 +1443,8 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     d.gden = p->gamma_den;
     d.color = p->color_space;
     if (d.color == 1 && upload_lab_tables() != cudaSuccess) return SEEDS_ERR_CUDA;
+    d.means_iters = p->means_iters;
+    d.means_w = (double)((int64_t)p->compactness * p->compactness * K) / (double)N;
     d.bins16 = nbins > 256;
     d.hist_jmajor = 0;
     d.hist_sk = nbins;
@@ -1315,7 +1465,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     const __int128 N2 = (__int128)N * N, lim = ((__int128)1) << 63;
     if ((__int128)amax * N2 >= lim || (__int128)(81 * p->gamma_den + 90 * p->gamma_num) * N2 >= lim)
         return SEEDS_ERR_INT64;
-    const int nops = num_ops(L, p->iters_per_level);
+    const int nops = num_ops(L, p->iters_per_level, p->means_iters);
     const int units_cap = (int)(((int64_t)(p->width + 1) / 2) * ((p->height + 1) / 2));
 
     // ---- layout inside the scratch
@@ -1344,7 +1494,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
             o_lab[l][q] = off;
             off = sal(off + 2 * (size_t)d.nbx[l] * d.nby[l]);
         }
-    size_t o_hist[2], o_size[2], o_dec[2];
+    size_t o_hist[2], o_size[2], o_dec[2], o_msum[2];
     for (int q = 0; q < 2; ++q) {
         o_hist[q] = off;
         off = sal(off + 4 * (size_t)K * nbins);
@@ -1352,6 +1502,8 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
         off = sal(off + 4 * (size_t)K);
         o_dec[q] = off;
         off = sal(off + 4 * (size_t)units_cap);
+        o_msum[q] = off;
+        if (p->means_iters > 0) off = sal(off + 40 * (size_t)K);
     }
     if (off > (size_t)SEEDS_STATIC_SCRATCH_BYTES) return SEEDS_ERR_STATIC_SIZE;
 
@@ -1372,6 +1524,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
         d.hist[q] = (int32_t *)(base + o_hist[q]);
         d.size[q] = (int32_t *)(base + o_size[q]);
         d.dec[q] = (uint32_t *)(base + o_dec[q]);
+        d.msum[q] = p->means_iters > 0 ? (unsigned long long *)(base + o_msum[q]) : nullptr;
     }
     d.units_cap = units_cap;
     d.rgb = d_rgb;

@@ -151,7 +151,7 @@ int get_schedule(seeds_ctx *c, int kind, int ob, int oe, const Schedule **out)
         for (int i = 0; i < n; ++i) {
             const int o = b[i] + s;
             if (o >= e[i]) continue;
-            const bool catchup = s == 0 ? (o > 0 && c->pending[i] == o - 1) : c->img[i].ops[o - 1].kind == OP_PHASE;
+            const bool catchup = s == 0 ? (o > 0 && c->pending[i] == o - 1) : is_phase(c->img[i].ops[o - 1].kind);
             const int m = emit_entries(c->h_imgs[i], i, o, catchup, two, &v);
             for (int q = 0; q < m; ++q) ent.push_back(two[q]);
         }
@@ -256,7 +256,7 @@ int launch(seeds_ctx *c, int kind, int ob, int oe, cudaStream_t s, int32_t stop_
         op_range(c->img[i], kind, ob, oe, &b, &e);
         if (e <= b) continue;
         c->cur[i] = e;
-        c->pending[i] = c->img[i].ops[e - 1].kind == OP_PHASE ? e - 1 : -1;
+        c->pending[i] = is_phase(c->img[i].ops[e - 1].kind) ? e - 1 : -1;
     }
     return rc;
 }

@@ -343,7 +343,7 @@ int seeds_server_step(seeds_server *s, int32_t *resident_out)
     for (int i = 0; i < plan.n; ++i) {
         Request *r = s->slots[plan.s[i].slot];
         r->progress = plan.s[i].end;
-        r->pending = r->h.ops[r->progress - 1].kind == OP_PHASE ? r->progress - 1 : -1;
+        r->pending = is_phase(r->h.ops[r->progress - 1].kind) ? r->progress - 1 : -1;
         if (r->progress < r->nops) continue;
         rc = from_cuda(cudaMemcpyAsync(r->h_out, s->arena + r->off + r->out_off, (size_t)r->h.N * 4,
                                        cudaMemcpyDeviceToHost, st));

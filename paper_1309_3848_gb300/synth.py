@@ -51,6 +51,8 @@ class JobSpec:
     gamma: Tuple[int, int] = (1, 1)
     clamp_levels: bool = False
     color_space: int = 0  # 0 = RGB bytes, 1 = CIE L*a*b* codes
+    means_iters: int = 0  # means-based pixel iterations after the histogram ones
+    compactness: int = 0  # SLIC's m in those iterations
 
     @property
     def pixels(self) -> int:

@@ -29,7 +29,8 @@ def gpu_levels(binding, job):
 def params_for(binding, job):
     L = gpu_levels(binding, job)
     return binding.make_params(job.image.width, job.image.height, job.num_superpixels, L, job.bins_per_channel,
-                               job.iters_per_level, job.patch, job.gamma, job.color_space)
+                               job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters,
+                               job.compactness)
 
 
 def make_images(jobs):
@@ -39,7 +40,7 @@ def make_images(jobs):
 
 def oracle_run(job, img):
     r = ref.Ref(job.image.width, job.image.height, job.num_superpixels, oracle_levels(job), job.bins_per_channel,
-                job.iters_per_level, job.patch, job.gamma, job.color_space)
+                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters, job.compactness)
     return r.run(img)
 
 

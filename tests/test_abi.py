@@ -70,7 +70,9 @@ def test_invalid_parameters(binding):
            binding.make_params(10, 10, 4, 0, 17, 1), binding.make_params(10, 10, 4, 0, 5, 0),
            binding.make_params(10, 10, 4, 0, 5, 1, patch=2), binding.make_params(10, 10, 4, 0, 5, 1, gamma=(1, 0)),
            binding.make_params(10, 10, 4, 13, 5, 1), binding.make_params(10, 10, 4, 0, 5, 1, color_space=2),
-           binding.make_params(10, 10, 4, 0, 5, 1, color_space=-1)]
+           binding.make_params(10, 10, 4, 0, 5, 1, color_space=-1), binding.make_params(10, 10, 4, 0, 5, 1, means_iters=-1),
+           binding.make_params(10, 10, 4, 0, 5, 1, means_iters=1001),
+           binding.make_params(10, 10, 4, 0, 5, 1, means_iters=1, compactness=1025)]
     for p in bad:
         assert binding.check_params(p)[0] == binding.SEEDS_ERR_INVALID
     assert binding.check_params(binding.make_params(16, 16, 4, 4, 5, 1))[0] == binding.SEEDS_ERR_GEOMETRY
