@@ -88,7 +88,8 @@ typedef struct seeds_ctx seeds_ctx;
  *                      plus (m/S)^2 times the squared distance to the
  *                      centroid, S^2 = W*H/K; strictly nearer than its own
  *                      superpixel's mean (with the pixel in it), ties to the
- *                      smallest label, IEEE double without fused operations
+ *                      smallest label, IEEE single precision without fused
+ *                      operations (a mean is its sum times 1/size)
  *   compactness        m in 0..1024 (0 = colour only) */
 typedef struct {
     int32_t width, height;

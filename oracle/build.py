@@ -16,7 +16,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + ".%d.tmp" % os.getpid()
-    # no fused multiply-add: the double-precision means distances (R17) must
+    # no fused multiply-add: the floating-point means distances (R17) must
     # round after every operation
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-Wall", "-Wextra", "-shared", "-fPIC", "-o", tmp, SRC,
            "-lm"]

@@ -72,7 +72,8 @@
  *       the superpixel's centroid (S^2 = N/K, m = compactness), if strictly
  *       nearer than its own superpixel's mean taken with the pixel in it;
  *       means from the phase-start state; no boundary term; evaluated in
- *       IEEE double in the order written in means_distance, so that any
+ *       IEEE single precision in the order written in means_distance (a
+ *       mean is its sum times the reciprocal of the size), so that any
  *       implementation doing the same operations decides the same way.
  *   R14 sequential mode (quality reference only): per iteration the units
  *       are visited in a random permutation (SplitMix64 + Fisher-Yates),
@@ -119,7 +120,7 @@ typedef struct {
     int64_t moves_cap;
     uint8_t *code;         /* colour code (the channels the bins are taken from) of every pixel */
     int64_t *msum;         /* R17: per superpixel: sums of the 3 codes, of x and of y */
-    double means_w;        /* R17: m^2 K / N, the spatial weight (m/S)^2 with S^2 = N/K */
+    float means_w;         /* R17: m^2 K / N, the spatial weight (m/S)^2 with S^2 = N/K */
     int64_t lab_lin[256];  /* R16: sRGB byte -> linear light * 2^24 */
     int64_t lab_m[3][3];   /* R16: linear RGB -> XYZ / white, * 2^20 */
 } ref_state;
@@ -225,7 +226,7 @@ int ref_create(const ref_params *p, ref_state **out)
     }
     st->code = (uint8_t *)calloc((size_t)N * 3, 1);
     st->msum = (int64_t *)calloc((size_t)st->K * 5, sizeof(int64_t));
-    st->means_w = (double)((int64_t)p->compactness * p->compactness * st->K) / (double)N;
+    st->means_w = (float)((int64_t)p->compactness * p->compactness * st->K) / (float)N;
     st->bin = (int *)calloc((size_t)N, sizeof(int));
     st->lab = (int *)calloc((size_t)N, sizeof(int));
     st->hist = (int64_t *)calloc((size_t)st->K * st->nbins, sizeof(int64_t));
@@ -648,21 +649,22 @@ static void means_recount(ref_state *st)
 }
 
 /* SLIC's squared distance of pixel (x,y) to the mean of superpixel `label`
- * (colour codes, then coordinates weighted by (m/S)^2), in IEEE double in
- * this order of operations */
-static double means_distance(const ref_state *st, int x, int y, int label)
+ * (colour codes, then coordinates weighted by (m/S)^2), in IEEE single
+ * precision in this order of operations; the mean of a sum S is
+ * S * (1/|A|) */
+static float means_distance(const ref_state *st, int x, int y, int label)
 {
     const int64_t *m = st->msum + (int64_t)label * 5;
     const uint8_t *c = st->code + 3 * ((int64_t)y * st->W + x);
-    double n = (double)st->size[label];
-    double dc = 0.0;
+    float r = 1.0f / (float)st->size[label];
+    float dc = 0.0f;
     for (int q = 0; q < 3; ++q) {
-        double t = (double)c[q] - (double)m[q] / n;
+        float t = (float)c[q] - (float)m[q] * r;
         dc = dc + t * t;
     }
-    double gx = (double)x - (double)m[3] / n;
-    double gy = (double)y - (double)m[4] / n;
-    double ds = gx * gx + gy * gy;
+    float gx = (float)x - (float)m[3] * r;
+    float gy = (float)y - (float)m[4] * r;
+    float ds = gx * gx + gy * gy;
     return dc + st->means_w * ds;
 }
 
@@ -678,9 +680,9 @@ static int decide_pixel_means(ref_state *st, int x, int y)
     if (nc == 0) return -1;
     if (!leaving_keeps_connected(st, 0, x, y, k)) return -1;
     int best = -1;
-    double db = 0.0;
+    float db = 0.0f;
     for (int c = 0; c < nc; ++c) {
-        double d = means_distance(st, x, y, cand[c]);
+        float d = means_distance(st, x, y, cand[c]);
         if (best < 0 || d < db) {
             best = cand[c];
             db = d;

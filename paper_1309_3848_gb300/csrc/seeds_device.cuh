@@ -43,7 +43,7 @@ struct DevImage {
     int32_t small_area;   // blocks up to this many pixels are judged by one thread
     int32_t color;        // 0: RGB bytes, 1: 8-bit CIE L*a*b* codes (Sec. 6.2)
     int32_t means_iters;  // means-based pixel iterations after the histogram ones
-    double means_w;       // (m/S)^2 = m^2 K / N, the spatial weight of SLIC's distance
+    float means_w;        // (m/S)^2 = m^2 K / N, the spatial weight of SLIC's distance
     int32_t nbx[kMaxLevels + 1], nby[kMaxLevels + 1];  // level 0 = W, H
     int32_t maxarea[kMaxLevels + 1];                   // largest block of a level
     const int32_t *xe[kMaxLevels + 1];                 // block column edges, level >= 1

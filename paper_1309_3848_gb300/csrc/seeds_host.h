@@ -171,7 +171,7 @@ inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const se
     d.color = h.p.color_space;
     d.means_iters = h.p.means_iters;
     // SLIC's (m/S)^2 with S^2 = N/K
-    d.means_w = (double)((int64_t)h.p.compactness * h.p.compactness * h.K) / (double)h.N;
+    d.means_w = (float)((int64_t)h.p.compactness * h.p.compactness * h.K) / (float)h.N;
     d.gnum = h.p.gamma_num;
     d.gden = h.p.gamma_den;
     d.bins16 = h.nbins > 256;

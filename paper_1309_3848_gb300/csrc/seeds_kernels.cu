@@ -440,22 +440,23 @@ __device__ __noinline__ void op_means_init(const DevImage &im, int o, int64_t un
 
 // SLIC's squared distance of a pixel (codes c, position x, y) to the mean of
 // superpixel `label` in buffer b: colour, plus (m/S)^2 times the squared
-// distance to the centroid, in IEEE double, one rounding per operation in
-// this order (no fused multiply-add)
-__device__ __noinline__ double means_distance(const DevImage &im, int b, int label, const int c[3], int x, int y)
+// distance to the centroid, in IEEE single precision, one rounding per
+// operation in this order (no fused multiply-add); a mean is its sum times
+// 1/|A|
+__device__ __forceinline__ float means_distance(const DevImage &im, int b, int label, const int c[3], int x, int y)
 {
     const unsigned long long *m = im.msum[b] + (int64_t)label * 5;
-    const double n = (double)im.size[b][label];
-    double dc = 0.0;
+    const float r = __fdiv_rn(1.0f, __int2float_rn(im.size[b][label]));
+    float dc = 0.0f;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const double t = __dsub_rn((double)c[q], __ddiv_rn((double)(long long)m[q], n));
-        dc = __dadd_rn(dc, __dmul_rn(t, t));
+        const float t = __fsub_rn(__int2float_rn(c[q]), __fmul_rn(__ll2float_rn((long long)m[q]), r));
+        dc = __fadd_rn(dc, __fmul_rn(t, t));
     }
-    const double gx = __dsub_rn((double)x, __ddiv_rn((double)(long long)m[3], n));
-    const double gy = __dsub_rn((double)y, __ddiv_rn((double)(long long)m[4], n));
-    const double ds = __dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy));
-    return __dadd_rn(dc, __dmul_rn(im.means_w, ds));
+    const float gx = __fsub_rn(__int2float_rn(x), __fmul_rn(__ll2float_rn((long long)m[3]), r));
+    const float gy = __fsub_rn(__int2float_rn(y), __fmul_rn(__ll2float_rn((long long)m[4]), r));
+    const float ds = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
+    return __fadd_rn(dc, __fmul_rn(im.means_w, ds));
 }
 
 // The means rule for boundary pixel p = (x, y) of label k that may leave:
@@ -468,11 +469,11 @@ __device__ __noinline__ uint32_t means_pixel(const DevImage &im, int b, int nb, 
     int c[3];
     pixel_code(im, x, y, c[0], c[1], c[2]);
     int best = kNoLabel;
-    double db = 0.0;
+    float db = 0.0f;
     for (int q = 0; q < 4; ++q) {
         const int n = cand[q];
         if (n == kNoLabel) continue;
-        const double d = means_distance(im, b, n, c, x, y);
+        const float d = means_distance(im, b, n, c, x, y);
         if (best == kNoLabel || d < db) {
             best = n;
             db = d;
@@ -1444,7 +1445,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     d.color = p->color_space;
     if (d.color == 1 && upload_lab_tables() != cudaSuccess) return SEEDS_ERR_CUDA;
     d.means_iters = p->means_iters;
-    d.means_w = (double)((int64_t)p->compactness * p->compactness * K) / (double)N;
+    d.means_w = (float)((int64_t)p->compactness * p->compactness * K) / (float)N;
     d.bins16 = nbins > 256;
     d.hist_jmajor = 0;
     d.hist_sk = nbins;

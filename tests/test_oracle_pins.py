@@ -701,8 +701,8 @@ def test_means_decisions_match_exact_fractions(seed, m, color):
     for y in range(H):
         for x in range(W):
             want, gap = exact_means_decision(labels, codes, r.K, m, x, y)
-            if gap is not None and gap < Fraction(1, 10 ** 9):
-                continue  # a near tie: double rounding may decide either way
+            if gap is not None and gap < Fraction(1, 10 ** 4):
+                continue  # a near tie: single-precision rounding may decide either way
             assert r.decide_means(x, y) == want, (x, y)
             checked += want >= 0
     assert checked > 0, "no pixel wanted to move"

@@ -79,3 +79,17 @@ def test_request_too_large_for_the_arena_is_refused(torch, serve):
         srv.submit(serve.job_params(job), img, out)
     assert e.value.code == binding.SEEDS_ERR_NO_MEMORY
     srv.close()
+
+
+def test_served_lab_and_means_requests(torch, serve):
+    """Requests with LAB bins (Sec. 6.2) and means-based iterations (Sec.
+    6.5) served among plain ones: the oracle's labels."""
+    import dataclasses
+    reqs = mixed_requests(11, 18, rate=3000.0)
+    reqs = [(t, dataclasses.replace(j, color_space=i % 2, means_iters=(i % 3), compactness=(0, 7, 30)[i % 3]))
+            for i, (t, j) in enumerate(reqs)]
+    imgs = [synth.make_image(j.image) for _, j in reqs]
+    res = serve.run_stream(reqs, imgs, arena_bytes=8 << 20, max_slots=4, epoch_steps=5)
+    want = gc.oracle_many([j for _, j in reqs], imgs)
+    for i in range(len(reqs)):
+        assert gc.first_mismatch(res.labels[i], want[i]) is None, "request %d" % i
