@@ -51,6 +51,44 @@ __device__ __forceinline__ int ld_relaxed_i32(const int32_t *p)
     return v;
 }
 
+// Grid-wide barrier without a stop decision: the arrival counter only grows
+// (zeroed before the launch), so barrier number s is passed once it reaches
+// (s+1) * gridDim.x: one atomic per CTA, no reset, no second word.  Thread 0
+// of each CTA fences the CTA's writes before it arrives and fences again
+// after the wait, so the CTA's later loads see every other CTA's writes.
+// Returns false when the wait ran out or another CTA reported an error.
+__device__ bool grid_sync_count(GridBarrier *bar, int32_t *err, unsigned target)
+{
+    __shared__ int s_go;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const unsigned v = atomicAdd(&bar->count, 1u);
+        if (v + 1 != target) {
+            const uint64_t t0 = global_ns();
+            for (unsigned it = 1; (int)(ld_acquire_u32(&bar->count) - target) < 0; ++it) {
+                if ((it & 31u) == 0) {
+                    if (ld_relaxed_i32(err) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    if (global_ns() - t0 > kBarrierTimeoutNs) {
+                        atomicOr(err, DERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_go = ok;
+    }
+    __syncthreads();
+    return s_go != 0;
+}
+
 constexpr unsigned kGenStop = 0x80000000u;  // generation bit: the grid stops here
 
 // Grid-wide barrier for a persistent launch whose blocks are all resident.
@@ -1127,15 +1165,18 @@ __global__ void __launch_bounds__(512, SEEDS_MIN_BLOCKS) seeds_persistent(const 
             }
         }
         if (s + 1 < S.nsteps) {
-            const bool want_stop = anytime && threadIdx.x == 0 &&
-                                   ((S.stop_steps > 0 && s + 1 >= S.stop_steps) ||
-                                    (S.budget_ns > 0 && global_ns() - t_start >= S.budget_ns));
-            const int go = grid_sync(bar, err, want_stop);
-            if (go == 0) return;
-            if (go == 2) {
-                anytime_output(imgs, S.nimg, s);
-                if (blockIdx.x == 0 && threadIdx.x == 0 && S.steps_out) *S.steps_out = s + 1;
-                return;
+            if (!anytime) {
+                if (!grid_sync_count(bar, err, (unsigned)(s + 1) * gridDim.x)) return;
+            } else {
+                const bool want_stop = threadIdx.x == 0 && ((S.stop_steps > 0 && s + 1 >= S.stop_steps) ||
+                                                            (S.budget_ns > 0 && global_ns() - t_start >= S.budget_ns));
+                const int go = grid_sync(bar, err, want_stop);
+                if (go == 0) return;
+                if (go == 2) {
+                    anytime_output(imgs, S.nimg, s);
+                    if (blockIdx.x == 0 && threadIdx.x == 0 && S.steps_out) *S.steps_out = s + 1;
+                    return;
+                }
             }
         }
         if (tracer) S.trace[1 + s] = global_ns();
