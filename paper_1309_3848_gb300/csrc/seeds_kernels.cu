@@ -1109,8 +1109,18 @@ __global__ void __launch_bounds__(512, SEEDS_MIN_BLOCKS) seeds_persistent(const 
     for (int i = lane; i < wbytes / 4; i += 32) wsh[i] = 0;
     __syncwarp();
 
-    const int64_t gwarp = (int64_t)blockIdx.x * nwarps_blk + warp;
+    // A step's virtual warps are dealt to the CTAs in rounds: round r gives
+    // CTA c the nwarps_blk virtual warps from (r * gridDim.x + c) * nwarps_blk
+    // on.  Warp w takes the w-th of round 0; after that the CTA's warps take
+    // its next one from a shared counter as they finish, so one slow unit
+    // does not hold up the units queued behind it on the same warp.  Two
+    // counters alternate between steps; the grid barrier's CTA barrier
+    // orders each reset before its use.
+    __shared__ unsigned s_next[2];
+    if (threadIdx.x == 0) s_next[0] = s_next[1] = 0;
+    __syncthreads();
     const int64_t nwarps = (int64_t)gridDim.x * nwarps_blk;
+    const int64_t cta_first = (int64_t)blockIdx.x * nwarps_blk;
     const bool tracer = S.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
     if (tracer) S.trace[0] = global_ns();
     const bool anytime = S.stop_steps > 0 || S.budget_ns > 0;
@@ -1119,7 +1129,11 @@ __global__ void __launch_bounds__(512, SEEDS_MIN_BLOCKS) seeds_persistent(const 
     for (int s = 0; s < S.nsteps; ++s) {
         const int e0 = S.step_first[s], e1 = S.step_first[s + 1];
         const int64_t total = S.step_vt[s];
-        for (int64_t base = gwarp * 32; base < total; base += nwarps * 32) {
+        if (threadIdx.x == 0) s_next[(s + 1) & 1] = 0;
+        const bool rounds = nwarps * 32 < total;  // work beyond round 0 for some CTA
+        for (unsigned i = warp;; ) {
+            const int64_t base = ((int64_t)(i / nwarps_blk) * nwarps + cta_first + (i % nwarps_blk)) * 32;
+            if (base >= total) break;
             int lo = e0, hi = e1 - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -1163,6 +1177,10 @@ __global__ void __launch_bounds__(512, SEEDS_MIN_BLOCKS) seeds_persistent(const 
             default:
                 break;
             }
+            if (!rounds) break;
+            unsigned nx = 0;
+            if (lane == 0) nx = atomicAdd(&s_next[s & 1], 1u);
+            i = __shfl_sync(0xffffffffu, nx, 0) + nwarps_blk;
         }
         if (s + 1 < S.nsteps) {
             if (!anytime) {
