@@ -105,7 +105,8 @@ typedef struct {
 } seeds_params;
 
 /* Result-invariant launch knobs (any value gives identical labels).
- *   threads_per_block  128, 256 or 512 (0 = default)
+ *   threads_per_block  128, 256, 512 or 1024 (0 = the largest whose
+ *                      shared scratch fits, 1024 unless B^3 is large)
  *   blocks_per_sm      resident CTAs per SM of the persistent kernel,
  *                      0 = as many as fit
  *   hist_layout        0: hist[k][j] (label-major), 1: hist[j][k] (bin-major)

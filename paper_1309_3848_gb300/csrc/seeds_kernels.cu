@@ -1088,13 +1088,9 @@ __device__ __noinline__ void anytime_output(const DevImage *imgs, int nimg, int 
 // the persistent kernel
 // ---------------------------------------------------------------------------
 
-// Resident 512-thread blocks per SM the register budget must allow (2 caps
-// registers at 64 per thread); a build-time knob.
-#ifndef SEEDS_MIN_BLOCKS
-#define SEEDS_MIN_BLOCKS 2
-#endif
-
-__global__ void __launch_bounds__(512, SEEDS_MIN_BLOCKS) seeds_persistent(const DevImage *__restrict__ imgs, Schedule S,
+// Up to 1024 threads per CTA, with registers capped at 64 per thread so that
+// a whole SM's worth of warps (2048 threads) stays resident.
+__global__ void __launch_bounds__(1024, 1) seeds_persistent(const DevImage *__restrict__ imgs, Schedule S,
                                                         GridBarrier *bar, int32_t *err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1598,13 +1594,22 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     S.nops = nops;
     S.img_out = (DevImage *)(base + o_img);
 
-    // ---- launch configuration of the persistent kernel (as a context would)
-    const int threads = 256;
-    const size_t smem = (size_t)(threads / 32) * warp_scratch_bytes(nbins);
-    int sms = 0, per_sm = 0;
+    // ---- launch configuration of the persistent kernel (as a context would):
+    // the largest CTA whose warps' shared scratch fits
+    int threads = 0, sms = 0, per_sm = 0;
+    size_t smem = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SEEDS_ERR_CUDA;
-    if (prepare_persistent(smem) != cudaSuccess) return SEEDS_ERR_CUDA;
-    if (persistent_max_blocks_per_sm(threads, smem, &per_sm) != cudaSuccess || per_sm < 1) return SEEDS_ERR_CUDA;
+    for (int t : {1024, 512, 256, 128}) {
+        smem = (size_t)(t / 32) * warp_scratch_bytes(nbins);
+        per_sm = 0;
+        if (prepare_persistent(smem) == cudaSuccess &&
+            persistent_max_blocks_per_sm(t, smem, &per_sm) == cudaSuccess && per_sm >= 1) {
+            threads = t;
+            break;
+        }
+        cudaGetLastError();  // a size that does not fit is not an error of the call
+    }
+    if (threads == 0) return SEEDS_ERR_CUDA;
 
     cudaStream_t s = (cudaStream_t)stream;
     static_setup_kernel<<<8, 256, 0, s>>>(S);

@@ -46,7 +46,7 @@ struct seeds_ctx {
     int32_t *d_err = nullptr;
     int32_t *d_steps = nullptr;  // steps run by the last anytime launch
     bool stopped_state = false;  // the last launch was an anytime run: no final state to output
-    seeds_tuning tune{256, 0, 0, 16};
+    seeds_tuning tune{1024, 0, 0, 16};
     int grid = 0;
     size_t smem = 0;
     int max_nbins = 1;
@@ -333,7 +333,16 @@ int create_ctx(const seeds_params *p, int32_t n, seeds_ctx **out)
         fill_dev_images(c);
         rc = from_cuda(cudaMemcpy(c->d_imgs, c->h_imgs.data(), sizeof(DevImage) * n, cudaMemcpyHostToDevice));
     }
-    if (!rc) rc = configure_launch(c);
+    // the largest CTA whose warps' shared scratch fits (a whole SM's warps in
+    // one CTA balance a step's units best)
+    if (!rc) {
+        for (int t : {1024, 512, 256, 128}) {
+            c->tune.threads_per_block = t;
+            rc = configure_launch(c);
+            if (!rc) break;
+            cudaGetLastError();  // a size that does not fit is not an error of the call
+        }
+    }
     if (rc) {
         destroy_ctx(c);
         return rc;
@@ -580,9 +589,9 @@ int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t)
 {
     if (!c || !t) return SEEDS_ERR_INVALID;
     seeds_tuning n = *t;
-    if (n.threads_per_block == 0) n.threads_per_block = 256;
     if (n.small_block_area == 0) n.small_block_area = 16;
-    if (n.threads_per_block != 128 && n.threads_per_block != 256 && n.threads_per_block != 512)
+    if (n.threads_per_block != 0 && n.threads_per_block != 128 && n.threads_per_block != 256 &&
+        n.threads_per_block != 512 && n.threads_per_block != 1024)
         return SEEDS_ERR_INVALID;
     if (n.blocks_per_sm < 0 || n.hist_layout < 0 || n.hist_layout > 1) return SEEDS_ERR_INVALID;
     if (n.small_block_area < 1 || n.small_block_area > 16) return SEEDS_ERR_INVALID;
@@ -596,8 +605,21 @@ int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t)
                                       cudaMemcpyHostToDevice));
         return rc ? rc : configure_launch(c);
     };
-    const int rc = apply(n);
-    if (rc) apply(old);  // a setting that cannot launch leaves the context as it was
+    int rc = SEEDS_ERR_INVALID;
+    if (n.threads_per_block != 0) {
+        rc = apply(n);
+    } else {  // the default: the largest CTA that fits
+        for (int threads : {1024, 512, 256, 128}) {
+            n.threads_per_block = threads;
+            rc = apply(n);
+            if (!rc) break;
+            cudaGetLastError();
+        }
+    }
+    if (rc) {  // a setting that cannot launch leaves the context as it was
+        apply(old);
+        cudaGetLastError();
+    }
     return rc;
 }
 
@@ -629,10 +651,10 @@ int seeds_autotune(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t
     float cur_ms = 0.f;
     if (!rc) rc = time_it(cur, &cur_ms);
     // coordinate descent, one pass over the knobs; a change must win by 2%
-    const int threads[] = {128, 256, 512}, blocks[] = {0, 1, 2, 3}, layouts[] = {0, 1}, areas[] = {4, 9, 16};
+    const int threads[] = {128, 256, 512, 1024}, blocks[] = {0, 1, 2, 3}, layouts[] = {0, 1}, areas[] = {4, 9, 16};
     for (int knob = 0; knob < 4 && !rc; ++knob) {
         const int *vals = knob == 0 ? threads : knob == 1 ? blocks : knob == 2 ? layouts : areas;
-        const int nv = knob == 0 ? 3 : knob == 1 ? 4 : knob == 2 ? 2 : 3;
+        const int nv = knob == 0 ? 4 : knob == 1 ? 4 : knob == 2 ? 2 : 3;
         for (int v = 0; v < nv && !rc; ++v) {
             seeds_tuning t = cur;
             int *field = knob == 0 ? &t.threads_per_block

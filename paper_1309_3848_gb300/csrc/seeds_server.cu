@@ -106,7 +106,7 @@ size_t request_bytes(const ImageHost &h, size_t *rgb_off, size_t *out_off)
 struct seeds_server {
     int device = 0, sm_count = 0;
     seeds_server_config cfg{};
-    seeds_tuning tune{256, 0, 0, 16};
+    seeds_tuning tune{1024, 0, 0, 16};
     int max_nbins = 1;
     unsigned char *arena = nullptr;
     ArenaAllocator alloc;
@@ -217,13 +217,18 @@ int seeds_server_create(const seeds_server_config *cfg, seeds_server **out)
     if (!rc) rc = from_cuda(cudaMalloc((void **)&s->d_vt, sizeof(int64_t) * cfg->epoch_steps));
     if (!rc) rc = from_cuda(upload_lab_tables());
     if (!rc) {
-        const int threads = s->tune.threads_per_block;
-        s->smem = (size_t)(threads / 32) * warp_scratch_bytes(s->max_nbins);
-        int per_sm = 0;
-        rc = from_cuda(prepare_persistent(s->smem));
-        if (!rc) rc = from_cuda(persistent_max_blocks_per_sm(threads, s->smem, &per_sm));
-        if (!rc && per_sm < 1) rc = SEEDS_ERR_INVALID;
-        s->grid = per_sm * s->sm_count;
+        // the largest CTA whose warps' shared scratch fits
+        for (int threads : {1024, 512, 256, 128}) {
+            s->tune.threads_per_block = threads;
+            s->smem = (size_t)(threads / 32) * warp_scratch_bytes(s->max_nbins);
+            int per_sm = 0;
+            rc = from_cuda(prepare_persistent(s->smem));
+            if (!rc) rc = from_cuda(persistent_max_blocks_per_sm(threads, s->smem, &per_sm));
+            if (!rc && per_sm < 1) rc = SEEDS_ERR_INVALID;
+            s->grid = per_sm * s->sm_count;
+            if (!rc) break;
+            cudaGetLastError();  // a size that does not fit is not an error of the call
+        }
     }
     if (!rc) rc = from_cuda(cudaEventCreate(&s->t0));
     if (!rc) rc = from_cuda(cudaEventRecord(s->t0, s->stream));
