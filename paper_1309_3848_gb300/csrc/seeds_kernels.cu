@@ -1127,9 +1127,13 @@ __global__ void __launch_bounds__(1024, 1) seeds_persistent(const DevImage *__re
         const int64_t total = S.step_vt[s];
         if (threadIdx.x == 0) s_next[(s + 1) & 1] = 0;
         const bool rounds = nwarps * 32 < total;  // work beyond round 0 for some CTA
+        // odd steps walk the step's units from the end, so a step starts on
+        // the images whose state the step before touched last (still in L2)
+        const bool reverse = (s & 1) != 0;
         for (unsigned i = warp;; ) {
-            const int64_t base = ((int64_t)(i / nwarps_blk) * nwarps + cta_first + (i % nwarps_blk)) * 32;
-            if (base >= total) break;
+            const int64_t fwd = ((int64_t)(i / nwarps_blk) * nwarps + cta_first + (i % nwarps_blk)) * 32;
+            if (fwd >= total) break;
+            const int64_t base = reverse ? total - 32 - fwd : fwd;
             int lo = e0, hi = e1 - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
