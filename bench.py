@@ -278,7 +278,8 @@ def timed_steps(torch, fn, steps, flush, kernel_ms=None):
 
 def batched_vs_plain(torch, binding, flush, steps=5):
     """64 mixed images: one context and one launch for all of them against
-    one context and one launch per image, same labels required."""
+    one context and one launch per image, same labels required; and the
+    batch call replayed from a CUDA graph."""
     from paper_1309_3848_gb300 import synth
     jobs = synth.batch_64()
     imgs = make_images(jobs)
@@ -302,6 +303,9 @@ def batched_vs_plain(torch, binding, flush, steps=5):
     torch.cuda.synchronize()
     tb, _ = timed_steps(torch, run_batch, steps, flush)
     tp, _ = timed_steps(torch, run_plain, steps, flush)
+    graph = batch.capture(d, outs_b)  # the same batch call recorded in a CUDA graph
+    graph.replay()
+    tg, _ = timed_steps(torch, graph.replay, steps, flush)
     batch.check_status()
     for c in plain:
         c.check_status()
@@ -309,8 +313,9 @@ def batched_vs_plain(torch, binding, flush, steps=5):
     px = sum(j.pixels for j in jobs)
     vb = px / (statistics.mean(tb) / 1e3) / 1e6
     vp = px / (statistics.mean(tp) / 1e3) / 1e6
+    vg = px / (statistics.mean(tg) / 1e3) / 1e6
     return {"workload": "batch64_mixed", "pixels": px, "batched_mpix_s": vb, "plain_mpix_s": vp,
-            "batched_over_plain": vb / vp, "labels_identical": bool(same)}
+            "batched_over_plain": vb / vp, "graph_replay_mpix_s": vg, "labels_identical": bool(same)}
 
 
 def next_rows(torch, binding, flush, jobs, imgs, rgb_value, steps=5):
@@ -447,7 +452,8 @@ def run_gpu(args):
     if not args.no_autotune:  # result-invariant knobs, picked before the timed region
         t = ctx.autotune(d, outs, reps=3)
         tuned = {"threads_per_block": t.threads_per_block, "blocks_per_sm": t.blocks_per_sm,
-                 "hist_layout": t.hist_layout, "small_block_area": t.small_block_area}
+                 "hist_layout": t.hist_layout, "small_block_area": t.small_block_area,
+                 "pixel_tile_rows": t.pixel_tile_rows}
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()

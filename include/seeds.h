@@ -110,6 +110,8 @@ typedef struct {
  *   blocks_per_sm      resident CTAs per SM of the persistent kernel,
  *                      0 = as many as fit
  *   hist_layout        0: hist[k][j] (label-major), 1: hist[j][k] (bin-major)
+ *   pixel_tile_rows    unit rows of a pixel-phase warp tile (32 units wide):
+ *                      2 or 4 (0 = 4); shorter tiles balance small images
  *   small_block_area   blocks of at most this many pixels are judged by one
  *                      thread, larger ones by a warp (1..16; 0 = default) */
 typedef struct {
@@ -117,6 +119,7 @@ typedef struct {
     int32_t blocks_per_sm;
     int32_t hist_layout;
     int32_t small_block_area;
+    int32_t pixel_tile_rows;
 } seeds_tuning;
 
 /* Fill p with the paper's defaults for a W x H image and K superpixels:
@@ -183,7 +186,11 @@ int seeds_batch_iterate(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const in
  * int32 H_i x W_i buffer.  Asynchronous. */
 int seeds_batch_labels(seeds_ctx *c, int32_t *const *h_label_ptrs, void *stream);
 
-/* seeds_batch_iterate and seeds_batch_labels fused into one launch. */
+/* seeds_batch_iterate and seeds_batch_labels fused into one launch.  Once a
+ * context has run this call, a repeat of it on the same buffers allocates
+ * and synchronises nothing (a pointer upload, a barrier reset and the
+ * persistent kernel), so it can be captured into a CUDA graph and replayed;
+ * after replays, synchronise the replay stream before seeds_status. */
 int seeds_batch_run(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides,
                     int32_t *const *h_label_ptrs, void *stream);
 

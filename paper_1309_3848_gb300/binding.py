@@ -71,7 +71,8 @@ class seeds_server_stats_t(ctypes.Structure):
 
 class seeds_tuning(ctypes.Structure):
     _fields_ = [("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("hist_layout", ctypes.c_int32), ("small_block_area", ctypes.c_int32)]
+                ("hist_layout", ctypes.c_int32), ("small_block_area", ctypes.c_int32),
+                ("pixel_tile_rows", ctypes.c_int32)]
 
 
 def _load():
@@ -243,6 +244,24 @@ class SeedsContext:
         check(lib.seeds_batch_run(self._h, rgb, strides, _ptrs([t.data_ptr() for t in outs]),
                                   _stream_handle(stream)), "seeds_batch_run")
 
+    def capture(self, images, outs):
+        """A CUDA graph of one run over these device buffers: runs once to
+        build and cache the schedule, then records the call (a pointer
+        upload, a barrier reset and the persistent launch: no allocation, no
+        synchronisation) on a side stream.  Refill `images` and call
+        graph.replay() to run again."""
+        import torch
+        self.run(images, outs)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                self.run(images, outs)
+        torch.cuda.current_stream().wait_stream(side)
+        return graph
+
     def run_anytime(self, images, outs, max_steps=0, budget_ns=0, stream=None):
         """Anytime termination (Sec. 5.4): run, stopping after max_steps
         steps or budget_ns of device time (0 = no limit); asynchronous, see
@@ -278,8 +297,8 @@ class SeedsContext:
     def check_status(self):
         check(self.status(), "seeds_status")
 
-    def set_tuning(self, threads_per_block=0, blocks_per_sm=0, hist_layout=0, small_block_area=0):
-        t = seeds_tuning(threads_per_block, blocks_per_sm, hist_layout, small_block_area)
+    def set_tuning(self, threads_per_block=0, blocks_per_sm=0, hist_layout=0, small_block_area=0, pixel_tile_rows=0):
+        t = seeds_tuning(threads_per_block, blocks_per_sm, hist_layout, small_block_area, pixel_tile_rows)
         check(lib.seeds_set_tuning(self._h, ctypes.byref(t)), "seeds_set_tuning")
 
     def autotune(self, images, outs, reps=3, stream=None) -> seeds_tuning:

@@ -41,6 +41,7 @@ struct DevImage {
     int32_t hist_jmajor;  // hist[j*K + k] instead of hist[k*nbins + j]
     int32_t hist_sk, hist_sj;  // hist index = k*hist_sk + j*hist_sj (either layout)
     int32_t small_area;   // blocks up to this many pixels are judged by one thread
+    int32_t tile_uy;      // unit rows of a pixel-phase warp tile: 2 or kTileUY
     int32_t color;        // 0: RGB bytes, 1: 8-bit CIE L*a*b* codes (Sec. 6.2)
     int32_t means_iters;  // means-based pixel iterations after the histogram ones
     float means_w;        // (m/S)^2 = m^2 K / N, the spatial weight of SLIC's distance
@@ -119,12 +120,14 @@ __host__ __device__ inline int warp_hist_scratch_bytes(int nbins)
     return (b + 15) & ~15;
 }
 
-// The pixel phase works on warp tiles of kTileUX x kTileUY units of one
-// parity class (a unit per lane and tile row); the warp stages the labels of
-// the tile plus a 2-pixel halo in shared memory, behind the histogram scratch.
+// The pixel phase works on warp tiles of kTileUX x (2 or kTileUY) units of
+// one parity class (a unit per lane and tile row; the row count is a launch
+// knob); the warp stages the labels of the tile plus a 2-pixel halo in shared
+// memory, behind the histogram scratch, sized here for the taller tile.
 constexpr int kTileUX = 32, kTileUY = 4;
 constexpr int kTileW = 2 * kTileUX + 4;  // pixel columns staged
-constexpr int kTileH = 2 * kTileUY + 3;  // pixel rows staged
+__host__ __device__ constexpr int tile_h(int uy) { return 2 * uy + 3; }  // pixel rows staged
+constexpr int kTileH = tile_h(kTileUY);
 // staged labels, the units' bins, the list of the tile's boundary units
 constexpr int kTileBytes = (kTileW * kTileH * 2 + kTileUY * kTileUX * 2 + kTileUY * kTileUX + 15) & ~15;
 // the pixel catch-up replays kCatchupPerLane units per lane
@@ -206,7 +209,7 @@ __host__ __device__ inline int64_t pixel_tiles(const DevImage &im, int phase, in
 {
     int cols, rows;
     lattice(im.W, im.H, phase, cphase, &cols, &rows);
-    return (int64_t)((cols + kTileUX - 1) / kTileUX) * ((rows + kTileUY - 1) / kTileUY);
+    return (int64_t)((cols + kTileUX - 1) / kTileUX) * ((rows + im.tile_uy - 1) / im.tile_uy);
 }
 
 // Entries of image `img` for its op `o`.  When the moves of op o-1 (a phase)

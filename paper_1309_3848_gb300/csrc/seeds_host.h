@@ -179,6 +179,7 @@ inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const se
     d.hist_sk = d.hist_jmajor ? 1 : h.nbins;
     d.hist_sj = d.hist_jmajor ? h.K : 1;
     d.small_area = t.small_block_area;
+    d.tile_uy = t.pixel_tile_rows == 2 ? 2 : kTileUY;
     for (int l = 0; l <= h.L; ++l) {
         d.nbx[l] = h.nbx[l];
         d.nby[l] = h.nby[l];

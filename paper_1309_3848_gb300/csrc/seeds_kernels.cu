@@ -542,7 +542,7 @@ __device__ __forceinline__ void replay_pixel(const DevImage &im, int buf, int p,
 }
 
 // One warp-tile of a pixel phase: units (ux, uy) with ux in a 32-wide column
-// range (one per lane) and uy in a kTileUY-row range.  The warp first
+// range (one per lane) and uy in a UY-row range.  The warp first
 // replays the moves of the previous phase (cphase >= 0) for the same unit
 // range, then judges its own units.  The labels of the tile and a 2-pixel
 // halo are staged in shared memory (kNoLabel outside the image) with
@@ -552,7 +552,7 @@ __device__ __forceinline__ void replay_pixel(const DevImage &im, int buf, int p,
 //
 // MEANS: a means-based phase (OP_MPHASE), whose moves also carry the
 // superpixel sums and whose units are judged by means_pixel.
-template <bool MEANS>
+template <bool MEANS, int UY>
 __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, int tiles, int tile, int lane,
                               uint16_t *tsh)
 {
@@ -565,10 +565,10 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
     lattice(W, H, phase, cphase, &mcols, &mrows);
     const int tiles_x = (mcols + kTileUX - 1) / kTileUX;
     const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-    const int ux = tx * kTileUX + lane, uy0 = ty * kTileUY;
+    const int ux = tx * kTileUX + lane, uy0 = ty * UY;
 
     // the previous phase's decisions for the same units (loads issued first)
-    uint32_t cd[kTileUY];
+    uint32_t cd[UY];
     int ccols = 0, crows = 0, cpx = 0, cpy = 0;
     if (cphase >= 0) {
         cpx = cphase & 1;
@@ -577,7 +577,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         crows = (H - cpy + 1) >> 1;
     }
 #pragma unroll
-    for (int r = 0; r < kTileUY; ++r) {
+    for (int r = 0; r < UY; ++r) {
         const int uy = uy0 + r;
         cd[r] = (ux < ccols && uy < crows) ? im.dec[nb][uy * ccols + ux] : kNoMove;
     }
@@ -586,7 +586,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
     const int X0 = 2 * tx * kTileUX + px - 2, Y0 = 2 * uy0 + py - 2;
     const uint16_t *lab = im.lab[0][b];
 #pragma unroll
-    for (int r = 0; r < kTileH; ++r) {
+    for (int r = 0; r < tile_h(UY); ++r) {
         const int yy = Y0 + r;
         const bool rowin = yy >= 0 && yy < H;
 #pragma unroll
@@ -595,17 +595,17 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
             tsh[r * kTileW + c] = (rowin && xx >= 0 && xx < W) ? lab[yy * W + xx] : kNoLabel;
         }
     }
-    uint16_t *jsh = tsh + kTileW * kTileH;
-    uint8_t *lst = (uint8_t *)(jsh + kTileUY * kTileUX);
+    uint16_t *jsh = tsh + kTileW * tile_h(UY);
+    uint8_t *lst = (uint8_t *)(jsh + UY * kTileUX);
 #pragma unroll
-    for (int r = 0; r < kTileUY; ++r) {
+    for (int r = 0; r < UY; ++r) {
         const int uy = uy0 + r;
         jsh[r * 32 + lane] = (ux < ncols && uy < nrows) ? bin_at(im, (2 * uy + py) * W + 2 * ux + px) : 0;
     }
 
     // replay the previous phase's moves into buffer nb
 #pragma unroll
-    for (int r = 0; r < kTileUY; ++r)
+    for (int r = 0; r < UY; ++r)
         if (cd[r] != kNoMove) {
             const int cx = 2 * ux + cpx, cy = 2 * (uy0 + r) + cpy;
             replay_pixel(im, nb, cy * W + cx, cd[r]);
@@ -616,7 +616,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
     // pass 1: boundary units that may leave; the others decide "stay" here
     unsigned mine = 0;
 #pragma unroll
-    for (int r = 0; r < kTileUY; ++r) {
+    for (int r = 0; r < UY; ++r) {
         const int uy = uy0 + r;
         if (ux < ncols && uy < nrows) {
             const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * lane + 2);
@@ -628,7 +628,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
     }
     int nbd = 0;
 #pragma unroll
-    for (int r = 0; r < kTileUY; ++r) {
+    for (int r = 0; r < UY; ++r) {
         const unsigned bal = __ballot_sync(0xffffffffu, (mine >> r) & 1u);
         if ((mine >> r) & 1u) lst[nbd + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(r * 32 + lane);
         nbd += __popc(bal);
@@ -736,7 +736,10 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
 __device__ __noinline__ void op_means_tile(const DevImage &im, int o, int phase, int cphase, int tiles, int tile,
                                            int lane, uint16_t *tsh)
 {
-    op_pixel_tile<true>(im, o, phase, cphase, tiles, tile, lane, tsh);
+    if (im.tile_uy == 2)
+        op_pixel_tile<true, 2>(im, o, phase, cphase, tiles, tile, lane, tsh);
+    else
+        op_pixel_tile<true, kTileUY>(im, o, phase, cphase, tiles, tile, lane, tsh);
 }
 
 // ---------------------------------------------------------------------------
@@ -1154,7 +1157,10 @@ __global__ void __launch_bounds__(1024, 1) seeds_persistent(const DevImage *__re
                 break;
             case OP_PHASE:
                 if (E.level == 0)
-                    op_pixel_tile<false>(im, E.opidx, E.phase, E.cphase, E.units, off >> 5, lane, tsh);
+                    if (im.tile_uy == 2)
+                        op_pixel_tile<false, 2>(im, E.opidx, E.phase, E.cphase, E.units, off >> 5, lane, tsh);
+                    else
+                        op_pixel_tile<false, kTileUY>(im, E.opidx, E.phase, E.cphase, E.units, off >> 5, lane, tsh);
                 else if (E.group == 1)
                     op_block_phase_thread(im, E.opidx, E.level, E.phase, E.cphase, E.units, off + lane);
                 else
@@ -1513,6 +1519,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     d.hist_sk = nbins;
     d.hist_sj = 1;
     d.small_area = 16;
+    d.tile_uy = kTileUY;
     d.nbx[0] = p->width;
     d.nby[0] = p->height;
     d.maxarea[0] = 1;

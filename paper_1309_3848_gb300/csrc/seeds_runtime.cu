@@ -46,7 +46,7 @@ struct seeds_ctx {
     int32_t *d_err = nullptr;
     int32_t *d_steps = nullptr;  // steps run by the last anytime launch
     bool stopped_state = false;  // the last launch was an anytime run: no final state to output
-    seeds_tuning tune{1024, 0, 0, 16};
+    seeds_tuning tune{1024, 0, 0, 16, 4};
     int grid = 0;
     size_t smem = 0;
     int max_nbins = 1;
@@ -242,7 +242,11 @@ int launch(seeds_ctx *c, int kind, int ob, int oe, cudaStream_t s, int32_t stop_
         if (rc) return rc;
     }
     c->profiled = c->profile;
-    rc = from_cuda(cudaEventRecord(c->done, s));
+    // while the stream is being captured into a CUDA graph the completion
+    // event keeps its last real record: the caller synchronises replays
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    rc = from_cuda(cudaStreamIsCapturing(s, &cap));
+    if (!rc && cap == cudaStreamCaptureStatusNone) rc = from_cuda(cudaEventRecord(c->done, s));
     c->launched = true;
     // where every image's state now lives, and which moves await catch-up
     c->stopped_state = anytime;
@@ -590,6 +594,8 @@ int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t)
     if (!c || !t) return SEEDS_ERR_INVALID;
     seeds_tuning n = *t;
     if (n.small_block_area == 0) n.small_block_area = 16;
+    if (n.pixel_tile_rows == 0) n.pixel_tile_rows = 4;
+    if (n.pixel_tile_rows != 2 && n.pixel_tile_rows != 4) return SEEDS_ERR_INVALID;
     if (n.threads_per_block != 0 && n.threads_per_block != 128 && n.threads_per_block != 256 &&
         n.threads_per_block != 512 && n.threads_per_block != 1024)
         return SEEDS_ERR_INVALID;
@@ -651,16 +657,18 @@ int seeds_autotune(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t
     float cur_ms = 0.f;
     if (!rc) rc = time_it(cur, &cur_ms);
     // coordinate descent, one pass over the knobs; a change must win by 2%
-    const int threads[] = {128, 256, 512, 1024}, blocks[] = {0, 1, 2, 3}, layouts[] = {0, 1}, areas[] = {4, 9, 16};
-    for (int knob = 0; knob < 4 && !rc; ++knob) {
-        const int *vals = knob == 0 ? threads : knob == 1 ? blocks : knob == 2 ? layouts : areas;
-        const int nv = knob == 0 ? 4 : knob == 1 ? 4 : knob == 2 ? 2 : 3;
+    const int threads[] = {128, 256, 512, 1024}, blocks[] = {0, 1, 2, 3}, layouts[] = {0, 1}, areas[] = {4, 9, 16},
+              rows[] = {2, 4};
+    for (int knob = 0; knob < 5 && !rc; ++knob) {
+        const int *vals = knob == 0 ? threads : knob == 1 ? blocks : knob == 2 ? layouts : knob == 3 ? areas : rows;
+        const int nv = knob == 0 ? 4 : knob == 1 ? 4 : knob == 2 ? 2 : knob == 3 ? 3 : 2;
         for (int v = 0; v < nv && !rc; ++v) {
             seeds_tuning t = cur;
-            int *field = knob == 0 ? &t.threads_per_block
+            int *field = knob == 0   ? &t.threads_per_block
                          : knob == 1 ? &t.blocks_per_sm
                          : knob == 2 ? &t.hist_layout
-                                     : &t.small_block_area;
+                         : knob == 3 ? &t.small_block_area
+                                     : &t.pixel_tile_rows;
             if (*field == vals[v]) continue;
             *field = vals[v];
             float ms = 0.f;

@@ -107,6 +107,15 @@ def test_batch_mixing_means_and_histogram_only_images(torch, binding):
     check(torch, binding, jobs)
 
 
+def test_means_with_short_pixel_tiles(torch, binding):
+    small = synth.JobSpec(synth.ImageSpec(200, 90, seed=8, cells=20, sigma=9.0), 40, 4, 2, 2)
+    jobs = [means(synth.plain_481()[0], 2, 6), means(small, 1, 0, 1)]
+    imgs = gc.make_images(jobs)
+    got, _ = gc.gpu_run(binding, torch, jobs, imgs, dict(pixel_tile_rows=2))
+    for i, (a, b) in enumerate(zip(got, gc.oracle_many(jobs, imgs))):
+        assert gc.first_mismatch(a, b) is None, "image %d" % i
+
+
 def test_anytime_stops_inside_the_means_iterations(torch, binding):
     job = means(synth.plain_481()[0], 2, 8)
     img = synth.make_image(job.image)

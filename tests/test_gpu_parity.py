@@ -74,7 +74,8 @@ def test_state_matches_after_every_op(torch, binding, job):
     assert moved_total > 0
 
 
-@pytest.mark.parametrize("tuning", [dict(small_block_area=1), dict(small_block_area=16, hist_layout=1)])
+@pytest.mark.parametrize("tuning", [dict(small_block_area=1), dict(small_block_area=16, hist_layout=1),
+                                    dict(pixel_tile_rows=2)])
 def test_mixed_bin_batch_matches_after_every_op(torch, binding, tuning):
     """Images with different bin counts (and so different scratch use) in
     one batch, every block judged by a warp or by a thread: full state of
@@ -200,7 +201,8 @@ def test_edge_sizes(torch, binding):
 
 TUNINGS = [dict(threads_per_block=128), dict(threads_per_block=512, hist_layout=1),
            dict(hist_layout=1, small_block_area=1), dict(blocks_per_sm=1, small_block_area=4),
-           dict(threads_per_block=256, blocks_per_sm=2, hist_layout=0, small_block_area=9)]
+           dict(threads_per_block=256, blocks_per_sm=2, hist_layout=0, small_block_area=9),
+           dict(pixel_tile_rows=2), dict(threads_per_block=512, pixel_tile_rows=2, small_block_area=1)]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)
@@ -306,8 +308,8 @@ def test_autotune_keeps_labels(torch, binding):
     best = ctx.autotune(d, outs, reps=2)
     assert best.threads_per_block in (128, 256, 512, 1024)
     t = ctx.get_tuning()
-    assert (t.threads_per_block, t.blocks_per_sm, t.hist_layout, t.small_block_area) == \
-        (best.threads_per_block, best.blocks_per_sm, best.hist_layout, best.small_block_area)
+    assert (t.threads_per_block, t.blocks_per_sm, t.hist_layout, t.small_block_area, t.pixel_tile_rows) == \
+        (best.threads_per_block, best.blocks_per_sm, best.hist_layout, best.small_block_area, best.pixel_tile_rows)
     for o in outs:
         o.fill_(-1)
     ctx.run(d, outs)
