@@ -1,7 +1,9 @@
 """Compile libseeds.so (sm_103a) in-tree with nvcc.
 
-Two translation units (kernels, host runtime) compile in parallel, then link
-into paper_1309_3848_gb300/libseeds.so.  No cmake; a minute at most.
+The translation units (kernels, host runtime, server) compile in parallel,
+then link into paper_1309_3848_gb300/libseeds.so.  No cmake; a minute at most.
+`build_debug()` makes libseeds_debug.so, the same code with every device
+index checked (SEEDS_DEBUG_BOUNDS), for the bounds tests.
 """
 import concurrent.futures
 import os
@@ -14,6 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libseeds.so")
+DEBUG_LIB = os.path.join(PKG, "libseeds_debug.so")
 SOURCES = ["seeds_kernels.cu", "seeds_runtime.cu", "seeds_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -32,24 +35,27 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, lib: str = LIB,
+          defines=()) -> str:
+    if not force and up_to_date(lib):
+        return lib
+    build_dir = BUILD if lib == LIB else BUILD + "_" + os.path.splitext(os.path.basename(lib))[0]
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    common += ["-D" + d for d in defines]
     if ptxas_info:
         common += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")
         cmd = [cc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
@@ -62,13 +68,18 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         for _, log in results:
             if log:
                 print(log)
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (res.stdout, res.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_debug(force: bool = False) -> str:
+    """libseeds_debug.so: every device index checked against its buffer."""
+    return build(force=force, lib=DEBUG_LIB, defines=("SEEDS_DEBUG_BOUNDS",))
 
 
 if __name__ == "__main__":

@@ -13,7 +13,9 @@ import os
 from typing import List, Optional, Sequence
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libseeds.so")
+# SEEDS_LIB selects another build of the library (the bounds-checked debug
+# build in its tests); unset, the in-tree libseeds.so
+LIB_PATH = os.environ.get("SEEDS_LIB") or os.path.join(_HERE, "libseeds.so")
 
 SEEDS_OK = 0
 SEEDS_ERR_INVALID = -1

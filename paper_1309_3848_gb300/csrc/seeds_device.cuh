@@ -57,6 +57,7 @@ struct DevImage {
     uint32_t *dec[2];                   // per unit of a phase: (k << 16 | n) or kNoMove
     unsigned long long *msum[2];        // K x 5: sums of the 3 colour codes, of x, of y (means iterations)
     int32_t units_cap;                  // entries of each dec buffer
+    int32_t *err;                       // the launch's error word (debug builds report bounds trips here)
     // per call
     const uint8_t *rgb;
     int64_t stride;

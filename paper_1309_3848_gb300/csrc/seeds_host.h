@@ -154,7 +154,8 @@ inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t 
 
 // The device record of an image whose state starts at `base` (laid out as
 // derive() planned), with the given launch knobs and per-call pointers.
-inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const seeds_tuning &t, const IoEntry &io)
+inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const seeds_tuning &t, const IoEntry &io,
+                               int32_t *err)
 {
     DevImage d;
     std::memset(&d, 0, sizeof(d));
@@ -198,6 +199,7 @@ inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const se
         d.msum[q] = h.p.means_iters > 0 ? (unsigned long long *)(base + h.off_msum[q]) : nullptr;
     }
     d.units_cap = h.units_cap;
+    d.err = err;
     d.rgb = io.rgb;
     d.stride = io.stride;
     d.out = io.out;

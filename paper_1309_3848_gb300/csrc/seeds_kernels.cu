@@ -142,11 +142,33 @@ __device__ int grid_sync(GridBarrier *bar, int32_t *err, bool want_stop = false)
 // small helpers
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ int hidx(const DevImage &im, int k, int j) { return k * im.hist_sk + j * im.hist_sj; }
+// Debug builds (SEEDS_DEBUG_BOUNDS): every histogram, size, bin, label and
+// decision index is checked against its buffer; one outside is recorded in
+// the error word (DERR_BOUNDS, reported as SEEDS_ERR_DEVICE) and replaced by
+// 0, so the access stays inside the buffer.  Release builds check nothing.
+#ifdef SEEDS_DEBUG_BOUNDS
+__device__ __forceinline__ int64_t checked_index(const DevImage &im, int64_t i, int64_t n)
+{
+    if (i < 0 || i >= n) {
+        atomicOr(im.err, DERR_BOUNDS);
+        return 0;
+    }
+    return i;
+}
+#define SEEDS_IDX(im, i, n) checked_index((im), (int64_t)(i), (int64_t)(n))
+#else
+#define SEEDS_IDX(im, i, n) (i)
+#endif
+
+__device__ __forceinline__ int hidx(const DevImage &im, int k, int j)
+{
+    return (int)SEEDS_IDX(im, k, im.K) * im.hist_sk + (int)SEEDS_IDX(im, j, im.nbins) * im.hist_sj;
+}
 
 __device__ __forceinline__ int bin_at(const DevImage &im, int p)
 {
-    return im.bins16 ? (int)((const uint16_t *)im.bins)[p] : (int)((const uint8_t *)im.bins)[p];
+    const int64_t q = SEEDS_IDX(im, p, (int64_t)im.W * im.H);
+    return im.bins16 ? (int)((const uint16_t *)im.bins)[q] : (int)((const uint8_t *)im.bins)[q];
 }
 
 // Ring of a unit, bit r: NW, N, NE, E, SE, S, SW, W (r = 0..7).  Odd bits
@@ -248,8 +270,8 @@ __device__ __forceinline__ void move_counts(const DevImage &im, int buf, int k, 
 
 __device__ __forceinline__ void move_size(const DevImage &im, int buf, int k, int n, int cnt)
 {
-    atomicSub(&im.size[buf][k], cnt);
-    atomicAdd(&im.size[buf][n], cnt);
+    atomicSub(&im.size[buf][SEEDS_IDX(im, k, im.K)], cnt);
+    atomicAdd(&im.size[buf][SEEDS_IDX(im, n, im.K)], cnt);
 }
 
 // Sparse colour histogram of block (bx,by) of a level in the warp's shared
@@ -521,7 +543,7 @@ __device__ __noinline__ uint32_t means_pixel(const DevImage &im, int b, int nb, 
         }
     }
     if (!(db < means_distance(im, b, k, c, x, y))) return kNoMove;
-    im.lab[0][nb][y * im.W + x] = (uint16_t)best;
+    im.lab[0][nb][SEEDS_IDX(im, y * im.W + x, (int64_t)im.W * im.H)] = (uint16_t)SEEDS_IDX(im, best, im.K);
     move_counts(im, nb, k, best, j, 1);
     move_size(im, nb, k, best, 1);
     move_sums(im, nb, k, best, x, y);
@@ -579,7 +601,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
 #pragma unroll
     for (int r = 0; r < UY; ++r) {
         const int uy = uy0 + r;
-        cd[r] = (ux < ccols && uy < crows) ? im.dec[nb][uy * ccols + ux] : kNoMove;
+        cd[r] = (ux < ccols && uy < crows) ? im.dec[nb][SEEDS_IDX(im, uy * ccols + ux, im.units_cap)] : kNoMove;
     }
 
     // stage the labels of buffer b and the units' bins
@@ -623,7 +645,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
             if (may_leave([&](int dx, int dy) { return (int)T[dy * kTileW + dx]; }, (int)T[0]))
                 mine |= 1u << r;
             else
-                im.dec[b][uy * ncols + ux] = kNoMove;
+                im.dec[b][SEEDS_IDX(im, uy * ncols + ux, im.units_cap)] = kNoMove;
         }
     }
     int nbd = 0;
@@ -650,7 +672,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         const int nc = sorted_candidates(T[-1], T[1], T[-kTileW], T[kTileW], k, cand);
         const int j = jsh[r * 32 + l];
         if constexpr (MEANS) {
-            im.dec[b][uy * ncols + uxe] = means_pixel(im, b, nb, x, y, k, j, cand);
+            im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = means_pixel(im, b, nb, x, y, k, j, cand);
             continue;
         }
         // Prop. 2 sums G_x = sum_{i in K_p} b_{N_i}(x) as a weighted count
@@ -708,7 +730,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         for (int c = 0; c < 4; ++c) {
             const int n = cand[c];
             if (n == kNoLabel) continue;
-            const int64_t a = hist[hidx(im, n, j)], sz = size[n];
+            const int64_t a = hist[hidx(im, n, j)], sz = size[SEEDS_IDX(im, n, im.K)];
             if (best == kNoLabel || gd81 * (a * s_b - a_b * sz) + gn * (int64_t)(Gc[c] - G_b) * sz * s_b > 0) {
                 best = n;
                 a_b = a;
@@ -716,17 +738,17 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
                 G_b = Gc[c];
             }
         }
-        const int64_t a_k = hist[hidx(im, k, j)], s_k = size[k];
+        const int64_t a_k = hist[hidx(im, k, j)], s_k = size[SEEDS_IDX(im, k, im.K)];
         const int64_t gain =
             gd81 * (a_b * (s_k - 1) - (a_k - 1) * s_b) + gn * (int64_t)(G_b + Kp - Gk) * s_b * (s_k - 1);
         uint32_t dec = kNoMove;
         if (gain > 0) {
             dec = ((uint32_t)k << 16) | (uint32_t)best;
-            im.lab[0][nb][p] = (uint16_t)best;
+            im.lab[0][nb][SEEDS_IDX(im, p, (int64_t)W * H)] = (uint16_t)SEEDS_IDX(im, best, im.K);
             move_counts(im, nb, k, best, j, 1);
             move_size(im, nb, k, best, 1);
         }
-        im.dec[b][uy * ncols + uxe] = dec;
+        im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = dec;
     }
     __syncwarp();
 }
@@ -757,7 +779,8 @@ __device__ void replay_small_block(const DevImage &im, int buf, int level, int b
     for (int yy = y0; yy < y1; ++yy)
         for (int xx = x0; xx < x1; ++xx) move_counts(im, buf, k, n, bin_at(im, yy * im.W + xx), 1);
     move_size(im, buf, k, n, (x1 - x0) * (y1 - y0));
-    im.lab[level][buf][by * im.nbx[level] + bx] = (uint16_t)n;
+    im.lab[level][buf][SEEDS_IDX(im, by * im.nbx[level] + bx, (int64_t)im.nbx[level] * im.nby[level])] =
+        (uint16_t)SEEDS_IDX(im, n, im.K);
 }
 
 // Judge small block (bx,by); SM bounds its pixel count, so the dedupe of its
@@ -786,8 +809,8 @@ __device__ uint32_t judge_small_block(const DevImage &im, int b, int nb, int lev
     int64_t S[4] = {0, 0, 0, 0}, S_st = 0;
     int64_t sz[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) sz[c] = cand[c] != kNoLabel ? size[cand[c]] : 1;
-    const int64_t s_k = size[k], s_rest = s_k - m;
+    for (int c = 0; c < 4; ++c) sz[c] = cand[c] != kNoLabel ? size[SEEDS_IDX(im, cand[c], im.K)] : 1;
+    const int64_t s_k = size[SEEDS_IDX(im, k, im.K)], s_rest = s_k - m;
     // S(A, L) = sum over the distinct bins j of L of min(A[j]*|L|, L_j*|A|)
 #pragma unroll
     for (int t = 0; t < SM; ++t) {
@@ -817,7 +840,7 @@ __device__ uint32_t judge_small_block(const DevImage &im, int b, int nb, int lev
             zb = sz[c];
         }
     if (!(Sb * s_rest > S_st * zb)) return kNoMove;
-    im.lab[level][nb][by * nx + bx] = (uint16_t)n;
+    im.lab[level][nb][SEEDS_IDX(im, by * nx + bx, (int64_t)nx * im.nby[level])] = (uint16_t)SEEDS_IDX(im, n, im.K);
 #pragma unroll
     for (int t = 0; t < SM; ++t)
         if (t < m) move_counts(im, nb, k, n, jj[t], 1);
@@ -840,7 +863,7 @@ __device__ void op_block_phase_thread(const DevImage &im, int o, int level, int 
         int ccols, crows;
         lattice(nx, ny, cphase, -1, &ccols, &crows);
         if (ux < ccols && uy < crows) {
-            const uint32_t d = im.dec[nb][uy * ccols + ux];
+            const uint32_t d = im.dec[nb][SEEDS_IDX(im, uy * ccols + ux, im.units_cap)];
             if (d != kNoMove) replay_small_block(im, nb, level, 2 * ux + (cphase & 1), 2 * uy + (cphase >> 1), d);
         }
     }
@@ -850,7 +873,7 @@ __device__ void op_block_phase_thread(const DevImage &im, int o, int level, int 
     const uint32_t dec = ma <= 4   ? judge_small_block<4>(im, b, nb, level, bx, by)
                          : ma <= 9 ? judge_small_block<9>(im, b, nb, level, bx, by)
                                    : judge_small_block<kSmallMax>(im, b, nb, level, bx, by);
-    im.dec[b][uy * ncols + ux] = dec;
+    im.dec[b][SEEDS_IDX(im, uy * ncols + ux, im.units_cap)] = dec;
 }
 
 // ---------------------------------------------------------------------------
@@ -873,7 +896,8 @@ __device__ void replay_large_block(const DevImage &im, int buf, int level, int b
     const int nd = block_sparse_hist(im, level, bx, by, lane, wsh, max_nbins, &m);
     block_sparse_apply_clear(im, buf, k, n, nd, lane, wsh, max_nbins);
     if (lane == 0) {
-        im.lab[level][buf][by * im.nbx[level] + bx] = (uint16_t)n;
+        im.lab[level][buf][SEEDS_IDX(im, by * im.nbx[level] + bx, (int64_t)im.nbx[level] * im.nby[level])] =
+            (uint16_t)SEEDS_IDX(im, n, im.K);
         move_size(im, buf, k, n, m);
     }
 }
@@ -894,7 +918,7 @@ __device__ void op_block_phase_warp(const DevImage &im, int o, int level, int ph
         int ccols, crows;
         lattice(nx, ny, cphase, -1, &ccols, &crows);
         if (ux < ccols && uy < crows) {
-            const uint32_t d = im.dec[nb][uy * ccols + ux];
+            const uint32_t d = im.dec[nb][SEEDS_IDX(im, uy * ccols + ux, im.units_cap)];
             if (d != kNoMove)
                 replay_large_block(im, nb, level, 2 * ux + (cphase & 1), 2 * uy + (cphase >> 1), d, lane, wsh,
                                    max_nbins);
@@ -908,7 +932,7 @@ __device__ void op_block_phase_warp(const DevImage &im, int o, int level, int ph
     int cand[4];
     const int nc = unit_candidates(lab, nx, ny, bx, by, k, cand);
     if (nc == 0) {
-        if (lane == 0) im.dec[b][uu] = kNoMove;
+        if (lane == 0) im.dec[b][SEEDS_IDX(im, uu, im.units_cap)] = kNoMove;
         return;
     }
     const int32_t *hist = im.hist[b], *size = im.size[b];
@@ -918,8 +942,8 @@ __device__ void op_block_phase_warp(const DevImage &im, int o, int level, int ph
     const uint16_t *lst = (const uint16_t *)(hsh + max_nbins);
     int64_t sz[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) sz[c] = cand[c] != kNoLabel ? size[cand[c]] : 1;
-    const int64_t s_k = size[k], s_rest = s_k - m;
+    for (int c = 0; c < 4; ++c) sz[c] = cand[c] != kNoLabel ? size[SEEDS_IDX(im, cand[c], im.K)] : 1;
+    const int64_t s_k = size[SEEDS_IDX(im, k, im.K)], s_rest = s_k - m;
     int64_t S[4] = {0, 0, 0, 0}, S_st = 0;
     for (int t = lane; t < nd; t += 32) {
         const int j = lst[t];
@@ -946,9 +970,9 @@ __device__ void op_block_phase_warp(const DevImage &im, int o, int level, int ph
     const bool moves = Sb * s_rest > S_st * zb;
     block_sparse_apply_clear(im, nb, moves ? k : -1, n, nd, lane, wsh, max_nbins);
     if (lane == 0) {
-        im.dec[b][uu] = moves ? (((uint32_t)k << 16) | (uint32_t)n) : kNoMove;
+        im.dec[b][SEEDS_IDX(im, uu, im.units_cap)] = moves ? (((uint32_t)k << 16) | (uint32_t)n) : kNoMove;
         if (moves) {
-            im.lab[level][nb][by * nx + bx] = (uint16_t)n;
+            im.lab[level][nb][SEEDS_IDX(im, by * nx + bx, (int64_t)nx * ny)] = (uint16_t)SEEDS_IDX(im, n, im.K);
             move_size(im, nb, k, n, m);
         }
     }
@@ -968,7 +992,7 @@ __device__ void op_catchup(const DevImage &im, int o, int level, int phase, int 
     if (group == 32) {  // large blocks: one warp per unit
         const int u = off >> 5;
         if (u >= units) return;
-        const uint32_t d = im.dec[nb][u];
+        const uint32_t d = im.dec[nb][SEEDS_IDX(im, u, im.units_cap)];
         if (d == kNoMove) return;
         int bx, by;
         unit_pos(u, phase, nx, &bx, &by);
@@ -981,7 +1005,7 @@ __device__ void op_catchup(const DevImage &im, int o, int level, int phase, int 
 #pragma unroll
         for (int r = 0; r < kCatchupPerLane; ++r) {
             const int u = chunk * 32 * kCatchupPerLane + 32 * r + lane;
-            d[r] = u < units ? im.dec[nb][u] : kNoMove;
+            d[r] = u < units ? im.dec[nb][SEEDS_IDX(im, u, im.units_cap)] : kNoMove;
         }
         const bool means = op_at(im.L, im.iters, im.means_iters, o - 1).kind == OP_MPHASE;
 #pragma unroll
@@ -996,7 +1020,7 @@ __device__ void op_catchup(const DevImage &im, int o, int level, int phase, int 
     }
     const int u = off + lane;  // small blocks: one thread per unit
     if (u >= units) return;
-    const uint32_t d = im.dec[nb][u];
+    const uint32_t d = im.dec[nb][SEEDS_IDX(im, u, im.units_cap)];
     if (d == kNoMove) return;
     int bx, by;
     unit_pos(u, phase, nx, &bx, &by);
@@ -1597,6 +1621,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
         d.msum[q] = p->means_iters > 0 ? (unsigned long long *)(base + o_msum[q]) : nullptr;
     }
     d.units_cap = units_cap;
+    d.err = (int32_t *)(base + o_err);
     d.rgb = d_rgb;
     d.stride = row_stride_bytes;
     d.out = d_labels_out;

@@ -93,7 +93,7 @@ void fill_dev_images(seeds_ctx *c)
     c->h_imgs.resize(c->img.size());
     unsigned char *base = c->pool;
     for (size_t i = 0; i < c->img.size(); ++i) {
-        c->h_imgs[i] = make_dev_image(c->img[i], base, c->tune, c->io[i]);
+        c->h_imgs[i] = make_dev_image(c->img[i], base, c->tune, c->io[i], c->d_err);
         base += c->img[i].bytes;
     }
 }

@@ -300,7 +300,8 @@ int seeds_server_step(seeds_server *s, int32_t *resident_out)
         rc = from_cuda(cudaMemcpy2DAsync(base + r->rgb_off, row, r->h_rgb, (size_t)r->stride, row,
                                          (size_t)r->h.p.height, cudaMemcpyHostToDevice, st));
         const DevImage rec =
-            make_dev_image(r->h, base, s->tune, IoEntry{base + r->rgb_off, (int64_t)row, (int32_t *)(base + r->out_off)});
+            make_dev_image(r->h, base, s->tune, IoEntry{base + r->rgb_off, (int64_t)row, (int32_t *)(base + r->out_off)},
+                           s->d_err);
         if (!rc) rc = from_cuda(launch_admit(s->d_imgs, slot, rec, st));
         if (rc) {
             s->alloc.release(r->off, r->bytes);

@@ -1,0 +1,41 @@
+"""Run a set of jobs through the library named by SEEDS_LIB (the
+bounds-checked debug build) and compare with the oracle; prints one JSON
+line.  Started by test_gpu_debug_bounds.py in a process of its own."""
+import dataclasses
+import json
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+
+import torch  # noqa: E402
+
+import gpu_cases as gc  # noqa: E402
+from paper_1309_3848_gb300 import binding, synth  # noqa: E402
+
+
+def main():
+    assert binding.LIB_PATH == os.environ["SEEDS_LIB"]
+    jobs = synth.plain_481() + synth.random_small_jobs(404, 20, max_side=160)
+    jobs += [dataclasses.replace(synth.plain_481()[0], color_space=1, means_iters=2, compactness=9)]
+    jobs += [synth.JobSpec(synth.ImageSpec(W, H, seed=W * 7 + H, cells=3, sigma=20.0), K, B, L, 2)
+             for W, H, K, B, L in [(1, 1, 1, 5, 0), (1, 40, 3, 4, 0), (40, 1, 3, 4, 0), (2, 2, 1, 16, 0),
+                                   (64, 64, 4, 16, 2)]]
+    imgs = gc.make_images(jobs)
+    results = {}
+    for tuning in (None, dict(small_block_area=1, pixel_tile_rows=2), dict(threads_per_block=256, hist_layout=1)):
+        got, ctx = gc.gpu_run(binding, torch, jobs, imgs, tuning)
+        results[str(tuning)] = [gc.first_mismatch(a, b) for a, b in zip(got, gc.oracle_many(jobs, imgs))]
+    # an anytime stop inside the block levels
+    ctx = binding.SeedsContext([gc.params_for(binding, j) for j in jobs])
+    d = [torch.from_numpy(im).cuda() for im in imgs]
+    outs = [torch.empty((j.image.height, j.image.width), dtype=torch.int32, device="cuda") for j in jobs]
+    ctx.run_anytime(d, outs, max_steps=7)
+    torch.cuda.synchronize()
+    ctx.check_status()
+    print(json.dumps({"mismatches": {k: [m for m in v if m] for k, v in results.items()}, "images": len(jobs)}))
+
+
+if __name__ == "__main__":
+    main()
