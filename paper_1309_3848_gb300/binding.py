@@ -184,6 +184,47 @@ def _stream_handle(stream) -> Optional[int]:
     return stream.cuda_stream
 
 
+# --------------------------------------------------------------------------
+# autotune cache: tunings in a JSON file keyed by the batch's shapes
+# --------------------------------------------------------------------------
+
+_TUNING_FIELDS = [f for f, _ in seeds_tuning._fields_]
+
+
+def tuning_cache_key(params: Sequence[seeds_params], device: str) -> str:
+    """The batch's parameter sets, in order, and the device name, hashed."""
+    import hashlib
+    import json
+    rows = [[getattr(p, f) for f, _ in seeds_params._fields_] for p in params]
+    return hashlib.sha256(json.dumps([device, rows]).encode()).hexdigest()[:32]
+
+
+def load_cached_tuning(path: str, key: str) -> Optional[seeds_tuning]:
+    import json
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    return seeds_tuning(*[int(rec[f]) for f in _TUNING_FIELDS])
+
+
+def store_tuning(path: str, key: str, t: seeds_tuning, note: str = "") -> None:
+    import json
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        data = {}
+    data[key] = dict({f: int(getattr(t, f)) for f in _TUNING_FIELDS}, note=note)
+    tmp = path + ".%d.tmp" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 class SeedsContext:
     """One library context over a list of image parameter sets.
 
@@ -303,12 +344,26 @@ class SeedsContext:
         t = seeds_tuning(threads_per_block, blocks_per_sm, hist_layout, small_block_area, pixel_tile_rows)
         check(lib.seeds_set_tuning(self._h, ctypes.byref(t)), "seeds_set_tuning")
 
-    def autotune(self, images, outs, reps=3, stream=None) -> seeds_tuning:
-        """Time the result-invariant knobs on these inputs and keep the fastest."""
+    def autotune(self, images, outs, reps=3, stream=None, cache: Optional[str] = None) -> seeds_tuning:
+        """Time the result-invariant knobs on these inputs and keep the
+        fastest.  With `cache` (a JSON file path), a batch of the same
+        parameter sets on the same device reuses the stored knobs without
+        timing, and a new one is stored after tuning."""
+        key = None
+        if cache:
+            import torch
+            key = tuning_cache_key(self.params, torch.cuda.get_device_name())
+            hit = load_cached_tuning(cache, key)
+            if hit is not None:
+                self.set_tuning(*[getattr(hit, f) for f in _TUNING_FIELDS])
+                return self.get_tuning()
         rgb, strides = self._rgb_args(images)
         best = seeds_tuning()
         check(lib.seeds_autotune(self._h, rgb, strides, _ptrs([t.data_ptr() for t in outs]), reps,
                                  _stream_handle(stream), ctypes.byref(best)), "seeds_autotune")
+        if cache:
+            store_tuning(cache, key, best, "%d images, first %dx%d" % (self.n, self.params[0].width,
+                                                                       self.params[0].height))
         return best
 
     def get_tuning(self) -> seeds_tuning:

@@ -95,3 +95,20 @@ def test_footprint_grows_with_the_images(binding):
     b = binding.footprint([binding.make_params(640, 480, 500, 3, 5, 2)] * 3)
     c = binding.footprint([binding.make_params(3840, 2160, 5000, 5, 8, 4)])
     assert a > 640 * 480 * 5 and b >= 3 * a and c > 8 * a
+
+
+def test_autotune_cache_round_trip(binding, tmp_path):
+    p = [binding.make_params(640, 480, 500, 3, 5, 2), binding.make_params(320, 240, 200, 2, 5, 2)]
+    k1 = binding.tuning_cache_key(p, "GPU A")
+    assert k1 == binding.tuning_cache_key(list(p), "GPU A")
+    assert k1 != binding.tuning_cache_key(p[::-1], "GPU A")
+    assert k1 != binding.tuning_cache_key(p, "GPU B")
+    assert k1 != binding.tuning_cache_key([p[0], binding.make_params(320, 240, 200, 2, 5, 3)], "GPU A")
+    path = str(tmp_path / "tune.json")
+    assert binding.load_cached_tuning(path, k1) is None
+    binding.store_tuning(path, k1, binding.seeds_tuning(512, 1, 1, 9, 2), "two images")
+    binding.store_tuning(path, "other", binding.seeds_tuning(1024, 0, 0, 16, 4))
+    t = binding.load_cached_tuning(path, k1)
+    assert (t.threads_per_block, t.blocks_per_sm, t.hist_layout, t.small_block_area, t.pixel_tile_rows) == \
+        (512, 1, 1, 9, 2)
+    assert binding.load_cached_tuning(path, "missing") is None

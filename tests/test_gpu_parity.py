@@ -330,3 +330,24 @@ def test_set_tuning_that_cannot_launch_leaves_context_usable(torch, binding):
     assert after.threads_per_block == before.threads_per_block
     got, _ = gc.gpu_run(binding, torch, [job], [synth.make_image(job.image)])
     assert np.array_equal(got[0], gc.oracle_run(job, synth.make_image(job.image)))
+
+
+def test_autotune_cache_reuses_the_knobs(torch, binding, tmp_path):
+    jobs = synth.random_small_jobs(33, 4, max_side=100)
+    imgs = gc.make_images(jobs)
+    d = [torch.from_numpy(im).cuda() for im in imgs]
+    outs = [torch.empty((j.image.height, j.image.width), dtype=torch.int32, device="cuda") for j in jobs]
+    path = str(tmp_path / "tunings.json")
+    first = binding.SeedsContext([gc.params_for(binding, j) for j in jobs])
+    t1 = first.autotune(d, outs, reps=1, cache=path)
+    second = binding.SeedsContext([gc.params_for(binding, j) for j in jobs])
+    n0 = second.launch_count()
+    t2 = second.autotune(d, outs, reps=1, cache=path)
+    assert second.launch_count() == n0  # a cache hit times nothing
+    fields = ("threads_per_block", "blocks_per_sm", "hist_layout", "small_block_area", "pixel_tile_rows")
+    assert [getattr(t1, f) for f in fields] == [getattr(t2, f) for f in fields]
+    second.run(d, outs)
+    torch.cuda.synchronize()
+    second.check_status()
+    for o, w in zip(outs, gc.oracle_many(jobs, imgs)):
+        assert gc.first_mismatch(o.cpu().numpy(), w) is None
