@@ -182,6 +182,20 @@ def oracle_run(job, img):
     return r.run(img)
 
 
+def moves_per_level(job, img):
+    """Accepted moves per level (L..1 blocks, 0 pixels) of the workload's
+    first image, counted by the oracle phase by phase; the GPU's labels equal
+    the oracle's, so these are the GPU's moves too."""
+    from oracle import ref
+    r = ref.Ref(job.image.width, job.image.height, job.num_superpixels, oracle_levels(job), job.bins_per_channel,
+                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters, job.compactness)
+    r.init(img)
+    moves = {}
+    for level, phase in r.schedule():
+        moves["L%d" % level] = moves.get("L%d" % level, 0) + int(r.run_phase(level, phase))
+    return moves
+
+
 def cpu_sample(jobs, imgs, min_seconds=10.0, max_seconds=30.0):
     """Time the oracle over copies of the workload's images on all host
     cores (one image per thread) until about min_seconds have passed."""
@@ -541,6 +555,7 @@ def run_gpu(args):
         import numpy as np
         line["parity"] = "bit-exact" if all(np.array_equal(gpu_labels[i], ref_labels[i])
                                             for i in range(len(jobs))) else "MISMATCH"
+        line["moves_per_level"] = moves_per_level(jobs[0], imgs[0])
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
