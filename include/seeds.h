@@ -10,7 +10,8 @@
  * (Prop. 2), with incremental histogram updates (Sec. 5.3).
  *
  * Fixed readings (the same ones the bundled CPU oracle follows):
- *  - colour bins from the RGB bytes: bin(v) = floor(v*B/256) per channel,
+ *  - colour bins from the RGB bytes, or from their 8-bit CIE L*a*b* codes
+ *    (color_space = 1, Sec. 6.2): bin(v) = floor(v*B/256) per channel,
  *    j = bR*B*B + bG*B + bB;
  *  - grid: gx = max(1, round(sqrt(K*W/H))), gy = max(1, round(K/gx)),
  *    K_actual = gx*gy; level-l block edges floor(i*W/(gx*2^(L-l+1)));
@@ -22,7 +23,9 @@
  *    best score wins, ties to the smallest label, accept on strict gain;
  *  - pixel score D*c_An(j) + gamma*(G_n + |K_p|) against
  *    D*c_{Ak\p}(j) + gamma*G_k with D = 81 (Prop. 1 + Prop. 2); blocks use
- *    the intersection alone; all compares are exact int64 products.
+ *    the intersection alone; all compares are exact int64 products, except
+ *    in the optional means-based pixel iterations (Sec. 6.3, 6.5), which
+ *    compare fixed-order single-precision distances.
  * Results are deterministic: the same image and parameters give the same
  * labels on any stream, in any batch, at any tuning.
  *
@@ -36,8 +39,9 @@
  *
  * Errors.  Every entry point returns an int status: SEEDS_OK or one of the
  * negative codes below.  No exception crosses the ABI.  Device-side faults
- * that the kernels detect themselves (a grid-barrier wait that ran out, an
- * index outside its buffer) are recorded in the context's error word and
+ * that the kernels detect themselves (a grid-barrier wait that ran out; in
+ * the bounds-checked debug build, an index outside its buffer) are recorded
+ * in the context's error word and
  * reported by seeds_status().
  */
 #ifndef SEEDS_H
