@@ -5,7 +5,8 @@
 //                  superpixel rectangle), build its histogram with
 //                  warp-aggregated shared-memory atomics, write the grid
 //                  labels (Sec. 5.1, Eq. 4)
-//   op_*_phase     judge every unit of one parity phase against the state
+//   op_block_phase_warp / op_block_phase_thread / op_pixel_tile
+//                  judge every unit of one parity phase against the state
 //                  at phase start (Sec. 5.2-5.3: Prop. 1 for blocks, Prop. 1 +
 //                  Prop. 2 for pixels); accepted moves update the other state
 //                  buffer at once (Sec. 5.3, "Updating the Color
@@ -13,9 +14,14 @@
 //   op_catchup     replay the previous phase's moves into the buffer that
 //                  phase read, so both buffers stay one step apart
 //   op_descend     copy block labels to the next finer grid (coarse to fine)
-//   op_output      int32 labels for the caller
+//   op_means_init / op_means_tile
+//                  the optional means-based pixel iterations (Sec. 6.3, 6.5)
+//   op_output      int32 labels for the caller; anytime_output the partition
+//                  of a launch stopped early (Sec. 5.4)
 // Every step ends in a grid barrier that spins with a time limit; a barrier
-// that runs out sets the error word and every block leaves the kernel.
+// that runs out sets the error word and every block leaves the kernel.  Work
+// inside a step is dealt to the CTAs in rounds and taken by their warps as
+// they finish.
 #include <cuda_runtime.h>
 
 #include <algorithm>
