@@ -141,10 +141,17 @@ def hbm_peak():
 
 
 def kernel_source_hash():
+    """sha256 (first 16 hex digits) of the kernel sources with comments and
+    blank lines removed: an edit of comments alone leaves the recorded
+    traffic valid, any change of code invalidates it."""
+    import re
     h = hashlib.sha256()
     for f in ("seeds_kernels.cu", "seeds_device.cuh"):
-        with open(os.path.join(ROOT, "paper_1309_3848_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1309_3848_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("\n".join(line.rstrip() for line in src.splitlines() if line.strip()).encode())
     return h.hexdigest()[:16]
 
 
