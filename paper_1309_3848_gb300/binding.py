@@ -184,6 +184,28 @@ def _stream_handle(stream) -> Optional[int]:
     return stream.cuda_stream
 
 
+def superpixels(images, num_superpixels, block_levels=None, bins_per_channel=5, iters_per_level=2, patch=3,
+                gamma=(1, 1), color_space=0, means_iters=0, compactness=0, stream=None):
+    """SEEDS labels for a list of uint8 (H, W, 3) CUDA images in one
+    persistent launch: a list of int32 (H, W) CUDA tensors, values in
+    [0, K_actual).  `num_superpixels` is one requested K or one per image;
+    block_levels=None takes min(4, the most the grid allows) per image.  The
+    context is built for this call; reuse a SeedsContext to keep it."""
+    import torch
+    n = len(images)
+    ks = list(num_superpixels) if hasattr(num_superpixels, "__len__") else [num_superpixels] * n
+    params = []
+    for img, k in zip(images, ks):
+        H, W = int(img.shape[0]), int(img.shape[1])
+        L = min(4, feasible_levels(W, H, k)) if block_levels is None else block_levels
+        params.append(make_params(W, H, k, L, bins_per_channel, iters_per_level, patch, gamma, color_space,
+                                  means_iters, compactness))
+    ctx = SeedsContext(params)
+    outs = [torch.empty((int(t.shape[0]), int(t.shape[1])), dtype=torch.int32, device=t.device) for t in images]
+    ctx.run(images, outs, stream)
+    return outs
+
+
 # --------------------------------------------------------------------------
 # autotune cache: tunings in a JSON file keyed by the batch's shapes
 # --------------------------------------------------------------------------

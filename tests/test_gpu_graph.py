@@ -48,3 +48,14 @@ def test_batch_run_replays_from_a_cuda_graph(torch, binding):
         for i, (o, w) in enumerate(zip(outs, gc.oracle_many(js, imgs))):
             msg = gc.first_mismatch(o.cpu().numpy(), w)
             assert msg is None, "replay with seed shift %d, image %d: %s" % (shift, i, msg)
+
+
+def test_superpixels_helper(torch, binding):
+    jobs = [synth.plain_481()[0], synth.JobSpec(synth.ImageSpec(160, 120, seed=9, cells=10, sigma=8.0), 80, 5, 4, 2,
+                                                clamp_levels=True)]
+    imgs = gc.make_images(jobs)
+    d = [torch.from_numpy(im).cuda() for im in imgs]
+    outs = binding.superpixels(d, [j.num_superpixels for j in jobs], iters_per_level=2)
+    torch.cuda.synchronize()
+    for o, w in zip(outs, gc.oracle_many(jobs, imgs)):
+        assert gc.first_mismatch(o.cpu().numpy(), w) is None
