@@ -189,6 +189,15 @@ def oracle_run(job, img):
     return r.run(img)
 
 
+def label_quality(job, labels):
+    """Sec. 6.1 metrics of the GPU labels of the workload's first image
+    against its Voronoi cells (the synthetic ground truth)."""
+    from paper_1309_3848_gb300 import metrics, synth
+    truth = synth.voronoi_truth(job.image)
+    return {"ue": metrics.ue(labels, truth), "cue": metrics.cue(labels, truth), "br": metrics.br(labels, truth),
+            "asa": metrics.asa(labels, truth), "truth": "Voronoi cells of the synthetic image"}
+
+
 def moves_per_level(job, img):
     """Accepted moves per level (L..1 blocks, 0 pixels) of the workload's
     first image, counted by the oracle phase by phase; the GPU's labels equal
@@ -563,6 +572,7 @@ def run_gpu(args):
         line["parity"] = "bit-exact" if all(np.array_equal(gpu_labels[i], ref_labels[i])
                                             for i in range(len(jobs))) else "MISMATCH"
         line["moves_per_level"] = moves_per_level(jobs[0], imgs[0])
+        line["quality"] = label_quality(jobs[0], gpu_labels[0])
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

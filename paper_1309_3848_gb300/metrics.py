@@ -1,7 +1,8 @@
-"""Superpixel quality metrics of Sec. 6.1 against a known ground truth
-(test helper, plain numpy): undersegmentation error (UE, Eq. of Sec. 6.1.1),
-corrected undersegmentation error (CUE), boundary recall (BR, tolerance
-epsilon = 2 pixels) and achievable segmentation accuracy (ASA)."""
+"""Superpixel quality metrics of Sec. 6.1 against a ground-truth
+segmentation (host numpy): undersegmentation error (UE, Sec. 6.1.1),
+corrected undersegmentation error (CUE, Sec. 6.1.2), boundary recall (BR,
+tolerance epsilon = 2 pixels, Sec. 6.1.3) and achievable segmentation
+accuracy (ASA, Sec. 6.1.4).  Labels and truth are integer H x W arrays."""
 import numpy as np
 from scipy import ndimage
 

@@ -4,8 +4,8 @@ parallel parity schedule (readings R5, R6) improves the grid as much as the
 paper's sequential order does (the oracle's sequential mode, R14)."""
 import pytest
 
-import quality
 from oracle import ref
+from paper_1309_3848_gb300 import metrics as quality
 from paper_1309_3848_gb300 import synth
 
 
