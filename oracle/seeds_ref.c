@@ -75,6 +75,12 @@
  *       IEEE single precision in the order written in means_distance (a
  *       mean is its sum times the reciprocal of the size), so that any
  *       implementation doing the same operations decides the same way.
+ *   R18 edge snapping (the edge prior of Sec. 6.4), optional: a boundary
+ *       between 4-neighbour pixels lies on a colour edge when the L1
+ *       distance of their colour codes (R1 bytes or R16 codes) is at least
+ *       edge_threshold; a pixel with a 4-neighbour of another label across
+ *       such an edge is snapped and no longer moves (pixel phases and R17
+ *       means phases; blocks are not affected).
  *   R14 sequential mode (quality reference only): per iteration the units
  *       are visited in a random permutation (SplitMix64 + Fisher-Yates),
  *       each boundary unit proposes one uniformly drawn candidate, and an
@@ -101,6 +107,7 @@ typedef struct {
     int32_t color_space; /* 0 = RGB bytes (R1), 1 = CIE L*a*b* (R16) */
     int32_t means_iters; /* R17: means-based pixel iterations after the histogram ones */
     int32_t compactness; /* R17: SLIC's m, weight of the spatial distance */
+    int32_t edge_threshold; /* R18: colour-edge strength that snaps a pixel boundary (0 = off) */
 } ref_params;
 
 typedef struct {
@@ -151,6 +158,7 @@ int ref_check_params(const ref_params *p)
     if (p->color_space != 0 && p->color_space != 1) return REF_EINVAL;
     if (p->means_iters < 0 || p->means_iters > 1000) return REF_EINVAL;
     if (p->compactness < 0 || p->compactness > 1024) return REF_EINVAL;
+    if (p->edge_threshold < 0 || p->edge_threshold > 765) return REF_EINVAL;
     return REF_OK;
 }
 
@@ -584,6 +592,8 @@ static int pixel_beats_stay(const ref_state *st, int x, int y, int k, int n, int
  *   f(n)    = D * A_n[j]/|A_n|           + gamma * (G_n + |K_p|)
  *   f_stay  = D * (A_k[j]-1)/(|A_k|-1)   + gamma * G_k
  * compared exactly after multiplying by gamma_den and the positive sizes. */
+static int edge_frozen(const ref_state *st, int x, int y, int k);
+
 static int decide_pixel(ref_state *st, int x, int y)
 {
     int k = st->lab[(int64_t)y * st->W + x];
@@ -591,6 +601,7 @@ static int decide_pixel(ref_state *st, int x, int y)
     int nc = candidates(st, 0, x, y, k, cand);
     if (nc == 0) return -1;
     if (!leaving_keeps_connected(st, 0, x, y, k)) return -1;
+    if (edge_frozen(st, x, y, k)) return -1;
     const int use_g = st->p.patch == 3;
     const i128 D = 81, gn = st->p.gamma_num, gd = st->p.gamma_den;
     int j = st->bin[(int64_t)y * st->W + x];
@@ -626,6 +637,36 @@ static void apply_move(ref_state *st, int level, int bx, int by, int k, int n)
             st->size[k] -= 1;
             st->size[n] += 1;
         }
+}
+
+/* ------------------------------------------------------------------ */
+/* edge snapping (R18)                                                  */
+/* ------------------------------------------------------------------ */
+
+/* The L1 distance of the colour codes of pixels i and j. */
+static int code_l1(const ref_state *st, int64_t i, int64_t j)
+{
+    int d = 0;
+    for (int q = 0; q < 3; ++q) d += abs((int)st->code[3 * i + q] - (int)st->code[3 * j + q]);
+    return d;
+}
+
+/* A pixel sits on a snapped boundary when one of its 4-neighbours has
+ * another label and the two pixels' colour codes differ by at least the
+ * edge threshold: such a pixel does not move. */
+static int edge_frozen(const ref_state *st, int x, int y, int k)
+{
+    int tau = st->p.edge_threshold;
+    if (tau <= 0) return 0;
+    static const int DX[4] = {-1, 1, 0, 0}, DY[4] = {0, 0, -1, 1};
+    int64_t i = (int64_t)y * st->W + x;
+    for (int d = 0; d < 4; ++d) {
+        int qx = x + DX[d], qy = y + DY[d];
+        if (qx < 0 || qy < 0 || qx >= st->W || qy >= st->H) continue;
+        int64_t j = (int64_t)qy * st->W + qx;
+        if (st->lab[j] != k && code_l1(st, i, j) >= tau) return 1;
+    }
+    return 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -679,6 +720,7 @@ static int decide_pixel_means(ref_state *st, int x, int y)
     int nc = candidates(st, 0, x, y, k, cand);
     if (nc == 0) return -1;
     if (!leaving_keeps_connected(st, 0, x, y, k)) return -1;
+    if (edge_frozen(st, x, y, k)) return -1;
     int best = -1;
     float db = 0.0f;
     for (int c = 0; c < nc; ++c) {

@@ -33,6 +33,11 @@ MUTANTS = {
     "means ties go to the largest label": ("if (best < 0 || d < db) {", "if (best < 0 || d <= db) {"),
     "means sums the bins, not the colour codes": ("m[0] += st->code[3 * i];", "m[0] += st->bin[i];"),
     "means centroid row from x": ("m[4] += y;", "m[4] += x;"),
+    "edge snapping ignores whether the neighbour's label differs": ("if (st->lab[j] != k && code_l1(st, i, j) >= tau)",
+                                                                     "if (code_l1(st, i, j) >= tau)"),
+    "edge threshold taken as strict": ("code_l1(st, i, j) >= tau) return 1;", "code_l1(st, i, j) > tau) return 1;"),
+    "edge snapping skipped in the means phases": ("    if (edge_frozen(st, x, y, k)) return -1;\n    int best = -1;\n    float db",
+                                                  "    int best = -1;\n    float db"),
     "anytime prefix skips the descent op": ("        if (level > 0) ++done; /* the descent", "        /* the descent"),
     "anytime prefix runs one phase too many": ("if (done >= nops) return total;", "if (done > nops) return total;"),
 }

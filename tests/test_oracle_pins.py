@@ -772,3 +772,79 @@ def test_means_equal_candidates_go_to_the_smallest_label():
     assert r.K == 3
     r.set_labels(labels)
     assert r.decide_means(4, 1) == 1
+
+
+# --------------------------------------------------------------------------
+# edge snapping (the edge prior of Sec. 6.4, reading R18)
+# --------------------------------------------------------------------------
+
+def frozen_mask(labels, codes, tau):
+    """Pixels with a 4-neighbour of another label whose colour codes differ
+    by at least tau in L1 (restated with numpy)."""
+    c = codes.astype(np.int64)
+    H, W = labels.shape
+    f = np.zeros((H, W), bool)
+    dh = np.abs(c[:, 1:] - c[:, :-1]).sum(axis=2) >= tau
+    eh = dh & (labels[:, 1:] != labels[:, :-1])
+    f[:, 1:] |= eh
+    f[:, :-1] |= eh
+    dv = np.abs(c[1:, :] - c[:-1, :]).sum(axis=2) >= tau
+    ev = dv & (labels[1:, :] != labels[:-1, :])
+    f[1:, :] |= ev
+    f[:-1, :] |= ev
+    return f
+
+
+@pytest.mark.parametrize("seed,tau,color", [(1, 250, 0), (2, 300, 0), (3, 120, 1), (4, 200, 1)])
+def test_edge_snapped_decisions_are_the_plain_ones_unless_frozen(seed, tau, color):
+    W, H, K = 30, 22, 7
+    img = rgb_noise(W, H, 200 + seed, 30, 230)
+    plain = ref.Ref(W, H, K, 1, 4, 1, color_space=color, means_iters=1, compactness=3)
+    plain.run_ops(img, 1 + 2 * 5)  # a state after some block and pixel phases
+    labels = plain.labels()
+    snap = ref.Ref(W, H, K, 1, 4, 1, color_space=color, means_iters=1, compactness=3, edge_threshold=tau)
+    snap.init(img)
+    snap.set_labels(labels)
+    codes = plain.lab8(img) if color else img
+    frozen = frozen_mask(labels, codes, tau)
+    n_frozen = n_moving = 0
+    for y in range(H):
+        for x in range(W):
+            want = plain.decide(0, x, y)
+            got = snap.decide(0, x, y)
+            want_m, got_m = plain.decide_means(x, y), snap.decide_means(x, y)
+            if frozen[y, x]:
+                assert got == -1 and got_m == -1, (x, y)
+                n_frozen += want >= 0
+            else:
+                assert got == want and got_m == want_m, (x, y)
+                n_moving += want >= 0
+    assert n_frozen > 0 and n_moving > 0, "the case must hold both kinds"
+
+
+def test_frozen_pixels_keep_their_labels_through_every_pixel_phase():
+    W, H = 36, 28
+    img = rgb_noise(W, H, 210, 0, 256)
+    tau = 200
+    r = ref.Ref(W, H, 8, 2, 4, 2, edge_threshold=tau)
+    r.run_ops(img, 1 + 2 * (8 + 1))  # grid and both block levels
+    held = 0
+    for _ in range(2):
+        for phase in range(4):
+            before = r.labels()
+            frozen = frozen_mask(before, img, tau)
+            r.run_phase(0, phase)
+            after = r.labels()
+            assert np.array_equal(after[frozen], before[frozen])
+            held += int(frozen.sum())
+    assert held > 0
+
+
+def test_threshold_above_every_edge_changes_nothing():
+    W, H = 33, 25
+    img = rgb_noise(W, H, 220, 60, 200)  # no two pixels differ by 3 * 140 = 420 or more
+    a = ref.Ref(W, H, 6, 1, 4, 2).run(img)
+    b = ref.Ref(W, H, 6, 1, 4, 2, edge_threshold=421).run(img)
+    c = ref.Ref(W, H, 6, 1, 4, 2, edge_threshold=30).run(img)
+    assert np.array_equal(a, b)
+    assert not np.array_equal(a, c)
