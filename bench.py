@@ -185,7 +185,8 @@ def oracle_levels(job):
 def oracle_run(job, img):
     from oracle import ref
     r = ref.Ref(job.image.width, job.image.height, job.num_superpixels, oracle_levels(job), job.bins_per_channel,
-                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters, job.compactness)
+                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters, job.compactness,
+                job.edge_threshold)
     return r.run(img)
 
 
@@ -204,7 +205,8 @@ def moves_per_level(job, img):
     the oracle's, so these are the GPU's moves too."""
     from oracle import ref
     r = ref.Ref(job.image.width, job.image.height, job.num_superpixels, oracle_levels(job), job.bins_per_channel,
-                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters, job.compactness)
+                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters, job.compactness,
+                job.edge_threshold)
     r.init(img)
     moves = {}
     for level, phase in r.schedule():
@@ -288,7 +290,7 @@ def gpu_params(binding, job):
         L = min(L, binding.feasible_levels(job.image.width, job.image.height, job.num_superpixels))
     return binding.make_params(job.image.width, job.image.height, job.num_superpixels, L, job.bins_per_channel,
                                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters,
-                               job.compactness)
+                               job.compactness, job.edge_threshold)
 
 
 def timed_steps(torch, fn, steps, flush, kernel_ms=None):
@@ -354,8 +356,8 @@ def batched_vs_plain(torch, binding, flush, steps=5):
 def next_rows(torch, binding, flush, jobs, imgs, rgb_value, steps=5):
     """The widened rows on the bench workload: LAB colour bins (Sec. 6.2) and
     two means-based pixel iterations after the histogram ones (Sec. 6.3,
-    6.5) in Mpixel/s beside the plain run, and anytime termination (Sec.
-    5.4) -- the
+    6.5), edge snapping at a colour-code threshold of 40 (Sec. 6.4), in
+    Mpixel/s beside the plain run, and anytime termination (Sec. 5.4) -- the
     steps a launch reaches within device-time budgets of a quarter, half and
     three quarters of a full run, and the time the stopped call takes."""
     import dataclasses
@@ -373,6 +375,7 @@ def next_rows(torch, binding, flush, jobs, imgs, rgb_value, steps=5):
 
     lab_value = variant(color_space=1)
     means_value = variant(means_iters=2, compactness=10)
+    edge_value = variant(edge_threshold=40)
 
     ctx = binding.SeedsContext([gpu_params(binding, j) for j in jobs])
     for _ in range(3):
@@ -389,6 +392,7 @@ def next_rows(torch, binding, flush, jobs, imgs, rgb_value, steps=5):
     return {"lab": {"mpix_s": lab_value, "over_rgb": lab_value / rgb_value},
             "means_post": {"means_iters": 2, "compactness": 10, "mpix_s": means_value,
                            "over_histogram_only": means_value / rgb_value},
+            "edge_snap": {"edge_threshold": 40, "mpix_s": edge_value, "over_plain": edge_value / rgb_value},
             "anytime": {"full_steps": full_steps, "full_ms": full_ms, "budgets": budgets}}
 
 

@@ -94,7 +94,13 @@ typedef struct seeds_ctx seeds_ctx;
  *                      superpixel's mean (with the pixel in it), ties to the
  *                      smallest label, IEEE single precision without fused
  *                      operations (a mean is its sum times 1/size)
- *   compactness        m in 0..1024 (0 = colour only) */
+ *   compactness        m in 0..1024 (0 = colour only)
+ *   edge_threshold     0..765, 0 = off: edge snapping (the edge prior of
+ *                      Sec. 6.4).  Two 4-neighbour pixels are across a colour
+ *                      edge when the L1 distance of their colour codes (the
+ *                      bytes the bins come from) is at least this; a pixel
+ *                      with a 4-neighbour of another label across an edge
+ *                      no longer moves (pixel and means phases) */
 typedef struct {
     int32_t width, height;
     int32_t num_superpixels;
@@ -106,6 +112,7 @@ typedef struct {
     int32_t color_space;
     int32_t means_iters;
     int32_t compactness;
+    int32_t edge_threshold;
 } seeds_params;
 
 /* Result-invariant launch knobs (any value gives identical labels).
@@ -128,7 +135,8 @@ typedef struct {
 
 /* Fill p with the paper's defaults for a W x H image and K superpixels:
  * 4 block levels (clamped to what the grid allows), 5 bins per channel,
- * 2 iterations, 3x3 patch, gamma = 1.  Host only. */
+ * 2 iterations, 3x3 patch, gamma = 1; RGB, no means iterations, no edge
+ * snapping.  Host only. */
 int seeds_params_default(seeds_params *p, int32_t width, int32_t height, int32_t num_superpixels);
 
 /* Largest block_levels the grid geometry of *p allows (>= 0), ignoring

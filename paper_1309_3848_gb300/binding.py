@@ -57,7 +57,7 @@ class seeds_params(ctypes.Structure):
                 ("block_levels", ctypes.c_int32), ("bins_per_channel", ctypes.c_int32),
                 ("iters_per_level", ctypes.c_int32), ("patch", ctypes.c_int32), ("gamma_num", ctypes.c_int32),
                 ("gamma_den", ctypes.c_int32), ("color_space", ctypes.c_int32), ("means_iters", ctypes.c_int32),
-                ("compactness", ctypes.c_int32)]
+                ("compactness", ctypes.c_int32), ("edge_threshold", ctypes.c_int32)]
 
 
 class seeds_server_config(ctypes.Structure):
@@ -142,13 +142,13 @@ def check(code: int, what: str) -> int:
 
 
 def make_params(width, height, num_superpixels, block_levels, bins_per_channel, iters_per_level, patch=3,
-                gamma=(1, 1), color_space=0, means_iters=0, compactness=0) -> seeds_params:
+                gamma=(1, 1), color_space=0, means_iters=0, compactness=0, edge_threshold=0) -> seeds_params:
     """color_space: 0 = RGB bytes, 1 = 8-bit CIE L*a*b* codes (Sec. 6.2);
     means_iters / compactness: means-based pixel iterations with SLIC's m
-    (Sec. 6.3, 6.5)."""
+    (Sec. 6.3, 6.5); edge_threshold: edge snapping (Sec. 6.4), 0 = off."""
     return seeds_params(int(width), int(height), int(num_superpixels), int(block_levels), int(bins_per_channel),
                         int(iters_per_level), int(patch), int(gamma[0]), int(gamma[1]), int(color_space),
-                        int(means_iters), int(compactness))
+                        int(means_iters), int(compactness), int(edge_threshold))
 
 
 def feasible_levels(width, height, num_superpixels) -> int:
@@ -185,7 +185,7 @@ def _stream_handle(stream) -> Optional[int]:
 
 
 def superpixels(images, num_superpixels, block_levels=None, bins_per_channel=5, iters_per_level=2, patch=3,
-                gamma=(1, 1), color_space=0, means_iters=0, compactness=0, stream=None):
+                gamma=(1, 1), color_space=0, means_iters=0, compactness=0, edge_threshold=0, stream=None):
     """SEEDS labels for a list of uint8 (H, W, 3) CUDA images in one
     persistent launch: a list of int32 (H, W) CUDA tensors, values in
     [0, K_actual).  `num_superpixels` is one requested K or one per image;
@@ -199,7 +199,7 @@ def superpixels(images, num_superpixels, block_levels=None, bins_per_channel=5, 
         H, W = int(img.shape[0]), int(img.shape[1])
         L = min(4, feasible_levels(W, H, k)) if block_levels is None else block_levels
         params.append(make_params(W, H, k, L, bins_per_channel, iters_per_level, patch, gamma, color_space,
-                                  means_iters, compactness))
+                                  means_iters, compactness, edge_threshold))
     ctx = SeedsContext(params)
     outs = [torch.empty((int(t.shape[0]), int(t.shape[1])), dtype=torch.int32, device=t.device) for t in images]
     ctx.run(images, outs, stream)

@@ -45,6 +45,7 @@ struct DevImage {
     int32_t color;        // 0: RGB bytes, 1: 8-bit CIE L*a*b* codes (Sec. 6.2)
     int32_t means_iters;  // means-based pixel iterations after the histogram ones
     float means_w;        // (m/S)^2 = m^2 K / N, the spatial weight of SLIC's distance
+    int32_t edge_tau;     // edge snapping threshold (Sec. 6.4), 0 = off
     int32_t nbx[kMaxLevels + 1], nby[kMaxLevels + 1];  // level 0 = W, H
     int32_t maxarea[kMaxLevels + 1];                   // largest block of a level
     const int32_t *xe[kMaxLevels + 1];                 // block column edges, level >= 1
@@ -56,6 +57,7 @@ struct DevImage {
     int32_t *size[2];                   // |A_k|, 2 buffers
     uint32_t *dec[2];                   // per unit of a phase: (k << 16 | n) or kNoMove
     unsigned long long *msum[2];        // K x 5: sums of the 3 colour codes, of x, of y (means iterations)
+    uint8_t *edges;                     // per pixel, edge snapping: bit 0 across to the right, bit 1 down
     int32_t units_cap;                  // entries of each dec buffer
     int32_t *err;                       // the launch's error word (debug builds report bounds trips here)
     // per call

@@ -31,7 +31,7 @@ struct ImageHost {
     int units_cap = 0;
     // byte offsets inside the context's pool
     size_t off_bins = 0, off_lab[kMaxLevels + 1][2] = {}, off_xe[kMaxLevels + 1] = {}, off_ye[kMaxLevels + 1] = {};
-    size_t off_hist[2] = {}, off_size[2] = {}, off_dec[2] = {}, off_msum[2] = {}, bytes = 0;
+    size_t off_hist[2] = {}, off_size[2] = {}, off_dec[2] = {}, off_msum[2] = {}, off_edges = 0, bytes = 0;
 };
 
 constexpr size_t kAlign = 256;
@@ -62,6 +62,7 @@ inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t 
     if (p->color_space != 0 && p->color_space != 1) return SEEDS_ERR_INVALID;
     if (p->means_iters < 0 || p->means_iters > 1000) return SEEDS_ERR_INVALID;
     if (p->compactness < 0 || p->compactness > 1024) return SEEDS_ERR_INVALID;
+    if (p->edge_threshold < 0 || p->edge_threshold > 765) return SEEDS_ERR_INVALID;
     if (p->gamma_num < 0 || p->gamma_num > 1024 || p->gamma_den < 1 || p->gamma_den > 1024) return SEEDS_ERR_INVALID;
     const double Kd = p->num_superpixels, Wd = p->width, Hd = p->height;
     long long gx = std::llround(std::sqrt(Kd * Wd / Hd));
@@ -147,6 +148,8 @@ inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t 
         h.off_msum[q] = off;  // per superpixel sums for the means iterations
         if (p->means_iters > 0) off = align_up(off + (size_t)h.K * 5 * 8);
     }
+    h.off_edges = off;  // the edge-snapping mask
+    if (p->edge_threshold > 0) off = align_up(off + (size_t)N);
     h.bytes = off;
     return SEEDS_OK;
 }
@@ -173,6 +176,8 @@ inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const se
     d.means_iters = h.p.means_iters;
     // SLIC's (m/S)^2 with S^2 = N/K
     d.means_w = (float)((int64_t)h.p.compactness * h.p.compactness * h.K) / (float)h.N;
+    d.edge_tau = h.p.edge_threshold;
+    d.edges = h.p.edge_threshold > 0 ? base + h.off_edges : nullptr;
     d.gnum = h.p.gamma_num;
     d.gden = h.p.gamma_den;
     d.bins16 = h.nbins > 256;

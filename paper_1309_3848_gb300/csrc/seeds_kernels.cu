@@ -384,6 +384,33 @@ __device__ __forceinline__ void lab8(int r, int g, int b, int &c0, int &c1, int 
 // op_init: one warp per initial superpixel rectangle
 // ---------------------------------------------------------------------------
 
+// Edge snapping (Sec. 6.4): the edge mask of the rectangle [x0,x1) x
+// [y0,y1), a lane per column.  Bit 0 of a pixel is set when it and its right
+// neighbour, bit 1 when it and the pixel below, have colour codes at least
+// the threshold apart (L1 over the 3 codes).
+__device__ __noinline__ void edge_mask_rect(const DevImage &im, int x0, int x1, int y0, int y1, int lane)
+{
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0 + lane; x < x1; x += 32) {
+            int c[3][3];
+            for (int d = 0; d < 3; ++d) {  // the pixel, its right neighbour, the pixel below
+                const int qx = min(x + (d == 1), im.W - 1), qy = min(y + (d == 2), im.H - 1);
+                const uint8_t *px = im.rgb + (int64_t)qy * im.stride + 3 * (int64_t)qx;
+                c[d][0] = px[0];
+                c[d][1] = px[1];
+                c[d][2] = px[2];
+                if (im.color) lab8(c[d][0], c[d][1], c[d][2], c[d][0], c[d][1], c[d][2]);
+            }
+            uint8_t m = 0;
+            for (int d = 1; d < 3; ++d) {
+                const bool inside = d == 1 ? x + 1 < im.W : y + 1 < im.H;
+                const int l1 = abs(c[d][0] - c[0][0]) + abs(c[d][1] - c[0][1]) + abs(c[d][2] - c[0][2]);
+                if (inside && l1 >= im.edge_tau) m |= (uint8_t)(1u << (d - 1));
+            }
+            im.edges[SEEDS_IDX(im, (int64_t)y * im.W + x, (int64_t)im.W * im.H)] = m;
+        }
+}
+
 __device__ void op_init(const DevImage &im, int k, int lane, int32_t *wsh)
 {
     if (k >= im.K) return;
@@ -424,6 +451,7 @@ __device__ void op_init(const DevImage &im, int k, int lane, int32_t *wsh)
             if (j[q] >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hsh[j[q]], __popc(peers));
         }
     }
+    if (im.edges) edge_mask_rect(im, x0, x1, y0, y1, lane);
     __syncwarp();
     for (int j = lane; j < im.nbins; j += 32) {
         const int v = hsh[j];
@@ -560,6 +588,16 @@ __device__ __noinline__ uint32_t means_pixel(const DevImage &im, int b, int nb, 
 // pixel phase: warp tiles
 // ---------------------------------------------------------------------------
 
+// Edge snapping (Sec. 6.4): a unit at pixel p whose 4-neighbours (labels
+// lf, rt, up, dn of the phase-start state, kNoLabel outside the image) hold
+// another label across an edge of the image does not move.
+__device__ __noinline__ bool edge_frozen(const DevImage &im, int p, int k, int lf, int rt, int up, int dn)
+{
+    const uint8_t *e = im.edges;
+    return (lf != k && lf != kNoLabel && (e[p - 1] & 1)) || (rt != k && rt != kNoLabel && (e[p] & 1)) ||
+           (up != k && up != kNoLabel && (e[p - im.W] & 2)) || (dn != k && dn != kNoLabel && (e[p] & 2));
+}
+
 // Replay one move k -> n of pixel p into buffer `buf`.
 __device__ __forceinline__ void replay_pixel(const DevImage &im, int buf, int p, uint32_t d)
 {
@@ -663,7 +701,8 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
     }
     __syncwarp();
 
-    // pass 2: judge the boundary units, every lane busy
+    // pass 2: judge the boundary units, every lane busy (a unit frozen by
+    // edge snapping stays)
     const int32_t *hist = im.hist[b], *size = im.size[b];
     const int64_t gd81 = 81ll * im.gden, gn = im.gnum;
     const bool use_g = im.patch != 0 && im.gnum != 0;
@@ -673,6 +712,10 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         const int x = 2 * uxe + px, y = 2 * uy + py, p = y * W + x;
         const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * l + 2);  // the unit's cell in the tile
         const int k = T[0];
+        if (im.edges && edge_frozen(im, p, k, T[-1], T[1], T[-kTileW], T[kTileW])) {
+            im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = kNoMove;
+            continue;
+        }
         int cand[4];
         // pass 1 found that it may leave
         const int nc = sorted_candidates(T[-1], T[1], T[-kTileW], T[kTileW], k, cand);
@@ -1515,6 +1558,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     if (p->color_space != 0 && p->color_space != 1) return SEEDS_ERR_INVALID;
     if (p->means_iters < 0 || p->means_iters > 1000 || p->compactness < 0 || p->compactness > 1024)
         return SEEDS_ERR_INVALID;
+    if (p->edge_threshold < 0 || p->edge_threshold > 765) return SEEDS_ERR_INVALID;
     const double Kd = p->num_superpixels, Wd = p->width, Hd = p->height;
     long long gx = std::llround(std::sqrt(Kd * Wd / Hd));
     if (gx < 1) gx = 1;
@@ -1544,6 +1588,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     if (d.color == 1 && upload_lab_tables() != cudaSuccess) return SEEDS_ERR_CUDA;
     d.means_iters = p->means_iters;
     d.means_w = (float)((int64_t)p->compactness * p->compactness * K) / (float)N;
+    d.edge_tau = p->edge_threshold;
     d.bins16 = nbins > 256;
     d.hist_jmajor = 0;
     d.hist_sk = nbins;
@@ -1605,6 +1650,8 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
         o_msum[q] = off;
         if (p->means_iters > 0) off = sal(off + 40 * (size_t)K);
     }
+    const size_t o_edges = off;
+    if (p->edge_threshold > 0) off = sal(off + (size_t)N);
     if (off > (size_t)SEEDS_STATIC_SCRATCH_BYTES) return SEEDS_ERR_STATIC_SIZE;
 
     // ---- the scratch's device address on the current device
@@ -1626,6 +1673,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
         d.dec[q] = (uint32_t *)(base + o_dec[q]);
         d.msum[q] = p->means_iters > 0 ? (unsigned long long *)(base + o_msum[q]) : nullptr;
     }
+    d.edges = p->edge_threshold > 0 ? base + o_edges : nullptr;
     d.units_cap = units_cap;
     d.err = (int32_t *)(base + o_err);
     d.rgb = d_rgb;

@@ -383,6 +383,10 @@ int seeds_params_default(seeds_params *p, int32_t width, int32_t height, int32_t
     p->patch = 3;
     p->gamma_num = 1;
     p->gamma_den = 1;
+    p->color_space = 0;
+    p->means_iters = 0;
+    p->compactness = 0;
+    p->edge_threshold = 0;
     int32_t lmax = 0;
     int rc = seeds_feasible_levels(p, &lmax);
     if (rc) return rc;

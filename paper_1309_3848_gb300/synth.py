@@ -53,6 +53,7 @@ class JobSpec:
     color_space: int = 0  # 0 = RGB bytes, 1 = CIE L*a*b* codes
     means_iters: int = 0  # means-based pixel iterations after the histogram ones
     compactness: int = 0  # SLIC's m in those iterations
+    edge_threshold: int = 0  # edge snapping, 0 = off
 
     @property
     def pixels(self) -> int:

@@ -30,7 +30,7 @@ def params_for(binding, job):
     L = gpu_levels(binding, job)
     return binding.make_params(job.image.width, job.image.height, job.num_superpixels, L, job.bins_per_channel,
                                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters,
-                               job.compactness)
+                               job.compactness, job.edge_threshold)
 
 
 def make_images(jobs):
@@ -40,7 +40,8 @@ def make_images(jobs):
 
 def oracle_run(job, img):
     r = ref.Ref(job.image.width, job.image.height, job.num_superpixels, oracle_levels(job), job.bins_per_channel,
-                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters, job.compactness)
+                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters, job.compactness,
+                job.edge_threshold)
     return r.run(img)
 
 

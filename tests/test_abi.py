@@ -72,7 +72,9 @@ def test_invalid_parameters(binding):
            binding.make_params(10, 10, 4, 13, 5, 1), binding.make_params(10, 10, 4, 0, 5, 1, color_space=2),
            binding.make_params(10, 10, 4, 0, 5, 1, color_space=-1), binding.make_params(10, 10, 4, 0, 5, 1, means_iters=-1),
            binding.make_params(10, 10, 4, 0, 5, 1, means_iters=1001),
-           binding.make_params(10, 10, 4, 0, 5, 1, means_iters=1, compactness=1025)]
+           binding.make_params(10, 10, 4, 0, 5, 1, means_iters=1, compactness=1025),
+           binding.make_params(10, 10, 4, 0, 5, 1, edge_threshold=-1),
+           binding.make_params(10, 10, 4, 0, 5, 1, edge_threshold=766)]
     for p in bad:
         assert binding.check_params(p)[0] == binding.SEEDS_ERR_INVALID
     assert binding.check_params(binding.make_params(16, 16, 4, 4, 5, 1))[0] == binding.SEEDS_ERR_GEOMETRY
@@ -82,6 +84,9 @@ def test_invalid_parameters(binding):
 
 
 def test_defaults_follow_the_paper(binding):
+    p = binding.make_params(1, 1, 1, 0, 1, 1, 0, (0, 1), 1, 7, 9, 11)  # every optional field set
+    assert binding.lib.seeds_params_default(ctypes.byref(p), 481, 321, 200) == 0
+    assert (p.color_space, p.means_iters, p.compactness, p.edge_threshold) == (0, 0, 0, 0)
     p = binding.seeds_params()
     assert binding.lib.seeds_params_default(ctypes.byref(p), 481, 321, 200) == 0
     assert (p.bins_per_channel, p.patch, p.gamma_num, p.gamma_den) == (5, 3, 1, 1)

@@ -33,7 +33,7 @@ def binding(torch):
 def oracle_ref(job):
     return ref.Ref(job.image.width, job.image.height, job.num_superpixels, gc.oracle_levels(job),
                    job.bins_per_channel, job.iters_per_level, job.patch, job.gamma, job.color_space,
-                   job.means_iters, job.compactness)
+                   job.means_iters, job.compactness, job.edge_threshold)
 
 
 def oracle_prefixes(job, img, counts):
