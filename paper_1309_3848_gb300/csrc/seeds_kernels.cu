@@ -307,6 +307,7 @@ __device__ int block_sparse_hist(const DevImage &im, int level, int bx, int by, 
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
+            if (base + 32 * q >= m) break;  // m is the warp's: the rest of the round is empty
             const unsigned peers = __match_any_sync(0xffffffffu, j[q]);
             if (j[q] >= 0 && lane == __ffs(peers) - 1) {
                 const int old = atomicAdd(&hsh[j[q]], __popc(peers));
@@ -1003,7 +1004,8 @@ __device__ void op_block_phase_warp(const DevImage &im, int o, int level, int ph
         S_st += min((int64_t)(hist[hidx(im, k, j)] - Lj) * m, (int64_t)Lj * s_rest);
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) S[c] = warp_sum64(S[c]);
+    for (int c = 0; c < 4; ++c)
+        if (cand[c] != kNoLabel) S[c] = warp_sum64(S[c]);  // the same slots are empty on every lane
     S_st = warp_sum64(S_st);
     // every lane holds the same sums, so every lane takes the same decision;
     // ascending candidates, strictly better replaces: ties to the smallest label
@@ -1097,17 +1099,26 @@ __device__ void op_descend(const DevImage &im, int o, int level, int units, int 
         const int W = im.W, cw = (W + 3) >> 2;
         const int y = c / cw, x0 = 4 * (c - y * cw);
         const int n1x = im.nbx[1], n1y = im.nby[1];
-        // block b holds x iff floor(b*W/n) <= x < floor((b+1)*W/n)
+        // block b holds x iff floor(b*W/n) <= x < floor((b+1)*W/n); the
+        // next pixels step into the next block when (bx+1)*W < (x+1)*n
         const int by = (int)(((int64_t)(y + 1) * n1y - 1) / im.H);
+        int bx = (int)(((int64_t)(x0 + 1) * n1x - 1) / W);
+        const uint16_t *row = src + by * n1x;
+        uint16_t v[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int x = x0 + q;
-            if (x < W) {
-                const int bx = (int)(((int64_t)(x + 1) * n1x - 1) / W);
-                const uint16_t v = src[by * n1x + bx];
-                im.lab[0][0][y * W + x] = v;
-                im.lab[0][1][y * W + x] = v;
-            }
+            if (q > 0 && (int64_t)(bx + 1) * W < (int64_t)(x0 + q + 1) * n1x) ++bx;
+            v[q] = row[min(bx, n1x - 1)];
+        }
+        const int64_t p0 = (int64_t)y * W + x0;
+        if ((W & 3) == 0) {  // 4 labels in one 8-byte store per buffer
+            const ushort4 w4 = make_ushort4(v[0], v[1], v[2], v[3]);
+            *(ushort4 *)(im.lab[0][0] + p0) = w4;
+            *(ushort4 *)(im.lab[0][1] + p0) = w4;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (x0 + q < W) im.lab[0][0][p0 + q] = im.lab[0][1][p0 + q] = v[q];
         }
     }
 }
@@ -1117,8 +1128,13 @@ __device__ void op_output(const DevImage &im, int o, int units, int c)
     if (c >= units) return;
     const int W = im.W, cw = (W + 3) >> 2;
     const int y = c / cw, x0 = 4 * (c - y * cw);
-    const uint16_t *lab = im.lab[0][o & 1] + y * W;
+    const uint16_t *lab = im.lab[0][o & 1] + (int64_t)y * W;
     int32_t *out = im.out + (int64_t)y * W;
+    if ((W & 3) == 0 && ((uintptr_t)im.out & 15) == 0) {  // one 8-byte load, one 16-byte store
+        const ushort4 v = *(const ushort4 *)(lab + x0);
+        *(int4 *)(out + x0) = make_int4(v.x, v.y, v.z, v.w);
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         if (x0 + q < W) out[x0 + q] = lab[x0 + q];
