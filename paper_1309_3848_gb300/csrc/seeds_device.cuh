@@ -216,19 +216,20 @@ __host__ __device__ inline int64_t pixel_tiles(const DevImage &im, int phase, in
 }
 
 // Entries of image `img` for its op `o`.  When the moves of op o-1 (a phase)
-// are pending, a phase of the same level replays them unit by unit before
-// judging its own units (one fused entry); any other op gets a catch-up
-// entry of its own first.  Returns the number of entries written; `vt`
+// are pending, a pixel phase, and a block phase of the same level when
+// `fuse_blocks`, replays them unit by unit before judging its own units (one
+// fused entry); otherwise they get a catch-up entry of their own first, whose
+// warps run beside the phase's.  Returns the number of entries written; `vt`
 // advances by their padded thread counts.
-__host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, bool catchup, StepEntry *out,
-                                            int64_t *vt)
+__host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, bool catchup, bool fuse_blocks,
+                                            StepEntry *out, int64_t *vt)
 {
     int n = 0;
     const OpDesc op = op_at(im.L, im.iters, im.means_iters, o);
     int cphase = -1;
     if (catchup && o > 0) {
         const OpDesc pv = op_at(im.L, im.iters, im.means_iters, o - 1);
-        if (is_phase(pv.kind) && op.kind == pv.kind && pv.level == op.level) {
+        if (is_phase(pv.kind) && op.kind == pv.kind && pv.level == op.level && (op.level == 0 || fuse_blocks)) {
             cphase = pv.phase;
         } else if (is_phase(pv.kind)) {
             // large blocks are replayed by a warp each, small blocks by a
@@ -284,6 +285,17 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
     return n;
 }
 
+// Whether the block phases of a step fuse their replays: a step whose fused
+// work is below `split_below` warps (the machine's warp slots) is bound by
+// its slowest unit, and a unit that replays a move and then judges is the
+// slowest, so the replays go to catch-up entries that run beside the
+// judges; a full step keeps them fused, which takes fewer warps.
+// `fused_vt` is the step's thread count with fused entries.
+__host__ __device__ inline bool fuse_step(int64_t fused_vt, int64_t split_below)
+{
+    return fused_vt / 32 >= split_below;
+}
+
 // An epoch of the serving runtime: for each resident slot, the range of its
 // ops to run; the device builds the step schedule from it.
 constexpr int kMaxEpochSlots = 128;
@@ -293,8 +305,9 @@ struct EpochSlot {
     int32_t catchup;     // op begin-1's moves are pending
 };
 struct EpochPlan {
-    int32_t n;       // slots in the epoch
-    int32_t nsteps;  // max over slots of end - begin (<= 1024)
+    int32_t n;            // slots in the epoch
+    int32_t nsteps;       // max over slots of end - begin (<= 1024)
+    int32_t split_below;  // fuse_step's threshold in warps
     EpochSlot s[kMaxEpochSlots];
 };
 

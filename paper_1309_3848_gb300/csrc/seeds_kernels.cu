@@ -280,24 +280,24 @@ __device__ __forceinline__ void move_size(const DevImage &im, int buf, int k, in
     atomicAdd(&im.size[buf][SEEDS_IDX(im, n, im.K)], cnt);
 }
 
-// Sparse colour histogram of block (bx,by) of a level in the warp's shared
-// scratch: counts in hsh[j], distinct bins listed in lst[0..nd).  Whole warp;
-// returns nd.  Loads of four rounds are issued before any is used.
-__device__ int block_sparse_hist(const DevImage &im, int level, int bx, int by, int lane, int32_t *wsh, int max_nbins,
-                                 int *m_out)
+constexpr int kHistRound = 4;  // bins loaded per lane before any is used
+
+// Sparse colour histogram of the block [x0,x1) x [y0,y1) in the warp's
+// shared scratch: counts in hsh[j], distinct bins listed in lst[0..nd).
+// Whole warp; returns nd.  A lane loads kHistRound bins before it uses any.
+__device__ int block_sparse_hist(const DevImage &im, int x0, int x1, int y0, int y1, int lane, int32_t *wsh,
+                                 int max_nbins)
 {
     int32_t *ndist = wsh;
     int32_t *hsh = wsh + kScratchHeader;
     // the list lives past the largest histogram of the context, so that it
     // never overlaps histogram entries another image's blocks rely on being 0
     uint16_t *lst = (uint16_t *)(hsh + max_nbins);
-    const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
-    const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
     const int bw = x1 - x0, m = bw * (y1 - y0);
-    for (int base = 0; base < m; base += 128) {
-        int j[4];
+    for (int base = 0; base < m; base += 32 * kHistRound) {
+        int j[kHistRound];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kHistRound; ++q) {
             const int t = base + 32 * q + lane;
             j[q] = -1;
             if (t < m) {
@@ -306,7 +306,7 @@ __device__ int block_sparse_hist(const DevImage &im, int level, int bx, int by, 
             }
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kHistRound; ++q) {
             if (base + 32 * q >= m) break;  // m is the warp's: the rest of the round is empty
             const unsigned peers = __match_any_sync(0xffffffffu, j[q]);
             if (j[q] >= 0 && lane == __ffs(peers) - 1) {
@@ -316,7 +316,6 @@ __device__ int block_sparse_hist(const DevImage &im, int level, int bx, int by, 
         }
     }
     __syncwarp();
-    *m_out = m;
     return *(volatile int32_t *)ndist;
 }
 
@@ -942,8 +941,10 @@ __device__ void replay_large_block(const DevImage &im, int buf, int level, int b
                                    int32_t *wsh, int max_nbins)
 {
     const int k = (int)(d >> 16), n = (int)(d & 0xFFFFu);
-    int m;
-    const int nd = block_sparse_hist(im, level, bx, by, lane, wsh, max_nbins, &m);
+    const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
+    const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
+    const int m = (x1 - x0) * (y1 - y0);
+    const int nd = block_sparse_hist(im, x0, x1, y0, y1, lane, wsh, max_nbins);
     block_sparse_apply_clear(im, buf, k, n, nd, lane, wsh, max_nbins);
     if (lane == 0) {
         im.lab[level][buf][SEEDS_IDX(im, by * im.nbx[level] + bx, (int64_t)im.nbx[level] * im.nby[level])] =
@@ -978,6 +979,10 @@ __device__ void op_block_phase_warp(const DevImage &im, int o, int level, int ph
     const int uu = uy * ncols + ux;
     const int bx = 2 * ux + (phase & 1), by = 2 * uy + (phase >> 1);
     const uint16_t *lab = im.lab[level][b];
+    // the block's extent is read with its labels, the sizes before the
+    // histogram build: fewer dependent trips to L2
+    const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
+    const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
     const int k = lab[by * nx + bx];
     int cand[4];
     const int nc = unit_candidates(lab, nx, ny, bx, by, k, cand);
@@ -986,15 +991,16 @@ __device__ void op_block_phase_warp(const DevImage &im, int o, int level, int ph
         return;
     }
     const int32_t *hist = im.hist[b], *size = im.size[b];
-    int m;
-    const int nd = block_sparse_hist(im, level, bx, by, lane, wsh, max_nbins, &m);
-    const int32_t *hsh = wsh + kScratchHeader;
-    const uint16_t *lst = (const uint16_t *)(hsh + max_nbins);
     int64_t sz[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) sz[c] = cand[c] != kNoLabel ? size[SEEDS_IDX(im, cand[c], im.K)] : 1;
+    const int m = (x1 - x0) * (y1 - y0);
     const int64_t s_k = size[SEEDS_IDX(im, k, im.K)], s_rest = s_k - m;
+    const int nd = block_sparse_hist(im, x0, x1, y0, y1, lane, wsh, max_nbins);
+    const int32_t *hsh = wsh + kScratchHeader;
+    const uint16_t *lst = (const uint16_t *)(hsh + max_nbins);
     int64_t S[4] = {0, 0, 0, 0}, S_st = 0;
+#pragma unroll 2
     for (int t = lane; t < nd; t += 32) {
         const int j = lst[t];
         const int Lj = hsh[j];
@@ -1366,16 +1372,27 @@ __global__ void epoch_schedule_kernel(const DevImage *imgs, EpochPlan plan, Step
     const int s = threadIdx.x;
     StepEntry tmp[2];
     int c = 0;
-    if (s < plan.nsteps)
-        for (int i = 0; i < plan.n; ++i) {
-            const EpochSlot &q = plan.s[i];
-            const int o = q.begin + s;
-            if (o >= q.end) continue;
-            const DevImage &im = imgs[q.slot];
-            const bool cu = s == 0 ? q.catchup != 0 : is_phase(op_at(im.L, im.iters, im.means_iters, o - 1).kind);
+    bool fuse = true;
+    if (s < plan.nsteps) {
+        int64_t vf = 0;  // the step's size with fused entries
+        for (int pass = 0; pass < 2; ++pass) {
             int64_t v = 0;
-            c += emit_entries(im, q.slot, o, cu, tmp, &v);
+            for (int i = 0; i < plan.n; ++i) {
+                const EpochSlot &q = plan.s[i];
+                const int o = q.begin + s;
+                if (o >= q.end) continue;
+                const DevImage &im = imgs[q.slot];
+                const bool cu =
+                    s == 0 ? q.catchup != 0 : is_phase(op_at(im.L, im.iters, im.means_iters, o - 1).kind);
+                const int m = emit_entries(im, q.slot, o, cu, fuse, tmp, &v);
+                if (pass == 1) c += m;
+            }
+            if (pass == 0) {
+                vf = v;
+                fuse = fuse_step(vf, plan.split_below);
+            }
         }
+    }
     cnt[s] = c;
     __syncthreads();
     if (s == 0) {  // exclusive scan over the steps (at most 1024)
@@ -1398,7 +1415,7 @@ __global__ void epoch_schedule_kernel(const DevImage *imgs, EpochPlan plan, Step
         if (o >= q.end) continue;
         const DevImage &im = imgs[q.slot];
         const bool cu = s == 0 ? q.catchup != 0 : is_phase(op_at(im.L, im.iters, im.means_iters, o - 1).kind);
-        e += emit_entries(im, q.slot, o, cu, ent + e, &v);
+        e += emit_entries(im, q.slot, o, cu, fuse, ent + e, &v);
     }
     vt[s] = v;
 }
@@ -1523,6 +1540,7 @@ struct StaticSetup {
     unsigned char *zero_begin;  // barrier and error word
     int32_t zero_bytes;
     int32_t nops;
+    int32_t split_below;  // fuse_step's threshold in warps
     DevImage *img_out;
 };
 
@@ -1546,7 +1564,10 @@ __global__ void static_setup_kernel(StaticSetup S)
         S.first[o] = ne;
         int64_t vt = 0;
         const bool catchup = o > 0 && is_phase(op_at(im.L, im.iters, im.means_iters, o - 1).kind);
-        ne += emit_entries(im, 0, o, catchup, S.ent + ne, &vt);
+        StepEntry tmp[2];
+        int64_t vf = 0;
+        emit_entries(im, 0, o, catchup, true, tmp, &vf);
+        ne += emit_entries(im, 0, o, catchup, fuse_step(vf, S.split_below), S.ent + ne, &vt);
         S.vt[o] = vt;
     }
     S.first[S.nops] = ne;
@@ -1720,6 +1741,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     }
     if (threads == 0) return SEEDS_ERR_CUDA;
 
+    S.split_below = sms * 32;
     cudaStream_t s = (cudaStream_t)stream;
     static_setup_kernel<<<8, 256, 0, s>>>(S);
     if (cudaGetLastError() != cudaSuccess) return SEEDS_ERR_CUDA;

@@ -145,17 +145,26 @@ int get_schedule(seeds_ctx *c, int kind, int ob, int oe, const Schedule **out)
     std::vector<int32_t> first;
     std::vector<int64_t> vt;
     StepEntry two[2];
+    const int64_t split_below = (int64_t)c->sm_count * 32;
     for (int s = 0; s < nsteps; ++s) {
         first.push_back((int32_t)ent.size());
-        int64_t v = 0;
-        for (int i = 0; i < n; ++i) {
-            const int o = b[i] + s;
-            if (o >= e[i]) continue;
-            const bool catchup = s == 0 ? (o > 0 && c->pending[i] == o - 1) : is_phase(c->img[i].ops[o - 1].kind);
-            const int m = emit_entries(c->h_imgs[i], i, o, catchup, two, &v);
-            for (int q = 0; q < m; ++q) ent.push_back(two[q]);
+        for (int pass = 0; pass < 2; ++pass) {  // the fused step's size, then its entries
+            int64_t v = 0;
+            const bool fuse = pass == 0 || fuse_step(vt.back(), split_below);
+            for (int i = 0; i < n; ++i) {
+                const int o = b[i] + s;
+                if (o >= e[i]) continue;
+                const bool catchup =
+                    s == 0 ? (o > 0 && c->pending[i] == o - 1) : is_phase(c->img[i].ops[o - 1].kind);
+                const int m = emit_entries(c->h_imgs[i], i, o, catchup, fuse, two, &v);
+                if (pass == 1)
+                    for (int q = 0; q < m; ++q) ent.push_back(two[q]);
+            }
+            if (pass == 0)
+                vt.push_back(v);
+            else
+                vt.back() = v;
         }
-        vt.push_back(v);
     }
     first.push_back((int32_t)ent.size());
     if (ent.empty()) ent.push_back(StepEntry{});  // keep the buffer non-empty

@@ -317,6 +317,7 @@ int seeds_server_step(seeds_server *s, int32_t *resident_out)
     // plan the epoch: every resident image advances by up to epoch_steps ops
     EpochPlan plan;
     std::memset(&plan, 0, sizeof(plan));
+    plan.split_below = s->sm_count * 32;
     for (Request *r : s->slots) {
         if (!r) continue;
         EpochSlot &q = plan.s[plan.n++];
