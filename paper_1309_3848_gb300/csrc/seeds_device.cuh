@@ -221,7 +221,7 @@ __host__ __device__ inline int64_t pixel_tiles(const DevImage &im, int phase, in
 // fused entry); otherwise they get a catch-up entry of their own first, whose
 // warps run beside the phase's.  Returns the number of entries written; `vt`
 // advances by their padded thread counts.
-__host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, bool catchup, bool fuse_blocks,
+__host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, bool catchup, int fuse,
                                             StepEntry *out, int64_t *vt)
 {
     int n = 0;
@@ -229,7 +229,7 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
     int cphase = -1;
     if (catchup && o > 0) {
         const OpDesc pv = op_at(im.L, im.iters, im.means_iters, o - 1);
-        if (is_phase(pv.kind) && op.kind == pv.kind && pv.level == op.level && (op.level == 0 || fuse_blocks)) {
+        if (is_phase(pv.kind) && op.kind == pv.kind && pv.level == op.level && fuse >= (op.level == 0 ? 1 : 2)) {
             cphase = pv.phase;
         } else if (is_phase(pv.kind)) {
             // large blocks are replayed by a warp each, small blocks by a
@@ -291,9 +291,9 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
 // slowest, so the replays go to catch-up entries that run beside the
 // judges; a full step keeps them fused, which takes fewer warps.
 // `fused_vt` is the step's thread count with fused entries.
-__host__ __device__ inline bool fuse_step(int64_t fused_vt, int64_t split_below)
+__host__ __device__ inline int fuse_step(int64_t fused_vt, int64_t split_below)
 {
-    return fused_vt / 32 >= split_below;
+    return fused_vt / 32 >= split_below ? 2 : fused_vt / 32 >= split_below / 8 ? 1 : 0;
 }
 
 // An epoch of the serving runtime: for each resident slot, the range of its

@@ -1212,7 +1212,10 @@ __global__ void __launch_bounds__(1024, 1) seeds_persistent(const DevImage *__re
     // its next one from a shared counter as they finish, so one slow unit
     // does not hold up the units queued behind it on the same warp.  Two
     // counters alternate between steps; the grid barrier's CTA barrier
-    // orders each reset before its use.
+    // orders each reset before its use.  A step that fits in one round is
+    // dealt round-robin instead (virtual warp w * gridDim.x + c to warp w of
+    // CTA c), so that its warps spread over every SM rather than filling the
+    // first CTAs.
     __shared__ unsigned s_next[2];
     if (threadIdx.x == 0) s_next[0] = s_next[1] = 0;
     __syncthreads();
@@ -1232,7 +1235,8 @@ __global__ void __launch_bounds__(1024, 1) seeds_persistent(const DevImage *__re
         // the images whose state the step before touched last (still in L2)
         const bool reverse = (s & 1) != 0;
         for (unsigned i = warp;; ) {
-            const int64_t fwd = ((int64_t)(i / nwarps_blk) * nwarps + cta_first + (i % nwarps_blk)) * 32;
+            const int64_t fwd = rounds ? ((int64_t)(i / nwarps_blk) * nwarps + cta_first + (i % nwarps_blk)) * 32
+                                       : ((int64_t)i * gridDim.x + blockIdx.x) * 32;
             if (fwd >= total) break;
             const int64_t base = reverse ? total - 32 - fwd : fwd;
             int lo = e0, hi = e1 - 1;
@@ -1372,7 +1376,7 @@ __global__ void epoch_schedule_kernel(const DevImage *imgs, EpochPlan plan, Step
     const int s = threadIdx.x;
     StepEntry tmp[2];
     int c = 0;
-    bool fuse = true;
+    int fuse = 2;
     if (s < plan.nsteps) {
         int64_t vf = 0;  // the step's size with fused entries
         for (int pass = 0; pass < 2; ++pass) {
@@ -1566,7 +1570,7 @@ __global__ void static_setup_kernel(StaticSetup S)
         const bool catchup = o > 0 && is_phase(op_at(im.L, im.iters, im.means_iters, o - 1).kind);
         StepEntry tmp[2];
         int64_t vf = 0;
-        emit_entries(im, 0, o, catchup, true, tmp, &vf);
+        emit_entries(im, 0, o, catchup, 2, tmp, &vf);
         ne += emit_entries(im, 0, o, catchup, fuse_step(vf, S.split_below), S.ent + ne, &vt);
         S.vt[o] = vt;
     }

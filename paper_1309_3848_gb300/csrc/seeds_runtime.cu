@@ -150,7 +150,7 @@ int get_schedule(seeds_ctx *c, int kind, int ob, int oe, const Schedule **out)
         first.push_back((int32_t)ent.size());
         for (int pass = 0; pass < 2; ++pass) {  // the fused step's size, then its entries
             int64_t v = 0;
-            const bool fuse = pass == 0 || fuse_step(vt.back(), split_below);
+            const int fuse = pass == 0 ? 2 : fuse_step(vt.back(), split_below);
             for (int i = 0; i < n; ++i) {
                 const int o = b[i] + s;
                 if (o >= e[i]) continue;
