@@ -216,11 +216,12 @@ __host__ __device__ inline int64_t pixel_tiles(const DevImage &im, int phase, in
 }
 
 // Entries of image `img` for its op `o`.  When the moves of op o-1 (a phase)
-// are pending, a pixel phase, and a block phase of the same level when
-// `fuse_blocks`, replays them unit by unit before judging its own units (one
-// fused entry); otherwise they get a catch-up entry of their own first, whose
-// warps run beside the phase's.  Returns the number of entries written; `vt`
-// advances by their padded thread counts.
+// are pending, a phase of the same level replays them unit by unit before
+// judging its own units (one fused entry) if `fuse` allows it (2: block and
+// pixel phases, 1: pixel phases only, 0: none; see fuse_step); otherwise
+// they get a catch-up entry of their own first, whose warps run beside the
+// phase's.  Returns the number of entries written; `vt` advances by their
+// padded thread counts.
 __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, bool catchup, int fuse,
                                             StepEntry *out, int64_t *vt)
 {
@@ -285,12 +286,15 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
     return n;
 }
 
-// Whether the block phases of a step fuse their replays: a step whose fused
-// work is below `split_below` warps (the machine's warp slots) is bound by
-// its slowest unit, and a unit that replays a move and then judges is the
-// slowest, so the replays go to catch-up entries that run beside the
-// judges; a full step keeps them fused, which takes fewer warps.
-// `fused_vt` is the step's thread count with fused entries.
+// Which phases of a step fuse their replays (emit_entries' `fuse`).  A step
+// whose fused work is below `split_below` warps (the machine's warp slots)
+// is bound by its slowest unit, and a unit that replays a move and then
+// judges is the slowest, so the replays of block phases go to catch-up
+// entries that run beside the judges; a pixel tile shares its staged labels
+// between replay and judge, so its replays move out only when the step is
+// below an eighth of the machine.  A full step keeps them fused, which
+// takes fewer warps.  `fused_vt` is the step's thread count with fused
+// entries.
 __host__ __device__ inline int fuse_step(int64_t fused_vt, int64_t split_below)
 {
     return fused_vt / 32 >= split_below ? 2 : fused_vt / 32 >= split_below / 8 ? 1 : 0;
