@@ -140,6 +140,27 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
+def host_cpu():
+    """The host CPU's model, from lscpu, else /proc/cpuinfo (None if neither
+    says)."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def kernel_source_hash():
     """sha256 (first 16 hex digits) of the kernel sources with comments and
     blank lines removed: an edit of comments alone leaves the recorded
@@ -274,7 +295,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "config": config_of(args.workload, jobs),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu(),
                              "sample": "the whole workload (%d image(s)) per step, one thread per image" % len(jobs)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -571,7 +592,8 @@ def run_gpu(args):
         line["next_rows"] = next_rows(torch, binding, flush, jobs, imgs, value)
         gpu_labels = [o.cpu().numpy() for o in outs]
         v, cores, sample, ref_labels = cpu_sample(jobs, imgs)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu(),
+                                "sample": sample}
         import numpy as np
         line["parity"] = "bit-exact" if all(np.array_equal(gpu_labels[i], ref_labels[i])
                                             for i in range(len(jobs))) else "MISMATCH"
