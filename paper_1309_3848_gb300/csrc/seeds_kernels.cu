@@ -648,26 +648,45 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         cd[r] = (ux < ccols && uy < crows) ? im.dec[nb][SEEDS_IDX(im, uy * ccols + ux, im.units_cap)] : kNoMove;
     }
 
-    // stage the labels of buffer b and the units' bins
+    // stage the labels of buffer b and the units' bins.  Every load is
+    // issued before the first shared-memory store: a warp issues in order,
+    // and a store waits for its load, so interleaving them would serialise
+    // one L2 round trip per store.  Lane l loads columns l, l+32 (packed in
+    // one register) and, for l < 4, l+64 of each row.
+    constexpr int TH = tile_h(UY);
+    static_assert(kTileW > 64 && kTileW <= 96, "three columns per lane");
     const int X0 = 2 * tx * kTileUX + px - 2, Y0 = 2 * uy0 + py - 2;
     const uint16_t *lab = im.lab[0][b];
+    uint32_t v01[TH];
+    uint16_t v2[TH];
 #pragma unroll
-    for (int r = 0; r < tile_h(UY); ++r) {
+    for (int r = 0; r < TH; ++r) {
         const int yy = Y0 + r;
         const bool rowin = yy >= 0 && yy < H;
-#pragma unroll
-        for (int c = lane; c < kTileW; c += 32) {
-            const int xx = X0 + c;
-            tsh[r * kTileW + c] = (rowin && xx >= 0 && xx < W) ? lab[yy * W + xx] : kNoLabel;
-        }
+        const uint16_t *row = lab + (int64_t)yy * W;
+        const int x0 = X0 + lane, x1 = x0 + 32, x2 = x0 + 64;
+        const uint32_t a = (rowin && x0 >= 0 && x0 < W) ? row[x0] : kNoLabel;
+        const uint32_t c = (rowin && x1 >= 0 && x1 < W) ? row[x1] : kNoLabel;
+        v01[r] = a | (c << 16);
+        v2[r] = (lane + 64 < kTileW && rowin && x2 >= 0 && x2 < W) ? row[x2] : kNoLabel;
     }
-    uint16_t *jsh = tsh + kTileW * tile_h(UY);
-    uint8_t *lst = (uint8_t *)(jsh + UY * kTileUX);
+    uint16_t jv[UY];
 #pragma unroll
     for (int r = 0; r < UY; ++r) {
         const int uy = uy0 + r;
-        jsh[r * 32 + lane] = (ux < ncols && uy < nrows) ? bin_at(im, (2 * uy + py) * W + 2 * ux + px) : 0;
+        jv[r] = (ux < ncols && uy < nrows) ? bin_at(im, (2 * uy + py) * W + 2 * ux + px) : 0;
     }
+    __syncwarp();  // keeps the loads above the stores
+    uint16_t *jsh = tsh + kTileW * TH;
+    uint8_t *lst = (uint8_t *)(jsh + UY * kTileUX);
+#pragma unroll
+    for (int r = 0; r < TH; ++r) {
+        tsh[r * kTileW + lane] = (uint16_t)(v01[r] & 0xFFFFu);
+        tsh[r * kTileW + lane + 32] = (uint16_t)(v01[r] >> 16);
+        if (lane + 64 < kTileW) tsh[r * kTileW + lane + 64] = v2[r];
+    }
+#pragma unroll
+    for (int r = 0; r < UY; ++r) jsh[r * 32 + lane] = jv[r];
 
     // replay the previous phase's moves into buffer nb
 #pragma unroll
@@ -770,6 +789,16 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
                 }
             }
         }
+        // the histogram and size lookups of every candidate and of k, all
+        // issued before the first is used
+        int32_t ac[4], zc[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int n = cand[c] != kNoLabel ? cand[c] : k;
+            ac[c] = hist[hidx(im, n, j)];
+            zc[c] = size[SEEDS_IDX(im, n, im.K)];
+        }
+        const int64_t a_k = hist[hidx(im, k, j)], s_k = size[SEEDS_IDX(im, k, im.K)];
         // candidates in ascending label order; a later one wins only if
         // strictly better, so ties go to the smallest label
         int best = kNoLabel;
@@ -779,7 +808,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         for (int c = 0; c < 4; ++c) {
             const int n = cand[c];
             if (n == kNoLabel) continue;
-            const int64_t a = hist[hidx(im, n, j)], sz = size[SEEDS_IDX(im, n, im.K)];
+            const int64_t a = ac[c], sz = zc[c];
             if (best == kNoLabel || gd81 * (a * s_b - a_b * sz) + gn * (int64_t)(Gc[c] - G_b) * sz * s_b > 0) {
                 best = n;
                 a_b = a;
@@ -787,7 +816,6 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
                 G_b = Gc[c];
             }
         }
-        const int64_t a_k = hist[hidx(im, k, j)], s_k = size[SEEDS_IDX(im, k, im.K)];
         const int64_t gain =
             gd81 * (a_b * (s_k - 1) - (a_k - 1) * s_b) + gn * (int64_t)(G_b + Kp - Gk) * s_b * (s_k - 1);
         uint32_t dec = kNoMove;
