@@ -425,17 +425,26 @@ __device__ void op_init(const DevImage &im, int k, int lane, int32_t *wsh)
         for (int xb = x0; xb < x1; xb += 32) {
         int j[8], p[8];
         const int x = xb + lane;
+        // the round's 24 byte loads first, then the arithmetic on them
+        uint32_t rgb[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int y = yb + q;
-            j[q] = -1;
-            p[q] = 0;
+            rgb[q] = 0xFFFFFFFFu;
             if (y < y1 && x < x1) {
                 const uint8_t *px = im.rgb + (int64_t)y * im.stride + 3 * (int64_t)x;
-                int r = px[0], g = px[1], b = px[2];
+                rgb[q] = (uint32_t)px[0] | ((uint32_t)px[1] << 8) | ((uint32_t)px[2] << 16);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            j[q] = -1;
+            p[q] = 0;
+            if (rgb[q] != 0xFFFFFFFFu) {
+                int r = rgb[q] & 255, g = (rgb[q] >> 8) & 255, b = (rgb[q] >> 16) & 255;
                 if (im.color) lab8(r, g, b, r, g, b);
                 j[q] = ((r * B) >> 8) * B * B + ((g * B) >> 8) * B + ((b * B) >> 8);
-                p[q] = y * im.W + x;
+                p[q] = (yb + q) * im.W + x;
             }
         }
 #pragma unroll
@@ -847,17 +856,40 @@ __device__ __noinline__ void op_means_tile(const DevImage &im, int o, int phase,
 
 constexpr int kSmallMax = 16;
 
-// Replay a small block's move into buffer `buf` (one thread).
-__device__ void replay_small_block(const DevImage &im, int buf, int level, int bx, int by, uint32_t d)
+// Replay a small block's move into buffer `buf` (one thread); SM bounds its
+// pixel count.  The block's bins are all loaded before the first atomic
+// that needs one, so the loads share one trip to L2.
+template <int SM>
+__device__ void replay_small_block_t(const DevImage &im, int buf, int level, int bx, int by, uint32_t d)
 {
     const int k = (int)(d >> 16), n = (int)(d & 0xFFFFu);
     const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
     const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
-    for (int yy = y0; yy < y1; ++yy)
-        for (int xx = x0; xx < x1; ++xx) move_counts(im, buf, k, n, bin_at(im, yy * im.W + xx), 1);
-    move_size(im, buf, k, n, (x1 - x0) * (y1 - y0));
+    const int bw = x1 - x0, m = bw * (y1 - y0);
+    int jj[SM];
+#pragma unroll
+    for (int t = 0; t < SM; ++t) {
+        const int dy = t / bw;
+        jj[t] = t < m ? bin_at(im, (y0 + dy) * im.W + x0 + (t - dy * bw)) : -1;
+    }
+#pragma unroll
+    for (int t = 0; t < SM; ++t)
+        if (jj[t] >= 0) move_counts(im, buf, k, n, jj[t], 1);
+    move_size(im, buf, k, n, m);
     im.lab[level][buf][SEEDS_IDX(im, by * im.nbx[level] + bx, (int64_t)im.nbx[level] * im.nby[level])] =
         (uint16_t)SEEDS_IDX(im, n, im.K);
+}
+
+__device__ __forceinline__ void replay_small_block(const DevImage &im, int buf, int level, int bx, int by,
+                                                   uint32_t d)
+{
+    const int ma = im.maxarea[level];
+    if (ma <= 4)
+        replay_small_block_t<4>(im, buf, level, bx, by, d);
+    else if (ma <= 9)
+        replay_small_block_t<9>(im, buf, level, bx, by, d);
+    else
+        replay_small_block_t<kSmallMax>(im, buf, level, bx, by, d);
 }
 
 // Judge small block (bx,by); SM bounds its pixel count, so the dedupe of its
@@ -867,12 +899,13 @@ __device__ uint32_t judge_small_block(const DevImage &im, int b, int nb, int lev
 {
     const int nx = im.nbx[level], ny = im.nby[level];
     const uint16_t *lab = im.lab[level][b];
+    // the block's extent is read with its labels: one trip to L2 fewer
+    const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
+    const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
     const int k = lab[by * nx + bx];
     int cand[4];
     if (unit_candidates(lab, nx, ny, bx, by, k, cand) == 0) return kNoMove;
     const int32_t *hist = im.hist[b], *size = im.size[b];
-    const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
-    const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
     const int bw = x1 - x0, m = bw * (y1 - y0);
     int jj[SM];
 #pragma unroll
