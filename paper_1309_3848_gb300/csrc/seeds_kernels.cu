@@ -867,10 +867,15 @@ __device__ void replay_small_block_t(const DevImage &im, int buf, int level, int
     const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
     const int bw = x1 - x0, m = bw * (y1 - y0);
     int jj[SM];
+    int p = y0 * im.W + x0, dx = 0;  // pixel t of the block, row-major, stepped without a division
 #pragma unroll
     for (int t = 0; t < SM; ++t) {
-        const int dy = t / bw;
-        jj[t] = t < m ? bin_at(im, (y0 + dy) * im.W + x0 + (t - dy * bw)) : -1;
+        jj[t] = t < m ? bin_at(im, p) : -1;
+        ++p;
+        if (++dx == bw) {
+            dx = 0;
+            p += im.W - bw;
+        }
     }
 #pragma unroll
     for (int t = 0; t < SM; ++t)
@@ -908,12 +913,14 @@ __device__ uint32_t judge_small_block(const DevImage &im, int b, int nb, int lev
     const int32_t *hist = im.hist[b], *size = im.size[b];
     const int bw = x1 - x0, m = bw * (y1 - y0);
     int jj[SM];
+    int p = y0 * im.W + x0, dx = 0;  // pixel t of the block, row-major, stepped without a division
 #pragma unroll
     for (int t = 0; t < SM; ++t) {
-        jj[t] = -1;
-        if (t < m) {
-            const int dy = t / bw;
-            jj[t] = bin_at(im, (y0 + dy) * im.W + x0 + (t - dy * bw));
+        jj[t] = t < m ? bin_at(im, p) : -1;
+        ++p;
+        if (++dx == bw) {
+            dx = 0;
+            p += im.W - bw;
         }
     }
     int64_t S[4] = {0, 0, 0, 0}, S_st = 0;
