@@ -187,9 +187,16 @@ __host__ __device__ inline int64_t phase_units(const DevImage &im, int level, in
     return (int64_t)((im.nbx[level] - (phase & 1) + 1) >> 1) * ((im.nby[level] - (phase >> 1) + 1) >> 1);
 }
 
+// Threads per unit of a block level: 1 (small blocks, up to small_area
+// pixels) or 32 (a warp per block).  A thread sums a block's intersections
+// in 32 bits, exact while kSmallMax * W * H < 2^31; larger images give
+// every block level to warps.
+constexpr int kSmallMax = 16;
 __host__ __device__ inline int level_group(const DevImage &im, int level)
 {
-    return (level > 0 && im.maxarea[level] > im.small_area) ? 32 : 1;
+    if (level == 0) return 1;
+    const bool thread = im.maxarea[level] <= im.small_area && (int64_t)im.W * im.H * kSmallMax < (1ll << 31);
+    return thread ? 1 : 32;
 }
 
 // The unit lattice of a phase on a grid nx x ny: unit (ux,uy) is cell

@@ -854,7 +854,26 @@ __device__ __noinline__ void op_means_tile(const DevImage &im, int o, int phase,
 // block phase, small blocks: one thread per block (at most 16 pixels)
 // ---------------------------------------------------------------------------
 
-constexpr int kSmallMax = 16;
+
+// Move the colour counts of a small block's pixels (bins jj[0..m), SM
+// bounding m) from k to n in buffer `buf`: one pair of atomics per distinct
+// bin with its count, rather than one per pixel.
+template <int SM>
+__device__ __forceinline__ void move_block_counts(const DevImage &im, int buf, int k, int n, const int (&jj)[SM], int m)
+{
+#pragma unroll
+    for (int t = 0; t < SM; ++t) {
+        if (t >= m) break;
+        bool first = true;
+        int Lj = 0;
+#pragma unroll
+        for (int q = 0; q < SM; ++q) {
+            if (q < t && jj[q] == jj[t]) first = false;
+            if (q >= t && jj[q] == jj[t]) ++Lj;
+        }
+        if (first) move_counts(im, buf, k, n, jj[t], Lj);
+    }
+}
 
 // Replay a small block's move into buffer `buf` (one thread); SM bounds its
 // pixel count.  The block's bins are all loaded before the first atomic
@@ -877,9 +896,7 @@ __device__ void replay_small_block_t(const DevImage &im, int buf, int level, int
             p += im.W - bw;
         }
     }
-#pragma unroll
-    for (int t = 0; t < SM; ++t)
-        if (jj[t] >= 0) move_counts(im, buf, k, n, jj[t], 1);
+    move_block_counts<SM>(im, buf, k, n, jj, m);
     move_size(im, buf, k, n, m);
     im.lab[level][buf][SEEDS_IDX(im, by * im.nbx[level] + bx, (int64_t)im.nbx[level] * im.nby[level])] =
         (uint16_t)SEEDS_IDX(im, n, im.K);
@@ -923,11 +940,14 @@ __device__ uint32_t judge_small_block(const DevImage &im, int b, int nb, int lev
             p += im.W - bw;
         }
     }
-    int64_t S[4] = {0, 0, 0, 0}, S_st = 0;
-    int64_t sz[4];
+    // the sums in 32 bits: every term is at most L_j * |A| and they add up
+    // to at most |L| * N <= kSmallMax * N < 2^31 (the thread path is only
+    // taken below that); the comparisons cross-multiply in 64 bits
+    int32_t S[4] = {0, 0, 0, 0}, S_st = 0;
+    int32_t sz[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) sz[c] = cand[c] != kNoLabel ? size[SEEDS_IDX(im, cand[c], im.K)] : 1;
-    const int64_t s_k = size[SEEDS_IDX(im, k, im.K)], s_rest = s_k - m;
+    const int32_t s_k = size[SEEDS_IDX(im, k, im.K)], s_rest = s_k - m;
     // S(A, L) = sum over the distinct bins j of L of min(A[j]*|L|, L_j*|A|)
 #pragma unroll
     for (int t = 0; t < SM; ++t) {
@@ -943,24 +963,22 @@ __device__ uint32_t judge_small_block(const DevImage &im, int b, int nb, int lev
         if (!first) continue;
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            if (cand[c] != kNoLabel) S[c] += min((int64_t)hist[hidx(im, cand[c], j)] * m, (int64_t)Lj * sz[c]);
-        S_st += min((int64_t)(hist[hidx(im, k, j)] - Lj) * m, (int64_t)Lj * s_rest);
+            if (cand[c] != kNoLabel) S[c] += min(hist[hidx(im, cand[c], j)] * m, Lj * sz[c]);
+        S_st += min((hist[hidx(im, k, j)] - Lj) * m, Lj * s_rest);
     }
     // ascending candidates, strictly better replaces: ties to the smallest label
     int n = kNoLabel;
     int64_t Sb = 0, zb = 1;
 #pragma unroll
     for (int c = 0; c < 4; ++c)
-        if (cand[c] != kNoLabel && (n == kNoLabel || S[c] * zb > Sb * sz[c])) {
+        if (cand[c] != kNoLabel && (n == kNoLabel || (int64_t)S[c] * zb > Sb * sz[c])) {
             n = cand[c];
             Sb = S[c];
             zb = sz[c];
         }
-    if (!(Sb * s_rest > S_st * zb)) return kNoMove;
+    if (!(Sb * s_rest > (int64_t)S_st * zb)) return kNoMove;
     im.lab[level][nb][SEEDS_IDX(im, by * nx + bx, (int64_t)nx * im.nby[level])] = (uint16_t)SEEDS_IDX(im, n, im.K);
-#pragma unroll
-    for (int t = 0; t < SM; ++t)
-        if (t < m) move_counts(im, nb, k, n, jj[t], 1);
+    move_block_counts<SM>(im, nb, k, n, jj, m);
     move_size(im, nb, k, n, m);
     return ((uint32_t)k << 16) | (uint32_t)n;
 }
