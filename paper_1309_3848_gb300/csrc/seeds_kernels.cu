@@ -807,26 +807,28 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
             ac[c] = hist[hidx(im, n, j)];
             zc[c] = size[SEEDS_IDX(im, n, im.K)];
         }
-        const int64_t a_k = hist[hidx(im, k, j)], s_k = size[SEEDS_IDX(im, k, im.K)];
+        const int32_t a_k = hist[hidx(im, k, j)], s_k = size[SEEDS_IDX(im, k, im.K)];
         // candidates in ascending label order; a later one wins only if
-        // strictly better, so ties go to the smallest label
+        // strictly better, so ties go to the smallest label.  Counts and
+        // sizes are held in 32 bits and multiplied in 64.
         int best = kNoLabel;
-        int64_t a_b = 0, s_b = 1;
+        int32_t a_b = 0, s_b = 1;
         int G_b = 0;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int n = cand[c];
             if (n == kNoLabel) continue;
-            const int64_t a = ac[c], sz = zc[c];
-            if (best == kNoLabel || gd81 * (a * s_b - a_b * sz) + gn * (int64_t)(Gc[c] - G_b) * sz * s_b > 0) {
+            const int32_t a = ac[c], sz = zc[c];
+            if (best == kNoLabel || gd81 * ((int64_t)a * s_b - (int64_t)a_b * sz) +
+                                            gn * (int64_t)(Gc[c] - G_b) * sz * s_b > 0) {
                 best = n;
                 a_b = a;
                 s_b = sz;
                 G_b = Gc[c];
             }
         }
-        const int64_t gain =
-            gd81 * (a_b * (s_k - 1) - (a_k - 1) * s_b) + gn * (int64_t)(G_b + Kp - Gk) * s_b * (s_k - 1);
+        const int64_t gain = gd81 * ((int64_t)a_b * (s_k - 1) - (int64_t)(a_k - 1) * s_b) +
+                             gn * (int64_t)(G_b + Kp - Gk) * s_b * (s_k - 1);
         uint32_t dec = kNoMove;
         if (gain > 0) {
             dec = ((uint32_t)k << 16) | (uint32_t)best;
@@ -1022,6 +1024,36 @@ __device__ __forceinline__ int64_t warp_sum64(int64_t v)
     return v;
 }
 
+__device__ __forceinline__ int32_t warp_sum(int32_t v) { return __reduce_add_sync(0xffffffffu, v); }
+__device__ __forceinline__ int64_t warp_sum(int64_t v) { return warp_sum64(v); }
+
+// The intersection sums of a block against its candidates (S) and against
+// k without the block (S_st), from the warp's sparse histogram of the block:
+// each lane sums its distinct bins in T, the warp adds the lanes up.
+template <typename T>
+__device__ __forceinline__ void warp_block_sums(const DevImage &im, int b, const int32_t *wsh, int max_nbins, int nd,
+                                                int lane, int k, const int cand[4], const int32_t sz[4],
+                                                int32_t s_rest, int m, int64_t S[4], int64_t &S_st)
+{
+    const int32_t *hist = im.hist[b];
+    const int32_t *hsh = wsh + kScratchHeader;
+    const uint16_t *lst = (const uint16_t *)(hsh + max_nbins);
+    T s[4] = {0, 0, 0, 0}, st = 0;
+#pragma unroll 2
+    for (int t = lane; t < nd; t += 32) {
+        const int j = lst[t];
+        const int Lj = hsh[j];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (cand[c] != kNoLabel) s[c] += min((T)hist[hidx(im, cand[c], j)] * m, (T)Lj * sz[c]);
+        st += min((T)(hist[hidx(im, k, j)] - Lj) * m, (T)Lj * s_rest);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (cand[c] != kNoLabel) S[c] = warp_sum(s[c]);  // the same slots are empty on every lane
+    S_st = warp_sum(st);
+}
+
 // Replay a large block's move into buffer `buf` (whole warp).
 __device__ void replay_large_block(const DevImage &im, int buf, int level, int bx, int by, uint32_t d, int lane,
                                    int32_t *wsh, int max_nbins)
@@ -1076,29 +1108,20 @@ __device__ void op_block_phase_warp(const DevImage &im, int o, int level, int ph
         if (lane == 0) im.dec[b][SEEDS_IDX(im, uu, im.units_cap)] = kNoMove;
         return;
     }
-    const int32_t *hist = im.hist[b], *size = im.size[b];
-    int64_t sz[4];
+    const int32_t *size = im.size[b];
+    int32_t sz[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) sz[c] = cand[c] != kNoLabel ? size[SEEDS_IDX(im, cand[c], im.K)] : 1;
     const int m = (x1 - x0) * (y1 - y0);
-    const int64_t s_k = size[SEEDS_IDX(im, k, im.K)], s_rest = s_k - m;
+    const int32_t s_k = size[SEEDS_IDX(im, k, im.K)], s_rest = s_k - m;
     const int nd = block_sparse_hist(im, x0, x1, y0, y1, lane, wsh, max_nbins);
-    const int32_t *hsh = wsh + kScratchHeader;
-    const uint16_t *lst = (const uint16_t *)(hsh + max_nbins);
     int64_t S[4] = {0, 0, 0, 0}, S_st = 0;
-#pragma unroll 2
-    for (int t = lane; t < nd; t += 32) {
-        const int j = lst[t];
-        const int Lj = hsh[j];
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (cand[c] != kNoLabel) S[c] += min((int64_t)hist[hidx(im, cand[c], j)] * m, (int64_t)Lj * sz[c]);
-        S_st += min((int64_t)(hist[hidx(im, k, j)] - Lj) * m, (int64_t)Lj * s_rest);
-    }
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-        if (cand[c] != kNoLabel) S[c] = warp_sum64(S[c]);  // the same slots are empty on every lane
-    S_st = warp_sum64(S_st);
+    // every sum is at most |L| * N: in 32 bits when that fits (the branch
+    // is the warp's: m is the block's)
+    if ((int64_t)m * im.W * im.H < (1ll << 31))
+        warp_block_sums<int32_t>(im, b, wsh, max_nbins, nd, lane, k, cand, sz, s_rest, m, S, S_st);
+    else
+        warp_block_sums<int64_t>(im, b, wsh, max_nbins, nd, lane, k, cand, sz, s_rest, m, S, S_st);
     // every lane holds the same sums, so every lane takes the same decision;
     // ascending candidates, strictly better replaces: ties to the smallest label
     int n = kNoLabel;
