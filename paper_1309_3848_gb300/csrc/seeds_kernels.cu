@@ -732,7 +732,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
     // pass 2: judge the boundary units, every lane busy (a unit frozen by
     // edge snapping stays)
     const int32_t *hist = im.hist[b], *size = im.size[b];
-    const int64_t gd81 = 81ll * im.gden, gn = im.gnum;
+    const int32_t gd81 = 81 * im.gden, gn = im.gnum;  // both below 2^17; the products below widen to 64 bits
     const bool use_g = im.patch != 0 && im.gnum != 0;
     for (int i = lane; i < nbd; i += 32) {
         const int e = lst[i], r = e >> 5, l = e & 31;
