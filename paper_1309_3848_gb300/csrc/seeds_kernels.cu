@@ -1328,18 +1328,22 @@ __global__ void __launch_bounds__(1024, 1) seeds_persistent(const DevImage *__re
     __shared__ unsigned s_next[2];
     if (threadIdx.x == 0) s_next[0] = s_next[1] = 0;
     __syncthreads();
-    const int64_t nwarps = (int64_t)gridDim.x * nwarps_blk;
-    const int64_t cta_first = (int64_t)blockIdx.x * nwarps_blk;
+    // values that live through every step are kept few: the grid's warp
+    // count and the CTA's first warp are 32-bit (a grid has fewer than 2^31
+    // warps) and the anytime start time waits in shared memory
+    const int nwarps = (int)gridDim.x * nwarps_blk;
+    const int cta_first = (int)blockIdx.x * nwarps_blk;
     const bool tracer = S.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
     if (tracer) S.trace[0] = global_ns();
     const bool anytime = S.stop_steps > 0 || S.budget_ns > 0;
-    const uint64_t t_start = anytime ? global_ns() : 0;
+    __shared__ uint64_t s_t_start;
+    if (threadIdx.x == 0) s_t_start = anytime ? global_ns() : 0;  // read by thread 0 only
 
     for (int s = 0; s < S.nsteps; ++s) {
         const int e0 = S.step_first[s], e1 = S.step_first[s + 1];
         const int64_t total = S.step_vt[s];
         if (threadIdx.x == 0) s_next[(s + 1) & 1] = 0;
-        const bool rounds = nwarps * 32 < total;  // work beyond round 0 for some CTA
+        const bool rounds = (int64_t)nwarps * 32 < total;  // work beyond round 0 for some CTA
         // odd steps walk the step's units from the end, so a step starts on
         // the images whose state the step before touched last (still in L2)
         const bool reverse = (s & 1) != 0;
@@ -1404,7 +1408,7 @@ __global__ void __launch_bounds__(1024, 1) seeds_persistent(const DevImage *__re
                 if (!grid_sync_count(bar, err, (unsigned)(s + 1) * gridDim.x)) return;
             } else {
                 const bool want_stop = threadIdx.x == 0 && ((S.stop_steps > 0 && s + 1 >= S.stop_steps) ||
-                                                            (S.budget_ns > 0 && global_ns() - t_start >= S.budget_ns));
+                                                            (S.budget_ns > 0 && global_ns() - s_t_start >= S.budget_ns));
                 const int go = grid_sync(bar, err, want_stop);
                 if (go == 0) return;
                 if (go == 2) {
