@@ -624,7 +624,7 @@ static int decide_pixel(ref_state *st, int x, int y)
 }
 
 /* move a whole unit from k to n: relabel its pixels and update the
- * histograms incrementally (Sec. 5.3, "Updating the Color Distributions") */
+ * histograms incrementally (the incremental update of Sec. 5.3) */
 static void apply_move(ref_state *st, int level, int bx, int by, int k, int n)
 {
     for (int y = st->ye[level][by]; y < st->ye[level][by + 1]; ++y)

@@ -9,8 +9,8 @@
 //                  judge every unit of one parity phase against the state
 //                  at phase start (Sec. 5.2-5.3: Prop. 1 for blocks, Prop. 1 +
 //                  Prop. 2 for pixels); accepted moves update the other state
-//                  buffer at once (Sec. 5.3, "Updating the Color
-//                  Distributions")
+//                  buffer at once (the incremental histogram update of
+//                  Sec. 5.3)
 //   op_catchup     replay the previous phase's moves into the buffer that
 //                  phase read, so both buffers stay one step apart
 //   op_descend     copy block labels to the next finer grid (coarse to fine)
@@ -21,7 +21,7 @@
 // Every step ends in a grid barrier that spins with a time limit; a barrier
 // that runs out sets the error word and every block leaves the kernel.  Work
 // inside a step is dealt to the CTAs in rounds and taken by their warps as
-// they finish.
+// they finish (a step that fits in one round: round-robin over the CTAs).
 #include <cuda_runtime.h>
 
 #include <algorithm>
