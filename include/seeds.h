@@ -151,6 +151,40 @@ int seeds_check_params(const seeds_params *p, int32_t *gx, int32_t *gy);
  * control by footprint).  Host only. */
 int seeds_footprint(const seeds_params *p, int32_t n, int64_t *bytes);
 
+/* One entry of a step schedule (seeds_plan): work of image `img` in one
+ * step, handed to the kernel as `units` units of `group` threads each (1: a
+ * thread per unit, 32: a warp per unit; pixel tiles and init rectangles are
+ * warp units), starting at virtual thread vt_begin of its step.
+ *   op      0 init, 1 phase, 2 descent, 3 output, 4 catch-up (replays the
+ *           moves of op opidx-1 into the buffer that op read), 5 start of
+ *           the means iterations, 6 means phase
+ *   level   the op's level (0 = pixels; a catch-up: the level of op opidx-1)
+ *   phase   parity phase (py*2 + px) of a phase or catch-up entry
+ *   opidx   the image's op number, which selects its state buffers
+ *   cphase  a phase entry whose units first replay the previous phase of
+ *           the same level (that phase's parity), or -1 */
+typedef struct {
+    int32_t img, op, level, phase, opidx, units, group, cphase;
+    int64_t vt_begin;
+} seeds_plan_entry;
+
+/* The step schedule a full run of the n images p[0..n) uses on a GPU with
+ * sm_count SMs, planned on the host alone (no device is touched): one step
+ * per op (the images of a batch share each step), a catch-up entry where a
+ * phase's moves are replayed beside the next op, and the fusion of replays
+ * into block or pixel phases that the step's size calls for.  t: launch
+ * knobs (NULL = defaults; only small_block_area and pixel_tile_rows shape
+ * a schedule).  Always writes *n_entries and *n_steps.  With out,
+ * step_first and step_threads all NULL it stops there; otherwise out[cap]
+ * receives the entries in step order, step_first[step_cap] the index of
+ * every step's first entry and one past the last (step_cap >= *n_steps+1),
+ * and step_threads (if not NULL) every step's padded thread count.
+ * Returns SEEDS_ERR_INVALID for bad parameters or buffers too small, and
+ * seeds_check_params' errors.  Host only. */
+int seeds_plan(const seeds_params *p, int32_t n, const seeds_tuning *t, int32_t sm_count, seeds_plan_entry *out,
+               int32_t cap, int32_t *n_entries, int32_t *step_first, int64_t *step_threads, int32_t step_cap,
+               int32_t *n_steps);
+
 /* Create a context for one image on the current CUDA device: validates the
  * parameters (grid geometry, int64 bound of the exact compares) and
  * allocates all device state.  Host call, synchronous. */

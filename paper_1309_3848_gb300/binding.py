@@ -34,7 +34,8 @@ _NAMES = {0: "SEEDS_OK", -1: "SEEDS_ERR_INVALID", -2: "SEEDS_ERR_GEOMETRY", -3: 
 
 # every entry point of include/seeds.h
 EXPORTS = [
-    "seeds_params_default", "seeds_feasible_levels", "seeds_check_params", "seeds_footprint", "seeds_create",
+    "seeds_params_default", "seeds_feasible_levels", "seeds_check_params", "seeds_footprint", "seeds_plan",
+    "seeds_create",
     "seeds_iterate", "seeds_labels", "seeds_num_superpixels", "seeds_status", "seeds_destroy",
     "seeds_batch_create", "seeds_batch_size", "seeds_batch_num_superpixels", "seeds_batch_iterate",
     "seeds_batch_labels", "seeds_batch_run", "seeds_batch_run_anytime", "seeds_anytime_steps", "seeds_run_host", "seeds_set_tuning", "seeds_get_tuning",
@@ -71,6 +72,12 @@ class seeds_server_stats_t(ctypes.Structure):
                 ("host_ms", ctypes.c_double)]
 
 
+class seeds_plan_entry(ctypes.Structure):
+    _fields_ = [("img", ctypes.c_int32), ("op", ctypes.c_int32), ("level", ctypes.c_int32),
+                ("phase", ctypes.c_int32), ("opidx", ctypes.c_int32), ("units", ctypes.c_int32),
+                ("group", ctypes.c_int32), ("cphase", ctypes.c_int32), ("vt_begin", ctypes.c_int64)]
+
+
 class seeds_tuning(ctypes.Structure):
     _fields_ = [("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("hist_layout", ctypes.c_int32), ("small_block_area", ctypes.c_int32),
@@ -88,6 +95,8 @@ def _load():
         "seeds_feasible_levels": [P(seeds_params), P(i32)],
         "seeds_check_params": [P(seeds_params), P(i32), P(i32)],
         "seeds_footprint": [P(seeds_params), i32, P(i64)],
+        "seeds_plan": [P(seeds_params), i32, P(seeds_tuning), i32, P(seeds_plan_entry), i32, P(i32), P(i32), P(i64),
+                       i32, P(i32)],
         "seeds_create": [P(seeds_params), P(vp)],
         "seeds_iterate": [vp, vp, i64, vp],
         "seeds_labels": [vp, vp, vp],
@@ -156,6 +165,30 @@ def feasible_levels(width, height, num_superpixels) -> int:
     out = ctypes.c_int32()
     check(lib.seeds_feasible_levels(ctypes.byref(p), ctypes.byref(out)), "seeds_feasible_levels")
     return out.value
+
+
+OP_KINDS = {0: "init", 1: "phase", 2: "descend", 3: "output", 4: "catchup", 5: "means_init", 6: "means_phase"}
+
+
+def plan(params: Sequence[seeds_params], sm_count: int, tuning: seeds_tuning = None):
+    """The step schedule a full run of these images uses on a GPU with
+    sm_count SMs, planned on the host (seeds_plan): a list of steps, each a
+    (thread count, [entry dicts]) pair."""
+    arr = (seeds_params * len(params))(*params)
+    tp = ctypes.byref(tuning) if tuning is not None else None
+    ne, ns = ctypes.c_int32(), ctypes.c_int32()
+    check(lib.seeds_plan(arr, len(params), tp, sm_count, None, 0, ctypes.byref(ne), None, None, 0, ctypes.byref(ns)),
+          "seeds_plan")
+    out = (seeds_plan_entry * max(1, ne.value))()
+    first = (ctypes.c_int32 * (ns.value + 1))()
+    threads = (ctypes.c_int64 * max(1, ns.value))()
+    check(lib.seeds_plan(arr, len(params), tp, sm_count, out, ne.value, ctypes.byref(ne), first, threads,
+                         ns.value + 1, ctypes.byref(ns)), "seeds_plan")
+    steps = []
+    for s in range(ns.value):
+        ents = [{f: getattr(out[q], f) for f, _ in seeds_plan_entry._fields_} for q in range(first[s], first[s + 1])]
+        steps.append((threads[s], ents))
+    return steps
 
 
 def check_params(p: seeds_params):

@@ -157,8 +157,10 @@ inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t 
 
 // The device record of an image whose state starts at `base` (laid out as
 // derive() planned), with the given launch knobs and per-call pointers.
-inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const seeds_tuning &t, const IoEntry &io,
-                               int32_t *err)
+// The fields of an image's device record that its op list and step
+// schedule depend on (size, grids, levels, iterations, launch knobs), with
+// no device pointer: enough to plan a schedule on a host without a GPU.
+inline DevImage plan_image(const ImageHost &h, const seeds_tuning &t)
 {
     DevImage d;
     std::memset(&d, 0, sizeof(d));
@@ -169,11 +171,25 @@ inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const se
     d.gy = h.gy;
     d.L = h.L;
     d.iters = h.p.iters_per_level;
+    d.means_iters = h.p.means_iters;
+    d.small_area = t.small_block_area;
+    d.tile_uy = t.pixel_tile_rows == 2 ? 2 : kTileUY;
+    for (int l = 0; l <= h.L; ++l) {
+        d.nbx[l] = h.nbx[l];
+        d.nby[l] = h.nby[l];
+        d.maxarea[l] = h.maxarea[l];
+    }
+    return d;
+}
+
+inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const seeds_tuning &t, const IoEntry &io,
+                               int32_t *err)
+{
+    DevImage d = plan_image(h, t);
     d.B = h.B;
     d.nbins = h.nbins;
     d.patch = h.p.patch;
     d.color = h.p.color_space;
-    d.means_iters = h.p.means_iters;
     // SLIC's (m/S)^2 with S^2 = N/K
     d.means_w = (float)((int64_t)h.p.compactness * h.p.compactness * h.K) / (float)h.N;
     d.edge_tau = h.p.edge_threshold;
@@ -184,12 +200,7 @@ inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const se
     d.hist_jmajor = t.hist_layout == 1;
     d.hist_sk = d.hist_jmajor ? 1 : h.nbins;
     d.hist_sj = d.hist_jmajor ? h.K : 1;
-    d.small_area = t.small_block_area;
-    d.tile_uy = t.pixel_tile_rows == 2 ? 2 : kTileUY;
     for (int l = 0; l <= h.L; ++l) {
-        d.nbx[l] = h.nbx[l];
-        d.nby[l] = h.nby[l];
-        d.maxarea[l] = h.maxarea[l];
         for (int q = 0; q < 2; ++q) d.lab[l][q] = (uint16_t *)(base + h.off_lab[l][q]);
         if (l >= 1) {
             d.xe[l] = (const int32_t *)(base + h.off_xe[l]);
@@ -209,6 +220,45 @@ inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const se
     d.stride = io.stride;
     d.out = io.out;
     return d;
+}
+
+// The step schedule of a set of images: image i runs its ops [b[i], e[i]),
+// one op per step; pend[i] says that the moves of op b[i]-1 are still
+// pending, so its first step catches them up.  Appends the entries of every
+// step to `ent`, the index of each step's first entry to `first` (and one
+// past the last step's), and each step's padded thread count to `vt`.  Each
+// step is planned twice: with every replay fused, to measure it, then with
+// the fusion fuse_step chooses for that size against split_below warps.
+inline void build_steps(const std::vector<DevImage> &imgs, const std::vector<int> &b, const std::vector<int> &e,
+                        const std::vector<char> &pend, int64_t split_below, std::vector<StepEntry> &ent,
+                        std::vector<int32_t> &first, std::vector<int64_t> &vt)
+{
+    const int n = (int)imgs.size();
+    int nsteps = 0;
+    for (int i = 0; i < n; ++i) nsteps = std::max(nsteps, e[i] - b[i]);
+    StepEntry two[2];
+    for (int s = 0; s < nsteps; ++s) {
+        first.push_back((int32_t)ent.size());
+        for (int pass = 0; pass < 2; ++pass) {
+            int64_t v = 0;
+            const int fuse = pass == 0 ? 2 : fuse_step(vt.back(), split_below);
+            for (int i = 0; i < n; ++i) {
+                const DevImage &im = imgs[i];
+                const int o = b[i] + s;
+                if (o >= e[i]) continue;
+                const bool catchup =
+                    s == 0 ? (o > 0 && pend[i]) : is_phase(op_at(im.L, im.iters, im.means_iters, o - 1).kind);
+                const int m = emit_entries(im, i, o, catchup, fuse, two, &v);
+                if (pass == 1)
+                    for (int q = 0; q < m; ++q) ent.push_back(two[q]);
+            }
+            if (pass == 0)
+                vt.push_back(v);
+            else
+                vt.back() = v;
+        }
+    }
+    first.push_back((int32_t)ent.size());
 }
 
 }  // namespace host

@@ -144,29 +144,9 @@ int get_schedule(seeds_ctx *c, int kind, int ob, int oe, const Schedule **out)
     std::vector<StepEntry> ent;
     std::vector<int32_t> first;
     std::vector<int64_t> vt;
-    StepEntry two[2];
-    const int64_t split_below = (int64_t)c->sm_count * 32;
-    for (int s = 0; s < nsteps; ++s) {
-        first.push_back((int32_t)ent.size());
-        for (int pass = 0; pass < 2; ++pass) {  // the fused step's size, then its entries
-            int64_t v = 0;
-            const int fuse = pass == 0 ? 2 : fuse_step(vt.back(), split_below);
-            for (int i = 0; i < n; ++i) {
-                const int o = b[i] + s;
-                if (o >= e[i]) continue;
-                const bool catchup =
-                    s == 0 ? (o > 0 && c->pending[i] == o - 1) : is_phase(c->img[i].ops[o - 1].kind);
-                const int m = emit_entries(c->h_imgs[i], i, o, catchup, fuse, two, &v);
-                if (pass == 1)
-                    for (int q = 0; q < m; ++q) ent.push_back(two[q]);
-            }
-            if (pass == 0)
-                vt.push_back(v);
-            else
-                vt.back() = v;
-        }
-    }
-    first.push_back((int32_t)ent.size());
+    std::vector<char> pend(n);
+    for (int i = 0; i < n; ++i) pend[i] = b[i] > 0 && c->pending[i] == b[i] - 1;
+    build_steps(c->h_imgs, b, e, pend, (int64_t)c->sm_count * 32, ent, first, vt);
     if (ent.empty()) ent.push_back(StepEntry{});  // keep the buffer non-empty
 
     const size_t b_ent = align_up(ent.size() * sizeof(StepEntry));
@@ -378,7 +358,60 @@ int check_io(const seeds_ctx *c, const uint8_t *const *rgb, const int64_t *strid
 // C ABI
 // ===========================================================================
 
+// A tuning with its zero fields at their defaults (threads_per_block stays 0:
+// the largest CTA that fits); SEEDS_ERR_INVALID for a value out of range.
+int normalize_tuning(const seeds_tuning &t, seeds_tuning *out)
+{
+    seeds_tuning n = t;
+    if (n.small_block_area == 0) n.small_block_area = 16;
+    if (n.pixel_tile_rows == 0) n.pixel_tile_rows = 4;
+    if (n.pixel_tile_rows != 2 && n.pixel_tile_rows != 4) return SEEDS_ERR_INVALID;
+    if (n.threads_per_block != 0 && n.threads_per_block != 128 && n.threads_per_block != 256 &&
+        n.threads_per_block != 512 && n.threads_per_block != 1024)
+        return SEEDS_ERR_INVALID;
+    if (n.blocks_per_sm < 0 || n.hist_layout < 0 || n.hist_layout > 1) return SEEDS_ERR_INVALID;
+    if (n.small_block_area < 1 || n.small_block_area > kSmallMax) return SEEDS_ERR_INVALID;
+    *out = n;
+    return SEEDS_OK;
+}
+
 extern "C" {
+
+int seeds_plan(const seeds_params *p, int32_t n, const seeds_tuning *t, int32_t sm_count, seeds_plan_entry *out,
+               int32_t cap, int32_t *n_entries, int32_t *step_first, int64_t *step_threads, int32_t step_cap,
+               int32_t *n_steps)
+{
+    if (!p || n <= 0 || n > SEEDS_MAX_BATCH || sm_count <= 0 || !n_entries || !n_steps || cap < 0 || step_cap < 0)
+        return SEEDS_ERR_INVALID;
+    seeds_tuning tune;
+    if (normalize_tuning(t ? *t : seeds_tuning{0, 0, 0, 0, 0}, &tune)) return SEEDS_ERR_INVALID;
+    std::vector<DevImage> imgs(n);
+    std::vector<int> b(n, 0), e(n);
+    std::vector<char> pend(n, 0);
+    for (int i = 0; i < n; ++i) {
+        ImageHost h;
+        const int rc = derive(&p[i], &h, nullptr, nullptr);
+        if (rc) return rc;
+        imgs[i] = plan_image(h, tune);
+        e[i] = (int)h.ops.size();
+    }
+    std::vector<StepEntry> ent;
+    std::vector<int32_t> first;
+    std::vector<int64_t> vt;
+    build_steps(imgs, b, e, pend, (int64_t)sm_count * 32, ent, first, vt);
+    *n_entries = (int32_t)ent.size();
+    *n_steps = (int32_t)vt.size();
+    if (!out && !step_first && !step_threads) return SEEDS_OK;  // the sizes alone
+    if (!out || !step_first || cap < *n_entries || step_cap < *n_steps + 1) return SEEDS_ERR_INVALID;
+    for (size_t q = 0; q < ent.size(); ++q) {
+        const StepEntry &E = ent[q];
+        out[q] = seeds_plan_entry{E.img, E.op, E.level, E.phase, E.opidx, E.units, E.group, E.cphase, E.vt_begin};
+    }
+    for (size_t s = 0; s < first.size(); ++s) step_first[s] = first[s];
+    if (step_threads)
+        for (size_t s = 0; s < vt.size(); ++s) step_threads[s] = vt[s];
+    return SEEDS_OK;
+}
 
 int seeds_params_default(seeds_params *p, int32_t width, int32_t height, int32_t num_superpixels)
 {
@@ -605,15 +638,8 @@ int seeds_status(seeds_ctx *c)
 int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t)
 {
     if (!c || !t) return SEEDS_ERR_INVALID;
-    seeds_tuning n = *t;
-    if (n.small_block_area == 0) n.small_block_area = 16;
-    if (n.pixel_tile_rows == 0) n.pixel_tile_rows = 4;
-    if (n.pixel_tile_rows != 2 && n.pixel_tile_rows != 4) return SEEDS_ERR_INVALID;
-    if (n.threads_per_block != 0 && n.threads_per_block != 128 && n.threads_per_block != 256 &&
-        n.threads_per_block != 512 && n.threads_per_block != 1024)
-        return SEEDS_ERR_INVALID;
-    if (n.blocks_per_sm < 0 || n.hist_layout < 0 || n.hist_layout > 1) return SEEDS_ERR_INVALID;
-    if (n.small_block_area < 1 || n.small_block_area > 16) return SEEDS_ERR_INVALID;
+    seeds_tuning n;
+    if (normalize_tuning(*t, &n)) return SEEDS_ERR_INVALID;
     if (c->launched) cudaEventSynchronize(c->done);
     const seeds_tuning old = c->tune;
     auto apply = [&](const seeds_tuning &v) {

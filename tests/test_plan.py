@@ -1,0 +1,209 @@
+"""Host logic of the step schedule (seeds_plan, no GPU): every op of every
+image runs once, in order, one op per step; a phase's moves are replayed
+exactly once into the buffer it read (fused into the next phase of the same
+level, or as a catch-up entry beside the next op); the fusion follows the
+step's size; the virtual threads of a step are laid out without gaps."""
+import ctypes
+
+import pytest
+
+from paper_1309_3848_gb300 import binding as b
+from paper_1309_3848_gb300 import synth
+
+INIT, PHASE, DESCEND, OUTPUT, CATCHUP, MINIT, MPHASE = range(7)
+
+
+def op_list(p):
+    """The op list of an image (kind, level, phase), written out from the
+    schedule the paper describes (Sec. 5: block levels L..1, then pixels;
+    iterations of four parity phases per level) and the means iterations."""
+    L, iters = p.block_levels, p.iters_per_level
+    ops = [(INIT, 0, 0)]
+    for level in range(L, -1, -1):
+        for it in range(iters):
+            for ph in range(4):
+                ops.append((PHASE, level, ph))
+        if level > 0:
+            ops.append((DESCEND, level, 0))
+    if p.means_iters > 0:
+        ops.append((MINIT, 0, 0))
+        for it in range(p.means_iters):
+            for ph in range(4):
+                ops.append((MPHASE, 0, ph))
+    ops.append((OUTPUT, 0, 0))
+    return ops
+
+
+def padded(e):
+    return (e["units"] * e["group"] + 31) // 32 * 32
+
+
+def grid(p):
+    rc, gx, gy = b.check_params(p)
+    assert rc == 0
+    L = p.block_levels
+    return [(gx << (L - l + 1), gy << (L - l + 1)) if l > 0 else (p.width, p.height) for l in range(L + 1)]
+
+
+def lattice(nx, ny, phase):
+    px, py = phase & 1, phase >> 1
+    return (nx - px + 1) >> 1, (ny - py + 1) >> 1
+
+
+def params_of(job):
+    L = min(job.levels, b.feasible_levels(job.image.width, job.image.height, job.num_superpixels))
+    return b.make_params(job.image.width, job.image.height, job.num_superpixels, L, job.bins_per_channel,
+                         job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters,
+                         job.compactness, job.edge_threshold)
+
+
+CASES = {
+    "1080p": [params_of(synth.plain_1080()[0])],
+    "481": [params_of(synth.plain_481()[0])],
+    "means": [b.make_params(200, 150, 60, 2, 5, 2, means_iters=2, compactness=10)],
+    "L0": [b.make_params(64, 48, 12, 0, 5, 3)],
+    "batch": [params_of(j) for j in synth.random_small_jobs(5, 12, max_side=300)],
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("sms", [1, 152, 1 << 20])
+def test_every_op_runs_once_in_order_and_every_phase_is_replayed_once(case, sms):
+    ps = CASES[case]
+    steps = b.plan(ps, sms)
+    ops = [op_list(p) for p in ps]
+    assert len(steps) == max(len(o) for o in ops)
+    seen = [[] for _ in ps]
+    replayed = [set() for _ in ps]
+    for s, (threads, ents) in enumerate(steps):
+        for e in ents:
+            i = e["img"]
+            if e["op"] == CATCHUP:
+                kind, level, phase = ops[i][e["opidx"] - 1]
+                assert kind in (PHASE, MPHASE) and (e["level"], e["phase"]) == (level, phase)
+                assert e["opidx"] == s
+                replayed[i].add(e["opidx"] - 1)
+                continue
+            assert e["opidx"] == s, "image %d runs op %d at step %d" % (i, e["opidx"], s)
+            assert (e["op"], e["level"]) == ops[i][s][:2]
+            if e["op"] in (PHASE, MPHASE):
+                assert e["phase"] == ops[i][s][2]
+            if e["cphase"] >= 0:  # fused: the previous op is a phase of the same kind and level
+                kind, level, phase = ops[i][s - 1]
+                assert (kind, level, phase) == (e["op"], e["level"], e["cphase"])
+                replayed[i].add(s - 1)
+            seen[i].append(s)
+    for i, o in enumerate(ops):
+        assert seen[i] == list(range(len(o)))
+        phases = {s for s, (kind, _, _) in enumerate(o) if kind in (PHASE, MPHASE)}
+        assert replayed[i] == phases, "phases never replayed: %s" % sorted(phases - replayed[i])
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_virtual_threads_are_laid_out_without_gaps(case):
+    for threads, ents in b.plan(CASES[case], 152):
+        at = 0
+        for e in ents:
+            assert e["vt_begin"] == at and e["group"] in (1, 32) and e["units"] > 0
+            at += padded(e)
+        assert threads == at
+
+
+def test_units_follow_the_lattices():
+    p = CASES["1080p"][0]
+    g = grid(p)
+    for threads, ents in b.plan([p], 152):
+        for e in ents:
+            if e["op"] not in (PHASE, CATCHUP) or e["level"] == 0:
+                continue
+            nx, ny = g[e["level"]]
+            cols, rows = lattice(nx, ny, e["phase"])
+            if e["cphase"] >= 0:  # the union of both phases' lattices
+                c2, r2 = lattice(nx, ny, e["cphase"])
+                cols, rows = max(cols, c2), max(rows, r2)
+            assert e["units"] == cols * rows
+    # pixel phases: warp tiles of 32 x 4 (or 32 x 2) units
+    for rows_per_tile in (4, 2):
+        t = b.seeds_tuning(0, 0, 0, 16, rows_per_tile)
+        for threads, ents in b.plan([p], 1, t):  # one SM: every step fused
+            for e in ents:
+                if e["op"] == PHASE and e["level"] == 0:
+                    cols, rows = lattice(p.width, p.height, e["phase"])
+                    if e["cphase"] >= 0:
+                        c2, r2 = lattice(p.width, p.height, e["cphase"])
+                        cols, rows = max(cols, c2), max(rows, r2)
+                    assert e["units"] == -(-cols // 32) * -(-rows // rows_per_tile)
+
+
+def test_fusion_follows_the_step_size():
+    """Below the machine's warp slots (sms x 32) block phases replay in
+    catch-up entries; pixel phases only below an eighth of that."""
+    p = CASES["1080p"][0]
+    ops = op_list(p)
+    for sms, fused in ((1, True), (1 << 20, False)):  # 32 warp slots; 33.5 M warp slots
+        for threads, ents in b.plan([p], sms):
+            for e in ents:
+                if e["op"] == PHASE and ops[e["opidx"] - 1][:2] == (PHASE, e["level"]):
+                    assert (e["cphase"] >= 0) == fused, (sms, e)
+    # one 1080p image on 152 SMs (4,864 warp slots): level 4 (1,008 warps of
+    # 484 px) and level 1 split, level 2 (16,128 warps) stays fused, and the
+    # pixel phases (4,050 tiles, above 608) stay fused
+    by_level = {}
+    for threads, ents in b.plan([p], 152):
+        for e in ents:
+            if e["op"] == PHASE and e["phase"] != 0:
+                by_level.setdefault(e["level"], set()).add(e["cphase"] >= 0)
+    assert by_level == {4: {False}, 3: {False}, 2: {True}, 1: {False}, 0: {True}}
+    # the 481x321 image's pixel phases (302 tiles) are below 608: split
+    small = CASES["481"][0]
+    pix = {e["cphase"] >= 0 for _, ents in b.plan([small], 152) for e in ents
+           if e["op"] == PHASE and e["level"] == 0 and e["phase"] != 0}
+    assert pix == {False}
+
+
+def test_small_blocks_take_a_thread_each():
+    p = CASES["481"][0]
+    g = grid(p)
+    W, H = p.width, p.height
+
+    def maxarea(level):
+        nx, ny = g[level]
+        w = max((i + 1) * W // nx - i * W // nx for i in range(nx))
+        h = max((i + 1) * H // ny - i * H // ny for i in range(ny))
+        return w * h
+
+    for area in (1, 4, 9, 16):
+        t = b.seeds_tuning(0, 0, 0, area, 4)
+        for _, ents in b.plan([p], 152, t):
+            for e in ents:
+                if e["op"] in (PHASE, CATCHUP) and e["level"] > 0:
+                    assert e["group"] == (1 if maxarea(e["level"]) <= area else 32)
+
+
+def test_a_batch_shares_every_step():
+    ps = CASES["batch"]
+    steps = b.plan(ps, 152)
+    for s, (_, ents) in enumerate(steps):
+        imgs = {e["img"] for e in ents if e["op"] != CATCHUP}
+        assert imgs == {i for i, p in enumerate(ps) if len(op_list(p)) > s}
+
+
+def test_bad_inputs():
+    p = CASES["481"][0]
+    arr = (b.seeds_params * 1)(p)
+    ne, ns = ctypes.c_int32(), ctypes.c_int32()
+    assert b.lib.seeds_plan(arr, 0, None, 152, None, 0, ctypes.byref(ne), None, None, 0, ctypes.byref(ns)) == \
+        b.SEEDS_ERR_INVALID
+    assert b.lib.seeds_plan(arr, 1, None, 0, None, 0, ctypes.byref(ne), None, None, 0, ctypes.byref(ns)) == \
+        b.SEEDS_ERR_INVALID
+    assert b.lib.seeds_plan(arr, 1, None, 152, None, 0, ctypes.byref(ne), None, None, 0, ctypes.byref(ns)) == 0
+    small = (b.seeds_plan_entry * 1)()
+    first = (ctypes.c_int32 * 2)()
+    assert b.lib.seeds_plan(arr, 1, None, 152, small, 1, ctypes.byref(ne), first, None, 2, ctypes.byref(ns)) == \
+        b.SEEDS_ERR_INVALID
+    bad_tuning = b.seeds_tuning(0, 0, 0, 17, 4)
+    assert b.lib.seeds_plan(arr, 1, ctypes.byref(bad_tuning), 152, None, 0, ctypes.byref(ne), None, None, 0,
+                            ctypes.byref(ns)) == b.SEEDS_ERR_INVALID
+    geo = (b.seeds_params * 1)(b.make_params(16, 16, 4, 4, 5, 1))
+    assert b.lib.seeds_plan(geo, 1, None, 152, None, 0, ctypes.byref(ne), None, None, 0, ctypes.byref(ns)) == \
+        b.SEEDS_ERR_GEOMETRY
