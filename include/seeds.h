@@ -272,6 +272,16 @@ int seeds_run_host(seeds_ctx *c, const uint8_t *const *h_rgb, const int64_t *h_r
 
 /* Launch knobs; see seeds_tuning. */
 int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t);
+
+/* The search seeds_autotune runs, with the timing supplied by the caller:
+ * coordinate descent from *start over threads_per_block {128, 256, 512,
+ * 1024}, blocks_per_sm {0..3}, hist_layout {0, 1}, small_block_area {4, 9,
+ * 16} and pixel_tile_rows {2, 4}, in that order, one pass; a value is kept
+ * only if cost() reports it at least 2% faster than the current setting.
+ * cost returns milliseconds (a huge value for a setting that cannot run).
+ * Writes the setting found to *best.  Host only; no device is touched. */
+typedef float (*seeds_tune_cost_fn)(const seeds_tuning *t, void *user);
+int seeds_tune_search(const seeds_tuning *start, seeds_tune_cost_fn cost, void *user, seeds_tuning *best);
 int seeds_get_tuning(const seeds_ctx *c, seeds_tuning *t);
 
 /* Pick the fastest result-invariant knobs for this context's images by

@@ -39,6 +39,7 @@ EXPORTS = [
     "seeds_iterate", "seeds_labels", "seeds_num_superpixels", "seeds_status", "seeds_destroy",
     "seeds_batch_create", "seeds_batch_size", "seeds_batch_num_superpixels", "seeds_batch_iterate",
     "seeds_batch_labels", "seeds_batch_run", "seeds_batch_run_anytime", "seeds_anytime_steps", "seeds_run_host", "seeds_set_tuning", "seeds_get_tuning",
+    "seeds_tune_search",
     "seeds_debug_num_ops", "seeds_debug_op_info", "seeds_debug_run_ops", "seeds_debug_read_state",
     "seeds_debug_set_labels", "seeds_debug_inject_error", "seeds_debug_launch_count", "seeds_profile_enable",
     "seeds_profile_last_ms", "seeds_profile_steps", "seeds_run_static", "seeds_autotune",
@@ -84,6 +85,9 @@ class seeds_tuning(ctypes.Structure):
                 ("pixel_tile_rows", ctypes.c_int32)]
 
 
+TUNE_COST_FN = ctypes.CFUNCTYPE(ctypes.c_float, ctypes.POINTER(seeds_tuning), ctypes.c_void_p)
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libseeds.so is not built (expected at %s); run __graft_entry__.build()" % LIB_PATH)
@@ -114,6 +118,7 @@ def _load():
         "seeds_run_host": [vp, P(vp), P(i64), P(vp), vp],
         "seeds_set_tuning": [vp, P(seeds_tuning)],
         "seeds_get_tuning": [vp, P(seeds_tuning)],
+        "seeds_tune_search": [P(seeds_tuning), TUNE_COST_FN, vp, P(seeds_tuning)],
         "seeds_debug_num_ops": [vp, i32, P(i32)],
         "seeds_debug_op_info": [vp, i32, i32, P(i32), P(i32), P(i32)],
         "seeds_debug_run_ops": [vp, P(vp), P(i64), i32, i32, vp],
@@ -165,6 +170,15 @@ def feasible_levels(width, height, num_superpixels) -> int:
     out = ctypes.c_int32()
     check(lib.seeds_feasible_levels(ctypes.byref(p), ctypes.byref(out)), "seeds_feasible_levels")
     return out.value
+
+
+def tune_search(start: seeds_tuning, cost) -> seeds_tuning:
+    """The autotuner's search (seeds_tune_search) with a Python cost: cost
+    takes a seeds_tuning and returns milliseconds."""
+    fn = TUNE_COST_FN(lambda t, _user: float(cost(t.contents)))
+    best = seeds_tuning()
+    check(lib.seeds_tune_search(ctypes.byref(start), fn, None, ctypes.byref(best)), "seeds_tune_search")
+    return best
 
 
 OP_KINDS = {0: "init", 1: "phase", 2: "descend", 3: "output", 4: "catchup", 5: "means_init", 6: "means_phase"}

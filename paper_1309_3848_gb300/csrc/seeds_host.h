@@ -222,6 +222,44 @@ inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const se
     return d;
 }
 
+// The autotuner's search: coordinate descent over the result-invariant
+// launch knobs (threads per CTA, CTAs per SM, histogram layout, small-block
+// area, pixel tile rows), one pass in that order, from `start`.  cost(t, &ms)
+// times a setting (ms = +inf if it cannot run; a nonzero return aborts the
+// search with that status); a value replaces the current one only if it is
+// at least 2% faster, so timing noise does not move the setting.
+template <class Cost>
+inline int tune_search(const seeds_tuning &start, Cost cost, seeds_tuning *best)
+{
+    seeds_tuning cur = start;
+    float cur_ms = 0.f;
+    int rc = cost(cur, &cur_ms);
+    const int threads[] = {128, 256, 512, 1024}, blocks[] = {0, 1, 2, 3}, layouts[] = {0, 1}, areas[] = {4, 9, 16},
+              rows[] = {2, 4};
+    for (int knob = 0; knob < 5 && !rc; ++knob) {
+        const int *vals = knob == 0 ? threads : knob == 1 ? blocks : knob == 2 ? layouts : knob == 3 ? areas : rows;
+        const int nv = knob == 0 ? 4 : knob == 1 ? 4 : knob == 2 ? 2 : knob == 3 ? 3 : 2;
+        for (int v = 0; v < nv && !rc; ++v) {
+            seeds_tuning t = cur;
+            int *field = knob == 0   ? &t.threads_per_block
+                         : knob == 1 ? &t.blocks_per_sm
+                         : knob == 2 ? &t.hist_layout
+                         : knob == 3 ? &t.small_block_area
+                                     : &t.pixel_tile_rows;
+            if (*field == vals[v]) continue;
+            *field = vals[v];
+            float ms = 0.f;
+            rc = cost(t, &ms);
+            if (!rc && ms < 0.98f * cur_ms) {
+                cur = t;
+                cur_ms = ms;
+            }
+        }
+    }
+    *best = cur;
+    return rc;
+}
+
 // The step schedule of a set of images: image i runs its ops [b[i], e[i]),
 // one op per step; pend[i] says that the moves of op b[i]-1 are still
 // pending, so its first step catches them up.  Appends the entries of every

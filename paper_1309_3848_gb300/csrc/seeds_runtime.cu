@@ -693,36 +693,24 @@ int seeds_autotune(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t
         return r;
     };
     seeds_tuning cur = c->tune;
-    float cur_ms = 0.f;
-    if (!rc) rc = time_it(cur, &cur_ms);
-    // coordinate descent, one pass over the knobs; a change must win by 2%
-    const int threads[] = {128, 256, 512, 1024}, blocks[] = {0, 1, 2, 3}, layouts[] = {0, 1}, areas[] = {4, 9, 16},
-              rows[] = {2, 4};
-    for (int knob = 0; knob < 5 && !rc; ++knob) {
-        const int *vals = knob == 0 ? threads : knob == 1 ? blocks : knob == 2 ? layouts : knob == 3 ? areas : rows;
-        const int nv = knob == 0 ? 4 : knob == 1 ? 4 : knob == 2 ? 2 : knob == 3 ? 3 : 2;
-        for (int v = 0; v < nv && !rc; ++v) {
-            seeds_tuning t = cur;
-            int *field = knob == 0   ? &t.threads_per_block
-                         : knob == 1 ? &t.blocks_per_sm
-                         : knob == 2 ? &t.hist_layout
-                         : knob == 3 ? &t.small_block_area
-                                     : &t.pixel_tile_rows;
-            if (*field == vals[v]) continue;
-            *field = vals[v];
-            float ms = 0.f;
-            rc = time_it(t, &ms);
-            if (!rc && ms < 0.98f * cur_ms) {
-                cur = t;
-                cur_ms = ms;
-            }
-        }
-    }
+    if (!rc) rc = tune_search(c->tune, time_it, &cur);  // coordinate descent, one pass; a change must win by 2%
     if (!rc) rc = seeds_set_tuning(c, &cur);
     if (!rc && best) *best = cur;
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
     return rc;
+}
+
+int seeds_tune_search(const seeds_tuning *start, seeds_tune_cost_fn cost, void *user, seeds_tuning *best)
+{
+    if (!start || !cost || !best) return SEEDS_ERR_INVALID;
+    return tune_search(
+        *start,
+        [&](const seeds_tuning &t, float *ms) {
+            *ms = cost(&t, user);
+            return SEEDS_OK;
+        },
+        best);
 }
 
 int seeds_get_tuning(const seeds_ctx *c, seeds_tuning *t)
