@@ -168,22 +168,25 @@ typedef struct {
     int64_t vt_begin;
 } seeds_plan_entry;
 
-/* The step schedule a full run of the n images p[0..n) uses on a GPU with
+/* The step schedule a launch over the n images p[0..n) uses on a GPU with
  * sm_count SMs, planned on the host alone (no device is touched): one step
  * per op (the images of a batch share each step), a catch-up entry where a
  * phase's moves are replayed beside the next op, and the fusion of replays
- * into block or pixel phases that the step's size calls for.  t: launch
- * knobs (NULL = defaults; only small_block_area and pixel_tile_rows shape
- * a schedule).  Always writes *n_entries and *n_steps.  With out,
+ * into block or pixel phases that the step's size calls for.  Image i runs
+ * its ops [op_begin[i], op_end[i]) (NULL = from the first op / to the last:
+ * a full run); a range that starts after a phase catches up that phase's
+ * moves first, as a launch resuming a stopped run does.  t: launch knobs
+ * (NULL = defaults; only small_block_area and pixel_tile_rows shape a
+ * schedule).  Always writes *n_entries and *n_steps.  With out,
  * step_first and step_threads all NULL it stops there; otherwise out[cap]
  * receives the entries in step order, step_first[step_cap] the index of
  * every step's first entry and one past the last (step_cap >= *n_steps+1),
  * and step_threads (if not NULL) every step's padded thread count.
  * Returns SEEDS_ERR_INVALID for bad parameters or buffers too small, and
  * seeds_check_params' errors.  Host only. */
-int seeds_plan(const seeds_params *p, int32_t n, const seeds_tuning *t, int32_t sm_count, seeds_plan_entry *out,
-               int32_t cap, int32_t *n_entries, int32_t *step_first, int64_t *step_threads, int32_t step_cap,
-               int32_t *n_steps);
+int seeds_plan(const seeds_params *p, int32_t n, const seeds_tuning *t, int32_t sm_count, const int32_t *op_begin,
+               const int32_t *op_end, seeds_plan_entry *out, int32_t cap, int32_t *n_entries, int32_t *step_first,
+               int64_t *step_threads, int32_t step_cap, int32_t *n_steps);
 
 /* Create a context for one image on the current CUDA device: validates the
  * parameters (grid geometry, int64 bound of the exact compares) and

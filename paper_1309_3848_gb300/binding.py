@@ -99,8 +99,8 @@ def _load():
         "seeds_feasible_levels": [P(seeds_params), P(i32)],
         "seeds_check_params": [P(seeds_params), P(i32), P(i32)],
         "seeds_footprint": [P(seeds_params), i32, P(i64)],
-        "seeds_plan": [P(seeds_params), i32, P(seeds_tuning), i32, P(seeds_plan_entry), i32, P(i32), P(i32), P(i64),
-                       i32, P(i32)],
+        "seeds_plan": [P(seeds_params), i32, P(seeds_tuning), i32, P(i32), P(i32), P(seeds_plan_entry), i32, P(i32),
+                       P(i32), P(i64), i32, P(i32)],
         "seeds_create": [P(seeds_params), P(vp)],
         "seeds_iterate": [vp, vp, i64, vp],
         "seeds_labels": [vp, vp, vp],
@@ -184,19 +184,23 @@ def tune_search(start: seeds_tuning, cost) -> seeds_tuning:
 OP_KINDS = {0: "init", 1: "phase", 2: "descend", 3: "output", 4: "catchup", 5: "means_init", 6: "means_phase"}
 
 
-def plan(params: Sequence[seeds_params], sm_count: int, tuning: seeds_tuning = None):
-    """The step schedule a full run of these images uses on a GPU with
+def plan(params: Sequence[seeds_params], sm_count: int, tuning: seeds_tuning = None, op_begin=None, op_end=None):
+    """The step schedule a launch over these images uses on a GPU with
     sm_count SMs, planned on the host (seeds_plan): a list of steps, each a
-    (thread count, [entry dicts]) pair."""
-    arr = (seeds_params * len(params))(*params)
+    (thread count, [entry dicts]) pair.  op_begin / op_end: per image, the
+    ops the launch runs (None = a full run)."""
+    n = len(params)
+    arr = (seeds_params * n)(*params)
     tp = ctypes.byref(tuning) if tuning is not None else None
+    ob = (ctypes.c_int32 * n)(*op_begin) if op_begin is not None else None
+    oe = (ctypes.c_int32 * n)(*op_end) if op_end is not None else None
     ne, ns = ctypes.c_int32(), ctypes.c_int32()
-    check(lib.seeds_plan(arr, len(params), tp, sm_count, None, 0, ctypes.byref(ne), None, None, 0, ctypes.byref(ns)),
+    check(lib.seeds_plan(arr, n, tp, sm_count, ob, oe, None, 0, ctypes.byref(ne), None, None, 0, ctypes.byref(ns)),
           "seeds_plan")
     out = (seeds_plan_entry * max(1, ne.value))()
     first = (ctypes.c_int32 * (ns.value + 1))()
     threads = (ctypes.c_int64 * max(1, ns.value))()
-    check(lib.seeds_plan(arr, len(params), tp, sm_count, out, ne.value, ctypes.byref(ne), first, threads,
+    check(lib.seeds_plan(arr, n, tp, sm_count, ob, oe, out, ne.value, ctypes.byref(ne), first, threads,
                          ns.value + 1, ctypes.byref(ns)), "seeds_plan")
     steps = []
     for s in range(ns.value):

@@ -377,9 +377,9 @@ int normalize_tuning(const seeds_tuning &t, seeds_tuning *out)
 
 extern "C" {
 
-int seeds_plan(const seeds_params *p, int32_t n, const seeds_tuning *t, int32_t sm_count, seeds_plan_entry *out,
-               int32_t cap, int32_t *n_entries, int32_t *step_first, int64_t *step_threads, int32_t step_cap,
-               int32_t *n_steps)
+int seeds_plan(const seeds_params *p, int32_t n, const seeds_tuning *t, int32_t sm_count, const int32_t *op_begin,
+               const int32_t *op_end, seeds_plan_entry *out, int32_t cap, int32_t *n_entries, int32_t *step_first,
+               int64_t *step_threads, int32_t step_cap, int32_t *n_steps)
 {
     if (!p || n <= 0 || n > SEEDS_MAX_BATCH || sm_count <= 0 || !n_entries || !n_steps || cap < 0 || step_cap < 0)
         return SEEDS_ERR_INVALID;
@@ -393,7 +393,12 @@ int seeds_plan(const seeds_params *p, int32_t n, const seeds_tuning *t, int32_t 
         const int rc = derive(&p[i], &h, nullptr, nullptr);
         if (rc) return rc;
         imgs[i] = plan_image(h, tune);
-        e[i] = (int)h.ops.size();
+        const int nops = (int)h.ops.size();
+        b[i] = op_begin ? op_begin[i] : 0;
+        e[i] = op_end ? op_end[i] : nops;
+        if (b[i] < 0 || e[i] < b[i] || e[i] > nops) return SEEDS_ERR_INVALID;
+        // a launch that starts after a phase has that phase's moves pending
+        pend[i] = b[i] > 0 && is_phase(h.ops[b[i] - 1].kind);
     }
     std::vector<StepEntry> ent;
     std::vector<int32_t> first;

@@ -192,18 +192,49 @@ def test_bad_inputs():
     p = CASES["481"][0]
     arr = (b.seeds_params * 1)(p)
     ne, ns = ctypes.c_int32(), ctypes.c_int32()
-    assert b.lib.seeds_plan(arr, 0, None, 152, None, 0, ctypes.byref(ne), None, None, 0, ctypes.byref(ns)) == \
-        b.SEEDS_ERR_INVALID
-    assert b.lib.seeds_plan(arr, 1, None, 0, None, 0, ctypes.byref(ne), None, None, 0, ctypes.byref(ns)) == \
-        b.SEEDS_ERR_INVALID
-    assert b.lib.seeds_plan(arr, 1, None, 152, None, 0, ctypes.byref(ne), None, None, 0, ctypes.byref(ns)) == 0
+
+    def call(params, n, tuning, sms, ob=None, oe=None, out=None, cap=0, first=None, step_cap=0):
+        return b.lib.seeds_plan(params, n, tuning, sms, ob, oe, out, cap, ctypes.byref(ne), first, None, step_cap,
+                                ctypes.byref(ns))
+
+    assert call(arr, 0, None, 152) == b.SEEDS_ERR_INVALID
+    assert call(arr, 1, None, 0) == b.SEEDS_ERR_INVALID
+    assert call(arr, 1, None, 152) == 0
     small = (b.seeds_plan_entry * 1)()
     first = (ctypes.c_int32 * 2)()
-    assert b.lib.seeds_plan(arr, 1, None, 152, small, 1, ctypes.byref(ne), first, None, 2, ctypes.byref(ns)) == \
-        b.SEEDS_ERR_INVALID
+    assert call(arr, 1, None, 152, out=small, cap=1, first=first, step_cap=2) == b.SEEDS_ERR_INVALID
     bad_tuning = b.seeds_tuning(0, 0, 0, 17, 4)
-    assert b.lib.seeds_plan(arr, 1, ctypes.byref(bad_tuning), 152, None, 0, ctypes.byref(ne), None, None, 0,
-                            ctypes.byref(ns)) == b.SEEDS_ERR_INVALID
+    assert call(arr, 1, ctypes.byref(bad_tuning), 152) == b.SEEDS_ERR_INVALID
+    nops = len(op_list(p))
+    for ob, oe in ((-1, 3), (5, 4), (0, nops + 1)):
+        assert call(arr, 1, None, 152, (ctypes.c_int32 * 1)(ob), (ctypes.c_int32 * 1)(oe)) == b.SEEDS_ERR_INVALID
     geo = (b.seeds_params * 1)(b.make_params(16, 16, 4, 4, 5, 1))
-    assert b.lib.seeds_plan(geo, 1, None, 152, None, 0, ctypes.byref(ne), None, None, 0, ctypes.byref(ns)) == \
-        b.SEEDS_ERR_GEOMETRY
+    assert call(geo, 1, None, 152) == b.SEEDS_ERR_GEOMETRY
+
+
+@pytest.mark.parametrize("case", ["1080p", "means", "batch"])
+def test_a_run_split_into_launches_runs_every_op_once(case):
+    """Launches that stop at chosen ops and resume there (anytime stops,
+    op ranges) together run every op once, in order, and replay every phase
+    once: a launch that starts after a phase catches its moves up first."""
+    ps = CASES[case]
+    ops = [op_list(p) for p in ps]
+    cuts = sorted({0, 1, 5, 17, 40, 41, 60, max(len(o) for o in ops)})
+    seen = [[] for _ in ps]
+    replayed = [set() for _ in ps]
+    for lo, hi in zip(cuts, cuts[1:]):
+        ob = [min(lo, len(o)) for o in ops]
+        oe = [min(hi, len(o)) for o in ops]
+        for s, (_, ents) in enumerate(b.plan(ps, 152, op_begin=ob, op_end=oe)):
+            for e in ents:
+                i = e["img"]
+                if e["op"] == CATCHUP:
+                    replayed[i].add(e["opidx"] - 1)
+                    continue
+                assert e["opidx"] == ob[i] + s
+                if e["cphase"] >= 0:
+                    replayed[i].add(e["opidx"] - 1)
+                seen[i].append(e["opidx"])
+    for i, o in enumerate(ops):
+        assert seen[i] == list(range(len(o)))
+        assert replayed[i] == {s for s, (kind, _, _) in enumerate(o) if kind in (PHASE, MPHASE)}
