@@ -176,18 +176,25 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
-    """DRAM bytes per launch of the persistent kernel from an ncu capture,
-    only while the kernel sources are unchanged since that capture."""
+def recorded_capture(workload):
+    """The ncu record of the persistent kernel on this workload
+    (profiles/traffic.json), only while the kernel sources are unchanged
+    since that capture; else an empty dict."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f).get(workload)
     except (OSError, ValueError):
-        return None
+        return {}
     if not rec or rec.get("kernel_sources") != kernel_source_hash():
-        return None
-    return rec.get("dram_bytes_per_launch")
+        return {}
+    return rec
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch of the persistent kernel from an ncu capture
+    (None unless the capture is of the current kernel sources)."""
+    return recorded_capture(workload).get("dram_bytes_per_launch")
 
 
 # ---------------------------------------------------------------------------
@@ -568,6 +575,7 @@ def run_gpu(args):
     stream_bytes = sum(j.pixels * (B_MIN_PER_PX + bb + (p.block_levels + 1) * j.iters_per_level * (bb + 2))
                        for j, p in zip(jobs, params))
     traffic = recorded_traffic(args.workload)
+    issue = recorded_capture(args.workload).get("issue_active_pct")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -580,7 +588,10 @@ def run_gpu(args):
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": bytes_min, "kernel_ms": kms,
                      "stream_model_bytes_per_launch": stream_bytes,
-                     "stream_model_frac": stream_bytes / (kms / 1e3) / 1e9 / peak},
+                     "stream_model_frac": stream_bytes / (kms / 1e3) / 1e9 / peak,
+                     # the path is issue- and latency-bound: the fraction of the SMs'
+                     # instruction issue slots used, from the same capture as traffic
+                     "issue_active_frac": None if issue is None else issue / 100.0},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": sum(3 * j.pixels for j in jobs),
                 "d2h_bytes_per_step": sum(4 * j.pixels for j in jobs), "labels_identical": bool(e2e_identical)},
         "clocks": clocks,
