@@ -54,6 +54,10 @@
  *       f_stay = D*c_{Ak\p}(j) + gamma*G_k, D = N^4 = 81, where
  *       G_x = sum_{i in K_p} b_{N_i}(x) in counts (Prop. 2); blocks use the
  *       intersection alone (no G, Sec. 5.3).
+ *   R11 (tests only) the paper's Prop. 1 agreement figures (Sec. 5.3,
+ *       6.2) are two different poolings; they serve as a loose band.
+ *   R12 s_t, described in Sec. 5 as the partition of lowest energy found,
+ *       is the highest: the method maximises the energy.
  *   R13 K_p and N_i contain in-image pixels only.
  *   R16 colour space LAB (Sec. 6.2), optional: the bins of R1 taken over
  *       the 8-bit CIE L*a*b* code of each pixel (sRGB, D65; L* scaled by
