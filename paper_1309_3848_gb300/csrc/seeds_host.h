@@ -20,18 +20,27 @@ struct Op {
     int kind, level, phase;
 };
 
-struct ImageHost {
+// The heap-free description of one image: its parameters, the grid and
+// block levels derived from them, and the byte offsets of its device state
+// inside one allocation (or inside the static scratch of seeds_run_static).
+struct ImageCore {
     seeds_params p{};
     int gx = 0, gy = 0, K = 0, L = 0, B = 0, nbins = 0;
     int64_t N = 0;
     int nbx[kMaxLevels + 1] = {}, nby[kMaxLevels + 1] = {};
-    std::vector<int32_t> xe[kMaxLevels + 1], ye[kMaxLevels + 1];
     int maxarea[kMaxLevels + 1] = {};
-    std::vector<Op> ops;  // full list, output op last
+    int nops = 0;
     int units_cap = 0;
-    // byte offsets inside the context's pool
+    // byte offsets of the state, from the image's base address
     size_t off_bins = 0, off_lab[kMaxLevels + 1][2] = {}, off_xe[kMaxLevels + 1] = {}, off_ye[kMaxLevels + 1] = {};
     size_t off_hist[2] = {}, off_size[2] = {}, off_dec[2] = {}, off_msum[2] = {}, off_edges = 0, bytes = 0;
+};
+
+// An image of a context or of the server: the core plus its block edge
+// tables (uploaded once) and its op list.
+struct ImageHost : ImageCore {
+    std::vector<int32_t> xe[kMaxLevels + 1], ye[kMaxLevels + 1];
+    std::vector<Op> ops;  // full list, output op last
 };
 
 constexpr size_t kAlign = 256;
@@ -47,8 +56,10 @@ inline int from_cuda(cudaError_t e)
 // Validate one image's parameters and derive its grid (gx, gy) and block
 // levels: gx = max(1, round(sqrt(K*W/H))), gy = max(1, round(K/gx)), level-l
 // edges floor(i*W/(gx*2^(L-l+1))) (Sec. 5.1).  Checks the int64 bound of the
-// exact compares.  Fills the host image record when `g` is given.
-inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t *gy_out)
+// exact compares and lays out the image's device state.  Allocates nothing:
+// the allocation-free entry point runs it as it is.  gx_out / gy_out receive
+// the grid as soon as it is known (also when the levels do not fit).
+inline int derive_core(const seeds_params *p, ImageCore *g, int32_t *gx_out, int32_t *gy_out)
 {
     if (!p) return SEEDS_ERR_INVALID;
     if (p->width < 1 || p->height < 1 || p->width > 32768 || p->height > 32768) return SEEDS_ERR_INVALID;
@@ -75,8 +86,8 @@ inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t 
     const int L = p->block_levels;
     if ((gx << L) > p->width || (gy << L) > p->height) return SEEDS_ERR_GEOMETRY;
 
-    ImageHost local;
-    ImageHost &h = g ? *g : local;
+    ImageCore local;
+    ImageCore &h = g ? *g : local;
     h.p = *p;
     h.gx = (int)gx;
     h.gy = (int)gy;
@@ -92,17 +103,11 @@ inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t 
     for (int l = 1; l <= L; ++l) {
         h.nbx[l] = (int)(gx << (L - l + 1));
         h.nby[l] = (int)(gy << (L - l + 1));
-        h.xe[l].resize(h.nbx[l] + 1);
-        h.ye[l].resize(h.nby[l] + 1);
-        int mw = 0, mh = 0;
-        for (int i = 0; i <= h.nbx[l]; ++i) {
-            h.xe[l][i] = (int32_t)((int64_t)i * p->width / h.nbx[l]);
-            if (i) mw = std::max(mw, h.xe[l][i] - h.xe[l][i - 1]);
-        }
-        for (int i = 0; i <= h.nby[l]; ++i) {
-            h.ye[l][i] = (int32_t)((int64_t)i * p->height / h.nby[l]);
-            if (i) mh = std::max(mh, h.ye[l][i] - h.ye[l][i - 1]);
-        }
+        // floor edges floor(i*W/n) give widths floor(W/n) and ceil(W/n); the
+        // widths add up to W, so ceil(W/n) occurs whenever n does not divide
+        // W: the widest block spans ceil(W/n) columns, the tallest
+        // ceil(H/n) rows, and blocks form a tensor product
+        const int mw = (p->width + h.nbx[l] - 1) / h.nbx[l], mh = (p->height + h.nby[l] - 1) / h.nby[l];
         h.maxarea[l] = mw * mh;
         amax = std::max(amax, mw * mh);
     }
@@ -112,18 +117,12 @@ inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t 
     const __int128 lim = ((__int128)1) << 63;
     if ((__int128)amax * N2 >= lim) return SEEDS_ERR_INT64;
     if ((__int128)(81 * p->gamma_den + 90 * p->gamma_num) * N2 >= lim) return SEEDS_ERR_INT64;
-
-    // op list (the same one the kernels derive with op_at)
-    h.ops.clear();
-    const int nops = num_ops(L, p->iters_per_level, p->means_iters);
-    for (int o = 0; o < nops; ++o) {
-        const OpDesc d = op_at(L, p->iters_per_level, p->means_iters, o);
-        h.ops.push_back({d.kind, d.level, d.phase});
-    }
+    h.nops = num_ops(L, p->iters_per_level, p->means_iters);
     h.units_cap = (int)(((int64_t)(p->width + 1) / 2) * ((p->height + 1) / 2));
 
-    // device layout: bins, then two buffers of every label grid, histogram,
-    // size vector and decision array
+    // device layout: bins, then two buffers of every label grid, the block
+    // edge tables, and two buffers of every histogram, size vector and
+    // decision array
     size_t off = 0;
     h.off_bins = off;
     off = align_up(off + (size_t)N * (h.nbins > 256 ? 2 : 1));
@@ -154,13 +153,35 @@ inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t 
     return SEEDS_OK;
 }
 
+// derive_core plus the host copies of the block edge tables and the op list
+// (the same one the kernels derive with op_at).
+inline int derive(const seeds_params *p, ImageHost *g, int32_t *gx_out, int32_t *gy_out)
+{
+    ImageHost local;
+    ImageHost &h = g ? *g : local;
+    const int rc = derive_core(p, &h, gx_out, gy_out);
+    if (rc || !g) return rc;
+    for (int l = 1; l <= h.L; ++l) {
+        h.xe[l].resize(h.nbx[l] + 1);
+        h.ye[l].resize(h.nby[l] + 1);
+        for (int i = 0; i <= h.nbx[l]; ++i) h.xe[l][i] = (int32_t)((int64_t)i * h.p.width / h.nbx[l]);
+        for (int i = 0; i <= h.nby[l]; ++i) h.ye[l][i] = (int32_t)((int64_t)i * h.p.height / h.nby[l]);
+    }
+    h.ops.clear();
+    for (int o = 0; o < h.nops; ++o) {
+        const OpDesc d = op_at(h.L, h.p.iters_per_level, h.p.means_iters, o);
+        h.ops.push_back({d.kind, d.level, d.phase});
+    }
+    return SEEDS_OK;
+}
+
 
 // The device record of an image whose state starts at `base` (laid out as
 // derive() planned), with the given launch knobs and per-call pointers.
 // The fields of an image's device record that its op list and step
 // schedule depend on (size, grids, levels, iterations, launch knobs), with
 // no device pointer: enough to plan a schedule on a host without a GPU.
-inline DevImage plan_image(const ImageHost &h, const seeds_tuning &t)
+inline DevImage plan_image(const ImageCore &h, const seeds_tuning &t)
 {
     DevImage d;
     std::memset(&d, 0, sizeof(d));
@@ -182,7 +203,7 @@ inline DevImage plan_image(const ImageHost &h, const seeds_tuning &t)
     return d;
 }
 
-inline DevImage make_dev_image(const ImageHost &h, unsigned char *base, const seeds_tuning &t, const IoEntry &io,
+inline DevImage make_dev_image(const ImageCore &h, unsigned char *base, const seeds_tuning &t, const IoEntry &io,
                                int32_t *err)
 {
     DevImage d = plan_image(h, t);

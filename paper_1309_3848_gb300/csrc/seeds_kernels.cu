@@ -31,6 +31,7 @@
 #include <mutex>
 
 #include "seeds_device.cuh"
+#include "seeds_host.h"
 
 namespace seeds {
 
@@ -1561,8 +1562,19 @@ cudaError_t launch_set_io(DevImage *d_imgs, const IoChunk &chunk, cudaStream_t s
     return cudaGetLastError();
 }
 
+// The kernel's dynamic shared-memory limit is one attribute per function and
+// device, shared by every context, server and static call in the process:
+// it is only ever raised, never lowered, so a launch configured for a large
+// histogram stays valid after a smaller one configures its own.  The current
+// value is read back each time, so a device reset (which clears it) is seen.
 cudaError_t prepare_persistent(size_t smem)
 {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, seeds_persistent);
+    if (e != cudaSuccess) return e;
+    if ((size_t)a.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
     return cudaFuncSetAttribute(seeds_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
@@ -1628,15 +1640,21 @@ constexpr int kStaticMaxDevices = 64;
 std::mutex g_static_mu;
 unsigned char *g_static_addr[kStaticMaxDevices] = {};
 
-// Host address stand-ins are not device addresses: ask the runtime, once per
-// device, with that device current.
-cudaError_t static_scratch_address(int dev, unsigned char **out)
+// Host address stand-ins are not device addresses: ask the runtime, with the
+// device current.  The lookup allocates nothing; it is repeated on every call
+// whose stream is not being captured (so a context the host application
+// rebuilt, e.g. after a device reset, is seen) and the last answer for the
+// device is kept for calls made during a capture.
+cudaError_t static_scratch_address(int dev, cudaStream_t stream, unsigned char **out)
 {
     if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return e;
+    if (cap == cudaStreamCaptureStatusNone || !g_static_addr[dev]) {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
         g_static_addr[dev] = (unsigned char *)p;
     }
@@ -1699,75 +1717,17 @@ using namespace seeds;
 extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int64_t row_stride_bytes,
                                 int32_t *d_labels_out, int32_t *d_status, void *stream)
 {
-    // ---- parameters and grid (Sec. 5.1), arithmetic only
+    // ---- parameters, grid (Sec. 5.1) and the image's state layout: the
+    // same heap-free derivation the allocating contexts use
     if (!p || !d_rgb || !d_labels_out) return SEEDS_ERR_INVALID;
-    if (p->width < 1 || p->height < 1 || p->width > 32768 || p->height > 32768) return SEEDS_ERR_INVALID;
-    const int64_t N = (int64_t)p->width * p->height;
-    if (N > 0x7fffffffLL || row_stride_bytes < 3 * (int64_t)p->width) return SEEDS_ERR_INVALID;
-    if (p->num_superpixels < 1 || p->block_levels < 0 || p->block_levels > kMaxLevels) return SEEDS_ERR_INVALID;
-    if (p->bins_per_channel < 1 || p->bins_per_channel > 16) return SEEDS_ERR_INVALID;
-    if (p->iters_per_level < 1 || p->iters_per_level > 1000) return SEEDS_ERR_INVALID;
-    if (p->patch != 0 && p->patch != 3) return SEEDS_ERR_INVALID;
-    if (p->gamma_num < 0 || p->gamma_num > 1024 || p->gamma_den < 1 || p->gamma_den > 1024) return SEEDS_ERR_INVALID;
-    if (p->color_space != 0 && p->color_space != 1) return SEEDS_ERR_INVALID;
-    if (p->means_iters < 0 || p->means_iters > 1000 || p->compactness < 0 || p->compactness > 1024)
-        return SEEDS_ERR_INVALID;
-    if (p->edge_threshold < 0 || p->edge_threshold > 765) return SEEDS_ERR_INVALID;
-    const double Kd = p->num_superpixels, Wd = p->width, Hd = p->height;
-    long long gx = std::llround(std::sqrt(Kd * Wd / Hd));
-    if (gx < 1) gx = 1;
-    long long gy = std::llround(Kd / (double)gx);
-    if (gy < 1) gy = 1;
-    if (gx * gy > 65535) return SEEDS_ERR_INVALID;
-    const int L = p->block_levels;
-    if ((gx << L) > p->width || (gy << L) > p->height) return SEEDS_ERR_GEOMETRY;
-    const int B = p->bins_per_channel, nbins = B * B * B, K = (int)(gx * gy);
+    host::ImageCore h;
+    int rc = host::derive_core(p, &h, nullptr, nullptr);
+    if (rc) return rc;
+    if (row_stride_bytes < 3 * (int64_t)p->width) return SEEDS_ERR_INVALID;
+    const int nops = h.nops;
 
-    StaticSetup S;
-    std::memset(&S, 0, sizeof(S));
-    DevImage &d = S.img;
-    d.W = p->width;
-    d.H = p->height;
-    d.K = K;
-    d.gx = (int)gx;
-    d.gy = (int)gy;
-    d.L = L;
-    d.iters = p->iters_per_level;
-    d.B = B;
-    d.nbins = nbins;
-    d.patch = p->patch;
-    d.gnum = p->gamma_num;
-    d.gden = p->gamma_den;
-    d.color = p->color_space;
-    if (d.color == 1 && upload_lab_tables() != cudaSuccess) return SEEDS_ERR_CUDA;
-    d.means_iters = p->means_iters;
-    d.means_w = (float)((int64_t)p->compactness * p->compactness * K) / (float)N;
-    d.edge_tau = p->edge_threshold;
-    d.bins16 = nbins > 256;
-    d.hist_jmajor = 0;
-    d.hist_sk = nbins;
-    d.hist_sj = 1;
-    d.small_area = 16;
-    d.tile_uy = kTileUY;
-    d.nbx[0] = p->width;
-    d.nby[0] = p->height;
-    d.maxarea[0] = 1;
-    int amax = 1;
-    for (int l = 1; l <= L; ++l) {
-        d.nbx[l] = (int)(gx << (L - l + 1));
-        d.nby[l] = (int)(gy << (L - l + 1));
-        // the widest block of a level spans ceil(W/n) columns (floor edges)
-        const int mw = (p->width + d.nbx[l] - 1) / d.nbx[l], mh = (p->height + d.nby[l] - 1) / d.nby[l];
-        d.maxarea[l] = mw * mh;
-        amax = std::max(amax, mw * mh);
-    }
-    const __int128 N2 = (__int128)N * N, lim = ((__int128)1) << 63;
-    if ((__int128)amax * N2 >= lim || (__int128)(81 * p->gamma_den + 90 * p->gamma_num) * N2 >= lim)
-        return SEEDS_ERR_INT64;
-    const int nops = num_ops(L, p->iters_per_level, p->means_iters);
-    const int units_cap = (int)(((int64_t)(p->width + 1) / 2) * ((p->height + 1) / 2));
-
-    // ---- layout inside the scratch
+    // ---- layout inside the scratch: the image record, the barrier and the
+    // error word, the schedule, then the image's state as derive_core laid it out
     size_t off = 0;
     const size_t o_img = off;
     off = sal(off + sizeof(DevImage));
@@ -1779,60 +1739,23 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     off = sal(off + 4 * (size_t)(nops + 1));
     const size_t o_vt = off;
     off = sal(off + 8 * (size_t)nops);
-    size_t o_xe[kMaxLevels + 1] = {}, o_ye[kMaxLevels + 1] = {}, o_lab[kMaxLevels + 1][2] = {};
-    for (int l = 1; l <= L; ++l) {
-        o_xe[l] = off;
-        off = sal(off + 4 * (size_t)(d.nbx[l] + 1));
-        o_ye[l] = off;
-        off = sal(off + 4 * (size_t)(d.nby[l] + 1));
-    }
-    const size_t o_bins = off;
-    off = sal(off + (size_t)N * (d.bins16 ? 2 : 1));
-    for (int l = 0; l <= L; ++l)
-        for (int q = 0; q < 2; ++q) {
-            o_lab[l][q] = off;
-            off = sal(off + 2 * (size_t)d.nbx[l] * d.nby[l]);
-        }
-    size_t o_hist[2], o_size[2], o_dec[2], o_msum[2];
-    for (int q = 0; q < 2; ++q) {
-        o_hist[q] = off;
-        off = sal(off + 4 * (size_t)K * nbins);
-        o_size[q] = off;
-        off = sal(off + 4 * (size_t)K);
-        o_dec[q] = off;
-        off = sal(off + 4 * (size_t)units_cap);
-        o_msum[q] = off;
-        if (p->means_iters > 0) off = sal(off + 40 * (size_t)K);
-    }
-    const size_t o_edges = off;
-    if (p->edge_threshold > 0) off = sal(off + (size_t)N);
+    const size_t o_state = off;
+    off += h.bytes;
     if (off > (size_t)SEEDS_STATIC_SCRATCH_BYTES) return SEEDS_ERR_STATIC_SIZE;
+    if (p->color_space == 1 && upload_lab_tables() != cudaSuccess) return SEEDS_ERR_CUDA;
 
     // ---- the scratch's device address on the current device
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SEEDS_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
     unsigned char *base = nullptr;
-    if (static_scratch_address(dev, &base) != cudaSuccess) return SEEDS_ERR_CUDA;
+    if (static_scratch_address(dev, s, &base) != cudaSuccess) return SEEDS_ERR_CUDA;
 
-    for (int l = 0; l <= L; ++l)
-        for (int q = 0; q < 2; ++q) d.lab[l][q] = (uint16_t *)(base + o_lab[l][q]);
-    for (int l = 1; l <= L; ++l) {
-        d.xe[l] = (const int32_t *)(base + o_xe[l]);
-        d.ye[l] = (const int32_t *)(base + o_ye[l]);
-    }
-    d.bins = base + o_bins;
-    for (int q = 0; q < 2; ++q) {
-        d.hist[q] = (int32_t *)(base + o_hist[q]);
-        d.size[q] = (int32_t *)(base + o_size[q]);
-        d.dec[q] = (uint32_t *)(base + o_dec[q]);
-        d.msum[q] = p->means_iters > 0 ? (unsigned long long *)(base + o_msum[q]) : nullptr;
-    }
-    d.edges = p->edge_threshold > 0 ? base + o_edges : nullptr;
-    d.units_cap = units_cap;
-    d.err = (int32_t *)(base + o_err);
-    d.rgb = d_rgb;
-    d.stride = row_stride_bytes;
-    d.out = d_labels_out;
+    StaticSetup S;
+    std::memset(&S, 0, sizeof(S));
+    const seeds_tuning knobs{0, 0, 0, kSmallMax, kTileUY};
+    S.img = host::make_dev_image(h, base + o_state, knobs, IoEntry{d_rgb, row_stride_bytes, d_labels_out},
+                                 (int32_t *)(base + o_err));
     S.ent = (StepEntry *)(base + o_ent);
     S.first = (int32_t *)(base + o_first);
     S.vt = (int64_t *)(base + o_vt);
@@ -1847,7 +1770,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     size_t smem = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SEEDS_ERR_CUDA;
     for (int t : {1024, 512, 256, 128}) {
-        smem = (size_t)(t / 32) * warp_scratch_bytes(nbins);
+        smem = (size_t)(t / 32) * warp_scratch_bytes(h.nbins);
         per_sm = 0;
         if (prepare_persistent(smem) == cudaSuccess &&
             persistent_max_blocks_per_sm(t, smem, &per_sm) == cudaSuccess && per_sm >= 1) {
@@ -1859,7 +1782,6 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     if (threads == 0) return SEEDS_ERR_CUDA;
 
     S.split_below = sms * 32;
-    cudaStream_t s = (cudaStream_t)stream;
     static_setup_kernel<<<8, 256, 0, s>>>(S);
     if (cudaGetLastError() != cudaSuccess) return SEEDS_ERR_CUDA;
     Schedule sch{};
@@ -1867,7 +1789,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     sch.step_first = S.first;
     sch.step_vt = S.vt;
     sch.nsteps = nops;
-    sch.max_nbins = nbins;
+    sch.max_nbins = h.nbins;
     sch.trace = nullptr;
     if (launch_persistent(S.img_out, sch, (GridBarrier *)(base + o_bar), (int32_t *)(base + o_err), per_sm * sms,
                           threads, smem, s) != cudaSuccess)

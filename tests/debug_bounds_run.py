@@ -1,6 +1,7 @@
 """Run a set of jobs through the library named by SEEDS_LIB (the
 bounds-checked debug build) and compare with the oracle; prints one JSON
 line.  Started by test_gpu_debug_bounds.py in a process of its own."""
+import ctypes
 import dataclasses
 import json
 import os
@@ -34,6 +35,23 @@ def main():
     ctx.run_anytime(d, outs, max_steps=7)
     torch.cuda.synchronize()
     ctx.check_status()
+    # the allocation-free entry point on the same build: a plain job, a LAB
+    # job with means iterations and an edge-snapped one
+    static_jobs = [jobs[0], jobs[1 + 20], dataclasses.replace(jobs[2], edge_threshold=30)]
+    static = []
+    for job in static_jobs:
+        img = synth.make_image(job.image)
+        p = gc.params_for(binding, job)
+        d_img = torch.from_numpy(img).cuda()
+        out = torch.full((job.image.height, job.image.width), -1, dtype=torch.int32, device="cuda")
+        st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        rc = binding.lib.seeds_run_static(ctypes.byref(p), d_img.data_ptr(), d_img.stride(0), out.data_ptr(),
+                                          st.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        want = gc.oracle_run(job, img)
+        static.append(None if rc == 0 and int(st.item()) == 0 and gc.first_mismatch(out.cpu().numpy(), want) is None
+                      else "rc %d status %d: %s" % (rc, int(st.item()), gc.first_mismatch(out.cpu().numpy(), want)))
+    results["static entry"] = static
     print(json.dumps({"mismatches": {k: [m for m in v if m] for k, v in results.items()}, "images": len(jobs)}))
 
 

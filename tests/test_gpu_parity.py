@@ -351,3 +351,30 @@ def test_autotune_cache_reuses_the_knobs(torch, binding, tmp_path):
     second.check_status()
     for o, w in zip(outs, gc.oracle_many(jobs, imgs)):
         assert gc.first_mismatch(o.cpu().numpy(), w) is None
+
+
+def test_contexts_of_different_bin_counts_interleave(torch, binding):
+    """The kernel's shared-memory limit is one setting per device: a context
+    made for 512 bins still launches after a 125-bin context and the
+    allocation-free entry point configured theirs, with the oracle's labels."""
+    import ctypes
+    big = synth.JobSpec(synth.ImageSpec(160, 120, seed=71, cells=30, sigma=6.0), 120, 8, 3, 2)
+    small = synth.JobSpec(synth.ImageSpec(120, 90, seed=72, cells=20, sigma=6.0), 60, 5, 2, 2)
+    imgs = [synth.make_image(big.image), synth.make_image(small.image)]
+    want = gc.oracle_many([big, small], imgs)
+    c_big = binding.SeedsContext([gc.params_for(binding, big)])
+    c_small = binding.SeedsContext([gc.params_for(binding, small)])
+    d = [torch.from_numpy(im).cuda() for im in imgs]
+    outs = [torch.full((j.image.height, j.image.width), -1, dtype=torch.int32, device="cuda") for j in (big, small)]
+    p = gc.params_for(binding, small)
+    rc = binding.lib.seeds_run_static(ctypes.byref(p), d[1].data_ptr(), d[1].stride(0), outs[1].data_ptr(), None,
+                                      torch.cuda.current_stream().cuda_stream)
+    assert rc == binding.SEEDS_OK
+    for _ in range(2):
+        c_big.run([d[0]], [outs[0]])
+        c_small.run([d[1]], [outs[1]])
+    torch.cuda.synchronize()
+    c_big.check_status()
+    c_small.check_status()
+    for o, w in zip(outs, want):
+        assert gc.first_mismatch(o.cpu().numpy(), w) is None

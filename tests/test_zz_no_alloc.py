@@ -68,6 +68,31 @@ def test_static_scratch_entry_matches_the_allocating_one(torch, binding):
         assert np.array_equal(got, want), "%d labels differ" % int((got != want).sum())
 
 
+def test_static_scratch_entry_allocates_nothing(torch, binding):
+    """After a first call of the same shape (which loads the kernels), a
+    call changes neither the device's free memory nor the caching
+    allocator's counters."""
+    job = synth.JobSpec(synth.ImageSpec(320, 240, seed=43, cells=40, sigma=8.0), 300, 5, 3, 2)
+    d_img = torch.from_numpy(synth.make_image(job.image)).cuda()
+    first = without_allocation(binding, torch, job, d_img)
+    p = job_params(binding, job)
+    out = torch.full((job.image.height, job.image.width), -1, dtype=torch.int32, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    rc = binding.lib.seeds_run_static(ctypes.byref(p), d_img.data_ptr(), d_img.stride(0), out.data_ptr(),
+                                      status.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    free2, _ = torch.cuda.mem_get_info()
+    stats2 = torch.cuda.memory_stats()
+    assert rc == binding.SEEDS_OK and int(status.item()) == 0
+    assert free2 == free1, "device free memory moved by %d bytes" % (free1 - free2)
+    for key in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current"):
+        assert stats2.get(key, 0) == stats1.get(key, 0), key
+    assert np.array_equal(out.cpu().numpy(), first)
+
+
 def test_static_scratch_entry_refuses_images_that_do_not_fit(torch, binding):
     p = binding.make_params(3840, 2160, 5000, 5, 8, 4)
     img = torch.zeros((2160, 3840, 3), dtype=torch.uint8, device="cuda")
