@@ -133,22 +133,29 @@ typedef struct {
     int32_t pixel_tile_rows;
 } seeds_tuning;
 
-/* Fill p with the paper's defaults for a W x H image and K superpixels:
- * 4 block levels (clamped to what the grid allows), 5 bins per channel,
- * 2 iterations, 3x3 patch, gamma = 1; RGB, no means iterations, no edge
- * snapping.  Host only. */
+/* Fill p with the paper's defaults for a W x H image and K superpixels
+ * (Sec. 6.2 for the bins, the 3x3 patch and gamma; Sec. 5.1 for the block
+ * levels): 4 block levels (clamped to what the grid allows), 5 bins per
+ * channel, 2 iterations, 3x3 patch, gamma = 1; RGB, no means iterations, no
+ * edge snapping.  Host only. */
 int seeds_params_default(seeds_params *p, int32_t width, int32_t height, int32_t num_superpixels);
 
 /* Largest block_levels the grid geometry of *p allows (>= 0), ignoring
- * p->block_levels itself.  Host only; SEEDS_ERR_INVALID for bad sizes. */
+ * p->block_levels itself: the block hierarchy of Sec. 5.1, where each level
+ * halves the block size down to blocks of a few pixels.  Host only;
+ * SEEDS_ERR_INVALID for bad sizes. */
 int seeds_feasible_levels(const seeds_params *p, int32_t *max_levels);
 
-/* Validate *p and compute its grid without allocating: K_actual = gx*gy.
- * Returns SEEDS_ERR_GEOMETRY / SEEDS_ERR_INT64 exactly as seeds_create would. */
+/* Validate *p and compute its grid without allocating: K_actual = gx*gy
+ * (the initial partition of Sec. 5.1).  Returns SEEDS_ERR_GEOMETRY /
+ * SEEDS_ERR_INT64 exactly as seeds_create would; the int64 bound covers the
+ * cross-multiplied compares of Prop. 1 and Prop. 2 (Sec. 5.3). */
 int seeds_check_params(const seeds_params *p, int32_t *gx, int32_t *gy);
 
 /* Device bytes a context for these images would hold (for admission
- * control by footprint).  Host only. */
+ * control by footprint).  The paper has no counterpart: it sizes the state
+ * of Sec. 5.1 (bin map, label grids of every level, Sec. 4 histograms).
+ * Host only. */
 int seeds_footprint(const seeds_params *p, int32_t n, int64_t *bytes);
 
 /* One entry of a step schedule (seeds_plan): work of image `img` in one
@@ -168,7 +175,8 @@ typedef struct {
     int64_t vt_begin;
 } seeds_plan_entry;
 
-/* The step schedule a launch over the n images p[0..n) uses on a GPU with
+/* The step schedule (the hill climbing of Sec. 5.2-5.3 as parity phases,
+ * level by level) a launch over the n images p[0..n) uses on a GPU with
  * sm_count SMs, planned on the host alone (no device is touched): one step
  * per op (the images of a batch share each step), a catch-up entry where a
  * phase's moves are replayed beside the next op, and the fusion of replays
@@ -189,53 +197,67 @@ int seeds_plan(const seeds_params *p, int32_t n, const seeds_tuning *t, int32_t 
                int64_t *step_threads, int32_t step_cap, int32_t *n_steps);
 
 /* Create a context for one image on the current CUDA device: validates the
- * parameters (grid geometry, int64 bound of the exact compares) and
- * allocates all device state.  Host call, synchronous. */
+ * parameters (the partition into K superpixels of Sec. 3, its initial grid
+ * and block levels of Sec. 5.1, the int64 bound of the exact compares of
+ * Sec. 5.3) and allocates all device state.  Host call, synchronous. */
 int seeds_create(const seeds_params *p, seeds_ctx **out);
 
-/* Run the whole schedule on one image: quantise, grid, histograms, block
- * levels L..1, pixel level.  d_rgb: device, H rows of W*3 uint8 (R,G,B),
+/* Run the whole schedule on one image: quantise, grid, histograms (Sec. 4,
+ * Sec. 5.1), block levels L..1 and the pixel level (Sec. 5.2-5.3), for
+ * iters_per_level iterations each (the stopping rule of Sec. 5.4 as a fixed
+ * iteration count).  d_rgb: device, H rows of W*3 uint8 (R,G,B),
  * row_stride_bytes >= 3*W apart.  Asynchronous on `stream`; d_rgb must stay
  * valid until the stream reaches this work.  Re-initialises from the image
  * on every call. */
 int seeds_iterate(seeds_ctx *c, const uint8_t *d_rgb, int64_t row_stride_bytes, void *stream);
 
-/* Write the labels of the last seeds_iterate: d_labels_out is a device
- * int32 H x W row-major buffer (caller-owned), values in [0, K_actual).
- * Asynchronous on `stream`. */
+/* Write the labels of the last seeds_iterate, the partition s of Sec. 3 (one
+ * superpixel label per pixel): d_labels_out is a device int32 H x W
+ * row-major buffer (caller-owned), values in [0, K_actual).  Asynchronous on
+ * `stream`. */
 int seeds_labels(seeds_ctx *c, int32_t *d_labels_out, void *stream);
 
-/* K_actual = gx*gy of image 0 of the context. */
+/* K_actual = gx*gy of image 0 of the context: the number of superpixels K
+ * of Sec. 3, fixed by the initial grid of Sec. 5.1. */
 int seeds_num_superpixels(const seeds_ctx *c, int32_t *k_out);
 
 /* Wait for the context's last launched work and report device-side errors:
  * SEEDS_OK, SEEDS_ERR_DEVICE (the error word was set; it is cleared), or
- * SEEDS_ERR_CUDA. */
+ * SEEDS_ERR_CUDA.  Failure reporting has no counterpart in the paper. */
 int seeds_status(seeds_ctx *c);
 
-/* Free the context (waits for its work first). */
+/* Free the context (waits for its work first).  Resource handling has no
+ * counterpart in the paper. */
 int seeds_destroy(seeds_ctx *c);
 
 /* ---- batches: many images of any sizes in one persistent launch ------- */
 
-/* Context for n images (1..SEEDS_MAX_BATCH); p[i] are their parameters. */
+/* Context for n images (1..SEEDS_MAX_BATCH); p[i] are their parameters.
+ * Each image is partitioned independently as in seeds_create (Sec. 3,
+ * Sec. 5.1); running many images in one launch has no counterpart in the
+ * paper. */
 int seeds_batch_create(const seeds_params *p, int32_t n, seeds_ctx **out);
 
-/* Number of images and K_actual of image i. */
+/* Number of images of the context (batching has no counterpart in the
+ * paper). */
 int seeds_batch_size(const seeds_ctx *c, int32_t *n_out);
+/* K_actual of image i: its superpixel count K (Sec. 3) after the grid of
+ * Sec. 5.1. */
 int seeds_batch_num_superpixels(const seeds_ctx *c, int32_t i, int32_t *k_out);
 
-/* Run all images: h_rgb_ptrs[i] is the DEVICE address of image i (an array
- * of n device pointers held in host memory), h_row_strides[i] its row
- * stride in bytes.  One persistent kernel launch.  Asynchronous. */
+/* Run all images through the schedule of seeds_iterate (Sec. 5.1-5.3):
+ * h_rgb_ptrs[i] is the DEVICE address of image i (an array of n device
+ * pointers held in host memory), h_row_strides[i] its row stride in bytes.
+ * One persistent kernel launch.  Asynchronous. */
 int seeds_batch_iterate(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides,
                         void *stream);
 
-/* Write every image's labels: h_label_ptrs[i] is the device address of an
- * int32 H_i x W_i buffer.  Asynchronous. */
+/* Write every image's labels (its partition s, Sec. 3): h_label_ptrs[i] is
+ * the device address of an int32 H_i x W_i buffer.  Asynchronous. */
 int seeds_batch_labels(seeds_ctx *c, int32_t *const *h_label_ptrs, void *stream);
 
-/* seeds_batch_iterate and seeds_batch_labels fused into one launch.  Once a
+/* seeds_batch_iterate and seeds_batch_labels fused into one launch (the
+ * whole of Sec. 5.1-5.3 and the partition of Sec. 3).  Once a
  * context has run this call, a repeat of it on the same buffers allocates
  * and synchronises nothing (a pointer upload, a barrier reset and the
  * persistent kernel), so it can be captured into a CUDA graph and replayed;
@@ -262,18 +284,19 @@ int seeds_batch_run_anytime(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, cons
                             int32_t *const *h_label_ptrs, int32_t max_steps, int64_t budget_ns, void *stream);
 
 /* Steps the last seeds_batch_run_anytime launch ran (waits for it); 0 if
- * there was none. */
+ * there was none.  The anytime stop of Sec. 5.4. */
 int seeds_anytime_steps(seeds_ctx *c, int32_t *steps);
 
 /* End to end from HOST memory: copies every image host->device into
- * context-owned staging buffers, runs the batch, and copies the labels
- * device->host.  h_rgb[i]: H_i rows of 3*W_i bytes, h_row_strides[i] apart;
+ * context-owned staging buffers, runs the batch (Sec. 5.1-5.3), and copies
+ * the labels (Sec. 3) device->host.  h_rgb[i]: H_i rows of 3*W_i bytes, h_row_strides[i] apart;
  * h_labels[i]: int32 H_i x W_i.  Asynchronous on `stream` (the host buffers
  * must stay valid until the stream completes; pinned buffers overlap). */
 int seeds_run_host(seeds_ctx *c, const uint8_t *const *h_rgb, const int64_t *h_row_strides, int32_t *const *h_labels,
                    void *stream);
 
-/* Launch knobs; see seeds_tuning. */
+/* Launch knobs; see seeds_tuning.  They change no label, so the paper has
+ * no counterpart. */
 int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t);
 
 /* The search seeds_autotune runs, with the timing supplied by the caller:
@@ -282,16 +305,19 @@ int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t);
  * 16} and pixel_tile_rows {2, 4}, in that order, one pass; a value is kept
  * only if cost() reports it at least 2% faster than the current setting.
  * cost returns milliseconds (a huge value for a setting that cannot run).
- * Writes the setting found to *best.  Host only; no device is touched. */
+ * Writes the setting found to *best.  Host only; no device is touched.  The
+ * knobs change no label, so the paper has no counterpart. */
 typedef float (*seeds_tune_cost_fn)(const seeds_tuning *t, void *user);
 int seeds_tune_search(const seeds_tuning *start, seeds_tune_cost_fn cost, void *user, seeds_tuning *best);
+/* The context's current launch knobs (no counterpart in the paper). */
 int seeds_get_tuning(const seeds_ctx *c, seeds_tuning *t);
 
 /* Pick the fastest result-invariant knobs for this context's images by
  * timing candidate settings on them (the labels do not depend on the
  * choice), apply them, and return them in *best (may be NULL).  Runs
  * `reps` timed batches per candidate on `stream` and synchronises.  The
- * inputs are as for seeds_batch_run (device images and label buffers). */
+ * inputs are as for seeds_batch_run (device images and label buffers).  No
+ * counterpart in the paper. */
 int seeds_autotune(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides,
                    int32_t *const *h_label_ptrs, int32_t reps, void *stream, seeds_tuning *best);
 
@@ -321,11 +347,15 @@ typedef struct {
     double host_ms;  /* host time since creation, on the clock done_ms uses */
 } seeds_server_stats_t;
 
+/* A server over a device arena (continuous batching has no counterpart in
+ * the paper; each served image runs the schedule of Sec. 5.1-5.3). */
 int seeds_server_create(const seeds_server_config *cfg, seeds_server **out);
+/* Free the server (waits for its work).  No counterpart in the paper. */
 int seeds_server_destroy(seeds_server *s);
 
-/* Queue one request.  h_rgb: host, H rows of 3*W bytes, row_stride_bytes
- * apart; h_labels: host int32 H x W that receives the labels.  Both must stay
+/* Queue one request (one image to partition, Sec. 3).  h_rgb: host, H rows
+ * of 3*W bytes, row_stride_bytes apart; h_labels: host int32 H x W that
+ * receives the labels.  Both must stay
  * valid until the request is reported done by seeds_server_poll (pinned
  * memory makes the copies asynchronous).  *id receives the request id.
  * SEEDS_ERR_NO_MEMORY if the image could never fit the arena. */
@@ -333,18 +363,22 @@ int seeds_server_submit(seeds_server *s, const seeds_params *p, const uint8_t *h
                         int32_t *h_labels, int64_t *id);
 
 /* Admit what fits, then launch one epoch over the resident images
- * (asynchronous; blocks only while two epochs are already queued).
+ * (asynchronous; blocks only while two epochs are already queued): up to
+ * epoch_steps ops of each image's schedule (Sec. 5.2-5.3).
  * *resident receives the number of images in the epoch (0: nothing to do). */
 int seeds_server_step(seeds_server *s, int32_t *resident);
 
 /* Requests finished since the last call (non-blocking): ids[i] and the
  * device-side completion time done_ms[i] in ms since the server was created,
- * for i < *n <= cap. */
+ * for i < *n <= cap.  No counterpart in the paper. */
 int seeds_server_poll(seeds_server *s, int64_t *ids, float *done_ms, int32_t cap, int32_t *n);
 
-/* Wait for all launched work; report device-side errors as seeds_status. */
+/* Wait for all launched work; report device-side errors as seeds_status.
+ * No counterpart in the paper. */
 int seeds_server_drain(seeds_server *s);
 
+/* Queue, residency, arena and epoch counters (no counterpart in the
+ * paper). */
 int seeds_server_stats(const seeds_server *s, seeds_server_stats_t *out);
 
 /* ---- one image without allocating ----------------------------------------
@@ -386,7 +420,8 @@ int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int64_t row_st
 
 /* ---- test hooks --------------------------------------------------------- */
 
-/* Operation list of image i: op 0 quantises and builds the grid and the
+/* Operation list of image i (the schedule of Sec. 5.1-5.3, Sec. 6.5 for the
+ * means iterations): op 0 quantises and builds the grid and the
  * histograms; then one op per phase (level L..0, iteration, phase 0..3)
  * with one descent op after each block level; with means_iters > 0 an op
  * that sums every superpixel's colour codes and coordinates, then one op per
@@ -394,14 +429,19 @@ int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int64_t row_st
  * seeds_batch_run).  kind: 0 init, 1 phase, 2 descend, 3 output, 5 start of
  * the means iterations, 6 means-based phase. */
 int seeds_debug_num_ops(const seeds_ctx *c, int32_t i, int32_t *n_ops);
+/* Kind, level and parity phase of op `op` of image i (Sec. 5.2-5.3). */
 int seeds_debug_op_info(const seeds_ctx *c, int32_t i, int32_t op, int32_t *kind, int32_t *level, int32_t *phase);
 
 /* Run ops [op_begin, op_end) of every image (clamped to each image's list)
- * from the current device state; inputs as seeds_batch_iterate. */
+ * from the current device state; inputs as seeds_batch_iterate.  A single
+ * op is one parity phase of the hill climbing (Sec. 5.2-5.3), a descent, the
+ * initialisation (Sec. 5.1) or the output. */
 int seeds_debug_run_ops(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t *h_row_strides, int32_t op_begin,
                         int32_t op_end, void *stream);
 
-/* Synchronous read of image i's state into host buffers (any may be NULL):
+/* Synchronous read of image i's state (the labels, the colour histograms of
+ * Sec. 4 and the superpixel sizes |A_k| of Prop. 1) into host buffers (any
+ * may be NULL):
  * h_labels: the label grid of `level` (level 0 = pixels, H x W; level l >=
  * 1: its block grid), h_hist: K x B^3 int32 label-major, h_sizes: K int32,
  * h_bins: H x W int32. */
@@ -409,32 +449,37 @@ int seeds_debug_read_state(seeds_ctx *c, int32_t i, int32_t level, int32_t *h_la
                            int32_t *h_bins);
 
 /* Replace image i's labels at `level` (host int32 grid as above, values in
- * [0,K)) and recount its histograms and sizes on the device from the
- * current bin map.  Synchronous. */
+ * [0,K)) and recount its histograms (Sec. 4) and sizes on the device from
+ * the current bin map, so that the next op judges from that partition
+ * (Sec. 5.3).  Synchronous. */
 int seeds_debug_set_labels(seeds_ctx *c, int32_t i, int32_t level, const int32_t *h_labels);
 
 /* Set the context's device error word (host-side fault injection: the next
- * seeds_status() must report SEEDS_ERR_DEVICE). */
+ * seeds_status() must report SEEDS_ERR_DEVICE).  No counterpart in the
+ * paper. */
 int seeds_debug_inject_error(seeds_ctx *c);
 
 /* Kernel launches issued by the context so far (every launch of the
- * persistent kernel and of the small pointer-upload kernel counts one). */
+ * persistent kernel and of the small pointer-upload kernel counts one).  No
+ * counterpart in the paper. */
 int seeds_debug_launch_count(const seeds_ctx *c, int64_t *n);
 
 /* ---- profiling ---------------------------------------------------------- */
 
 /* enable != 0: record a CUDA event pair on the launch stream around every
- * persistent-kernel launch of this context (off by default). */
+ * persistent-kernel launch of this context (off by default).  Profiling has
+ * no counterpart in the paper. */
 int seeds_profile_enable(seeds_ctx *c, int32_t enable);
 
 /* Device time in ms of the context's most recent persistent-kernel launch
- * (waits for it).  SEEDS_ERR_INVALID if profiling was off for it. */
+ * (waits for it).  SEEDS_ERR_INVALID if profiling was off for it.  No
+ * counterpart in the paper. */
 int seeds_profile_last_ms(seeds_ctx *c, float *ms);
 
 /* Step stamps of the most recent profiled persistent launch: *n = 1 +
- * 2*steps values (ns since the kernel began, read on the device's global
- * timer by one thread): [0] start, [1+2s] end of step s's evaluate slot,
- * [2+2s] end of its apply slot.  Call with h_ns = NULL to get *n. */
+ * steps values (ns since the kernel began, read on the device's global
+ * timer by one thread): [0] start, [1+s] the end of step s (one op of every
+ * image, Sec. 5.2-5.3).  Call with h_ns = NULL to get *n. */
 int seeds_profile_steps(seeds_ctx *c, int64_t *h_ns, int32_t cap, int32_t *n);
 
 #ifdef __cplusplus

@@ -117,3 +117,23 @@ def test_autotune_cache_round_trip(binding, tmp_path):
     assert (t.threads_per_block, t.blocks_per_sm, t.hist_layout, t.small_block_area, t.pixel_tile_rows) == \
         (512, 1, 1, 9, 2)
     assert binding.load_cached_tuning(path, "missing") is None
+
+
+def declaration_comments():
+    """Each declared function with the comment text between the previous
+    declaration (or section rule) and its own."""
+    text = open(HEADER).read()
+    out = {}
+    prev_end = 0
+    for m in re.finditer(r"\bint\s+(seeds_\w+)\s*\(", text):
+        chunk = text[prev_end:m.start()]
+        comments = " ".join(re.findall(r"/\*.*?\*/", chunk, flags=re.S))
+        out[m.group(1)] = comments
+        prev_end = text.index(";", m.end()) + 1
+    return out
+
+
+def test_every_declaration_cites_the_paper_or_says_it_has_no_counterpart():
+    for name, comment in declaration_comments().items():
+        flat = " ".join(re.sub(r"\n\s*\*(?!/)", " ", comment).split())
+        assert re.search(r"\b(Sec\.|Prop\.|Eq\.)", flat) or "no counterpart" in flat.lower(), name
