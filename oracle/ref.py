@@ -32,6 +32,7 @@ class RefParams(ctypes.Structure):
         ("means_iters", ctypes.c_int32),
         ("compactness", ctypes.c_int32),
         ("edge_threshold", ctypes.c_int32),
+        ("compact_prior", ctypes.c_int32),
     ]
 
 
@@ -90,10 +91,11 @@ class OracleError(RuntimeError):
 
 
 def make_params(width, height, num_superpixels, block_levels, bins_per_channel, iters_per_level,
-                patch=3, gamma=(1, 1), color_space=0, means_iters=0, compactness=0, edge_threshold=0):
+                patch=3, gamma=(1, 1), color_space=0, means_iters=0, compactness=0, edge_threshold=0,
+                compact_prior=0):
     return RefParams(int(width), int(height), int(num_superpixels), int(block_levels), int(bins_per_channel),
                      int(iters_per_level), int(patch), int(gamma[0]), int(gamma[1]), int(color_space),
-                     int(means_iters), int(compactness), int(edge_threshold))
+                     int(means_iters), int(compactness), int(edge_threshold), int(compact_prior))
 
 
 def grid(width, height, num_superpixels, block_levels=0, bins_per_channel=5, iters_per_level=1, patch=3,
@@ -115,10 +117,11 @@ class Ref:
     """One image's oracle state."""
 
     def __init__(self, width, height, num_superpixels, block_levels, bins_per_channel, iters_per_level,
-                 patch=3, gamma=(1, 1), color_space=0, means_iters=0, compactness=0, edge_threshold=0):
+                 patch=3, gamma=(1, 1), color_space=0, means_iters=0, compactness=0, edge_threshold=0,
+                 compact_prior=0):
         self.params = make_params(width, height, num_superpixels, block_levels, bins_per_channel,
                                   iters_per_level, patch, gamma, color_space, means_iters, compactness,
-                                  edge_threshold)
+                                  edge_threshold, compact_prior)
         self.means_iters = int(means_iters)
         self._h = ctypes.c_void_p()
         rc = lib().ref_create(ctypes.byref(self.params), ctypes.byref(self._h))

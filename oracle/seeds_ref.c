@@ -85,6 +85,21 @@
  *       edge_threshold; a pixel with a 4-neighbour of another label across
  *       such an edge is snapped and no longer moves (pixel phases and R17
  *       means phases; blocks are not affected).
+ *   R19 compactness prior (the second boundary prior of Sec. 6.4),
+ *       optional: in the histogram pixel phases the score of every option
+ *       loses w*D*d^2/S^2, where d^2 is the squared distance of the pixel to
+ *       the option's centre of gravity (the stay option's with the pixel in
+ *       it, as in R17), S^2 = N/K the nominal superpixel area, D = 81 and
+ *       w = compact_prior/16.  The paper gives no formula, and the exact
+ *       rational compare would overflow 128 bits, so with the prior on the
+ *       whole pixel score is evaluated in IEEE single precision in the order
+ *       written in compact_score (the colour term by one division, the
+ *       centroid as its sum times the reciprocal of the size), centres from
+ *       the phase-start state; blocks are not affected.  With
+ *       compact_prior = 0 the exact integer test of R10 applies.
+ *   R20 SPM on its own (Sec. 6.3): iters_per_level = 0 with means_iters > 0
+ *       runs no histogram iteration: the block levels only descend, and the
+ *       means-based iterations start from the grid.
  *   R14 sequential mode (quality reference only): per iteration the units
  *       are visited in a random permutation (SplitMix64 + Fisher-Yates),
  *       each boundary unit proposes one uniformly drawn candidate, and an
@@ -112,6 +127,7 @@ typedef struct {
     int32_t means_iters; /* R17: means-based pixel iterations after the histogram ones */
     int32_t compactness; /* R17: SLIC's m, weight of the spatial distance */
     int32_t edge_threshold; /* R18: colour-edge strength that snaps a pixel boundary (0 = off) */
+    int32_t compact_prior;  /* R19: weight of the compactness prior, in 1/16 (0 = off) */
 } ref_params;
 
 typedef struct {
@@ -132,6 +148,8 @@ typedef struct {
     uint8_t *code;         /* colour code (the channels the bins are taken from) of every pixel */
     int64_t *msum;         /* R17: per superpixel: sums of the 3 codes, of x and of y */
     float means_w;         /* R17: m^2 K / N, the spatial weight (m/S)^2 with S^2 = N/K */
+    float compact_w;       /* R19: (compact_prior/16) * D * K / N, the weight of d^2 */
+    float gamma_f;         /* R19: gamma as a float (0 without patches) */
     int64_t lab_lin[256];  /* R16: sRGB byte -> linear light * 2^24 */
     int64_t lab_m[3][3];   /* R16: linear RGB -> XYZ / white, * 2^20 */
 } ref_state;
@@ -155,7 +173,9 @@ int ref_check_params(const ref_params *p)
     if (p->num_superpixels < 1) return REF_EINVAL;
     if (p->block_levels < 0 || p->block_levels > REF_MAX_LEVELS) return REF_EINVAL;
     if (p->bins_per_channel < 1 || p->bins_per_channel > 16) return REF_EINVAL;
-    if (p->iters_per_level < 1) return REF_EINVAL;
+    /* R20: no histogram iteration only for a means-only run (SPM) */
+    if (p->iters_per_level < 0 || p->iters_per_level > 1000) return REF_EINVAL;
+    if (p->iters_per_level == 0 && p->means_iters == 0) return REF_EINVAL;
     if (p->patch != 0 && p->patch != 3) return REF_EINVAL;
     if (p->gamma_num < 0 || p->gamma_num > 1024) return REF_EINVAL;
     if (p->gamma_den < 1 || p->gamma_den > 1024) return REF_EINVAL;
@@ -163,6 +183,7 @@ int ref_check_params(const ref_params *p)
     if (p->means_iters < 0 || p->means_iters > 1000) return REF_EINVAL;
     if (p->compactness < 0 || p->compactness > 1024) return REF_EINVAL;
     if (p->edge_threshold < 0 || p->edge_threshold > 765) return REF_EINVAL;
+    if (p->compact_prior < 0 || p->compact_prior > 1024) return REF_EINVAL;
     return REF_OK;
 }
 
@@ -239,6 +260,8 @@ int ref_create(const ref_params *p, ref_state **out)
     st->code = (uint8_t *)calloc((size_t)N * 3, 1);
     st->msum = (int64_t *)calloc((size_t)st->K * 5, sizeof(int64_t));
     st->means_w = (float)((int64_t)p->compactness * p->compactness * st->K) / (float)N;
+    st->compact_w = (float)((int64_t)p->compact_prior * 81 * st->K) / (float)((int64_t)16 * N);
+    st->gamma_f = p->patch == 3 ? (float)p->gamma_num / (float)p->gamma_den : 0.0f;
     st->bin = (int *)calloc((size_t)N, sizeof(int));
     st->lab = (int *)calloc((size_t)N, sizeof(int));
     st->hist = (int64_t *)calloc((size_t)st->K * st->nbins, sizeof(int64_t));
@@ -598,6 +621,8 @@ static int pixel_beats_stay(const ref_state *st, int x, int y, int k, int n, int
  * compared exactly after multiplying by gamma_den and the positive sizes. */
 static int edge_frozen(const ref_state *st, int x, int y, int k);
 
+static int decide_pixel_compact(ref_state *st, int x, int y, int k, const int *cand, int nc);
+
 static int decide_pixel(ref_state *st, int x, int y)
 {
     int k = st->lab[(int64_t)y * st->W + x];
@@ -606,6 +631,7 @@ static int decide_pixel(ref_state *st, int x, int y)
     if (nc == 0) return -1;
     if (!leaving_keeps_connected(st, 0, x, y, k)) return -1;
     if (edge_frozen(st, x, y, k)) return -1;
+    if (st->p.compact_prior > 0) return decide_pixel_compact(st, x, y, k, cand, nc);
     const int use_g = st->p.patch == 3;
     const i128 D = 81, gn = st->p.gamma_num, gd = st->p.gamma_den;
     int j = st->bin[(int64_t)y * st->W + x];
@@ -738,6 +764,55 @@ static int decide_pixel_means(ref_state *st, int x, int y)
 }
 
 /* ------------------------------------------------------------------ */
+/* compactness prior (R19)                                              */
+/* ------------------------------------------------------------------ */
+
+/* The pixel score of one option with the compactness prior, in IEEE single
+ * precision in this order: colour term D * a/s (a = the pixel's bin count,
+ * s = the size, of the option as it would be: A_n, or A_k without the
+ * pixel), boundary term gamma * G (G_n + |K_p| or G_k), minus
+ * compact_w * d^2, where d^2 is the squared distance of (x, y) to the
+ * centre of gravity of the option's superpixel as it stands (sums from
+ * msum over `sc` pixels; the stay option keeps the pixel). */
+static float compact_score(const ref_state *st, int x, int y, int label, int64_t a, int64_t s, int64_t sc, int64_t G)
+{
+    const int64_t *m = st->msum + (int64_t)label * 5;
+    float r = 1.0f / (float)sc;
+    float gx = (float)x - (float)m[3] * r;
+    float gy = (float)y - (float)m[4] * r;
+    float d2 = gx * gx + gy * gy;
+    float col = (float)a / (float)s;
+    float t1 = 81.0f * col;
+    float t2 = st->gamma_f * (float)G;
+    float t3 = st->compact_w * d2;
+    return (t1 + t2) - t3;
+}
+
+/* R19: the best candidate by compact_score (ascending, a later one only if
+ * strictly higher: ties to the smallest label), accepted if strictly above
+ * the stay score.  Centres come from st->msum, recounted at phase start. */
+static int decide_pixel_compact(ref_state *st, int x, int y, int k, const int *cand, int nc)
+{
+    const int use_g = st->p.patch == 3;
+    int j = st->bin[(int64_t)y * st->W + x];
+    int64_t Kp = 0;
+    int64_t Gk = use_g ? patch_label_count(st, x, y, k, &Kp) : 0;
+    int best = -1;
+    float fb = 0.0f;
+    for (int c = 0; c < nc; ++c) {
+        int n = cand[c];
+        int64_t G = use_g ? patch_label_count(st, x, y, n, NULL) + Kp : 0;
+        float f = compact_score(st, x, y, n, st->hist[(int64_t)n * st->nbins + j], st->size[n], st->size[n], G);
+        if (best < 0 || f > fb) {
+            best = n;
+            fb = f;
+        }
+    }
+    float fk = compact_score(st, x, y, k, st->hist[(int64_t)k * st->nbins + j] - 1, st->size[k] - 1, st->size[k], Gk);
+    return fb > fk ? best : -1;
+}
+
+/* ------------------------------------------------------------------ */
 /* the parity schedule (R4, R6)                                         */
 /* ------------------------------------------------------------------ */
 
@@ -748,6 +823,7 @@ int64_t ref_run_phase(ref_state *st, int level, int phase)
     if (level < 0 || level > st->L || phase < 0 || phase > 3) return REF_EINVAL;
     int py = phase >> 1, px = phase & 1;
     int64_t nm = 0;
+    if (level == 0 && st->p.compact_prior > 0) means_recount(st); /* R19: centres at phase start */
     for (int by = py; by < st->nby[level]; by += 2)
         for (int bx = px; bx < st->nbx[level]; bx += 2) {
             int n = level == 0 ? decide_pixel(st, bx, by) : decide_block(st, level, bx, by);
@@ -903,6 +979,7 @@ int ref_decide(ref_state *st, int level, int bx, int by)
 {
     if (level < 0 || level > st->L || bx < 0 || by < 0 || bx >= st->nbx[level] || by >= st->nby[level])
         return REF_EINVAL;
+    if (level == 0 && st->p.compact_prior > 0) means_recount(st); /* R19: centres of the current labels */
     return level == 0 ? decide_pixel(st, bx, by) : decide_block(st, level, bx, by);
 }
 
@@ -988,7 +1065,8 @@ static int exact_energy_rises(ref_state *st, int level, int bx, int by, int k, i
 }
 
 /* Sequential hill climbing.  accept_mode 0: the parity schedule's proxy
- * rule (Props. 1 and 2) for the one drawn candidate; 1: exact energy rise
+ * rule (Props. 1 and 2, R10; the priors of R18 and R19 are not applied) for
+ * the one drawn candidate; 1: exact energy rise
  * (small images only, N <= 1024).  Accepted moves are written to `trace` as
  * (level, unit, k, n) quadruples while room is left.  Returns the number of
  * accepted moves, or a negative error. */

@@ -40,6 +40,20 @@ MUTANTS = {
                                                   "    int best = -1;\n    float db"),
     "anytime prefix skips the descent op": ("        if (level > 0) ++done; /* the descent", "        /* the descent"),
     "anytime prefix runs one phase too many": ("if (done >= nops) return total;", "if (done > nops) return total;"),
+    "compact prior with the sign of the distance term flipped": ("return (t1 + t2) - t3;", "return (t1 + t2) + t3;"),
+    "compact prior stay centre without the pixel": (
+        "st->size[k] - 1, st->size[k], Gk);", "st->size[k] - 1, st->size[k] - 1, Gk);"),
+    "compact prior centre row from x": ("float gy = (float)y - (float)m[4] * r;", "float gy = (float)y - (float)m[3] * r;"),
+    "compact prior drops the boundary term": ("float t2 = st->gamma_f * (float)G;", "float t2 = 0.0f * (float)G;"),
+    "compact prior ignores the superpixel area": (
+        "(float)((int64_t)p->compact_prior * 81 * st->K) / (float)((int64_t)16 * N)",
+        "(float)((int64_t)p->compact_prior * 81) / (float)16"),
+    "compact prior centres taken once, not at every phase start": (
+        "    if (level == 0 && st->p.compact_prior > 0) means_recount(st); /* R19: centres at phase start */\n",
+        "    if (level == 0 && st->p.compact_prior > 0 && phase == 0 && 0) means_recount(st);\n"),
+    "SPM alone runs one histogram iteration": (
+        "        for (int it = 0; it < st->p.iters_per_level; ++it)\n            for (int phase = 0; phase < 4; ++phase) total += ref_run_phase(st, level, phase);",
+        "        for (int it = 0; it < (st->p.iters_per_level ? st->p.iters_per_level : 1); ++it)\n            for (int phase = 0; phase < 4; ++phase) total += ref_run_phase(st, level, phase);"),
 }
 
 

@@ -848,3 +848,182 @@ def test_threshold_above_every_edge_changes_nothing():
     c = ref.Ref(W, H, 6, 1, 4, 2, edge_threshold=30).run(img)
     assert np.array_equal(a, b)
     assert not np.array_equal(a, c)
+
+
+# --------------------------------------------------------------------------
+# compactness prior (Sec. 6.4; reading R19)
+# --------------------------------------------------------------------------
+
+def exact_compact_decision(labels, bins, nbins, x, y, gamma, patch, omega):
+    """The pixel rule with the compactness prior in exact fractions, in the
+    units of the intersection (Prop. 1): every option scores its colour
+    term (a one-pixel intersection), gamma times half the exact change of G
+    (Eq. 7, Prop. 2) for a candidate, and loses (omega/16) (K/N) d^2, d^2
+    the squared distance of the pixel to the option's centre of gravity
+    (recounted from the labels; the stay option keeps the pixel).  Returns
+    (target or -1, the smallest gap between the winner and the runner-up or
+    the stay score), or (-1, None) for a pixel that may not leave."""
+    H, W = labels.shape
+    k = int(labels[y, x])
+    cand = brute.candidates(labels, x, y)
+    if not cand or not brute.ring_connected(labels, x, y, k):
+        return -1, None
+    K = int(labels.max()) + 1
+    w = Fraction(omega, 16) * Fraction(K, W * H)
+    j = int(bins[y, x])
+
+    def centre_d2(lbl):
+        ys, xs = np.nonzero(labels == lbl)
+        n = len(xs)
+        return (x - Fraction(int(xs.sum()), n)) ** 2 + (y - Fraction(int(ys.sum()), n)) ** 2
+
+    def colour(lbl, without_p):
+        sel = labels == lbl
+        a, s = int((bins[sel] == j).sum()), int(sel.sum())
+        return Fraction(a - 1, s - 1) if without_p else Fraction(a, s)
+
+    g = Fraction(gamma[0], gamma[1]) if patch else Fraction(0)
+    stay = colour(k, True) - w * centre_d2(k)
+    scores = sorted(((colour(n, False) + g * brute.delta_G(labels, x, y, n) / 2 - w * centre_d2(n), -n)
+                     for n in cand), reverse=True)
+    best, neg_n = scores[0]
+    gaps = [abs(best - stay)] + ([best - scores[1][0]] if len(scores) > 1 and scores[1][0] != best else [])
+    return (-neg_n if best > stay else -1), min(gaps)
+
+
+@pytest.mark.parametrize("seed,omega,gamma,patch", [(1, 16, (1, 1), 3), (2, 160, (1, 1), 3), (3, 40, (2, 3), 0),
+                                                    (4, 1024, (1, 1), 3)])
+def test_compact_prior_decisions_match_exact_fractions(seed, omega, gamma, patch):
+    W, H, K = 26, 20, 6
+    img = synth.make_image(synth.ImageSpec(W, H, seed=300 + seed, cells=5, sigma=20.0))
+    r = ref.Ref(W, H, K, 1, 4, 1, patch, gamma, compact_prior=omega)
+    r.run_ops(img, 1 + 4 + 1 + seed % 4)  # the grid, the block level and a few pixel phases
+    labels, bins = r.labels(), r.bins()
+    checked = moved = 0
+    for y in range(H):
+        for x in range(W):
+            want, gap = exact_compact_decision(labels, bins, r.nbins, x, y, gamma, patch, omega)
+            if gap is not None and gap < Fraction(1, 10 ** 4):
+                continue  # a near tie: single-precision rounding may decide either way
+            assert r.decide(0, x, y) == want, (x, y)
+            checked += gap is not None
+            moved += want >= 0
+    assert checked > 20 and moved > 0
+
+
+def strips(x_split, omega, patch=0):
+    """12 x 4 constant image, K = 2; the left superpixel is columns
+    0..x_split-1 (set by hand), the right one the rest."""
+    img = np.full((4, 12, 3), 90, np.uint8)
+    r = ref.Ref(12, 4, 2, 0, 4, 1, patch, (1, 1), compact_prior=omega)
+    r.init(img)
+    assert (r.gx, r.gy) == (2, 1)
+    lab = np.zeros((4, 12), np.int32)
+    lab[:, x_split:] = 1
+    r.set_labels(lab)
+    return r
+
+
+def test_compact_prior_moves_a_pixel_to_the_nearer_centre():
+    """One colour everywhere: the colour terms tie, so the prior alone
+    decides.  Left superpixel columns 0..8 (centre x = 4), right 9..11
+    (centre x = 10): column 8 is nearer the right centre and moves, column 9
+    stays, and without the prior nothing moves (strict gain)."""
+    r = strips(9, 64)
+    for y in range(4):
+        assert r.decide(0, 8, y) == 1
+        assert r.decide(0, 9, y) == -1
+        assert r.decide(0, 7, y) == -1  # not on the boundary
+    assert all(strips(9, 0).decide(0, 8, y) == -1 for y in range(4))
+
+
+def test_compact_prior_pixel_nearer_its_own_centre_stays():
+    """Left superpixel columns 0..5 (centre 2.5), right 6..11 (centre 8.5):
+    column 5 is 2.5 from its own centre and 3.5 from the right one."""
+    r = strips(6, 64)
+    assert all(r.decide(0, 5, y) == -1 for y in range(4))
+    assert all(r.decide(0, 6, y) == -1 for y in range(4))
+
+
+def spread(labels):
+    """Mean squared distance of the pixels to their superpixel's centre."""
+    H, W = labels.shape
+    ys, xs = np.mgrid[0:H, 0:W]
+    total = 0.0
+    for k in np.unique(labels):
+        sel = labels == k
+        total += ((xs[sel] - xs[sel].mean()) ** 2 + (ys[sel] - ys[sel].mean()) ** 2).sum()
+    return total / (W * H)
+
+
+def test_compact_prior_makes_superpixels_more_compact():
+    W, H = 96, 72
+    img = synth.make_image(synth.ImageSpec(W, H, seed=77, cells=9, sigma=10.0, texture=True))
+    s = [spread(ref.Ref(W, H, 24, 2, 5, 2, compact_prior=w).run(img)) for w in (0, 64, 512)]
+    assert s[0] > s[1] > s[2], s
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_invariants_after_every_phase_with_the_compact_prior(seed):
+    W, H = 37, 29
+    img = rgb_noise(W, H, 120 + seed)
+    r = ref.Ref(W, H, 8, 1, 3, 2, compact_prior=48 * (seed + 1))
+    r.init(img)
+    bins = r.bins()
+    for level, phase in r.schedule():
+        r.run_phase(level, phase)
+        lab = r.labels()
+        h, s = r.hist()
+        h2, s2 = recount(lab, bins, r.K, r.nbins)
+        assert np.array_equal(h, h2) and np.array_equal(s, s2)
+        assert_valid_partition(lab, r.K)
+
+
+def test_compact_prior_leaves_the_block_levels_alone():
+    W, H = 64, 48
+    img = synth.make_image(synth.ImageSpec(W, H, seed=78, cells=7, sigma=12.0))
+    nblock = 1 + 2 * (4 * 2 + 1)  # the grid and two block levels of two iterations, with their descents
+    a = ref.Ref(W, H, 12, 2, 4, 2)
+    b = ref.Ref(W, H, 12, 2, 4, 2, compact_prior=512)
+    assert np.array_equal(a.run_ops(img, nblock), b.run_ops(img, nblock))
+    assert not np.array_equal(a.run(img), b.run(img))
+
+
+# --------------------------------------------------------------------------
+# SPM on its own (Sec. 6.3; reading R20)
+# --------------------------------------------------------------------------
+
+def test_spm_alone_starts_the_means_iterations_from_the_grid():
+    W, H = 40, 30
+    img = synth.make_image(synth.ImageSpec(W, H, seed=79, cells=6, sigma=10.0))
+    r = ref.Ref(W, H, 10, 2, 4, 0, means_iters=2, compactness=8)
+    grid = ref.Ref(W, H, 10, 2, 4, 1)
+    grid.init(img)
+    # init and the two descents leave the grid as it is
+    assert np.array_equal(r.run_ops(img, 1 + 2), grid.labels())
+    assert r.num_ops() == 1 + 2 + 1 + 4 * 2 + 1
+    # the means phases from the grid, against their exact-fraction rule
+    r.run_ops(img, 1 + 2 + 1)
+    labels, codes = r.labels(), img
+    moved = 0
+    for y in range(H):
+        for x in range(W):
+            want, gap = exact_means_decision(labels, codes, r.K, 8, x, y)
+            if gap is not None and gap < Fraction(1, 10 ** 4):
+                continue
+            assert r.decide_means(x, y) == want, (x, y)
+            moved += want >= 0
+    assert moved > 0
+    full = r.run(img)
+    assert not np.array_equal(full, grid.labels())
+    # the whole run is the means phases applied to the grid, nothing else
+    m = ref.Ref(W, H, 10, 2, 4, 0, means_iters=2, compactness=8)
+    m.init(img)
+    for _ in range(2):
+        for phase in range(4):
+            m.run_means_phase(phase)
+    assert np.array_equal(full, m.labels())
+
+
+def test_no_iterations_at_all_is_refused():
+    assert ref.grid(40, 30, 10, 2, 4, 0)[0] == ref.EINVAL
