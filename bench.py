@@ -3,8 +3,11 @@
 
 One step = one pass of the whole path (quantise, grid, histograms, block
 levels, pixel level, int32 labels) over one batch of synthetic images that
-already sit in device memory.  Default workload: one 1920x1080 image, 1000
-superpixels, 4 block levels, 4 iterations per level, 5 bins per channel.
+already sit in device memory.  Default workload: the batched 4K
+configuration, sixteen 3840x2160 images in one persistent launch, 5000
+superpixels, 8 bins per channel (512-bin histograms), 5 block levels, 4
+iterations per level; the same images run one launch per image give the
+plain per-image figure beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   # the CPU oracle on the host cores
@@ -14,6 +17,7 @@ independent; no collective touches the data) and rank 0 prints one JSON line.
 """
 import argparse
 import concurrent.futures
+import dataclasses
 import hashlib
 import json
 import os
@@ -22,6 +26,8 @@ import subprocess
 import sys
 import tempfile
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -41,18 +47,21 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gseeds", choices=["gseeds", "reference"])
-    ap.add_argument("--workload", default="plain_1920x1080",
+    ap.add_argument("--workload", default="batch16_3840x2160",
                     help="plain_481x321 | plain_1920x1080 | batch64_mixed | batch16_3840x2160 | serve_poisson")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window per rate (serve_poisson)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched comparison, the serving sample and the CPU baseline")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch knobs")
+    ap.add_argument("--images", type=int, default=0,
+                    help="run only the workload's first N images (0 = all): a smaller case for profiler captures")
     return ap.parse_args()
 
 
-def workload_jobs(name):
+def workload_jobs(name, images=0):
     from paper_1309_3848_gb300 import synth
-    return synth.WORKLOADS[name]()
+    jobs = synth.WORKLOADS[name]()
+    return jobs[:images] if images > 0 else jobs
 
 
 def make_images(jobs):
@@ -61,17 +70,22 @@ def make_images(jobs):
         return list(ex.map(lambda j: synth.make_image(j.image), jobs))
 
 
-def config_of(name, jobs, extra=None):
+L2_NOTE = "flushed before every timed GPU step (256 MiB write)"
+
+
+def config_of(name, jobs):
+    """The workload, described the same way on both arms (GPU and oracle)."""
     px = sum(j.pixels for j in jobs)
-    cfg = {"workload": name, "images": len(jobs), "pixels_per_step": px}
-    if len(jobs) == 1:
+    cfg = {"workload": name, "images": len(jobs), "pixels_per_step": px, "l2": L2_NOTE}
+    def shape(j):  # a job without its image seed
+        return dataclasses.replace(j, image=dataclasses.replace(j.image, seed=0))
+
+    if all(shape(j) == shape(jobs[0]) for j in jobs):
         j = jobs[0]
         cfg.update({"width": j.image.width, "height": j.image.height, "superpixels_requested": j.num_superpixels,
                     "bins_per_channel": j.bins_per_channel, "block_levels": j.levels,
                     "iters_per_level": j.iters_per_level, "patch": j.patch,
                     "gamma": "%d/%d" % tuple(j.gamma)})
-    if extra:
-        cfg.update(extra)
     return cfg
 
 
@@ -227,10 +241,61 @@ def label_quality(job, labels):
             "asa": metrics.asa(labels, truth), "truth": "Voronoi cells of the synthetic image"}
 
 
-def moves_per_level(job, img):
-    """Accepted moves per level (L..1 blocks, 0 pixels) of the workload's
-    first image, counted by the oracle phase by phase; the GPU's labels equal
-    the oracle's, so these are the GPU's moves too."""
+SAMPLE_MAX_PIXELS = 2_100_000  # larger images are sampled by their top-left quarter
+
+
+def oracle_sample(jobs, imgs):
+    """A bounded sample of the workload for timing the oracle: every image
+    up to 1920x1080 as it is; a larger one (3840x2160) by its top-left
+    quarter, with a quarter of the superpixels (the same superpixel area)
+    and the same bins, levels and iterations.  Returns (jobs, images, what)."""
+    sj, si, cropped = [], [], 0
+    for j, im in zip(jobs, imgs):
+        if j.pixels <= SAMPLE_MAX_PIXELS:
+            sj.append(j)
+            si.append(im)
+            continue
+        W, H = j.image.width // 2, j.image.height // 2
+        spec = dataclasses.replace(j.image, width=W, height=H)
+        sj.append(dataclasses.replace(j, image=spec, num_superpixels=max(1, round(j.num_superpixels / 4))))
+        si.append(np.ascontiguousarray(im[:H, :W]))
+        cropped += 1
+    what = "the workload's %d image(s)" % len(jobs)
+    if cropped:
+        what += " (%d sampled by their top-left %dx%d quarter with a quarter of the superpixels)" % (
+            cropped, sj[0].image.width, sj[0].image.height)
+    return sj, si, what
+
+
+def cpu_sample(jobs, imgs, min_seconds=10.0, max_seconds=30.0):
+    """Time the oracle on a bounded sample of the workload (oracle_sample)
+    on all host cores, one image per thread, repeating the sample until
+    about min_seconds have passed."""
+    cores = os.cpu_count() or 1
+    sj, si, what = oracle_sample(jobs, imgs)
+    work = []
+    while len(work) < max(cores, len(sj)):
+        work.extend(zip(sj, si))
+    px = 0
+    t0 = time.perf_counter()
+    rounds = 0
+    with concurrent.futures.ThreadPoolExecutor(cores) as ex:
+        while True:
+            for f in [ex.submit(oracle_run, j, im) for j, im in work]:
+                f.result()
+            px += sum(j.pixels for j, _ in work)
+            rounds += 1
+            el = time.perf_counter() - t0
+            if el >= min_seconds or el + el / rounds > max_seconds:
+                break
+    el = time.perf_counter() - t0
+    return px / el / 1e6, cores, "%s; %d images in %.1f s on %d threads" % (what, len(work) * rounds, el, cores)
+
+
+def oracle_counting_run(job, img):
+    """The oracle's labels of a histogram-only job, run phase by phase so
+    that the accepted moves of every level (L..1 blocks, 0 pixels) are
+    counted on the way."""
     from oracle import ref
     r = ref.Ref(job.image.width, job.image.height, job.num_superpixels, oracle_levels(job), job.bins_per_channel,
                 job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters, job.compactness,
@@ -239,35 +304,21 @@ def moves_per_level(job, img):
     moves = {}
     for level, phase in r.schedule():
         moves["L%d" % level] = moves.get("L%d" % level, 0) + int(r.run_phase(level, phase))
-    return moves
+    return r.labels(), moves
 
 
-def cpu_sample(jobs, imgs, min_seconds=10.0, max_seconds=30.0):
-    """Time the oracle over copies of the workload's images on all host
-    cores (one image per thread) until about min_seconds have passed."""
+def oracle_parity(jobs, imgs, gpu_labels):
+    """Every image of the workload through the oracle on all host cores;
+    'bit-exact' if the GPU's labels equal the oracle's everywhere.  Also
+    returns the accepted moves per level of the first image."""
     cores = os.cpu_count() or 1
-    work = []
-    while len(work) < max(cores, len(jobs)):
-        work.extend(zip(jobs, imgs))
-    labels = {}
-    px = 0
-    t0 = time.perf_counter()
-    rounds = 0
     with concurrent.futures.ThreadPoolExecutor(cores) as ex:
-        while True:
-            futs = [ex.submit(oracle_run, j, im) for j, im in work]
-            for i, f in enumerate(futs):
-                lab = f.result()
-                if i < len(jobs):
-                    labels[i] = lab
-            px += sum(j.pixels for j, _ in work)
-            rounds += 1
-            el = time.perf_counter() - t0
-            if el >= min_seconds or el + el / rounds > max_seconds:
-                break
-    el = time.perf_counter() - t0
-    return px / el / 1e6, cores, "%d images (%d copies of the workload's %d) in %.1f s on %d threads" % (
-        len(work) * rounds, len(work) * rounds // max(1, len(jobs)), len(jobs), el, cores), labels
+        first = ex.submit(oracle_counting_run, jobs[0], imgs[0]) if jobs[0].means_iters == 0 else None
+        rest = [ex.submit(oracle_run, j, im) for j, im in zip(jobs[1:] if first else jobs, imgs[1:] if first else imgs)]
+        want = ([first.result()[0]] if first else []) + [f.result() for f in rest]
+        moves = first.result()[1] if first else None
+    ok = all(np.array_equal(a, b) for a, b in zip(gpu_labels, want))
+    return ("bit-exact" if ok else "MISMATCH"), moves
 
 
 def run_reference(args):
@@ -281,9 +332,12 @@ def run_reference(args):
         pool = serve.image_pool(synth.IMAGE_SIZES_SERVE, 3, seed=4)
         jobs = [j for _, j in reqs]
         imgs = serve.stream_images(reqs, pool)
+        cfg = serve_config(args)
+        what = "%d requests of the 500 req/s stream" % len(jobs)
     else:
-        jobs = workload_jobs(args.workload)
-        imgs = make_images(jobs)
+        wjobs = workload_jobs(args.workload, args.images)
+        cfg = config_of(args.workload, wjobs)
+        jobs, imgs, what = oracle_sample(wjobs, make_images(wjobs))
     cores = min(os.cpu_count() or 1, len(jobs))
     px = sum(j.pixels for j in jobs)
 
@@ -301,9 +355,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": config_of(args.workload, jobs),
+            "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu(),
-                             "sample": "the whole workload (%d image(s)) per step, one thread per image" % len(jobs)},
+                             "sample": "per step %s, one thread per image" % what},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -381,6 +435,29 @@ def batched_vs_plain(torch, binding, flush, steps=5):
             "batched_over_plain": vb / vp, "graph_replay_mpix_s": vg, "labels_identical": bool(same)}
 
 
+def plain_per_image(torch, binding, params, d, outs, flush, px, steps=3):
+    """The workload's images with one context and one persistent launch
+    each, back to back on one stream: the plain per-image path the batched
+    launch is compared with; its labels must equal the batch's."""
+    ctxs = [binding.SeedsContext([p]) for p in params]
+    outs_p = [torch.empty_like(o) for o in outs]
+
+    def run_plain():
+        for c, x, o in zip(ctxs, d, outs_p):
+            c.run([x], [o])
+
+    for _ in range(2):
+        run_plain()
+    torch.cuda.synchronize()
+    t, _ = timed_steps(torch, run_plain, steps, flush)
+    for c in ctxs:
+        c.check_status()
+    same = all(torch.equal(a, b) for a, b in zip(outs, outs_p))
+    ms = statistics.mean(t)
+    return {"mpix_s": px / (ms / 1e3) / 1e6, "ms_per_step": ms, "launches_per_step": len(ctxs),
+            "labels_identical": bool(same)}
+
+
 def next_rows(torch, binding, flush, jobs, imgs, rgb_value, steps=5):
     """The widened rows on the bench workload: LAB colour bins (Sec. 6.2) and
     two means-based pixel iterations after the histogram ones (Sec. 6.3,
@@ -449,6 +526,16 @@ def serve_sample(rates, seconds, per_size=3, arena_gib=8, epoch_steps=16):
     return out
 
 
+SERVE_RATES = (100.0, 250.0, 500.0, 1000.0, 2000.0)
+
+
+def serve_config(args):
+    """The serving workload as both arms describe it."""
+    return {"workload": "serve_poisson", "rates_req_s": list(SERVE_RATES), "arrival_window_s": args.serve_seconds,
+            "sizes": "320x240..3840x2160", "superpixels": "200..5000", "bins_per_channel": 5,
+            "iters_per_level": 2, "l2": L2_NOTE}
+
+
 def run_serve(args):
     """The serving workload: Poisson streams at 100..2000 req/s."""
     import torch
@@ -457,7 +544,7 @@ def run_serve(args):
         return
     import __graft_entry__
     __graft_entry__.build_library()
-    rates = (100.0, 250.0, 500.0, 1000.0, 2000.0)
+    rates = SERVE_RATES
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     sampler.start()
     served = serve_sample(rates, seconds=args.serve_seconds)
@@ -466,9 +553,7 @@ def run_serve(args):
     line = {"metric": METRIC, "value": top["mpix_s"], "unit": UNIT, "n_gpus": 1, "steps": len(served),
             "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic",
-            "config": {"workload": "serve_poisson", "rates_req_s": list(rates),
-                       "arrival_window_s": args.serve_seconds, "sizes": "320x240..3840x2160",
-                       "superpixels": "200..5000", "bins_per_channel": 5, "iters_per_level": 2},
+            "config": serve_config(args),
             "served": served, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
@@ -500,7 +585,7 @@ def run_gpu(args):
     __graft_entry__.build_library()
     from paper_1309_3848_gb300 import binding
 
-    jobs = workload_jobs(args.workload)
+    jobs = workload_jobs(args.workload, args.images)
     imgs = make_images(jobs)
     params = [gpu_params(binding, j) for j in jobs]
     px = sum(j.pixels for j in jobs)
@@ -518,7 +603,7 @@ def run_gpu(args):
         t = ctx.autotune(d, outs, reps=3)
         tuned = {"threads_per_block": t.threads_per_block, "blocks_per_sm": t.blocks_per_sm,
                  "hist_layout": t.hist_layout, "small_block_area": t.small_block_area,
-                 "pixel_tile_rows": t.pixel_tile_rows}
+                 "pixel_tile_rows": t.pixel_tile_rows, "block_tiles": t.block_tiles}
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -580,10 +665,10 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": config_of(args.workload, jobs, {
-            "l2": "flushed before every step (256 MiB write)",
-            "superpixels_actual": ctx.num_superpixels if len(jobs) > 1 else ctx.num_superpixels[0],
-            "parallelism": "replicas" if world > 1 else "single GPU", "tuning": tuned}),
+        "config": config_of(args.workload, jobs),
+        "superpixels_actual": sorted(set(ctx.num_superpixels)) if len(jobs) > 1 else ctx.num_superpixels[0],
+        "parallelism": "replicas, no collective on the data" if world > 1 else "single GPU",
+        "launch": "one persistent launch per step for all %d image(s)" % len(jobs), "tuning": tuned,
         "roofline": {"bound": "hbm", "kernel": "seeds_persistent", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": bytes_min, "kernel_ms": kms,
@@ -598,17 +683,19 @@ def run_gpu(args):
         "gpu_launches": launches,
     }
     if world == 1 and not args.no_extras:
-        line["batched"] = batched_vs_plain(torch, binding, flush)
-        line["served"] = serve_sample(rates=(500.0, 2000.0), seconds=1.0)
+        if len(jobs) > 1:  # the same images, one context and one launch per image
+            line["plain"] = plain_per_image(torch, binding, params, d, outs, flush, px)
+            line["batched_over_plain"] = value / line["plain"]["mpix_s"]
+        if args.workload != "batch64_mixed":
+            line["batch64_mixed"] = batched_vs_plain(torch, binding, flush)
+        line["served"] = serve_sample(rates=SERVE_RATES, seconds=2.0)
         line["next_rows"] = next_rows(torch, binding, flush, jobs, imgs, value)
         gpu_labels = [o.cpu().numpy() for o in outs]
-        v, cores, sample, ref_labels = cpu_sample(jobs, imgs)
+        v, cores, sample = cpu_sample(jobs, imgs)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu(),
                                 "sample": sample}
-        import numpy as np
-        line["parity"] = "bit-exact" if all(np.array_equal(gpu_labels[i], ref_labels[i])
-                                            for i in range(len(jobs))) else "MISMATCH"
-        line["moves_per_level"] = moves_per_level(jobs[0], imgs[0])
+        line["parity"], line["moves_per_level"] = oracle_parity(jobs, imgs, gpu_labels)
+        line["parity_images"] = len(jobs)
         line["quality"] = label_quality(jobs[0], gpu_labels[0])
     print(json.dumps(line), flush=True)
     if world > 1:

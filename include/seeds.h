@@ -124,13 +124,18 @@ typedef struct {
  *   pixel_tile_rows    unit rows of a pixel-phase warp tile (32 units wide):
  *                      2 or 4 (0 = 4); shorter tiles balance small images
  *   small_block_area   blocks of at most this many pixels are judged by one
- *                      thread, larger ones by a warp (1..16; 0 = default) */
+ *                      thread, larger ones by a warp (1..16; 0 = default)
+ *   block_tiles        block phases in warp tiles (labels staged in shared
+ *                      memory, only boundary blocks judged): 0 = never (the
+ *                      default), 1 = in steps with at least two tiles per
+ *                      warp slot of the GPU, 2 = always */
 typedef struct {
     int32_t threads_per_block;
     int32_t blocks_per_sm;
     int32_t hist_layout;
     int32_t small_block_area;
     int32_t pixel_tile_rows;
+    int32_t block_tiles;
 } seeds_tuning;
 
 /* Fill p with the paper's defaults for a W x H image and K superpixels

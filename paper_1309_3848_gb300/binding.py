@@ -82,7 +82,7 @@ class seeds_plan_entry(ctypes.Structure):
 class seeds_tuning(ctypes.Structure):
     _fields_ = [("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("hist_layout", ctypes.c_int32), ("small_block_area", ctypes.c_int32),
-                ("pixel_tile_rows", ctypes.c_int32)]
+                ("pixel_tile_rows", ctypes.c_int32), ("block_tiles", ctypes.c_int32)]
 
 
 TUNE_COST_FN = ctypes.CFUNCTYPE(ctypes.c_float, ctypes.POINTER(seeds_tuning), ctypes.c_void_p)
@@ -281,7 +281,7 @@ def load_cached_tuning(path: str, key: str) -> Optional[seeds_tuning]:
         return None
     if not rec:
         return None
-    return seeds_tuning(*[int(rec[f]) for f in _TUNING_FIELDS])
+    return seeds_tuning(*[int(rec.get(f, 0)) for f in _TUNING_FIELDS])
 
 
 def store_tuning(path: str, key: str, t: seeds_tuning, note: str = "") -> None:
@@ -413,8 +413,10 @@ class SeedsContext:
     def check_status(self):
         check(self.status(), "seeds_status")
 
-    def set_tuning(self, threads_per_block=0, blocks_per_sm=0, hist_layout=0, small_block_area=0, pixel_tile_rows=0):
-        t = seeds_tuning(threads_per_block, blocks_per_sm, hist_layout, small_block_area, pixel_tile_rows)
+    def set_tuning(self, threads_per_block=0, blocks_per_sm=0, hist_layout=0, small_block_area=0, pixel_tile_rows=0,
+                   block_tiles=0):
+        t = seeds_tuning(threads_per_block, blocks_per_sm, hist_layout, small_block_area, pixel_tile_rows,
+                         block_tiles)
         check(lib.seeds_set_tuning(self._h, ctypes.byref(t)), "seeds_set_tuning")
 
     def autotune(self, images, outs, reps=3, stream=None, cache: Optional[str] = None) -> seeds_tuning:

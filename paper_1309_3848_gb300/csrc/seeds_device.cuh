@@ -26,8 +26,20 @@ constexpr uint16_t kNoLabel = 0xFFFF;   // labels are < 65535
 constexpr uint32_t kNoMove = 0xFFFFFFFFu;
 
 // op kinds (as in the debug hooks of seeds.h); OP_MINIT and OP_MPHASE are
-// the start and the phases of the means-based pixel iterations (Sec. 6.5)
-enum : int32_t { OP_INIT = 0, OP_PHASE = 1, OP_DESCEND = 2, OP_OUTPUT = 3, OP_CATCHUP = 4, OP_MINIT = 5, OP_MPHASE = 6 };
+// the start and the phases of the means-based pixel iterations (Sec. 6.5).
+// OP_CATCHUP and OP_BTILE occur only in step entries: a catch-up replays the
+// previous phase's moves, and OP_BTILE is a block phase (OP_PHASE, level >=
+// 1) run in warp tiles.
+enum : int32_t {
+    OP_INIT = 0,
+    OP_PHASE = 1,
+    OP_DESCEND = 2,
+    OP_OUTPUT = 3,
+    OP_CATCHUP = 4,
+    OP_MINIT = 5,
+    OP_MPHASE = 6,
+    OP_BTILE = 7
+};
 
 __host__ __device__ inline bool is_phase(int kind) { return kind == OP_PHASE || kind == OP_MPHASE; }
 
@@ -135,6 +147,8 @@ constexpr int kTileH = tile_h(kTileUY);
 constexpr int kTileBytes = (kTileW * kTileH * 2 + kTileUY * kTileUX * 2 + kTileUY * kTileUX + 15) & ~15;
 // the pixel catch-up replays kCatchupPerLane units per lane
 constexpr int kCatchupPerLane = 4;
+// descents and the output: cells (pixels) of a row per thread
+constexpr int kRowChunk = 8;
 
 __host__ __device__ inline int warp_scratch_bytes(int nbins) { return warp_hist_scratch_bytes(nbins) + kTileBytes; }
 
@@ -214,13 +228,22 @@ __host__ __device__ inline void lattice(int nx, int ny, int phase, int cphase, i
     }
 }
 
-// warp tiles of a pixel phase
-__host__ __device__ inline int64_t pixel_tiles(const DevImage &im, int phase, int cphase)
+// warp tiles of a phase on a level's grid (level 0: pixels)
+__host__ __device__ inline int64_t level_tiles(const DevImage &im, int level, int phase, int cphase)
 {
     int cols, rows;
-    lattice(im.W, im.H, phase, cphase, &cols, &rows);
+    lattice(im.nbx[level], im.nby[level], phase, cphase, &cols, &rows);
     return (int64_t)((cols + kTileUX - 1) / kTileUX) * ((rows + im.tile_uy - 1) / im.tile_uy);
 }
+
+__host__ __device__ inline int64_t pixel_tiles(const DevImage &im, int phase, int cphase)
+{
+    return level_tiles(im, 0, phase, cphase);
+}
+
+// emit_entries' `fuse` argument: bits 0-1 the fusion of replays (fuse_step),
+// bit 2 block phases in warp tiles (step_mode)
+constexpr int kTileBlocks = 4;
 
 // Entries of image `img` for its op `o`.  When the moves of op o-1 (a phase)
 // are pending, a phase of the same level replays them unit by unit before
@@ -229,9 +252,11 @@ __host__ __device__ inline int64_t pixel_tiles(const DevImage &im, int phase, in
 // they get a catch-up entry of their own first, whose warps run beside the
 // phase's.  Returns the number of entries written; `vt` advances by their
 // padded thread counts.
-__host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, bool catchup, int fuse,
+__host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, bool catchup, int mode,
                                             StepEntry *out, int64_t *vt)
 {
+    const int fuse = mode & 3;
+    const bool tiles = (mode & kTileBlocks) != 0;
     int n = 0;
     const OpDesc op = op_at(im.L, im.iters, im.means_iters, o);
     int cphase = -1;
@@ -255,6 +280,7 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
     }
     int64_t units = 0;
     int group = 1;
+    int kind = op.kind;
     switch (op.kind) {
     case OP_INIT:
         units = im.K;
@@ -264,6 +290,10 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
     case OP_PHASE:
         if (op.level == 0) {  // warp tiles
             units = pixel_tiles(im, op.phase, cphase);
+            group = 32;
+        } else if (tiles && op.kind == OP_PHASE) {  // block phase in warp tiles
+            kind = OP_BTILE;
+            units = level_tiles(im, op.level, op.phase, cphase);
             group = 32;
         } else {
             int cols, rows;
@@ -275,18 +305,16 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
     case OP_MINIT:  // a thread per pixel
         units = (int64_t)im.W * im.H;
         break;
-    case OP_DESCEND:
-        // a thread per cell of the finer grid, or per 4 pixels of a row
-        units = op.level - 1 >= 1 ? (int64_t)im.nbx[op.level - 1] * im.nby[op.level - 1]
-                                  : (int64_t)im.H * ((im.W + 3) / 4);
+    case OP_DESCEND:  // a thread per kRowChunk cells of a row of the finer grid
+        units = (int64_t)im.nby[op.level - 1] * ((im.nbx[op.level - 1] + kRowChunk - 1) / kRowChunk);
         break;
-    default:  // OP_OUTPUT: a thread per 4 pixels of a row
-        units = (int64_t)im.H * ((im.W + 3) / 4);
+    default:  // OP_OUTPUT: a thread per kRowChunk pixels of a row
+        units = (int64_t)im.H * ((im.W + kRowChunk - 1) / kRowChunk);
         break;
     }
     const int64_t count = (units * group + 31) / 32 * 32;
     if (count > 0) {
-        StepEntry e{img, op.kind, op.level, op.phase, o, (int32_t)units, *vt, group, cphase};
+        StepEntry e{img, kind, op.level, op.phase, o, (int32_t)units, *vt, group, cphase};
         out[n++] = e;
         *vt += count;
     }
@@ -305,6 +333,21 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
 __host__ __device__ inline int fuse_step(int64_t fused_vt, int64_t split_below)
 {
     return fused_vt / 32 >= split_below ? 2 : fused_vt / 32 >= split_below / 8 ? 1 : 0;
+}
+
+// The mode of a step (emit_entries' `mode`): its fusion, and block phases in
+// warp tiles when the step has at least kTileRounds warp tiles per warp slot
+// of the machine.  A tile stages its labels once and judges only its
+// boundary units (compacted), which cuts the per-unit cost of steps with
+// many units; with fewer units the per-unit ops keep more warps busy.
+// `fused_vt`: the step's thread count with fused per-unit entries,
+// `tiled_vt`: with fused tile entries.
+// `policy` (seeds_tuning.block_tiles): 0 never, 1 by that rule, 2 always.
+constexpr int kTileRounds = 2;
+__host__ __device__ inline int step_mode(int64_t fused_vt, int64_t tiled_vt, int64_t split_below, int policy = 0)
+{
+    const bool tiles = policy == 2 || (policy == 1 && tiled_vt / 32 >= kTileRounds * split_below);
+    return fuse_step(fused_vt, split_below) | (tiles ? kTileBlocks : 0);
 }
 
 // An epoch of the serving runtime: for each resident slot, the range of its

@@ -286,10 +286,11 @@ inline int tune_search(const seeds_tuning &start, Cost cost, seeds_tuning *best)
 // pending, so its first step catches them up.  Appends the entries of every
 // step to `ent`, the index of each step's first entry to `first` (and one
 // past the last step's), and each step's padded thread count to `vt`.  Each
-// step is planned twice: with every replay fused, to measure it, then with
-// the fusion fuse_step chooses for that size against split_below warps.
+// step is planned three times: with every replay fused, per-unit block
+// entries and then block tiles, to measure it, then with the mode step_mode
+// chooses for those sizes against split_below warps and tile_policy.
 inline void build_steps(const std::vector<DevImage> &imgs, const std::vector<int> &b, const std::vector<int> &e,
-                        const std::vector<char> &pend, int64_t split_below, std::vector<StepEntry> &ent,
+                        const std::vector<char> &pend, int64_t split_below, int tile_policy, std::vector<StepEntry> &ent,
                         std::vector<int32_t> &first, std::vector<int64_t> &vt)
 {
     const int n = (int)imgs.size();
@@ -298,23 +299,25 @@ inline void build_steps(const std::vector<DevImage> &imgs, const std::vector<int
     StepEntry two[2];
     for (int s = 0; s < nsteps; ++s) {
         first.push_back((int32_t)ent.size());
-        for (int pass = 0; pass < 2; ++pass) {
+        int64_t sized[2] = {0, 0};
+        for (int pass = 0; pass < 3; ++pass) {
             int64_t v = 0;
-            const int fuse = pass == 0 ? 2 : fuse_step(vt.back(), split_below);
+            const int mode =
+                pass == 0 ? 2 : pass == 1 ? 2 | kTileBlocks : step_mode(sized[0], sized[1], split_below, tile_policy);
             for (int i = 0; i < n; ++i) {
                 const DevImage &im = imgs[i];
                 const int o = b[i] + s;
                 if (o >= e[i]) continue;
                 const bool catchup =
                     s == 0 ? (o > 0 && pend[i]) : is_phase(op_at(im.L, im.iters, im.means_iters, o - 1).kind);
-                const int m = emit_entries(im, i, o, catchup, fuse, two, &v);
-                if (pass == 1)
+                const int m = emit_entries(im, i, o, catchup, mode, two, &v);
+                if (pass == 2)
                     for (int q = 0; q < m; ++q) ent.push_back(two[q]);
             }
-            if (pass == 0)
-                vt.push_back(v);
+            if (pass < 2)
+                sized[pass] = v;
             else
-                vt.back() = v;
+                vt.push_back(v);
         }
     }
     first.push_back((int32_t)ent.size());

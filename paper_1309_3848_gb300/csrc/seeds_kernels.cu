@@ -608,6 +608,48 @@ __device__ __noinline__ bool edge_frozen(const DevImage &im, int p, int k, int l
            (up != k && up != kNoLabel && (e[p - im.W] & 2)) || (dn != k && dn != kNoLabel && (e[p] & 2));
 }
 
+// The labels of a warp tile plus a 2-cell halo, from a label grid nx x ny
+// (kNoLabel outside), in TH rows of kTileW cells: lane l loads columns l,
+// l+32 (packed in one register) and, for l < 4, l+64 of every row.  The
+// loads (tile_load) are all issued before the first shared-memory store
+// (tile_store, after a __syncwarp): a warp issues in order, and a store
+// waits for its load, so interleaving them would serialise one L2 round trip
+// per store.
+template <int TH>
+struct TileRegs {
+    uint32_t v01[TH];
+    uint16_t v2[TH];
+};
+
+template <int TH>
+__device__ __forceinline__ void tile_load(TileRegs<TH> &t, const uint16_t *lab, int nx, int ny, int X0, int Y0,
+                                          int lane)
+{
+    static_assert(kTileW > 64 && kTileW <= 96, "three columns per lane");
+#pragma unroll
+    for (int r = 0; r < TH; ++r) {
+        const int yy = Y0 + r;
+        const bool rowin = yy >= 0 && yy < ny;
+        const uint16_t *row = lab + (int64_t)yy * nx;
+        const int x0 = X0 + lane, x1 = x0 + 32, x2 = x0 + 64;
+        const uint32_t a = (rowin && x0 >= 0 && x0 < nx) ? row[x0] : kNoLabel;
+        const uint32_t c = (rowin && x1 >= 0 && x1 < nx) ? row[x1] : kNoLabel;
+        t.v01[r] = a | (c << 16);
+        t.v2[r] = (lane + 64 < kTileW && rowin && x2 >= 0 && x2 < nx) ? row[x2] : kNoLabel;
+    }
+}
+
+template <int TH>
+__device__ __forceinline__ void tile_store(const TileRegs<TH> &t, uint16_t *tsh, int lane)
+{
+#pragma unroll
+    for (int r = 0; r < TH; ++r) {
+        tsh[r * kTileW + lane] = (uint16_t)(t.v01[r] & 0xFFFFu);
+        tsh[r * kTileW + lane + 32] = (uint16_t)(t.v01[r] >> 16);
+        if (lane + 64 < kTileW) tsh[r * kTileW + lane + 64] = t.v2[r];
+    }
+}
+
 // Replay one move k -> n of pixel p into buffer `buf`.
 __device__ __forceinline__ void replay_pixel(const DevImage &im, int buf, int p, uint32_t d)
 {
@@ -664,22 +706,8 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
     // one L2 round trip per store.  Lane l loads columns l, l+32 (packed in
     // one register) and, for l < 4, l+64 of each row.
     constexpr int TH = tile_h(UY);
-    static_assert(kTileW > 64 && kTileW <= 96, "three columns per lane");
-    const int X0 = 2 * tx * kTileUX + px - 2, Y0 = 2 * uy0 + py - 2;
-    const uint16_t *lab = im.lab[0][b];
-    uint32_t v01[TH];
-    uint16_t v2[TH];
-#pragma unroll
-    for (int r = 0; r < TH; ++r) {
-        const int yy = Y0 + r;
-        const bool rowin = yy >= 0 && yy < H;
-        const uint16_t *row = lab + (int64_t)yy * W;
-        const int x0 = X0 + lane, x1 = x0 + 32, x2 = x0 + 64;
-        const uint32_t a = (rowin && x0 >= 0 && x0 < W) ? row[x0] : kNoLabel;
-        const uint32_t c = (rowin && x1 >= 0 && x1 < W) ? row[x1] : kNoLabel;
-        v01[r] = a | (c << 16);
-        v2[r] = (lane + 64 < kTileW && rowin && x2 >= 0 && x2 < W) ? row[x2] : kNoLabel;
-    }
+    TileRegs<TH> stage;
+    tile_load<TH>(stage, im.lab[0][b], W, H, 2 * tx * kTileUX + px - 2, 2 * uy0 + py - 2, lane);
     uint16_t jv[UY];
 #pragma unroll
     for (int r = 0; r < UY; ++r) {
@@ -689,12 +717,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
     __syncwarp();  // keeps the loads above the stores
     uint16_t *jsh = tsh + kTileW * TH;
     uint8_t *lst = (uint8_t *)(jsh + UY * kTileUX);
-#pragma unroll
-    for (int r = 0; r < TH; ++r) {
-        tsh[r * kTileW + lane] = (uint16_t)(v01[r] & 0xFFFFu);
-        tsh[r * kTileW + lane + 32] = (uint16_t)(v01[r] >> 16);
-        if (lane + 64 < kTileW) tsh[r * kTileW + lane + 64] = v2[r];
-    }
+    tile_store<TH>(stage, tsh, lane);
 #pragma unroll
     for (int r = 0; r < UY; ++r) jsh[r * 32 + lane] = jv[r];
 
@@ -917,19 +940,14 @@ __device__ __forceinline__ void replay_small_block(const DevImage &im, int buf, 
         replay_small_block_t<kSmallMax>(im, buf, level, bx, by, d);
 }
 
-// Judge small block (bx,by); SM bounds its pixel count, so the dedupe of its
-// bins unrolls to SM*SM compares.
+// Judge small block (bx,by) of label k that may leave, with candidates
+// cand (ascending, kNoLabel in empty slots); SM bounds its pixel count, so
+// the dedupe of its bins unrolls to SM*SM compares.
 template <int SM>
-__device__ uint32_t judge_small_block(const DevImage &im, int b, int nb, int level, int bx, int by)
+__device__ uint32_t judge_small_block_c(const DevImage &im, int b, int nb, int level, int bx, int by, int k,
+                                        const int cand[4], int x0, int x1, int y0, int y1)
 {
-    const int nx = im.nbx[level], ny = im.nby[level];
-    const uint16_t *lab = im.lab[level][b];
-    // the block's extent is read with its labels: one trip to L2 fewer
-    const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
-    const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
-    const int k = lab[by * nx + bx];
-    int cand[4];
-    if (unit_candidates(lab, nx, ny, bx, by, k, cand) == 0) return kNoMove;
+    const int nx = im.nbx[level];
     const int32_t *hist = im.hist[b], *size = im.size[b];
     const int bw = x1 - x0, m = bw * (y1 - y0);
     int jj[SM];
@@ -984,6 +1002,21 @@ __device__ uint32_t judge_small_block(const DevImage &im, int b, int nb, int lev
     move_block_counts<SM>(im, nb, k, n, jj, m);
     move_size(im, nb, k, n, m);
     return ((uint32_t)k << 16) | (uint32_t)n;
+}
+
+// Judge small block (bx,by) from the label grid: its candidates, then the core.
+template <int SM>
+__device__ uint32_t judge_small_block(const DevImage &im, int b, int nb, int level, int bx, int by)
+{
+    const int nx = im.nbx[level], ny = im.nby[level];
+    const uint16_t *lab = im.lab[level][b];
+    // the block's extent is read with its labels: one trip to L2 fewer
+    const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
+    const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
+    const int k = lab[by * nx + bx];
+    int cand[4];
+    if (unit_candidates(lab, nx, ny, bx, by, k, cand) == 0) return kNoMove;
+    return judge_small_block_c<SM>(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1);
 }
 
 // Unit (ux,uy) of the union lattice: replay the previous phase's move of that
@@ -1072,6 +1105,10 @@ __device__ void replay_large_block(const DevImage &im, int buf, int level, int b
     }
 }
 
+__device__ uint32_t judge_large_block_c(const DevImage &im, int b, int nb, int level, int bx, int by, int k,
+                                        const int cand[4], int x0, int x1, int y0, int y1, int lane, int32_t *wsh,
+                                        int max_nbins);
+
 // Unit (ux,uy) of the union lattice, one warp: replay the previous phase's
 // move of that unit (cphase >= 0), then judge this phase's unit.
 __device__ void op_block_phase_warp(const DevImage &im, int o, int level, int phase, int cphase, int units, int u,
@@ -1098,17 +1135,28 @@ __device__ void op_block_phase_warp(const DevImage &im, int o, int level, int ph
     const int uu = uy * ncols + ux;
     const int bx = 2 * ux + (phase & 1), by = 2 * uy + (phase >> 1);
     const uint16_t *lab = im.lab[level][b];
-    // the block's extent is read with its labels, the sizes before the
-    // histogram build: fewer dependent trips to L2
+    // the block's extent is read with its labels: fewer dependent trips to L2
     const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
     const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
     const int k = lab[by * nx + bx];
     int cand[4];
     const int nc = unit_candidates(lab, nx, ny, bx, by, k, cand);
-    if (nc == 0) {
-        if (lane == 0) im.dec[b][SEEDS_IDX(im, uu, im.units_cap)] = kNoMove;
-        return;
-    }
+    const uint32_t d = nc == 0 ? kNoMove
+                               : judge_large_block_c(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1, lane, wsh,
+                                                     max_nbins);
+    if (lane == 0) im.dec[b][SEEDS_IDX(im, uu, im.units_cap)] = d;
+}
+
+// Judge large block (bx,by) of label k that may leave, with candidates cand
+// (ascending, kNoLabel in empty slots), the whole warp: the block's sparse
+// histogram in the warp's scratch, the intersection sums of Prop. 1, the
+// move applied to buffer nb.  Returns the decision (the same on every lane).
+__device__ uint32_t judge_large_block_c(const DevImage &im, int b, int nb, int level, int bx, int by, int k,
+                                        const int cand[4], int x0, int x1, int y0, int y1, int lane, int32_t *wsh,
+                                        int max_nbins)
+{
+    const int nx = im.nbx[level], ny = im.nby[level];
+    // the sizes are read before the histogram build: fewer dependent trips to L2
     const int32_t *size = im.size[b];
     int32_t sz[4];
 #pragma unroll
@@ -1136,13 +1184,148 @@ __device__ void op_block_phase_warp(const DevImage &im, int o, int level, int ph
         }
     const bool moves = Sb * s_rest > S_st * zb;
     block_sparse_apply_clear(im, nb, moves ? k : -1, n, nd, lane, wsh, max_nbins);
-    if (lane == 0) {
-        im.dec[b][SEEDS_IDX(im, uu, im.units_cap)] = moves ? (((uint32_t)k << 16) | (uint32_t)n) : kNoMove;
-        if (moves) {
-            im.lab[level][nb][SEEDS_IDX(im, by * nx + bx, (int64_t)nx * ny)] = (uint16_t)SEEDS_IDX(im, n, im.K);
-            move_size(im, nb, k, n, m);
+    if (lane == 0 && moves) {
+        im.lab[level][nb][SEEDS_IDX(im, by * nx + bx, (int64_t)nx * ny)] = (uint16_t)SEEDS_IDX(im, n, im.K);
+        move_size(im, nb, k, n, m);
+    }
+    return moves ? (((uint32_t)k << 16) | (uint32_t)n) : kNoMove;
+}
+
+// ---------------------------------------------------------------------------
+// block phase in warp tiles (steps with many units)
+// ---------------------------------------------------------------------------
+
+// One warp-tile of a block phase: units (ux, uy) of the phase's parity class
+// on the level's block grid, ux in a 32-wide column range (one per lane), uy
+// in a UY-row range, as in the pixel tile.  The block labels of the tile and
+// a 2-cell halo are staged in shared memory; the warp replays the previous
+// phase's moves of the same unit positions (cphase >= 0), marks the units
+// that sit on a boundary and may leave (pass 1, from shared memory), and
+// judges only those.  SMALL: blocks of at most small_area pixels, judged a
+// lane each over the compacted list; otherwise the warp judges the marked
+// blocks one after another (sparse histogram in its scratch).  The moves
+// and decisions are the ones the per-unit ops take.
+template <bool SMALL, int UY>
+__device__ __noinline__ void op_block_tile(const DevImage &im, int o, int level, int phase, int cphase, int tiles, int tile,
+                              int lane, int32_t *wsh, uint16_t *tsh, int max_nbins)
+{
+    if (tile >= tiles) return;
+    const int b = o & 1, nb = b ^ 1;
+    const int nx = im.nbx[level], ny = im.nby[level];
+    const int px = phase & 1, py = phase >> 1;
+    const int ncols = (nx - px + 1) >> 1, nrows = (ny - py + 1) >> 1;
+    int mcols, mrows;
+    lattice(nx, ny, phase, cphase, &mcols, &mrows);
+    const int tiles_x = (mcols + kTileUX - 1) / kTileUX;
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const int ux = tx * kTileUX + lane, uy0 = ty * UY;
+
+    // the previous phase's decisions for the same unit positions
+    uint32_t cd[UY];
+    int ccols = 0, crows = 0, cpx = 0, cpy = 0;
+    if (cphase >= 0) {
+        cpx = cphase & 1;
+        cpy = cphase >> 1;
+        ccols = (nx - cpx + 1) >> 1;
+        crows = (ny - cpy + 1) >> 1;
+    }
+#pragma unroll
+    for (int r = 0; r < UY; ++r) {
+        const int uy = uy0 + r;
+        cd[r] = (ux < ccols && uy < crows) ? im.dec[nb][SEEDS_IDX(im, uy * ccols + ux, im.units_cap)] : kNoMove;
+    }
+    constexpr int TH = tile_h(UY);
+    TileRegs<TH> stage;
+    tile_load<TH>(stage, im.lab[level][b], nx, ny, 2 * tx * kTileUX + px - 2, 2 * uy0 + py - 2, lane);
+    __syncwarp();  // keeps the loads above the stores
+    tile_store<TH>(stage, tsh, lane);
+
+    // replay the previous phase's moves into buffer nb (the staged labels
+    // are buffer b's)
+    if constexpr (SMALL) {
+#pragma unroll
+        for (int r = 0; r < UY; ++r)
+            if (cd[r] != kNoMove) replay_small_block(im, nb, level, 2 * ux + cpx, 2 * (uy0 + r) + cpy, cd[r]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < UY; ++r) {
+            unsigned m = __ballot_sync(0xffffffffu, cd[r] != kNoMove);
+            while (m) {
+                const int l = __ffs(m) - 1;
+                m &= m - 1;
+                const uint32_t d = __shfl_sync(0xffffffffu, cd[r], l);
+                replay_large_block(im, nb, level, 2 * (tx * kTileUX + l) + cpx, 2 * (uy0 + r) + cpy, d, lane, wsh,
+                                   max_nbins);
+            }
         }
     }
+    __syncwarp();
+
+    // pass 1: boundary units that may leave; the others decide "stay" here
+    unsigned mine = 0;
+#pragma unroll
+    for (int r = 0; r < UY; ++r) {
+        const int uy = uy0 + r;
+        if (ux < ncols && uy < nrows) {
+            const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * lane + 2);
+            if (may_leave([&](int dx, int dy) { return (int)T[dy * kTileW + dx]; }, (int)T[0]))
+                mine |= 1u << r;
+            else
+                im.dec[b][SEEDS_IDX(im, uy * ncols + ux, im.units_cap)] = kNoMove;
+        }
+    }
+
+    if constexpr (SMALL) {
+        // compacted: every lane judges one marked unit at a time
+        uint8_t *lst = (uint8_t *)(tsh + kTileW * TH);
+        int nbd = 0;
+#pragma unroll
+        for (int r = 0; r < UY; ++r) {
+            const unsigned bal = __ballot_sync(0xffffffffu, (mine >> r) & 1u);
+            if ((mine >> r) & 1u) lst[nbd + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(r * 32 + lane);
+            nbd += __popc(bal);
+        }
+        __syncwarp();
+        for (int i = lane; i < nbd; i += 32) {
+            const int e = lst[i], r = e >> 5, l = e & 31;
+            const int uxe = tx * kTileUX + l, uy = uy0 + r;
+            const int bx = 2 * uxe + px, by = 2 * uy + py;
+            const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
+            const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
+            const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * l + 2);
+            const int k = T[0];
+            int cand[4];
+            sorted_candidates(T[-1], T[1], T[-kTileW], T[kTileW], k, cand);  // pass 1 found that it may leave
+            const int ma = im.maxarea[level];
+            const uint32_t d =
+                ma <= 4   ? judge_small_block_c<4>(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1)
+                : ma <= 9 ? judge_small_block_c<9>(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1)
+                          : judge_small_block_c<kSmallMax>(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1);
+            im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = d;
+        }
+    } else {
+        // the warp judges the marked blocks one after another
+#pragma unroll
+        for (int r = 0; r < UY; ++r) {
+            unsigned m = __ballot_sync(0xffffffffu, (mine >> r) & 1u);
+            while (m) {
+                const int l = __ffs(m) - 1;
+                m &= m - 1;
+                const int uxe = tx * kTileUX + l, uy = uy0 + r;
+                const int bx = 2 * uxe + px, by = 2 * uy + py;
+                const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
+                const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
+                const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * l + 2);
+                const int k = T[0];
+                int cand[4];
+                sorted_candidates(T[-1], T[1], T[-kTileW], T[kTileW], k, cand);
+                const uint32_t d =
+                    judge_large_block_c(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1, lane, wsh, max_nbins);
+                if (lane == 0) im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = d;
+            }
+        }
+    }
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -1199,60 +1382,66 @@ __device__ void op_catchup(const DevImage &im, int o, int level, int phase, int 
 // ---------------------------------------------------------------------------
 
 // level `level` -> level-1 (both buffers); the finer grid splits each block
-// 2x2; at the pixel level a thread writes 4 pixels of a row
+// 2x2.  A thread writes kRowChunk consecutive cells of one row of the finer
+// grid (pixels at the last descent), with one 16-byte store per buffer where
+// the row allows it.
 __device__ void op_descend(const DevImage &im, int o, int level, int units, int c)
 {
     if (c >= units) return;
-    const int b = o & 1, t = level - 1;
-    const uint16_t *src = im.lab[level][b];
-    if (t >= 1) {
-        const int nx = im.nbx[t];
-        const int cy = c / nx, cx = c - cy * nx;
-        const uint16_t v = src[(cy >> 1) * im.nbx[level] + (cx >> 1)];
-        im.lab[t][0][c] = v;
-        im.lab[t][1][c] = v;
-    } else {
-        const int W = im.W, cw = (W + 3) >> 2;
-        const int y = c / cw, x0 = 4 * (c - y * cw);
-        const int n1x = im.nbx[1], n1y = im.nby[1];
-        // block b holds x iff floor(b*W/n) <= x < floor((b+1)*W/n); the
-        // next pixels step into the next block when (bx+1)*W < (x+1)*n
-        const int by = (int)(((int64_t)(y + 1) * n1y - 1) / im.H);
-        int bx = (int)(((int64_t)(x0 + 1) * n1x - 1) / W);
-        const uint16_t *row = src + by * n1x;
-        uint16_t v[4];
+    const int t = level - 1;
+    const uint16_t *src = im.lab[level][o & 1];
+    const int nx = im.nbx[t];  // W at the pixel level
+    const int cpr = (nx + kRowChunk - 1) / kRowChunk;
+    const int y = c / cpr, x0 = (c - y * cpr) * kRowChunk;
+    uint16_t v[kRowChunk];
+    if (t >= 1) {  // cell (x, y) of the finer grid lies in cell (x/2, y/2)
+        const uint16_t *row = src + (y >> 1) * im.nbx[level];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (q > 0 && (int64_t)(bx + 1) * W < (int64_t)(x0 + q + 1) * n1x) ++bx;
+        for (int q = 0; q < kRowChunk; ++q) v[q] = x0 + q < nx ? row[(x0 + q) >> 1] : 0;
+    } else {
+        // level-1 block bx holds x iff floor(bx*W/n) <= x < floor((bx+1)*W/n);
+        // the next pixel steps into the next block when (bx+1)*W < (x+1)*n
+        // (every product is below 2^31: W, H, n <= 32768)
+        const int W = nx, n1x = im.nbx[1], n1y = im.nby[1];
+        const int by = ((y + 1) * n1y - 1) / im.H;
+        int bx = ((x0 + 1) * n1x - 1) / W;
+        const uint16_t *row = src + by * n1x;
+#pragma unroll
+        for (int q = 0; q < kRowChunk; ++q) {
+            if (q > 0 && (bx + 1) * W < (x0 + q + 1) * n1x) ++bx;
             v[q] = row[min(bx, n1x - 1)];
         }
-        const int64_t p0 = (int64_t)y * W + x0;
-        if ((W & 3) == 0) {  // 4 labels in one 8-byte store per buffer
-            const ushort4 w4 = make_ushort4(v[0], v[1], v[2], v[3]);
-            *(ushort4 *)(im.lab[0][0] + p0) = w4;
-            *(ushort4 *)(im.lab[0][1] + p0) = w4;
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (x0 + q < W) im.lab[0][0][p0 + q] = im.lab[0][1][p0 + q] = v[q];
-        }
     }
-}
-
-__device__ void op_output(const DevImage &im, int o, int units, int c)
-{
-    if (c >= units) return;
-    const int W = im.W, cw = (W + 3) >> 2;
-    const int y = c / cw, x0 = 4 * (c - y * cw);
-    const uint16_t *lab = im.lab[0][o & 1] + (int64_t)y * W;
-    int32_t *out = im.out + (int64_t)y * W;
-    if ((W & 3) == 0 && ((uintptr_t)im.out & 15) == 0) {  // one 8-byte load, one 16-byte store
-        const ushort4 v = *(const ushort4 *)(lab + x0);
-        *(int4 *)(out + x0) = make_int4(v.x, v.y, v.z, v.w);
+    uint16_t *d0 = im.lab[t][0] + (int64_t)y * nx + x0, *d1 = im.lab[t][1] + (int64_t)y * nx + x0;
+    if (nx % kRowChunk == 0) {  // whole chunks, rows 16-byte aligned
+        const uint4 w = make_uint4(v[0] | (uint32_t)v[1] << 16, v[2] | (uint32_t)v[3] << 16,
+                                   v[4] | (uint32_t)v[5] << 16, v[6] | (uint32_t)v[7] << 16);
+        *(uint4 *)d0 = w;
+        *(uint4 *)d1 = w;
         return;
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < kRowChunk; ++q)
+        if (x0 + q < nx) d0[q] = d1[q] = v[q];
+}
+
+// int32 labels: a thread converts kRowChunk consecutive pixels of a row
+// (one 16-byte load, two 16-byte stores where the row allows it)
+__device__ void op_output(const DevImage &im, int o, int units, int c)
+{
+    if (c >= units) return;
+    const int W = im.W, cpr = (W + kRowChunk - 1) / kRowChunk;
+    const int y = c / cpr, x0 = (c - y * cpr) * kRowChunk;
+    const uint16_t *lab = im.lab[0][o & 1] + (int64_t)y * W;
+    int32_t *out = im.out + (int64_t)y * W;
+    if (W % kRowChunk == 0 && ((uintptr_t)im.out & 15) == 0) {
+        const uint4 v = *(const uint4 *)(lab + x0);
+        *(int4 *)(out + x0) = make_int4(v.x & 0xFFFF, v.x >> 16, v.y & 0xFFFF, v.y >> 16);
+        *(int4 *)(out + x0 + 4) = make_int4(v.z & 0xFFFF, v.z >> 16, v.w & 0xFFFF, v.w >> 16);
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < kRowChunk; ++q)
         if (x0 + q < W) out[x0 + q] = lab[x0 + q];
 }
 
@@ -1380,6 +1569,23 @@ __global__ void __launch_bounds__(1024, 1) seeds_persistent(const DevImage *__re
                     op_block_phase_warp(im, E.opidx, E.level, E.phase, E.cphase, E.units, off >> 5, lane, wsh,
                                         S.max_nbins);
                 break;
+            case OP_BTILE:
+                if (level_group(im, E.level) == 1) {
+                    if (im.tile_uy == 2)
+                        op_block_tile<true, 2>(im, E.opidx, E.level, E.phase, E.cphase, E.units, off >> 5, lane, wsh,
+                                               tsh, S.max_nbins);
+                    else
+                        op_block_tile<true, kTileUY>(im, E.opidx, E.level, E.phase, E.cphase, E.units, off >> 5, lane,
+                                                     wsh, tsh, S.max_nbins);
+                } else {
+                    if (im.tile_uy == 2)
+                        op_block_tile<false, 2>(im, E.opidx, E.level, E.phase, E.cphase, E.units, off >> 5, lane,
+                                                wsh, tsh, S.max_nbins);
+                    else
+                        op_block_tile<false, kTileUY>(im, E.opidx, E.level, E.phase, E.cphase, E.units, off >> 5,
+                                                      lane, wsh, tsh, S.max_nbins);
+                }
+                break;
             case OP_MPHASE:
                 op_means_tile(im, E.opidx, E.phase, E.cphase, E.units, off >> 5, lane, tsh);
                 break;
@@ -1492,9 +1698,10 @@ __global__ void epoch_schedule_kernel(const DevImage *imgs, EpochPlan plan, Step
     int c = 0;
     int fuse = 2;
     if (s < plan.nsteps) {
-        int64_t vf = 0;  // the step's size with fused entries
-        for (int pass = 0; pass < 2; ++pass) {
+        int64_t sized[2] = {0, 0};  // the step's size with fused per-unit entries, with fused tiles
+        for (int pass = 0; pass < 3; ++pass) {
             int64_t v = 0;
+            const int mode = pass == 0 ? 2 : pass == 1 ? 2 | kTileBlocks : fuse;
             for (int i = 0; i < plan.n; ++i) {
                 const EpochSlot &q = plan.s[i];
                 const int o = q.begin + s;
@@ -1502,13 +1709,11 @@ __global__ void epoch_schedule_kernel(const DevImage *imgs, EpochPlan plan, Step
                 const DevImage &im = imgs[q.slot];
                 const bool cu =
                     s == 0 ? q.catchup != 0 : is_phase(op_at(im.L, im.iters, im.means_iters, o - 1).kind);
-                const int m = emit_entries(im, q.slot, o, cu, fuse, tmp, &v);
-                if (pass == 1) c += m;
+                const int m = emit_entries(im, q.slot, o, cu, mode, tmp, &v);
+                if (pass == 2) c += m;
             }
-            if (pass == 0) {
-                vf = v;
-                fuse = fuse_step(vf, plan.split_below);
-            }
+            if (pass < 2) sized[pass] = v;
+            if (pass == 1) fuse = step_mode(sized[0], sized[1], plan.split_below);
         }
     }
     cnt[s] = c;
@@ -1700,9 +1905,10 @@ __global__ void static_setup_kernel(StaticSetup S)
         int64_t vt = 0;
         const bool catchup = o > 0 && is_phase(op_at(im.L, im.iters, im.means_iters, o - 1).kind);
         StepEntry tmp[2];
-        int64_t vf = 0;
+        int64_t vf = 0, vtile = 0;
         emit_entries(im, 0, o, catchup, 2, tmp, &vf);
-        ne += emit_entries(im, 0, o, catchup, fuse_step(vf, S.split_below), S.ent + ne, &vt);
+        emit_entries(im, 0, o, catchup, 2 | kTileBlocks, tmp, &vtile);
+        ne += emit_entries(im, 0, o, catchup, step_mode(vf, vtile, S.split_below), S.ent + ne, &vt);
         S.vt[o] = vt;
     }
     S.first[S.nops] = ne;
@@ -1753,7 +1959,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
 
     StaticSetup S;
     std::memset(&S, 0, sizeof(S));
-    const seeds_tuning knobs{0, 0, 0, kSmallMax, kTileUY};
+    const seeds_tuning knobs{0, 0, 0, kSmallMax, kTileUY, 0};
     S.img = host::make_dev_image(h, base + o_state, knobs, IoEntry{d_rgb, row_stride_bytes, d_labels_out},
                                  (int32_t *)(base + o_err));
     S.ent = (StepEntry *)(base + o_ent);

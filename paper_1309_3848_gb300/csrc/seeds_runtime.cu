@@ -46,7 +46,7 @@ struct seeds_ctx {
     int32_t *d_err = nullptr;
     int32_t *d_steps = nullptr;  // steps run by the last anytime launch
     bool stopped_state = false;  // the last launch was an anytime run: no final state to output
-    seeds_tuning tune{1024, 0, 0, 16, 4};
+    seeds_tuning tune{1024, 0, 0, 16, 4, 0};
     int grid = 0;
     size_t smem = 0;
     int max_nbins = 1;
@@ -146,7 +146,7 @@ int get_schedule(seeds_ctx *c, int kind, int ob, int oe, const Schedule **out)
     std::vector<int64_t> vt;
     std::vector<char> pend(n);
     for (int i = 0; i < n; ++i) pend[i] = b[i] > 0 && c->pending[i] == b[i] - 1;
-    build_steps(c->h_imgs, b, e, pend, (int64_t)c->sm_count * 32, ent, first, vt);
+    build_steps(c->h_imgs, b, e, pend, (int64_t)c->sm_count * 32, c->tune.block_tiles, ent, first, vt);
     if (ent.empty()) ent.push_back(StepEntry{});  // keep the buffer non-empty
 
     const size_t b_ent = align_up(ent.size() * sizeof(StepEntry));
@@ -371,6 +371,7 @@ int normalize_tuning(const seeds_tuning &t, seeds_tuning *out)
         return SEEDS_ERR_INVALID;
     if (n.blocks_per_sm < 0 || n.hist_layout < 0 || n.hist_layout > 1) return SEEDS_ERR_INVALID;
     if (n.small_block_area < 1 || n.small_block_area > kSmallMax) return SEEDS_ERR_INVALID;
+    if (n.block_tiles < 0 || n.block_tiles > 2) return SEEDS_ERR_INVALID;
     *out = n;
     return SEEDS_OK;
 }
@@ -384,7 +385,7 @@ int seeds_plan(const seeds_params *p, int32_t n, const seeds_tuning *t, int32_t 
     if (!p || n <= 0 || n > SEEDS_MAX_BATCH || sm_count <= 0 || !n_entries || !n_steps || cap < 0 || step_cap < 0)
         return SEEDS_ERR_INVALID;
     seeds_tuning tune;
-    if (normalize_tuning(t ? *t : seeds_tuning{0, 0, 0, 0, 0}, &tune)) return SEEDS_ERR_INVALID;
+    if (normalize_tuning(t ? *t : seeds_tuning{0, 0, 0, 0, 0, 0}, &tune)) return SEEDS_ERR_INVALID;
     std::vector<DevImage> imgs(n);
     std::vector<int> b(n, 0), e(n);
     std::vector<char> pend(n, 0);
@@ -403,7 +404,7 @@ int seeds_plan(const seeds_params *p, int32_t n, const seeds_tuning *t, int32_t 
     std::vector<StepEntry> ent;
     std::vector<int32_t> first;
     std::vector<int64_t> vt;
-    build_steps(imgs, b, e, pend, (int64_t)sm_count * 32, ent, first, vt);
+    build_steps(imgs, b, e, pend, (int64_t)sm_count * 32, tune.block_tiles, ent, first, vt);
     *n_entries = (int32_t)ent.size();
     *n_steps = (int32_t)vt.size();
     if (!out && !step_first && !step_threads) return SEEDS_OK;  // the sizes alone

@@ -106,7 +106,7 @@ size_t request_bytes(const ImageHost &h, size_t *rgb_off, size_t *out_off)
 struct seeds_server {
     int device = 0, sm_count = 0;
     seeds_server_config cfg{};
-    seeds_tuning tune{1024, 0, 0, 16, 4};
+    seeds_tuning tune{1024, 0, 0, 16, 4, 0};
     int max_nbins = 1;
     unsigned char *arena = nullptr;
     ArenaAllocator alloc;

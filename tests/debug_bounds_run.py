@@ -25,7 +25,8 @@ def main():
                                    (64, 64, 4, 16, 2)]]
     imgs = gc.make_images(jobs)
     results = {}
-    for tuning in (None, dict(small_block_area=1, pixel_tile_rows=2), dict(threads_per_block=256, hist_layout=1)):
+    for tuning in (None, dict(small_block_area=1, pixel_tile_rows=2), dict(threads_per_block=256, hist_layout=1),
+                   dict(block_tiles=2, small_block_area=4), dict(block_tiles=2, pixel_tile_rows=2, hist_layout=1)):
         got, ctx = gc.gpu_run(binding, torch, jobs, imgs, tuning)
         results[str(tuning)] = [gc.first_mismatch(a, b) for a, b in zip(got, gc.oracle_many(jobs, imgs))]
     # an anytime stop inside the block levels

@@ -43,3 +43,29 @@ def test_reference_line():
 
 def test_other_ranks_print_nothing():
     assert run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_reference_config_is_the_gpu_arms():
+    """Both arms describe the workload with the same config (the GPU arm
+    calls config_of on the workload's jobs)."""
+    bench = bench_module()
+    d = json.loads(run()[0])
+    assert d["config"] == bench.config_of("plain_481x321", bench.workload_jobs("plain_481x321"))
+
+
+def test_oracle_sample_of_the_4k_batch():
+    """Images above 1920x1080 are timed by their top-left quarter with a
+    quarter of the superpixels; smaller ones as they are."""
+    import numpy as np
+    from paper_1309_3848_gb300 import synth
+    bench = bench_module()
+    jobs = synth.batch_4k(2) + synth.plain_481()
+    imgs = [np.zeros((j.image.height, j.image.width, 3), np.uint8) for j in jobs]
+    imgs[0][:1080, :1920] = 7
+    sj, si, what = bench.oracle_sample(jobs, imgs)
+    assert [(j.image.width, j.image.height, j.num_superpixels) for j in sj] == \
+        [(1920, 1080, 1250), (1920, 1080, 1250), (481, 321, 200)]
+    assert all(j.bins_per_channel == o.bins_per_channel and j.levels == o.levels and
+               j.iters_per_level == o.iters_per_level for j, o in zip(sj, jobs))
+    assert si[0].shape == (1080, 1920, 3) and int(si[0].min()) == 7 and si[2] is imgs[2]
+    assert "quarter" in what

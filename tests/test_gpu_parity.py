@@ -38,14 +38,16 @@ STEP_CASES = [
 ]
 
 
+@pytest.mark.parametrize("tiles", [0, 2], ids=["per-unit", "tiled"])
 @pytest.mark.parametrize("job", STEP_CASES, ids=["481x321", "64x48", "97x61_B8", "50x37_L0"])
-def test_state_matches_after_every_op(torch, binding, job):
+def test_state_matches_after_every_op(torch, binding, job, tiles):
     W, H = job.image.width, job.image.height
     img = synth.make_image(job.image)
     L = gc.oracle_levels(job)
     assert L == gc.gpu_levels(binding, job)
     r = ref.Ref(W, H, job.num_superpixels, L, job.bins_per_channel, job.iters_per_level, job.patch, job.gamma)
     ctx = binding.SeedsContext([gc.params_for(binding, job)])
+    ctx.set_tuning(block_tiles=tiles)
     d = torch.from_numpy(img).cuda()
     nops = ctx.num_ops(0)
     moved_total = 0
@@ -75,7 +77,9 @@ def test_state_matches_after_every_op(torch, binding, job):
 
 
 @pytest.mark.parametrize("tuning", [dict(small_block_area=1), dict(small_block_area=16, hist_layout=1),
-                                    dict(pixel_tile_rows=2)])
+                                    dict(pixel_tile_rows=2), dict(block_tiles=2),
+                                    dict(block_tiles=2, pixel_tile_rows=2, small_block_area=4, hist_layout=1),
+                                    dict(block_tiles=2, small_block_area=1)])
 def test_mixed_bin_batch_matches_after_every_op(torch, binding, tuning):
     """Images with different bin counts (and so different scratch use) in
     one batch, every block judged by a warp or by a thread: full state of
@@ -202,7 +206,9 @@ def test_edge_sizes(torch, binding):
 TUNINGS = [dict(threads_per_block=128), dict(threads_per_block=512, hist_layout=1),
            dict(hist_layout=1, small_block_area=1), dict(blocks_per_sm=1, small_block_area=4),
            dict(threads_per_block=256, blocks_per_sm=2, hist_layout=0, small_block_area=9),
-           dict(pixel_tile_rows=2), dict(threads_per_block=512, pixel_tile_rows=2, small_block_area=1)]
+           dict(pixel_tile_rows=2), dict(threads_per_block=512, pixel_tile_rows=2, small_block_area=1),
+           dict(block_tiles=2), dict(block_tiles=2, small_block_area=4, pixel_tile_rows=2),
+           dict(block_tiles=1, threads_per_block=256)]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)

@@ -10,7 +10,12 @@ import pytest
 from paper_1309_3848_gb300 import binding as b
 from paper_1309_3848_gb300 import synth
 
-INIT, PHASE, DESCEND, OUTPUT, CATCHUP, MINIT, MPHASE = range(7)
+INIT, PHASE, DESCEND, OUTPUT, CATCHUP, MINIT, MPHASE, BTILE = range(8)
+
+
+def kind_of(e):
+    """The op an entry runs: a block phase in warp tiles is a phase."""
+    return PHASE if e["op"] == BTILE else e["op"]
 
 
 def op_list(p):
@@ -85,12 +90,13 @@ def test_every_op_runs_once_in_order_and_every_phase_is_replayed_once(case, sms)
                 replayed[i].add(e["opidx"] - 1)
                 continue
             assert e["opidx"] == s, "image %d runs op %d at step %d" % (i, e["opidx"], s)
-            assert (e["op"], e["level"]) == ops[i][s][:2]
-            if e["op"] in (PHASE, MPHASE):
+            assert (kind_of(e), e["level"]) == ops[i][s][:2]
+            assert e["op"] != BTILE or e["level"] > 0
+            if kind_of(e) in (PHASE, MPHASE):
                 assert e["phase"] == ops[i][s][2]
             if e["cphase"] >= 0:  # fused: the previous op is a phase of the same kind and level
                 kind, level, phase = ops[i][s - 1]
-                assert (kind, level, phase) == (e["op"], e["level"], e["cphase"])
+                assert (kind, level, phase) == (kind_of(e), e["level"], e["cphase"])
                 replayed[i].add(s - 1)
             seen[i].append(s)
     for i, o in enumerate(ops):
@@ -123,16 +129,23 @@ def test_units_follow_the_lattices():
                 cols, rows = max(cols, c2), max(rows, r2)
             assert e["units"] == cols * rows
     # pixel phases: warp tiles of 32 x 4 (or 32 x 2) units
+    # pixel phases, and block phases of steps run in tiles: warp tiles of
+    # 32 x 4 (or 32 x 2) units
     for rows_per_tile in (4, 2):
-        t = b.seeds_tuning(0, 0, 0, 16, rows_per_tile)
-        for threads, ents in b.plan([p], 1, t):  # one SM: every step fused
+        t = b.seeds_tuning(0, 0, 0, 16, rows_per_tile, 1)
+        tiled = 0
+        for threads, ents in b.plan([p], 1, t):  # one SM: every step fused, block steps tiled
             for e in ents:
-                if e["op"] == PHASE and e["level"] == 0:
-                    cols, rows = lattice(p.width, p.height, e["phase"])
+                if (e["op"] == PHASE and e["level"] == 0) or e["op"] == BTILE:
+                    cols, rows = lattice(*g[e["level"]], e["phase"])
                     if e["cphase"] >= 0:
-                        c2, r2 = lattice(p.width, p.height, e["cphase"])
+                        c2, r2 = lattice(*g[e["level"]], e["cphase"])
                         cols, rows = max(cols, c2), max(rows, r2)
-                    assert e["units"] == -(-cols // 32) * -(-rows // rows_per_tile)
+                    assert e["units"] == -(-cols // 32) * -(-rows // rows_per_tile) and e["group"] == 32
+                    tiled += e["op"] == BTILE
+        # with 32 warp slots, levels 2 and 1 of 1080p have at least 64 tiles per
+        # phase (levels 4 and 3 have 12 and 36 at 4 rows: per-unit entries)
+        assert tiled == 2 * 4 * p.iters_per_level if rows_per_tile == 4 else tiled >= 2 * 4 * p.iters_per_level
 
 
 def test_fusion_follows_the_step_size():
@@ -143,7 +156,7 @@ def test_fusion_follows_the_step_size():
     for sms, fused in ((1, True), (1 << 20, False)):  # 32 warp slots; 33.5 M warp slots
         for threads, ents in b.plan([p], sms):
             for e in ents:
-                if e["op"] == PHASE and ops[e["opidx"] - 1][:2] == (PHASE, e["level"]):
+                if kind_of(e) == PHASE and ops[e["opidx"] - 1][:2] == (PHASE, e["level"]):
                     assert (e["cphase"] >= 0) == fused, (sms, e)
     # one 1080p image on 152 SMs (4,864 warp slots): level 4 (1,008 warps of
     # 484 px) and level 1 split, level 2 (16,128 warps) stays fused, and the
@@ -178,6 +191,31 @@ def test_small_blocks_take_a_thread_each():
             for e in ents:
                 if e["op"] in (PHASE, CATCHUP) and e["level"] > 0:
                     assert e["group"] == (1 if maxarea(e["level"]) <= area else 32)
+
+
+def test_block_steps_run_in_tiles_when_they_fill_the_machine_twice():
+    """With block_tiles = 1 a block step runs in warp tiles exactly when its
+    tiles (fused form) number at least twice the machine's warp slots
+    (sms x 32); otherwise its blocks keep one thread or one warp each (and
+    with the default, 0, always)."""
+    ps = [params_of(j) for j in synth.batch_4k(4)]
+    g = grid(ps[0])
+    rule = b.seeds_tuning(0, 0, 0, 16, 4, 1)
+    for sms in (1, 16, 152, 1 << 12):
+        for threads, ents in b.plan(ps, sms, rule):
+            blocks = [e for e in ents if kind_of(e) == PHASE and e["level"] > 0]
+            if not blocks:
+                continue
+            level, phase = blocks[0]["level"], blocks[0]["phase"]
+            cols, rows = lattice(*g[level], phase)
+            prev = [e["cphase"] for e in blocks if e["cphase"] >= 0]
+            if prev:
+                c2, r2 = lattice(*g[level], prev[0])
+                cols, rows = max(cols, c2), max(rows, r2)
+            tiles = len(ps) * -(-cols // 32) * -(-rows // 4)
+            tiled = tiles >= 2 * sms * 32
+            assert all((e["op"] == BTILE) == tiled for e in blocks), (sms, level, tiles)
+        assert not any(e["op"] == BTILE for _, ents in b.plan(ps, sms) for e in ents)
 
 
 def test_a_batch_shares_every_step():
