@@ -228,7 +228,7 @@ def oracle_run(job, img):
     from oracle import ref
     r = ref.Ref(job.image.width, job.image.height, job.num_superpixels, oracle_levels(job), job.bins_per_channel,
                 job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters, job.compactness,
-                job.edge_threshold)
+                job.edge_threshold, job.compact_prior)
     return r.run(img)
 
 
@@ -299,7 +299,7 @@ def oracle_counting_run(job, img):
     from oracle import ref
     r = ref.Ref(job.image.width, job.image.height, job.num_superpixels, oracle_levels(job), job.bins_per_channel,
                 job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters, job.compactness,
-                job.edge_threshold)
+                job.edge_threshold, job.compact_prior)
     r.init(img)
     moves = {}
     for level, phase in r.schedule():
@@ -372,7 +372,7 @@ def gpu_params(binding, job):
         L = min(L, binding.feasible_levels(job.image.width, job.image.height, job.num_superpixels))
     return binding.make_params(job.image.width, job.image.height, job.num_superpixels, L, job.bins_per_channel,
                                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters,
-                               job.compactness, job.edge_threshold)
+                               job.compactness, job.edge_threshold, job.compact_prior)
 
 
 def timed_steps(torch, fn, steps, flush, kernel_ms=None):

@@ -74,7 +74,9 @@ typedef struct seeds_ctx seeds_ctx;
  *   num_superpixels    requested K (>= 1); the grid gives gx*gy <= 65535
  *   block_levels       L >= 0 (0 = pixel moves only)
  *   bins_per_channel   B in 1..16; histograms have B^3 bins
- *   iters_per_level    >= 1, for every block level and the pixel level
+ *   iters_per_level    0..1000, for every block level and the pixel level;
+ *                      0 only with means_iters > 0: SPM on its own (Sec.
+ *                      6.3), the means iterations start from the grid
  *   patch              0 (no boundary term) or 3 (3x3 patches, Prop. 2)
  *   gamma_num/den      gamma = num/den, 0 <= num <= 1024, 1 <= den <= 1024
  *   color_space        0: bins of the RGB bytes; 1: bins of the 8-bit CIE
@@ -100,7 +102,16 @@ typedef struct seeds_ctx seeds_ctx;
  *                      edge when the L1 distance of their colour codes (the
  *                      bytes the bins come from) is at least this; a pixel
  *                      with a 4-neighbour of another label across an edge
- *                      no longer moves (pixel and means phases) */
+ *                      no longer moves (pixel and means phases)
+ *   compact_prior      0..1024, 0 = off: the compactness prior of Sec. 6.4 in
+ *                      the histogram pixel phases.  Every option's score
+ *                      loses w*D*d^2/S^2, d^2 the squared distance of the
+ *                      pixel to the option's centre of gravity (its own
+ *                      superpixel's with the pixel in it), S^2 = W*H/K,
+ *                      D = 81, w = compact_prior/16; with the prior on, the
+ *                      pixel score is compared in IEEE single precision in a
+ *                      fixed order (colour term a/s by one division, centre
+ *                      as sum times 1/size) instead of exact integers */
 typedef struct {
     int32_t width, height;
     int32_t num_superpixels;
@@ -113,6 +124,7 @@ typedef struct {
     int32_t means_iters;
     int32_t compactness;
     int32_t edge_threshold;
+    int32_t compact_prior;
 } seeds_params;
 
 /* Result-invariant launch knobs (any value gives identical labels).
@@ -307,7 +319,8 @@ int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t);
 /* The search seeds_autotune runs, with the timing supplied by the caller:
  * coordinate descent from *start over threads_per_block {128, 256, 512,
  * 1024}, blocks_per_sm {0..3}, hist_layout {0, 1}, small_block_area {4, 9,
- * 16} and pixel_tile_rows {2, 4}, in that order, one pass; a value is kept
+ * 16}, pixel_tile_rows {2, 4} and block_tiles {0, 1, 2}, in that order, one
+ * pass; a value is kept
  * only if cost() reports it at least 2% faster than the current setting.
  * cost returns milliseconds (a huge value for a setting that cannot run).
  * Writes the setting found to *best.  Host only; no device is touched.  The
@@ -463,6 +476,15 @@ int seeds_debug_set_labels(seeds_ctx *c, int32_t i, int32_t level, const int32_t
  * seeds_status() must report SEEDS_ERR_DEVICE).  No counterpart in the
  * paper. */
 int seeds_debug_inject_error(seeds_ctx *c);
+
+/* Failure test of the device-side wait: the grid barrier of this context's
+ * next launches gives up after timeout_ns nanoseconds instead of 2 s (0 =
+ * the default), and, with withhold_step >= 0, CTA 0 does not arrive at the
+ * barrier that ends step withhold_step, so that every CTA's wait there runs
+ * out: each sets the error word (SEEDS_ERR_DEVICE at the next seeds_status)
+ * and leaves the kernel; no output is written.  (0, -1) restores normal
+ * launches.  No GPU fault is involved, and the paper has no counterpart. */
+int seeds_debug_barrier_test(seeds_ctx *c, int64_t timeout_ns, int32_t withhold_step);
 
 /* Kernel launches issued by the context so far (every launch of the
  * persistent kernel and of the small pointer-upload kernel counts one).  No

@@ -41,7 +41,7 @@ EXPORTS = [
     "seeds_batch_labels", "seeds_batch_run", "seeds_batch_run_anytime", "seeds_anytime_steps", "seeds_run_host", "seeds_set_tuning", "seeds_get_tuning",
     "seeds_tune_search",
     "seeds_debug_num_ops", "seeds_debug_op_info", "seeds_debug_run_ops", "seeds_debug_read_state",
-    "seeds_debug_set_labels", "seeds_debug_inject_error", "seeds_debug_launch_count", "seeds_profile_enable",
+    "seeds_debug_set_labels", "seeds_debug_inject_error", "seeds_debug_barrier_test", "seeds_debug_launch_count", "seeds_profile_enable",
     "seeds_profile_last_ms", "seeds_profile_steps", "seeds_run_static", "seeds_autotune",
     "seeds_server_create", "seeds_server_destroy", "seeds_server_submit", "seeds_server_step", "seeds_server_poll",
     "seeds_server_drain", "seeds_server_stats",
@@ -59,7 +59,8 @@ class seeds_params(ctypes.Structure):
                 ("block_levels", ctypes.c_int32), ("bins_per_channel", ctypes.c_int32),
                 ("iters_per_level", ctypes.c_int32), ("patch", ctypes.c_int32), ("gamma_num", ctypes.c_int32),
                 ("gamma_den", ctypes.c_int32), ("color_space", ctypes.c_int32), ("means_iters", ctypes.c_int32),
-                ("compactness", ctypes.c_int32), ("edge_threshold", ctypes.c_int32)]
+                ("compactness", ctypes.c_int32), ("edge_threshold", ctypes.c_int32),
+                ("compact_prior", ctypes.c_int32)]
 
 
 class seeds_server_config(ctypes.Structure):
@@ -125,6 +126,7 @@ def _load():
         "seeds_debug_read_state": [vp, i32, i32, vp, vp, vp, vp],
         "seeds_debug_set_labels": [vp, i32, i32, vp],
         "seeds_debug_inject_error": [vp],
+        "seeds_debug_barrier_test": [vp, i64, i32],
         "seeds_debug_launch_count": [vp, P(i64)],
         "seeds_profile_enable": [vp, i32],
         "seeds_profile_last_ms": [vp, P(ctypes.c_float)],
@@ -156,13 +158,16 @@ def check(code: int, what: str) -> int:
 
 
 def make_params(width, height, num_superpixels, block_levels, bins_per_channel, iters_per_level, patch=3,
-                gamma=(1, 1), color_space=0, means_iters=0, compactness=0, edge_threshold=0) -> seeds_params:
+                gamma=(1, 1), color_space=0, means_iters=0, compactness=0, edge_threshold=0,
+                compact_prior=0) -> seeds_params:
     """color_space: 0 = RGB bytes, 1 = 8-bit CIE L*a*b* codes (Sec. 6.2);
     means_iters / compactness: means-based pixel iterations with SLIC's m
-    (Sec. 6.3, 6.5); edge_threshold: edge snapping (Sec. 6.4), 0 = off."""
+    (Sec. 6.3, 6.5); edge_threshold: edge snapping (Sec. 6.4), 0 = off;
+    compact_prior: the compactness prior of Sec. 6.4 in the histogram pixel
+    phases, weight compact_prior/16, 0 = off."""
     return seeds_params(int(width), int(height), int(num_superpixels), int(block_levels), int(bins_per_channel),
                         int(iters_per_level), int(patch), int(gamma[0]), int(gamma[1]), int(color_space),
-                        int(means_iters), int(compactness), int(edge_threshold))
+                        int(means_iters), int(compactness), int(edge_threshold), int(compact_prior))
 
 
 def feasible_levels(width, height, num_superpixels) -> int:
@@ -236,7 +241,8 @@ def _stream_handle(stream) -> Optional[int]:
 
 
 def superpixels(images, num_superpixels, block_levels=None, bins_per_channel=5, iters_per_level=2, patch=3,
-                gamma=(1, 1), color_space=0, means_iters=0, compactness=0, edge_threshold=0, stream=None):
+                gamma=(1, 1), color_space=0, means_iters=0, compactness=0, edge_threshold=0, compact_prior=0,
+                stream=None):
     """SEEDS labels for a list of uint8 (H, W, 3) CUDA images in one
     persistent launch: a list of int32 (H, W) CUDA tensors, values in
     [0, K_actual).  `num_superpixels` is one requested K or one per image;
@@ -250,7 +256,7 @@ def superpixels(images, num_superpixels, block_levels=None, bins_per_channel=5, 
         H, W = int(img.shape[0]), int(img.shape[1])
         L = min(4, feasible_levels(W, H, k)) if block_levels is None else block_levels
         params.append(make_params(W, H, k, L, bins_per_channel, iters_per_level, patch, gamma, color_space,
-                                  means_iters, compactness, edge_threshold))
+                                  means_iters, compactness, edge_threshold, compact_prior))
     ctx = SeedsContext(params)
     outs = [torch.empty((int(t.shape[0]), int(t.shape[1])), dtype=torch.int32, device=t.device) for t in images]
     ctx.run(images, outs, stream)
@@ -504,6 +510,12 @@ class SeedsContext:
 
     def inject_error(self):
         check(lib.seeds_debug_inject_error(self._h), "seeds_debug_inject_error")
+
+    def barrier_test(self, timeout_ns: int, withhold_step: int = -1):
+        """Failure test: barrier time limit and a withheld arrival (see
+        seeds_debug_barrier_test); (0, -1) restores normal launches."""
+        check(lib.seeds_debug_barrier_test(self._h, int(timeout_ns), int(withhold_step)),
+              "seeds_debug_barrier_test")
 
 
 class Server:

@@ -58,6 +58,9 @@ struct DevImage {
     int32_t means_iters;  // means-based pixel iterations after the histogram ones
     float means_w;        // (m/S)^2 = m^2 K / N, the spatial weight of SLIC's distance
     int32_t edge_tau;     // edge snapping threshold (Sec. 6.4), 0 = off
+    int32_t prior;        // the compactness prior (Sec. 6.4) in the histogram pixel phases
+    float compact_w;      // its weight of d^2: (compact_prior/16) * 81 * K / N
+    float gamma_f;        // gamma as a float (0 without patches), for the prior's score
     int32_t nbx[kMaxLevels + 1], nby[kMaxLevels + 1];  // level 0 = W, H
     int32_t maxarea[kMaxLevels + 1];                   // largest block of a level
     const int32_t *xe[kMaxLevels + 1];                 // block column edges, level >= 1
@@ -68,7 +71,8 @@ struct DevImage {
     int32_t *hist[2];                   // K x nbins counts, 2 buffers
     int32_t *size[2];                   // |A_k|, 2 buffers
     uint32_t *dec[2];                   // per unit of a phase: (k << 16 | n) or kNoMove
-    unsigned long long *msum[2];        // K x 5: sums of the 3 colour codes, of x, of y (means iterations)
+    unsigned long long *msum[2];        // K x 5: sums of the 3 colour codes, of x, of y (means iterations;
+                                        // x and y through every move with the compactness prior)
     uint8_t *edges;                     // per pixel, edge snapping: bit 0 across to the right, bit 1 down
     int32_t units_cap;                  // entries of each dec buffer
     int32_t *err;                       // the launch's error word (debug builds report bounds trips here)
@@ -105,6 +109,11 @@ struct Schedule {
     int32_t nimg;
     unsigned long long budget_ns;
     int32_t *steps_out;
+    // failure tests: the barrier's time limit (0: 2 s), and a step whose
+    // barrier CTA 0 does not arrive at (step + 1; 0: none), so that every
+    // wait there runs out and the kernel returns with DERR_TIMEOUT
+    unsigned long long timeout_ns;
+    int32_t withhold;
 };
 
 struct GridBarrier {

@@ -68,12 +68,14 @@ inline int derive_core(const seeds_params *p, ImageCore *g, int32_t *gx_out, int
     if (p->num_superpixels < 1) return SEEDS_ERR_INVALID;
     if (p->block_levels < 0 || p->block_levels > kMaxLevels) return SEEDS_ERR_INVALID;
     if (p->bins_per_channel < 1 || p->bins_per_channel > 16) return SEEDS_ERR_INVALID;
-    if (p->iters_per_level < 1 || p->iters_per_level > 1000) return SEEDS_ERR_INVALID;
+    if (p->iters_per_level < 0 || p->iters_per_level > 1000) return SEEDS_ERR_INVALID;
+    if (p->iters_per_level == 0 && p->means_iters == 0) return SEEDS_ERR_INVALID;  // SPM alone needs means
     if (p->patch != 0 && p->patch != 3) return SEEDS_ERR_INVALID;
     if (p->color_space != 0 && p->color_space != 1) return SEEDS_ERR_INVALID;
     if (p->means_iters < 0 || p->means_iters > 1000) return SEEDS_ERR_INVALID;
     if (p->compactness < 0 || p->compactness > 1024) return SEEDS_ERR_INVALID;
     if (p->edge_threshold < 0 || p->edge_threshold > 765) return SEEDS_ERR_INVALID;
+    if (p->compact_prior < 0 || p->compact_prior > 1024) return SEEDS_ERR_INVALID;
     if (p->gamma_num < 0 || p->gamma_num > 1024 || p->gamma_den < 1 || p->gamma_den > 1024) return SEEDS_ERR_INVALID;
     const double Kd = p->num_superpixels, Wd = p->width, Hd = p->height;
     long long gx = std::llround(std::sqrt(Kd * Wd / Hd));
@@ -144,8 +146,8 @@ inline int derive_core(const seeds_params *p, ImageCore *g, int32_t *gx_out, int
         off = align_up(off + (size_t)h.K * 4);
         h.off_dec[q] = off;
         off = align_up(off + (size_t)h.units_cap * 4);
-        h.off_msum[q] = off;  // per superpixel sums for the means iterations
-        if (p->means_iters > 0) off = align_up(off + (size_t)h.K * 5 * 8);
+        h.off_msum[q] = off;  // per superpixel sums: means iterations, compactness prior
+        if (p->means_iters > 0 || p->compact_prior > 0) off = align_up(off + (size_t)h.K * 5 * 8);
     }
     h.off_edges = off;  // the edge-snapping mask
     if (p->edge_threshold > 0) off = align_up(off + (size_t)N);
@@ -213,6 +215,10 @@ inline DevImage make_dev_image(const ImageCore &h, unsigned char *base, const se
     d.color = h.p.color_space;
     // SLIC's (m/S)^2 with S^2 = N/K
     d.means_w = (float)((int64_t)h.p.compactness * h.p.compactness * h.K) / (float)h.N;
+    // the compactness prior: (compact_prior/16) * D * K / N, and gamma as a float
+    d.prior = h.p.compact_prior > 0;
+    d.compact_w = (float)((int64_t)h.p.compact_prior * 81 * h.K) / (float)((int64_t)16 * h.N);
+    d.gamma_f = h.p.patch == 3 ? (float)h.p.gamma_num / (float)h.p.gamma_den : 0.0f;
     d.edge_tau = h.p.edge_threshold;
     d.edges = h.p.edge_threshold > 0 ? base + h.off_edges : nullptr;
     d.gnum = h.p.gamma_num;
@@ -233,7 +239,7 @@ inline DevImage make_dev_image(const ImageCore &h, unsigned char *base, const se
         d.hist[q] = (int32_t *)(base + h.off_hist[q]);
         d.size[q] = (int32_t *)(base + h.off_size[q]);
         d.dec[q] = (uint32_t *)(base + h.off_dec[q]);
-        d.msum[q] = h.p.means_iters > 0 ? (unsigned long long *)(base + h.off_msum[q]) : nullptr;
+        d.msum[q] = h.p.means_iters > 0 || d.prior ? (unsigned long long *)(base + h.off_msum[q]) : nullptr;
     }
     d.units_cap = h.units_cap;
     d.err = err;
@@ -245,7 +251,7 @@ inline DevImage make_dev_image(const ImageCore &h, unsigned char *base, const se
 
 // The autotuner's search: coordinate descent over the result-invariant
 // launch knobs (threads per CTA, CTAs per SM, histogram layout, small-block
-// area, pixel tile rows), one pass in that order, from `start`.  cost(t, &ms)
+// area, tile rows, block tiles), one pass in that order, from `start`.  cost(t, &ms)
 // times a setting (ms = +inf if it cannot run; a nonzero return aborts the
 // search with that status); a value replaces the current one only if it is
 // at least 2% faster, so timing noise does not move the setting.
@@ -256,17 +262,23 @@ inline int tune_search(const seeds_tuning &start, Cost cost, seeds_tuning *best)
     float cur_ms = 0.f;
     int rc = cost(cur, &cur_ms);
     const int threads[] = {128, 256, 512, 1024}, blocks[] = {0, 1, 2, 3}, layouts[] = {0, 1}, areas[] = {4, 9, 16},
-              rows[] = {2, 4};
-    for (int knob = 0; knob < 5 && !rc; ++knob) {
-        const int *vals = knob == 0 ? threads : knob == 1 ? blocks : knob == 2 ? layouts : knob == 3 ? areas : rows;
-        const int nv = knob == 0 ? 4 : knob == 1 ? 4 : knob == 2 ? 2 : knob == 3 ? 3 : 2;
+              rows[] = {2, 4}, tiles[] = {0, 1, 2};
+    for (int knob = 0; knob < 6 && !rc; ++knob) {
+        const int *vals = knob == 0   ? threads
+                          : knob == 1 ? blocks
+                          : knob == 2 ? layouts
+                          : knob == 3 ? areas
+                          : knob == 4 ? rows
+                                      : tiles;
+        const int nv = knob == 0 ? 4 : knob == 1 ? 4 : knob == 2 ? 2 : knob == 3 ? 3 : knob == 4 ? 2 : 3;
         for (int v = 0; v < nv && !rc; ++v) {
             seeds_tuning t = cur;
             int *field = knob == 0   ? &t.threads_per_block
                          : knob == 1 ? &t.blocks_per_sm
                          : knob == 2 ? &t.hist_layout
                          : knob == 3 ? &t.small_block_area
-                                     : &t.pixel_tile_rows;
+                         : knob == 4 ? &t.pixel_tile_rows
+                                     : &t.block_tiles;
             if (*field == vals[v]) continue;
             *field = vals[v];
             float ms = 0.f;

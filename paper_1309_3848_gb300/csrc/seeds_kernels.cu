@@ -67,16 +67,17 @@ __device__ __forceinline__ int ld_relaxed_i32(const int32_t *p)
 // of the fence did not make the other warps' writes visible in tests, and a
 // second fence after the wait costs ~0.4 us per step for nothing the acquire
 // does not already give.  Returns false when the wait ran out or another CTA
-// reported an error.
-__device__ bool grid_sync_count(GridBarrier *bar, int32_t *err, unsigned target)
+// reported an error.  A CTA with arrive == false (a failure test) waits
+// without arriving, so that the wait of every CTA runs out.
+__device__ bool grid_sync_count(GridBarrier *bar, int32_t *err, unsigned target, uint64_t limit_ns, bool arrive)
 {
     __shared__ int s_go;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         __threadfence();
-        const unsigned v = atomicAdd(&bar->count, 1u);
-        if (v + 1 != target) {
+        const unsigned v = arrive ? atomicAdd(&bar->count, 1u) : 0u;
+        if (!arrive || v + 1 != target) {
             const uint64_t t0 = global_ns();
             for (unsigned it = 1; (int)(ld_acquire_u32(&bar->count) - target) < 0; ++it) {
                 if ((it & 31u) == 0) {
@@ -84,7 +85,7 @@ __device__ bool grid_sync_count(GridBarrier *bar, int32_t *err, unsigned target)
                         ok = 0;
                         break;
                     }
-                    if (global_ns() - t0 > kBarrierTimeoutNs) {
+                    if (global_ns() - t0 > limit_ns) {
                         atomicOr(err, DERR_TIMEOUT);
                         ok = 0;
                         break;
@@ -104,8 +105,9 @@ constexpr unsigned kGenStop = 0x80000000u;  // generation bit: the grid stops he
 // Grid-wide barrier for a persistent launch whose blocks are all resident.
 // Returns 0 when the wait ran out or another block reported an error, 1 to
 // go on, 2 to stop: the last block to arrive decides (its thread 0 passes
-// want_stop) and publishes the decision in the generation word it bumps.
-__device__ int grid_sync(GridBarrier *bar, int32_t *err, bool want_stop = false)
+// want_stop) and publishes the decision in the generation word it bumps.  A
+// CTA with arrive == false (a failure test) waits without arriving.
+__device__ int grid_sync(GridBarrier *bar, int32_t *err, bool want_stop, uint64_t limit_ns, bool arrive)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -113,7 +115,7 @@ __device__ int grid_sync(GridBarrier *bar, int32_t *err, bool want_stop = false)
         int ok = 1;
         const unsigned g = ld_acquire_u32(&bar->gen);
         __threadfence();
-        const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
+        const unsigned arrived = arrive ? atomicAdd(&bar->count, 1u) + 1u : 0u;
         if (arrived == gridDim.x) {
             atomicExch(&bar->count, 0u);
             __threadfence();
@@ -128,7 +130,7 @@ __device__ int grid_sync(GridBarrier *bar, int32_t *err, bool want_stop = false)
                         ok = 0;
                         break;
                     }
-                    if (global_ns() - t0 > kBarrierTimeoutNs) {
+                    if (global_ns() - t0 > limit_ns) {
                         atomicOr(err, DERR_TIMEOUT);
                         ok = 0;
                         break;
@@ -279,6 +281,28 @@ __device__ __forceinline__ void move_size(const DevImage &im, int buf, int k, in
 {
     atomicSub(&im.size[buf][SEEDS_IDX(im, k, im.K)], cnt);
     atomicAdd(&im.size[buf][SEEDS_IDX(im, n, im.K)], cnt);
+}
+
+// The compactness prior (Sec. 6.4) keeps every superpixel's coordinate sums
+// (msum entries 3 and 4) exact through every move.  Sum of x over [x0, x1):
+__device__ __forceinline__ unsigned long long range_sum(int x0, int x1)
+{
+    const long long a = x1 - x0;
+    return (unsigned long long)(a * x0 + a * (a - 1) / 2);
+}
+
+// move the coordinate sums of the rectangle [x0,x1) x [y0,y1) from k to n in
+// buffer `buf`
+__device__ __forceinline__ void move_xy(const DevImage &im, int buf, int k, int n, int x0, int x1, int y0, int y1)
+{
+    const unsigned long long sx = range_sum(x0, x1) * (unsigned long long)(y1 - y0);
+    const unsigned long long sy = range_sum(y0, y1) * (unsigned long long)(x1 - x0);
+    unsigned long long *mk = im.msum[buf] + (int64_t)SEEDS_IDX(im, k, im.K) * 5;
+    unsigned long long *mn = im.msum[buf] + (int64_t)SEEDS_IDX(im, n, im.K) * 5;
+    atomicAdd(mk + 3, 0ull - sx);
+    atomicAdd(mn + 3, sx);
+    atomicAdd(mk + 4, 0ull - sy);
+    atomicAdd(mn + 4, sy);
 }
 
 constexpr int kHistRound = 4;  // bins loaded per lane before any is used
@@ -471,7 +495,13 @@ __device__ void op_init(const DevImage &im, int k, int lane, int32_t *wsh)
     }
     __syncwarp();
     if (lane == 0) im.size[0][k] = im.size[1][k] = area;
-    if (im.means_iters > 0 && lane < 10) im.msum[lane / 5][(int64_t)k * 5 + lane % 5] = 0;
+    if (im.msum[0] && lane < 10) {  // colour sums zero; with the prior, the rectangle's coordinate sums
+        const int q = lane % 5;
+        unsigned long long v = 0;
+        if (im.prior && q == 3) v = range_sum(x0, x1) * (unsigned long long)(y1 - y0);
+        if (im.prior && q == 4) v = range_sum(y0, y1) * (unsigned long long)(x1 - x0);
+        im.msum[lane / 5][(int64_t)k * 5 + q] = v;
+    }
     if (im.L >= 1 && lane < 4) {
         const int L = im.L;
         const int bx = 2 * sx + (lane & 1), by = 2 * sy + (lane >> 1);
@@ -510,7 +540,8 @@ __device__ __noinline__ void move_sums(const DevImage &im, int buf, int k, int n
 }
 
 // OP_MINIT: the sums from the labels of buffer o&1, into both buffers (zeroed
-// by the init op).  A thread per pixel; the warp adds up each label's lanes
+// by the init op; with the compactness prior the coordinate sums are already
+// kept, so only the colour sums are added).  A thread per pixel; the warp adds up each label's lanes
 // and one lane per label adds them to memory.  The whole warp calls this.
 __device__ __noinline__ void op_means_init(const DevImage &im, int o, int64_t units, int64_t t, int lane)
 {
@@ -538,6 +569,7 @@ __device__ __noinline__ void op_means_init(const DevImage &im, int o, int64_t un
         if (lane == leader && kl >= 0)
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
+                if (q >= 3 && im.prior) break;
                 atomicAdd(&im.msum[0][(int64_t)kl * 5 + q], (unsigned long long)s[q]);
                 atomicAdd(&im.msum[1][(int64_t)kl * 5 + q], (unsigned long long)s[q]);
             }
@@ -592,6 +624,57 @@ __device__ __noinline__ uint32_t means_pixel(const DevImage &im, int b, int nb, 
     move_size(im, nb, k, best, 1);
     move_sums(im, nb, k, best, x, y);
     return ((uint32_t)k << 16) | (uint32_t)best;
+}
+
+// ---------------------------------------------------------------------------
+// the compactness prior (Sec. 6.4) in the histogram pixel phases
+// ---------------------------------------------------------------------------
+
+// The pixel score of one option: D*a/s + gamma*G - compact_w*d^2, d^2 the
+// squared distance of (x, y) to the centre of gravity of `label` in buffer b
+// (coordinate sums over sc pixels), in IEEE single precision with one
+// rounding per operation in this order (no fused multiply-add).
+__device__ __forceinline__ float compact_score(const DevImage &im, int b, int label, int x, int y, int32_t a,
+                                               int32_t s, int32_t sc, int G)
+{
+    const unsigned long long *m = im.msum[b] + (int64_t)label * 5;
+    const float r = __fdiv_rn(1.0f, __int2float_rn(sc));
+    const float gx = __fsub_rn(__int2float_rn(x), __fmul_rn(__ll2float_rn((long long)m[3]), r));
+    const float gy = __fsub_rn(__int2float_rn(y), __fmul_rn(__ll2float_rn((long long)m[4]), r));
+    const float d2 = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
+    const float col = __fdiv_rn(__int2float_rn(a), __int2float_rn(s));
+    const float t1 = __fmul_rn(81.0f, col);
+    const float t2 = __fmul_rn(im.gamma_f, __int2float_rn(G));
+    const float t3 = __fmul_rn(im.compact_w, d2);
+    return __fsub_rn(__fadd_rn(t1, t2), t3);
+}
+
+// The best candidate (ascending, a later one only if strictly higher: ties to
+// the smallest label) if its score is strictly above staying, else kNoLabel.
+// A candidate scores its colour count A_n[j] and size |A_n| with
+// G_n + |K_p|; staying scores A_k without the pixel (A_k[j] - 1, |A_k| - 1)
+// with G_k, its centre taken with the pixel in it.  The candidate labels
+// come packed two to a word (kNoLabel in empty slots), their G values a
+// byte each (at most 81); the counts are looked up here.
+__device__ __noinline__ int compact_pick(const DevImage &im, int b, int x, int y, int k, int j, uint32_t c01,
+                                         uint32_t c23, uint32_t gpack, int Kp, int Gk)
+{
+    const int32_t *hist = im.hist[b], *size = im.size[b];
+    int best = kNoLabel;
+    float fb = 0.0f;
+    for (int c = 0; c < 4; ++c) {
+        const int n = (int)(((c < 2 ? c01 : c23) >> (16 * (c & 1))) & 0xFFFFu);
+        if (n == kNoLabel) continue;
+        const int32_t a = hist[hidx(im, n, j)], sz = size[SEEDS_IDX(im, n, im.K)];
+        const float f = compact_score(im, b, n, x, y, a, sz, sz, (int)((gpack >> (8 * c)) & 0xFFu) + Kp);
+        if (best == kNoLabel || f > fb) {
+            best = n;
+            fb = f;
+        }
+    }
+    const int32_t a_k = hist[hidx(im, k, j)], s_k = size[SEEDS_IDX(im, k, im.K)];
+    const float fk = compact_score(im, b, k, x, y, a_k - 1, s_k - 1, s_k, Gk);
+    return fb > fk ? best : (int)kNoLabel;
 }
 
 // ---------------------------------------------------------------------------
@@ -727,7 +810,10 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         if (cd[r] != kNoMove) {
             const int cx = 2 * ux + cpx, cy = 2 * (uy0 + r) + cpy;
             replay_pixel(im, nb, cy * W + cx, cd[r]);
-            if constexpr (MEANS) move_sums(im, nb, (int)(cd[r] >> 16), (int)(cd[r] & 0xFFFFu), cx, cy);
+            if constexpr (MEANS)
+                move_sums(im, nb, (int)(cd[r] >> 16), (int)(cd[r] & 0xFFFFu), cx, cy);
+            else if (im.prior)
+                move_xy(im, nb, (int)(cd[r] >> 16), (int)(cd[r] & 0xFFFFu), cx, cx + 1, cy, cy + 1);
         }
     __syncwarp();
 
@@ -821,6 +907,23 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
                         if (lq == cand[c]) Gc[c] += w;  // empty slots only meet w = 0 cells
                 }
             }
+        }
+        if (im.prior) {  // the compactness prior: single-precision scores
+            const int best = compact_pick(im, b, x, y, k, j, (uint32_t)cand[0] | ((uint32_t)cand[1] << 16),
+                                          (uint32_t)cand[2] | ((uint32_t)cand[3] << 16),
+                                          (uint32_t)Gc[0] | ((uint32_t)Gc[1] << 8) | ((uint32_t)Gc[2] << 16) |
+                                              ((uint32_t)Gc[3] << 24),
+                                          Kp, Gk);
+            uint32_t dec = kNoMove;
+            if (best != kNoLabel) {
+                dec = ((uint32_t)k << 16) | (uint32_t)best;
+                im.lab[0][nb][SEEDS_IDX(im, p, (int64_t)W * H)] = (uint16_t)SEEDS_IDX(im, best, im.K);
+                move_counts(im, nb, k, best, j, 1);
+                move_size(im, nb, k, best, 1);
+                move_xy(im, nb, k, best, x, x + 1, y, y + 1);
+            }
+            im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = dec;
+            continue;
         }
         // the histogram and size lookups of every candidate and of k, all
         // issued before the first is used
@@ -924,6 +1027,7 @@ __device__ void replay_small_block_t(const DevImage &im, int buf, int level, int
     }
     move_block_counts<SM>(im, buf, k, n, jj, m);
     move_size(im, buf, k, n, m);
+    if (im.prior) move_xy(im, buf, k, n, x0, x1, y0, y1);
     im.lab[level][buf][SEEDS_IDX(im, by * im.nbx[level] + bx, (int64_t)im.nbx[level] * im.nby[level])] =
         (uint16_t)SEEDS_IDX(im, n, im.K);
 }
@@ -1001,6 +1105,7 @@ __device__ uint32_t judge_small_block_c(const DevImage &im, int b, int nb, int l
     im.lab[level][nb][SEEDS_IDX(im, by * nx + bx, (int64_t)nx * im.nby[level])] = (uint16_t)SEEDS_IDX(im, n, im.K);
     move_block_counts<SM>(im, nb, k, n, jj, m);
     move_size(im, nb, k, n, m);
+    if (im.prior) move_xy(im, nb, k, n, x0, x1, y0, y1);
     return ((uint32_t)k << 16) | (uint32_t)n;
 }
 
@@ -1102,6 +1207,7 @@ __device__ void replay_large_block(const DevImage &im, int buf, int level, int b
         im.lab[level][buf][SEEDS_IDX(im, by * im.nbx[level] + bx, (int64_t)im.nbx[level] * im.nby[level])] =
             (uint16_t)SEEDS_IDX(im, n, im.K);
         move_size(im, buf, k, n, m);
+        if (im.prior) move_xy(im, buf, k, n, x0, x1, y0, y1);
     }
 }
 
@@ -1155,7 +1261,7 @@ __device__ uint32_t judge_large_block_c(const DevImage &im, int b, int nb, int l
                                         const int cand[4], int x0, int x1, int y0, int y1, int lane, int32_t *wsh,
                                         int max_nbins)
 {
-    const int nx = im.nbx[level], ny = im.nby[level];
+    const int nx = im.nbx[level];
     // the sizes are read before the histogram build: fewer dependent trips to L2
     const int32_t *size = im.size[b];
     int32_t sz[4];
@@ -1185,8 +1291,9 @@ __device__ uint32_t judge_large_block_c(const DevImage &im, int b, int nb, int l
     const bool moves = Sb * s_rest > S_st * zb;
     block_sparse_apply_clear(im, nb, moves ? k : -1, n, nd, lane, wsh, max_nbins);
     if (lane == 0 && moves) {
-        im.lab[level][nb][SEEDS_IDX(im, by * nx + bx, (int64_t)nx * ny)] = (uint16_t)SEEDS_IDX(im, n, im.K);
+        im.lab[level][nb][SEEDS_IDX(im, by * nx + bx, (int64_t)nx * im.nby[level])] = (uint16_t)SEEDS_IDX(im, n, im.K);
         move_size(im, nb, k, n, m);
+        if (im.prior) move_xy(im, nb, k, n, x0, x1, y0, y1);
     }
     return moves ? (((uint32_t)k << 16) | (uint32_t)n) : kNoMove;
 }
@@ -1364,7 +1471,10 @@ __device__ void op_catchup(const DevImage &im, int o, int level, int phase, int 
             int x, y;
             unit_pos(chunk * 32 * kCatchupPerLane + 32 * r + lane, phase, im.W, &x, &y);
             replay_pixel(im, nb, y * im.W + x, d[r]);
-            if (means) move_sums(im, nb, (int)(d[r] >> 16), (int)(d[r] & 0xFFFFu), x, y);
+            if (means)
+                move_sums(im, nb, (int)(d[r] >> 16), (int)(d[r] & 0xFFFFu), x, y);
+            else if (im.prior)
+                move_xy(im, nb, (int)(d[r] >> 16), (int)(d[r] & 0xFFFFu), x, x + 1, y, y + 1);
         }
         return;
     }
@@ -1612,11 +1722,15 @@ __global__ void __launch_bounds__(1024, 1) seeds_persistent(const DevImage *__re
         }
         if (s + 1 < S.nsteps) {
             if (!anytime) {
-                if (!grid_sync_count(bar, err, (unsigned)(s + 1) * gridDim.x)) return;
+                if (!grid_sync_count(bar, err, (unsigned)(s + 1) * gridDim.x,
+                                     S.timeout_ns ? S.timeout_ns : kBarrierTimeoutNs,
+                                     blockIdx.x != 0 || S.withhold != s + 1))
+                    return;
             } else {
                 const bool want_stop = threadIdx.x == 0 && ((S.stop_steps > 0 && s + 1 >= S.stop_steps) ||
                                                             (S.budget_ns > 0 && global_ns() - s_t_start >= S.budget_ns));
-                const int go = grid_sync(bar, err, want_stop);
+                const int go = grid_sync(bar, err, want_stop, S.timeout_ns ? S.timeout_ns : kBarrierTimeoutNs,
+                                         blockIdx.x != 0 || S.withhold != s + 1);
                 if (go == 0) return;
                 if (go == 2) {
                     anytime_output(imgs, S.nimg, s);
@@ -1652,6 +1766,8 @@ __global__ void recount_kernel(const DevImage *imgs, int img, int level, int64_t
         const int64_t nh = (int64_t)im.K * im.nbins;
         for (int64_t t = i; t < nh; t += stride) im.hist[0][t] = im.hist[1][t] = 0;
         for (int64_t t = i; t < im.K; t += stride) im.size[0][t] = im.size[1][t] = 0;
+        if (im.prior)  // the compactness prior's coordinate sums
+            for (int64_t t = i; t < (int64_t)im.K * 5; t += stride) im.msum[0][t] = im.msum[1][t] = 0;
         return;
     }
     if (i >= npix) return;
@@ -1670,6 +1786,11 @@ __global__ void recount_kernel(const DevImage *imgs, int img, int level, int64_t
     atomicAdd(&im.hist[1][hidx(im, k, j)], 1);
     atomicAdd(&im.size[0][k], 1);
     atomicAdd(&im.size[1][k], 1);
+    if (im.prior)
+        for (int q = 0; q < 2; ++q) {
+            atomicAdd(&im.msum[q][(int64_t)k * 5 + 3], (unsigned long long)x);
+            atomicAdd(&im.msum[q][(int64_t)k * 5 + 4], (unsigned long long)y);
+        }
 }
 
 // ---------------------------------------------------------------------------

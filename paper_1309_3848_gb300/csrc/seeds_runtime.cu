@@ -58,6 +58,8 @@ struct seeds_ctx {
     unsigned long long *d_trace = nullptr;  // step stamps while profiling
     int trace_cap = 0, traced_steps = 0;
     int64_t launches = 0;
+    unsigned long long dbg_timeout_ns = 0;  // failure tests: barrier limit, withheld arrival
+    int32_t dbg_withhold = 0;
     unsigned char *stage = nullptr;
     size_t stage_bytes = 0;
     std::vector<size_t> stage_rgb, stage_out;
@@ -212,6 +214,8 @@ int launch(seeds_ctx *c, int kind, int ob, int oe, cudaStream_t s, int32_t stop_
     run.stop_steps = stop_steps;
     run.budget_ns = (unsigned long long)budget_ns;
     run.steps_out = anytime ? c->d_steps : nullptr;
+    run.timeout_ns = c->dbg_timeout_ns;
+    run.withhold = c->dbg_withhold;
     if (c->profile) {
         rc = from_cuda(cudaEventRecord(c->ev0, s));
         if (rc) return rc;
@@ -435,6 +439,7 @@ int seeds_params_default(seeds_params *p, int32_t width, int32_t height, int32_t
     p->means_iters = 0;
     p->compactness = 0;
     p->edge_threshold = 0;
+    p->compact_prior = 0;
     int32_t lmax = 0;
     int rc = seeds_feasible_levels(p, &lmax);
     if (rc) return rc;
@@ -829,6 +834,14 @@ int seeds_debug_inject_error(seeds_ctx *c)
     if (!c) return SEEDS_ERR_INVALID;
     const int32_t v = DERR_INJECTED;
     return from_cuda(cudaMemcpy(c->d_err, &v, sizeof(v), cudaMemcpyHostToDevice));
+}
+
+int seeds_debug_barrier_test(seeds_ctx *c, int64_t timeout_ns, int32_t withhold_step)
+{
+    if (!c || timeout_ns < 0 || withhold_step < -1) return SEEDS_ERR_INVALID;
+    c->dbg_timeout_ns = (unsigned long long)timeout_ns;
+    c->dbg_withhold = withhold_step + 1;
+    return SEEDS_OK;
 }
 
 int seeds_debug_launch_count(const seeds_ctx *c, int64_t *n)

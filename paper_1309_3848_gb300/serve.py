@@ -40,7 +40,7 @@ def job_params(job: synth.JobSpec) -> binding.seeds_params:
         L = min(L, binding.feasible_levels(job.image.width, job.image.height, job.num_superpixels))
     return binding.make_params(job.image.width, job.image.height, job.num_superpixels, L, job.bins_per_channel,
                                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters,
-                               job.compactness, job.edge_threshold)
+                               job.compactness, job.edge_threshold, job.compact_prior)
 
 
 def run_stream(requests: Sequence[Tuple[float, synth.JobSpec]], images: Sequence, arena_bytes: int,

@@ -54,6 +54,7 @@ class JobSpec:
     means_iters: int = 0  # means-based pixel iterations after the histogram ones
     compactness: int = 0  # SLIC's m in those iterations
     edge_threshold: int = 0  # edge snapping, 0 = off
+    compact_prior: int = 0  # the compactness prior in the histogram pixel phases, 0 = off
 
     @property
     def pixels(self) -> int:

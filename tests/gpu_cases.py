@@ -30,7 +30,7 @@ def params_for(binding, job):
     L = gpu_levels(binding, job)
     return binding.make_params(job.image.width, job.image.height, job.num_superpixels, L, job.bins_per_channel,
                                job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters,
-                               job.compactness, job.edge_threshold)
+                               job.compactness, job.edge_threshold, job.compact_prior)
 
 
 def make_images(jobs):
@@ -41,7 +41,7 @@ def make_images(jobs):
 def oracle_run(job, img):
     r = ref.Ref(job.image.width, job.image.height, job.num_superpixels, oracle_levels(job), job.bins_per_channel,
                 job.iters_per_level, job.patch, job.gamma, job.color_space, job.means_iters, job.compactness,
-                job.edge_threshold)
+                job.edge_threshold, job.compact_prior)
     return r.run(img)
 
 

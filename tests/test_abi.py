@@ -74,7 +74,9 @@ def test_invalid_parameters(binding):
            binding.make_params(10, 10, 4, 0, 5, 1, means_iters=1001),
            binding.make_params(10, 10, 4, 0, 5, 1, means_iters=1, compactness=1025),
            binding.make_params(10, 10, 4, 0, 5, 1, edge_threshold=-1),
-           binding.make_params(10, 10, 4, 0, 5, 1, edge_threshold=766)]
+           binding.make_params(10, 10, 4, 0, 5, 1, edge_threshold=766),
+           binding.make_params(10, 10, 4, 0, 5, 0), binding.make_params(10, 10, 4, 0, 5, 1, compact_prior=-1),
+           binding.make_params(10, 10, 4, 0, 5, 1, compact_prior=1025)]
     for p in bad:
         assert binding.check_params(p)[0] == binding.SEEDS_ERR_INVALID
     assert binding.check_params(binding.make_params(16, 16, 4, 4, 5, 1))[0] == binding.SEEDS_ERR_GEOMETRY
@@ -84,9 +86,11 @@ def test_invalid_parameters(binding):
 
 
 def test_defaults_follow_the_paper(binding):
-    p = binding.make_params(1, 1, 1, 0, 1, 1, 0, (0, 1), 1, 7, 9, 11)  # every optional field set
+    p = binding.make_params(1, 1, 1, 0, 1, 1, 0, (0, 1), 1, 7, 9, 11, 13)  # every optional field set
     assert binding.lib.seeds_params_default(ctypes.byref(p), 481, 321, 200) == 0
-    assert (p.color_space, p.means_iters, p.compactness, p.edge_threshold) == (0, 0, 0, 0)
+    assert (p.color_space, p.means_iters, p.compactness, p.edge_threshold, p.compact_prior) == (0, 0, 0, 0, 0)
+    # SPM on its own: no histogram iteration, only with means iterations
+    assert binding.check_params(binding.make_params(40, 30, 10, 2, 4, 0, means_iters=1))[0] == 0
     p = binding.seeds_params()
     assert binding.lib.seeds_params_default(ctypes.byref(p), 481, 321, 200) == 0
     assert (p.bins_per_channel, p.patch, p.gamma_num, p.gamma_den) == (5, 3, 1, 1)

@@ -294,6 +294,36 @@ def test_device_error_word_is_reported_and_cleared(torch, binding):
     assert np.array_equal(out.cpu().numpy(), gc.oracle_run(job, img))
 
 
+@pytest.mark.parametrize("anytime", [False, True], ids=["counting_barrier", "stop_barrier"])
+def test_barrier_wait_that_runs_out_is_reported_and_the_context_recovers(torch, binding, anytime):
+    """A bounded device-side wait made to run out (CTA 0 withholds its
+    arrival at one barrier; the limit is 0.2 ms): every CTA gives up, sets
+    the error word and leaves the kernel, no label is written, the status
+    reads SEEDS_ERR_DEVICE, and the next normal run on the same context
+    gives the oracle's labels."""
+    job = synth.plain_481()[0]
+    img = synth.make_image(job.image)
+    ctx = binding.SeedsContext([gc.params_for(binding, job)])
+    d = torch.from_numpy(img).cuda()
+    out = torch.full((job.image.height, job.image.width), -1, dtype=torch.int32, device="cuda")
+    for step in (0, 5, ctx.num_ops(0) - 2):
+        ctx.barrier_test(200_000, step)
+        out.fill_(-1)
+        if anytime:
+            ctx.run_anytime([d], [out])
+        else:
+            ctx.run([d], [out])
+        torch.cuda.synchronize()
+        assert ctx.status() == binding.SEEDS_ERR_DEVICE, step
+        assert ctx.status() == binding.SEEDS_OK
+        assert int((out != -1).sum()) == 0, "labels written after the wait ran out at step %d" % step
+    ctx.barrier_test(0, -1)
+    ctx.run([d], [out])
+    torch.cuda.synchronize()
+    ctx.check_status()
+    assert np.array_equal(out.cpu().numpy(), gc.oracle_run(job, img))
+
+
 def test_launch_count(torch, binding):
     job = synth.plain_481()[0]
     ctx = binding.SeedsContext([gc.params_for(binding, job)])

@@ -93,3 +93,30 @@ def test_served_lab_and_means_requests(torch, serve):
     want = gc.oracle_many([j for _, j in reqs], imgs)
     for i in range(len(reqs)):
         assert gc.first_mismatch(res.labels[i], want[i]) is None, "request %d" % i
+
+
+def test_served_labels_at_serving_sizes(torch, serve):
+    """The serving workload's sizes (up to 3840x2160, up to 5000
+    superpixels, 5 bins per channel, up to 4 levels, 2 iterations) in one
+    stream with small requests, in an arena that holds one 4K request at a
+    time, so that large and small requests overlap and reuse its space:
+    every label map equals the same request alone and the oracle."""
+    from paper_1309_3848_gb300 import binding
+    shapes = [(320, 240, 300), (3840, 2160, 5000), (640, 480, 900), (1920, 1080, 3000), (481, 321, 200),
+              (1280, 720, 2000), (320, 240, 4000), (3840, 2160, 1200), (640, 480, 250), (1920, 1080, 800)]
+    reqs, t = [], 0.0
+    for i, (W, H, K) in enumerate(shapes):
+        t += 0.0001  # all within a millisecond: they queue and share epochs
+        img = synth.ImageSpec(W, H, seed=7000 + i, cells=max(1, W * H // 2000), sigma=8.0)
+        reqs.append((t, synth.JobSpec(img, K, 5, 4, 2, clamp_levels=True)))
+    imgs = gc.make_images([j for _, j in reqs])
+    big = binding.footprint([serve.job_params(reqs[1][1])]) + 3840 * 2160 * 7
+    res = serve.run_stream(reqs, imgs, arena_bytes=big + (48 << 20), max_slots=6, epoch_steps=8,
+                           max_bins_per_channel=5)
+    assert res.max_resident > 1
+    want = gc.oracle_many([j for _, j in reqs], imgs)
+    for i, ((_, job), img) in enumerate(zip(reqs, imgs)):
+        assert gc.first_mismatch(res.labels[i], want[i]) is None, "request %d (%dx%d)" % (
+            i, job.image.width, job.image.height)
+        alone, _ = gc.gpu_run(binding, torch, [job], [img])
+        assert np.array_equal(alone[0], res.labels[i])

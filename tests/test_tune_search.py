@@ -1,14 +1,14 @@
 """The autotuner's search (seeds_tune_search, the code seeds_autotune runs)
 with synthetic timings on the host: one pass of coordinate descent over the
-five launch knobs in a fixed order, a 2% bar for a change, settings that
+six launch knobs in a fixed order, a 2% bar for a change, settings that
 cannot run never chosen, every candidate timed once."""
 import math
 
 from paper_1309_3848_gb300 import binding as b
 
 KNOBS = [("threads_per_block", (128, 256, 512, 1024)), ("blocks_per_sm", (0, 1, 2, 3)), ("hist_layout", (0, 1)),
-         ("small_block_area", (4, 9, 16)), ("pixel_tile_rows", (2, 4))]
-START = (1024, 0, 0, 16, 4)
+         ("small_block_area", (4, 9, 16)), ("pixel_tile_rows", (2, 4)), ("block_tiles", (0, 1, 2))]
+START = (1024, 0, 0, 16, 4, 0)
 
 
 def key(t):
@@ -28,7 +28,7 @@ def run(cost, start=START):
 
 def test_separable_costs_reach_the_minimum_of_every_knob():
     want = {"threads_per_block": 256, "blocks_per_sm": 2, "hist_layout": 1, "small_block_area": 4,
-            "pixel_tile_rows": 2}
+            "pixel_tile_rows": 2, "block_tiles": 1}
     best, calls = run(lambda t: 1.0 + sum(0.1 * (t[k] != v) for k, v in want.items()))
     assert best == tuple(want[k] for k, _ in KNOBS)
     # the start, then each knob's values other than the current one as the
@@ -41,7 +41,7 @@ def test_separable_costs_reach_the_minimum_of_every_knob():
 def test_a_change_must_win_by_two_percent():
     # 1% faster threads, 3% faster tile rows: only the tile rows move
     best, _ = run(lambda t: 1.0 - 0.01 * (t["threads_per_block"] == 512) - 0.03 * (t["pixel_tile_rows"] == 2))
-    assert best == (1024, 0, 0, 16, 2)
+    assert best == (1024, 0, 0, 16, 2, 0)
 
 
 def test_settings_that_cannot_run_are_never_taken():
