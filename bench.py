@@ -461,8 +461,9 @@ def plain_per_image(torch, binding, params, d, outs, flush, px, steps=3):
 def next_rows(torch, binding, flush, jobs, imgs, rgb_value, steps=5):
     """The widened rows on the bench workload: LAB colour bins (Sec. 6.2) and
     two means-based pixel iterations after the histogram ones (Sec. 6.3,
-    6.5), edge snapping at a colour-code threshold of 40 (Sec. 6.4), in
-    Mpixel/s beside the plain run, and anytime termination (Sec. 5.4) -- the
+    6.5), edge snapping at a colour-code threshold of 40, the compactness
+    prior at weight 64/16 and the combined prior (Sec. 6.4), SPM on its own
+    (Sec. 6.3), in Mpixel/s beside the plain run, and anytime termination (Sec. 5.4) -- the
     steps a launch reaches within device-time budgets of a quarter, half and
     three quarters of a full run, and the time the stopped call takes."""
     import dataclasses
@@ -481,6 +482,9 @@ def next_rows(torch, binding, flush, jobs, imgs, rgb_value, steps=5):
     lab_value = variant(color_space=1)
     means_value = variant(means_iters=2, compactness=10)
     edge_value = variant(edge_threshold=40)
+    prior_value = variant(compact_prior=64)
+    combined_value = variant(compact_prior=64, edge_threshold=40, color_space=1)
+    spm_value = variant(iters_per_level=0, means_iters=2, compactness=10)
 
     ctx = binding.SeedsContext([gpu_params(binding, j) for j in jobs])
     for _ in range(3):
@@ -498,6 +502,11 @@ def next_rows(torch, binding, flush, jobs, imgs, rgb_value, steps=5):
             "means_post": {"means_iters": 2, "compactness": 10, "mpix_s": means_value,
                            "over_histogram_only": means_value / rgb_value},
             "edge_snap": {"edge_threshold": 40, "mpix_s": edge_value, "over_plain": edge_value / rgb_value},
+            "compact_prior": {"compact_prior": 64, "mpix_s": prior_value, "over_plain": prior_value / rgb_value},
+            "combined_prior": {"compact_prior": 64, "edge_threshold": 40, "color_space": "lab", "patch": 3,
+                               "mpix_s": combined_value, "over_plain": combined_value / rgb_value},
+            "spm_alone": {"iters_per_level": 0, "means_iters": 2, "compactness": 10, "mpix_s": spm_value,
+                          "over_plain": spm_value / rgb_value},
             "anytime": {"full_steps": full_steps, "full_ms": full_ms, "budgets": budgets}}
 
 
