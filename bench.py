@@ -515,7 +515,14 @@ def serve_requests(rate, seconds, seed, max_requests=4000):
     return synth.serve_requests(rate, seconds, seed, max_requests=max_requests)
 
 
-def serve_sample(rates, seconds, per_size=3, arena_gib=8, epoch_steps=16):
+# ops per image per serving epoch: measured on the Poisson streams (2 s per
+# rate), 24-96 all keep p99 under 10 ms at 1000 req/s; at 2000 req/s 48 and
+# more give p99 61-72 ms against 104-114 ms for 24-32, and 16 or fewer let
+# short epochs' fixed costs build a backlog
+SERVE_EPOCH_STEPS = 48
+
+
+def serve_sample(rates, seconds, per_size=3, arena_gib=8, epoch_steps=SERVE_EPOCH_STEPS):
     """Poisson request streams (sizes 320x240..3840x2160, 200..5000
     superpixels) through the continuous-batching server: latency
     percentiles from each request's scheduled arrival to its completion,
@@ -531,7 +538,8 @@ def serve_sample(rates, seconds, per_size=3, arena_gib=8, epoch_steps=16):
                                epoch_steps=epoch_steps, max_bins_per_channel=5)
         out.append({"rate_req_s": rate, "requests": len(reqs), "mpix_s": res.mpix_per_s,
                     "p50_ms": res.percentile(50), "p99_ms": res.percentile(99), "max_resident": res.max_resident,
-                    "epochs": res.epochs, "arrival_window_s": seconds})
+                    "epochs": res.epochs, "epoch_steps": epoch_steps, "arrival_window_s": seconds,
+                    "offered_mpix_s": sum(j.pixels for _, j in reqs) / seconds / 1e6})
     return out
 
 
