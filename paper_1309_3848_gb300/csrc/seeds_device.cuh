@@ -29,7 +29,7 @@ constexpr uint32_t kNoMove = 0xFFFFFFFFu;
 // the start and the phases of the means-based pixel iterations (Sec. 6.5).
 // OP_CATCHUP and OP_BTILE occur only in step entries: a catch-up replays the
 // previous phase's moves, and OP_BTILE is a block phase (OP_PHASE, level >=
-// 1) run in warp tiles.
+// 1, blocks judged by a warp) run in warp tiles.
 enum : int32_t {
     OP_INIT = 0,
     OP_PHASE = 1,
@@ -237,12 +237,19 @@ __host__ __device__ inline void lattice(int nx, int ny, int phase, int cphase, i
     }
 }
 
+// Warp tiles of a block phase are one unit row high.  The warp judges its
+// tile's boundary blocks one after another, each a chain of trips to memory,
+// so a step is bound by its longest tile; short tiles keep that chain short
+// and give the step more warps.
+constexpr int kBlockTileUY = 1;
+
 // warp tiles of a phase on a level's grid (level 0: pixels)
 __host__ __device__ inline int64_t level_tiles(const DevImage &im, int level, int phase, int cphase)
 {
     int cols, rows;
     lattice(im.nbx[level], im.nby[level], phase, cphase, &cols, &rows);
-    return (int64_t)((cols + kTileUX - 1) / kTileUX) * ((rows + im.tile_uy - 1) / im.tile_uy);
+    const int uy = level > 0 ? kBlockTileUY : im.tile_uy;
+    return (int64_t)((cols + kTileUX - 1) / kTileUX) * ((rows + uy - 1) / uy);
 }
 
 __host__ __device__ inline int64_t pixel_tiles(const DevImage &im, int phase, int cphase)
@@ -300,7 +307,7 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
         if (op.level == 0) {  // warp tiles
             units = pixel_tiles(im, op.phase, cphase);
             group = 32;
-        } else if (tiles && op.kind == OP_PHASE) {  // block phase in warp tiles
+        } else if (tiles && op.kind == OP_PHASE && level_group(im, op.level) == 32) {  // warp blocks in tiles
             kind = OP_BTILE;
             units = level_tiles(im, op.level, op.phase, cphase);
             group = 32;
@@ -344,18 +351,20 @@ __host__ __device__ inline int fuse_step(int64_t fused_vt, int64_t split_below)
     return fused_vt / 32 >= split_below ? 2 : fused_vt / 32 >= split_below / 8 ? 1 : 0;
 }
 
-// The mode of a step (emit_entries' `mode`): its fusion, and block phases in
-// warp tiles when the step has at least kTileRounds warp tiles per warp slot
-// of the machine.  A tile stages its labels once and judges only its
-// boundary units (compacted), which cuts the per-unit cost of steps with
-// many units; with fewer units the per-unit ops keep more warps busy.
+// The mode of a step (emit_entries' `mode`): its fusion, and the phases of
+// warp-judged blocks in warp tiles when the step has at least kTileRounds
+// warp tiles per warp slot of the machine.  A tile stages its block labels
+// once and judges only its boundary blocks, which cuts the per-block cost of
+// steps with many blocks; with fewer blocks the per-unit ops keep more warps
+// busy.  Blocks judged by a thread each keep their per-unit op: a lane per
+// block already runs 32 judges at once.
 // `fused_vt`: the step's thread count with fused per-unit entries,
 // `tiled_vt`: with fused tile entries.
-// `policy` (seeds_tuning.block_tiles): 0 never, 1 by that rule, 2 always.
+// `policy` (seeds_tuning.block_tiles): 0 by that rule, 1 never, 2 always.
 constexpr int kTileRounds = 2;
 __host__ __device__ inline int step_mode(int64_t fused_vt, int64_t tiled_vt, int64_t split_below, int policy = 0)
 {
-    const bool tiles = policy == 2 || (policy == 1 && tiled_vt / 32 >= kTileRounds * split_below);
+    const bool tiles = policy == 2 || (policy == 0 && tiled_vt / 32 >= kTileRounds * split_below);
     return fuse_step(fused_vt, split_below) | (tiles ? kTileBlocks : 0);
 }
 
@@ -371,6 +380,7 @@ struct EpochPlan {
     int32_t n;            // slots in the epoch
     int32_t nsteps;       // max over slots of end - begin (<= 1024)
     int32_t split_below;  // fuse_step's threshold in warps
+    int32_t tile_policy;  // step_mode's policy (seeds_tuning.block_tiles)
     EpochSlot s[kMaxEpochSlots];
 };
 

@@ -1302,20 +1302,19 @@ __device__ uint32_t judge_large_block_c(const DevImage &im, int b, int nb, int l
 // block phase in warp tiles (steps with many units)
 // ---------------------------------------------------------------------------
 
-// One warp-tile of a block phase: units (ux, uy) of the phase's parity class
-// on the level's block grid, ux in a 32-wide column range (one per lane), uy
-// in a UY-row range, as in the pixel tile.  The block labels of the tile and
-// a 2-cell halo are staged in shared memory; the warp replays the previous
-// phase's moves of the same unit positions (cphase >= 0), marks the units
-// that sit on a boundary and may leave (pass 1, from shared memory), and
-// judges only those.  SMALL: blocks of at most small_area pixels, judged a
-// lane each over the compacted list; otherwise the warp judges the marked
-// blocks one after another (sparse histogram in its scratch).  The moves
-// and decisions are the ones the per-unit ops take.
-template <bool SMALL, int UY>
-__device__ __noinline__ void op_block_tile(const DevImage &im, int o, int level, int phase, int cphase, int tiles, int tile,
-                              int lane, int32_t *wsh, uint16_t *tsh, int max_nbins)
+// One warp-tile of a block phase on a level of warp-judged blocks: units
+// (ux, uy) of the phase's parity class on the level's block grid, ux in a
+// 32-wide column range (one per lane), uy in a kBlockTileUY-row range, as in
+// the pixel tile.  The block labels of the tile and a 2-cell halo are staged
+// in shared memory; the warp replays the previous phase's moves of the same
+// unit positions (cphase >= 0), marks the units that sit on a boundary and
+// may leave (from shared memory), decides "stay" for the others, and judges
+// the marked blocks one after another (sparse histogram in its scratch).
+// The moves and decisions are the ones the per-unit ops take.
+__device__ __forceinline__ void op_block_tile(const DevImage &im, int o, int level, int phase, int cphase, int tiles,
+                                              int tile, int lane, int32_t *wsh, uint16_t *tsh, int max_nbins)
 {
+    constexpr int UY = kBlockTileUY;
     if (tile >= tiles) return;
     const int b = o & 1, nb = b ^ 1;
     const int nx = im.nbx[level], ny = im.nby[level];
@@ -1348,27 +1347,21 @@ __device__ __noinline__ void op_block_tile(const DevImage &im, int o, int level,
     tile_store<TH>(stage, tsh, lane);
 
     // replay the previous phase's moves into buffer nb (the staged labels
-    // are buffer b's)
-    if constexpr (SMALL) {
+    // are buffer b's), a block at a time by the whole warp
 #pragma unroll
-        for (int r = 0; r < UY; ++r)
-            if (cd[r] != kNoMove) replay_small_block(im, nb, level, 2 * ux + cpx, 2 * (uy0 + r) + cpy, cd[r]);
-    } else {
-#pragma unroll
-        for (int r = 0; r < UY; ++r) {
-            unsigned m = __ballot_sync(0xffffffffu, cd[r] != kNoMove);
-            while (m) {
-                const int l = __ffs(m) - 1;
-                m &= m - 1;
-                const uint32_t d = __shfl_sync(0xffffffffu, cd[r], l);
-                replay_large_block(im, nb, level, 2 * (tx * kTileUX + l) + cpx, 2 * (uy0 + r) + cpy, d, lane, wsh,
-                                   max_nbins);
-            }
+    for (int r = 0; r < UY; ++r) {
+        unsigned m = __ballot_sync(0xffffffffu, cd[r] != kNoMove);
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t d = __shfl_sync(0xffffffffu, cd[r], l);
+            replay_large_block(im, nb, level, 2 * (tx * kTileUX + l) + cpx, 2 * (uy0 + r) + cpy, d, lane, wsh,
+                               max_nbins);
         }
     }
     __syncwarp();
 
-    // pass 1: boundary units that may leave; the others decide "stay" here
+    // boundary units that may leave; the others decide "stay" here
     unsigned mine = 0;
 #pragma unroll
     for (int r = 0; r < UY; ++r) {
@@ -1382,19 +1375,13 @@ __device__ __noinline__ void op_block_tile(const DevImage &im, int o, int level,
         }
     }
 
-    if constexpr (SMALL) {
-        // compacted: every lane judges one marked unit at a time
-        uint8_t *lst = (uint8_t *)(tsh + kTileW * TH);
-        int nbd = 0;
+    // the warp judges the marked blocks one after another
 #pragma unroll
-        for (int r = 0; r < UY; ++r) {
-            const unsigned bal = __ballot_sync(0xffffffffu, (mine >> r) & 1u);
-            if ((mine >> r) & 1u) lst[nbd + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(r * 32 + lane);
-            nbd += __popc(bal);
-        }
-        __syncwarp();
-        for (int i = lane; i < nbd; i += 32) {
-            const int e = lst[i], r = e >> 5, l = e & 31;
+    for (int r = 0; r < UY; ++r) {
+        unsigned m = __ballot_sync(0xffffffffu, (mine >> r) & 1u);
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
             const int uxe = tx * kTileUX + l, uy = uy0 + r;
             const int bx = 2 * uxe + px, by = 2 * uy + py;
             const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
@@ -1402,34 +1389,10 @@ __device__ __noinline__ void op_block_tile(const DevImage &im, int o, int level,
             const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * l + 2);
             const int k = T[0];
             int cand[4];
-            sorted_candidates(T[-1], T[1], T[-kTileW], T[kTileW], k, cand);  // pass 1 found that it may leave
-            const int ma = im.maxarea[level];
+            sorted_candidates(T[-1], T[1], T[-kTileW], T[kTileW], k, cand);
             const uint32_t d =
-                ma <= 4   ? judge_small_block_c<4>(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1)
-                : ma <= 9 ? judge_small_block_c<9>(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1)
-                          : judge_small_block_c<kSmallMax>(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1);
-            im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = d;
-        }
-    } else {
-        // the warp judges the marked blocks one after another
-#pragma unroll
-        for (int r = 0; r < UY; ++r) {
-            unsigned m = __ballot_sync(0xffffffffu, (mine >> r) & 1u);
-            while (m) {
-                const int l = __ffs(m) - 1;
-                m &= m - 1;
-                const int uxe = tx * kTileUX + l, uy = uy0 + r;
-                const int bx = 2 * uxe + px, by = 2 * uy + py;
-                const int x0 = im.xe[level][bx], x1 = im.xe[level][bx + 1];
-                const int y0 = im.ye[level][by], y1 = im.ye[level][by + 1];
-                const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * l + 2);
-                const int k = T[0];
-                int cand[4];
-                sorted_candidates(T[-1], T[1], T[-kTileW], T[kTileW], k, cand);
-                const uint32_t d =
-                    judge_large_block_c(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1, lane, wsh, max_nbins);
-                if (lane == 0) im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = d;
-            }
+                judge_large_block_c(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1, lane, wsh, max_nbins);
+            if (lane == 0) im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = d;
         }
     }
     __syncwarp();
@@ -1680,21 +1643,7 @@ __global__ void __launch_bounds__(1024, 1) seeds_persistent(const DevImage *__re
                                         S.max_nbins);
                 break;
             case OP_BTILE:
-                if (level_group(im, E.level) == 1) {
-                    if (im.tile_uy == 2)
-                        op_block_tile<true, 2>(im, E.opidx, E.level, E.phase, E.cphase, E.units, off >> 5, lane, wsh,
-                                               tsh, S.max_nbins);
-                    else
-                        op_block_tile<true, kTileUY>(im, E.opidx, E.level, E.phase, E.cphase, E.units, off >> 5, lane,
-                                                     wsh, tsh, S.max_nbins);
-                } else {
-                    if (im.tile_uy == 2)
-                        op_block_tile<false, 2>(im, E.opidx, E.level, E.phase, E.cphase, E.units, off >> 5, lane,
-                                                wsh, tsh, S.max_nbins);
-                    else
-                        op_block_tile<false, kTileUY>(im, E.opidx, E.level, E.phase, E.cphase, E.units, off >> 5,
-                                                      lane, wsh, tsh, S.max_nbins);
-                }
+                op_block_tile(im, E.opidx, E.level, E.phase, E.cphase, E.units, off >> 5, lane, wsh, tsh, S.max_nbins);
                 break;
             case OP_MPHASE:
                 op_means_tile(im, E.opidx, E.phase, E.cphase, E.units, off >> 5, lane, tsh);
@@ -1834,7 +1783,7 @@ __global__ void epoch_schedule_kernel(const DevImage *imgs, EpochPlan plan, Step
                 if (pass == 2) c += m;
             }
             if (pass < 2) sized[pass] = v;
-            if (pass == 1) fuse = step_mode(sized[0], sized[1], plan.split_below);
+            if (pass == 1) fuse = step_mode(sized[0], sized[1], plan.split_below, plan.tile_policy);
         }
     }
     cnt[s] = c;

@@ -106,7 +106,12 @@ size_t request_bytes(const ImageHost &h, size_t *rgb_off, size_t *out_off)
 struct seeds_server {
     int device = 0, sm_count = 0;
     seeds_server_config cfg{};
-    seeds_tuning tune{1024, 0, 0, 16, 4, 0};
+    // Block phases stay per unit (block_tiles 1): an epoch's step mixes
+    // images at different levels, and the tile rule, which decides per step,
+    // would also tile the levels of small images with large blocks, whose
+    // warps then judge a tile's boundary blocks one after another for longer
+    // than the rest of the step takes.
+    seeds_tuning tune{1024, 0, 0, 16, 4, 1};
     int max_nbins = 1;
     unsigned char *arena = nullptr;
     ArenaAllocator alloc;
@@ -318,6 +323,7 @@ int seeds_server_step(seeds_server *s, int32_t *resident_out)
     EpochPlan plan;
     std::memset(&plan, 0, sizeof(plan));
     plan.split_below = s->sm_count * 32;
+    plan.tile_policy = s->tune.block_tiles;
     for (Request *r : s->slots) {
         if (!r) continue;
         EpochSlot &q = plan.s[plan.n++];

@@ -38,7 +38,7 @@ STEP_CASES = [
 ]
 
 
-@pytest.mark.parametrize("tiles", [0, 2], ids=["per-unit", "tiled"])
+@pytest.mark.parametrize("tiles", [1, 2], ids=["per-unit", "tiled"])
 @pytest.mark.parametrize("job", STEP_CASES, ids=["481x321", "64x48", "97x61_B8", "50x37_L0"])
 def test_state_matches_after_every_op(torch, binding, job, tiles):
     W, H = job.image.width, job.image.height
@@ -208,7 +208,7 @@ TUNINGS = [dict(threads_per_block=128), dict(threads_per_block=512, hist_layout=
            dict(threads_per_block=256, blocks_per_sm=2, hist_layout=0, small_block_area=9),
            dict(pixel_tile_rows=2), dict(threads_per_block=512, pixel_tile_rows=2, small_block_area=1),
            dict(block_tiles=2), dict(block_tiles=2, small_block_area=4, pixel_tile_rows=2),
-           dict(block_tiles=1, threads_per_block=256)]
+           dict(block_tiles=1, threads_per_block=256), dict(block_tiles=2, small_block_area=1, blocks_per_sm=1)]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)

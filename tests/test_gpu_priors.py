@@ -56,7 +56,7 @@ STEP_CASES = {
 }
 
 
-@pytest.mark.parametrize("tiles", [0, 2], ids=["per-unit", "tiled"])
+@pytest.mark.parametrize("tiles", [1, 2], ids=["per-unit", "tiled"])
 @pytest.mark.parametrize("name", sorted(STEP_CASES))
 def test_state_matches_after_every_op(torch, binding, name, tiles):
     job = STEP_CASES[name]

@@ -128,24 +128,40 @@ def test_units_follow_the_lattices():
                 c2, r2 = lattice(nx, ny, e["cphase"])
                 cols, rows = max(cols, c2), max(rows, r2)
             assert e["units"] == cols * rows
-    # pixel phases: warp tiles of 32 x 4 (or 32 x 2) units
-    # pixel phases, and block phases of steps run in tiles: warp tiles of
-    # 32 x 4 (or 32 x 2) units
+    # pixel phases: warp tiles of 32 x 4 (or 32 x 2) units; block phases of
+    # warp-judged levels, in steps with at least two tiles per warp slot:
+    # warp tiles of 32 x 1 units
+    W, H = p.width, p.height
+
+    def maxarea(level):
+        nx, ny = g[level]
+        w = max((i + 1) * W // nx - i * W // nx for i in range(nx))
+        h = max((i + 1) * H // ny - i * H // ny for i in range(ny))
+        return w * h
+
     for rows_per_tile in (4, 2):
-        t = b.seeds_tuning(0, 0, 0, 16, rows_per_tile, 1)
+        t = b.seeds_tuning(0, 0, 0, 16, rows_per_tile, 0)
         tiled = 0
-        for threads, ents in b.plan([p], 1, t):  # one SM: every step fused, block steps tiled
+        for threads, ents in b.plan([p], 1, t):  # one SM (32 warp slots): every step fused
             for e in ents:
-                if (e["op"] == PHASE and e["level"] == 0) or e["op"] == BTILE:
-                    cols, rows = lattice(*g[e["level"]], e["phase"])
-                    if e["cphase"] >= 0:
-                        c2, r2 = lattice(*g[e["level"]], e["cphase"])
-                        cols, rows = max(cols, c2), max(rows, r2)
+                if e["op"] not in (PHASE, BTILE):
+                    continue
+                cols, rows = lattice(*g[e["level"]], e["phase"])
+                if e["cphase"] >= 0:
+                    c2, r2 = lattice(*g[e["level"]], e["cphase"])
+                    cols, rows = max(cols, c2), max(rows, r2)
+                if e["level"] == 0:
                     assert e["units"] == -(-cols // 32) * -(-rows // rows_per_tile) and e["group"] == 32
-                    tiled += e["op"] == BTILE
-        # with 32 warp slots, levels 2 and 1 of 1080p have at least 64 tiles per
-        # phase (levels 4 and 3 have 12 and 36 at 4 rows: per-unit entries)
-        assert tiled == 2 * 4 * p.iters_per_level if rows_per_tile == 4 else tiled >= 2 * 4 * p.iters_per_level
+                    continue
+                tiles = -(-cols // 32) * rows
+                expect = maxarea(e["level"]) > 16 and tiles >= 2 * 32
+                assert (e["op"] == BTILE) == expect, (e, tiles)
+                if expect:
+                    assert e["units"] == tiles and e["group"] == 32
+                    tiled += 1
+        # levels 4..2 of 1080p judge their blocks by warps; 2 and 3 have
+        # more than 64 one-row tiles per phase
+        assert tiled >= 2 * 4 * p.iters_per_level
 
 
 def test_fusion_follows_the_step_size():
@@ -194,13 +210,15 @@ def test_small_blocks_take_a_thread_each():
 
 
 def test_block_steps_run_in_tiles_when_they_fill_the_machine_twice():
-    """With block_tiles = 1 a block step runs in warp tiles exactly when its
-    tiles (fused form) number at least twice the machine's warp slots
-    (sms x 32); otherwise its blocks keep one thread or one warp each (and
-    with the default, 0, always)."""
+    """By default (block_tiles = 0) a step of warp-judged blocks runs in warp
+    tiles of 32 x 1 units exactly when its tiles (fused form) number at least
+    twice the machine's warp slots (sms x 32); otherwise, and always with
+    block_tiles = 1, its blocks keep a warp each.  Blocks judged by a thread
+    never run in tiles, and block_tiles = 2 tiles every warp-judged step."""
     ps = [params_of(j) for j in synth.batch_4k(4)]
     g = grid(ps[0])
-    rule = b.seeds_tuning(0, 0, 0, 16, 4, 1)
+    rule = b.seeds_tuning(0, 0, 0, 16, 4, 0)
+    seen = set()
     for sms in (1, 16, 152, 1 << 12):
         for threads, ents in b.plan(ps, sms, rule):
             blocks = [e for e in ents if kind_of(e) == PHASE and e["level"] > 0]
@@ -212,10 +230,19 @@ def test_block_steps_run_in_tiles_when_they_fill_the_machine_twice():
             if prev:
                 c2, r2 = lattice(*g[level], prev[0])
                 cols, rows = max(cols, c2), max(rows, r2)
-            tiles = len(ps) * -(-cols // 32) * -(-rows // 4)
-            tiled = tiles >= 2 * sms * 32
+            warp = all(e["group"] == 32 for e in blocks)
+            tiles = len(ps) * -(-cols // 32) * rows
+            tiled = warp and tiles >= 2 * sms * 32
+            seen.add((warp, tiled))
             assert all((e["op"] == BTILE) == tiled for e in blocks), (sms, level, tiles)
-        assert not any(e["op"] == BTILE for _, ents in b.plan(ps, sms) for e in ents)
+        never = b.seeds_tuning(0, 0, 0, 16, 4, 1)
+        assert not any(e["op"] == BTILE for _, ents in b.plan(ps, sms, never) for e in ents)
+        always = b.seeds_tuning(0, 0, 0, 16, 4, 2)
+        for _, ents in b.plan(ps, sms, always):
+            for e in ents:
+                if kind_of(e) == PHASE and e["level"] > 0:
+                    assert (e["op"] == BTILE) == (e["group"] == 32), (sms, e)
+    assert seen == {(False, False), (True, False), (True, True)}
 
 
 def test_a_batch_shares_every_step():
