@@ -137,11 +137,12 @@ typedef struct {
  *                      2 or 4 (0 = 4); shorter tiles balance small images
  *   small_block_area   blocks of at most this many pixels are judged by one
  *                      thread, larger ones by a warp (1..16; 0 = default)
- *   block_tiles        phases of warp-judged block levels in warp tiles
- *                      (32 x 1 units, labels staged in shared memory, only
- *                      boundary blocks judged): 0 = in steps with at least
- *                      two tiles per warp slot of the GPU (the default),
- *                      1 = never, 2 = always */
+ *   block_tiles        wide steps: phases of warp-judged block levels in
+ *                      warp tiles (32 x 1 units, labels staged in shared
+ *                      memory, only boundary blocks judged) and catch-ups
+ *                      with more units per lane: 0 = steps with at least two
+ *                      tiles per warp slot of the GPU (the default),
+ *                      1 = never, 2 = every step */
 typedef struct {
     int32_t threads_per_block;
     int32_t blocks_per_sm;

@@ -154,8 +154,14 @@ __host__ __device__ constexpr int tile_h(int uy) { return 2 * uy + 3; }  // pixe
 constexpr int kTileH = tile_h(kTileUY);
 // staged labels, the units' bins, the list of the tile's boundary units
 constexpr int kTileBytes = (kTileW * kTileH * 2 + kTileUY * kTileUX * 2 + kTileUY * kTileUX + 15) & ~15;
-// the pixel catch-up replays kCatchupPerLane units per lane
+// A catch-up entry (the replay of a phase's moves on its own) gives a lane
+// kCatchupPerLane pixels, a small block a lane each and a block that a warp
+// judges a warp each.  In a wide step (kWideStep) a lane takes
+// kCatchupPerLane small blocks, and blocks a warp judges of at most
+// kCatchupLaneArea pixels take a lane each to read their decisions; the
+// warp then replays the moved ones one after another.
 constexpr int kCatchupPerLane = 4;
+constexpr int kCatchupLaneArea = 64;
 // descents and the output: cells (pixels) of a row per thread
 constexpr int kRowChunk = 8;
 
@@ -222,6 +228,16 @@ __host__ __device__ inline int level_group(const DevImage &im, int level)
     return thread ? 1 : 32;
 }
 
+// threads per unit of a catch-up entry, and units per lane where that is 1
+__host__ __device__ inline int catchup_group(const DevImage &im, int level, bool wide)
+{
+    return level > 0 && level_group(im, level) == 32 && (!wide || im.maxarea[level] > kCatchupLaneArea) ? 32 : 1;
+}
+__host__ __device__ inline int catchup_per_lane(const DevImage &im, int level, bool wide)
+{
+    return level == 0 || (wide && level_group(im, level) == 1) ? kCatchupPerLane : 1;
+}
+
 // The unit lattice of a phase on a grid nx x ny: unit (ux,uy) is cell
 // (2ux + px, 2uy + py).  A phase entry that also replays the previous phase
 // (cphase >= 0) walks the union of both lattices, so that one thread or warp
@@ -257,35 +273,37 @@ __host__ __device__ inline int64_t pixel_tiles(const DevImage &im, int phase, in
     return level_tiles(im, 0, phase, cphase);
 }
 
-// emit_entries' `fuse` argument: bits 0-1 the fusion of replays (fuse_step),
-// bit 2 block phases in warp tiles (step_mode)
-constexpr int kTileBlocks = 4;
+// emit_entries' `mode` argument: bits 0-1 the fusion of replays
+// (fuse_step), bit 2 a wide step (step_mode): phases of warp-judged blocks
+// in warp tiles, catch-ups with more units per lane
+constexpr int kWideStep = 4;
 
 // Entries of image `img` for its op `o`.  When the moves of op o-1 (a phase)
 // are pending, a phase of the same level replays them unit by unit before
 // judging its own units (one fused entry) if `fuse` allows it (2: block and
 // pixel phases, 1: pixel phases only, 0: none; see fuse_step); otherwise
 // they get a catch-up entry of their own first, whose warps run beside the
-// phase's.  Returns the number of entries written; `vt` advances by their
-// padded thread counts.
+// phase's.  The output op needs none: it reads the buffer that the last
+// phase wrote its moves into, and nothing reads the other buffer or the
+// histograms after it.  Returns the number of entries written; `vt` advances
+// by their padded thread counts.
 __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, bool catchup, int mode,
                                             StepEntry *out, int64_t *vt)
 {
     const int fuse = mode & 3;
-    const bool tiles = (mode & kTileBlocks) != 0;
+    const bool wide = (mode & kWideStep) != 0;
     int n = 0;
     const OpDesc op = op_at(im.L, im.iters, im.means_iters, o);
     int cphase = -1;
-    if (catchup && o > 0) {
+    if (catchup && o > 0 && op.kind != OP_OUTPUT) {
         const OpDesc pv = op_at(im.L, im.iters, im.means_iters, o - 1);
         if (is_phase(pv.kind) && op.kind == pv.kind && pv.level == op.level && fuse >= (op.level == 0 ? 1 : 2)) {
             cphase = pv.phase;
         } else if (is_phase(pv.kind)) {
-            // large blocks are replayed by a warp each, small blocks by a
-            // thread each, pixels kCatchupPerLane to a thread
-            int64_t units = phase_units(im, pv.level, pv.phase);
-            const int group = level_group(im, pv.level);
-            if (pv.level == 0) units = (units + kCatchupPerLane - 1) / kCatchupPerLane;
+            const int64_t pu = phase_units(im, pv.level, pv.phase);
+            const int group = catchup_group(im, pv.level, wide);
+            const int per = catchup_per_lane(im, pv.level, wide);
+            const int64_t units = (pu + per - 1) / per;  // lanes (group 1) or warps (group 32)
             const int64_t count = (units * group + 31) / 32 * 32;
             if (count > 0) {
                 StepEntry e{img, OP_CATCHUP, pv.level, pv.phase, o, (int32_t)units, *vt, group, -1};
@@ -307,7 +325,7 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
         if (op.level == 0) {  // warp tiles
             units = pixel_tiles(im, op.phase, cphase);
             group = 32;
-        } else if (tiles && op.kind == OP_PHASE && level_group(im, op.level) == 32) {  // warp blocks in tiles
+        } else if (wide && op.kind == OP_PHASE && level_group(im, op.level) == 32) {  // warp blocks in tiles
             kind = OP_BTILE;
             units = level_tiles(im, op.level, op.phase, cphase);
             group = 32;
@@ -351,13 +369,16 @@ __host__ __device__ inline int fuse_step(int64_t fused_vt, int64_t split_below)
     return fused_vt / 32 >= split_below ? 2 : fused_vt / 32 >= split_below / 8 ? 1 : 0;
 }
 
-// The mode of a step (emit_entries' `mode`): its fusion, and the phases of
-// warp-judged blocks in warp tiles when the step has at least kTileRounds
-// warp tiles per warp slot of the machine.  A tile stages its block labels
-// once and judges only its boundary blocks, which cuts the per-block cost of
-// steps with many blocks; with fewer blocks the per-unit ops keep more warps
-// busy.  Blocks judged by a thread each keep their per-unit op: a lane per
-// block already runs 32 judges at once.
+// The mode of a step (emit_entries' `mode`): its fusion, and kWideStep when
+// the step has at least kTileRounds warp tiles per warp slot of the machine.
+// A wide step runs the phases of warp-judged blocks in warp tiles: a tile
+// stages its block labels once and judges only its boundary blocks, which
+// cuts the per-block cost of steps with many blocks.  Blocks judged by a
+// thread each keep their per-unit op: a lane per block already runs 32
+// judges at once.  Its catch-ups read more decisions per lane and replay
+// more moves per warp (kCatchupPerLane), which pays once the machine is
+// full.  With fewer units the per-unit forms keep more warps busy and each
+// warp's chain of dependent loads short.
 // `fused_vt`: the step's thread count with fused per-unit entries,
 // `tiled_vt`: with fused tile entries.
 // `policy` (seeds_tuning.block_tiles): 0 by that rule, 1 never, 2 always.
@@ -365,7 +386,7 @@ constexpr int kTileRounds = 2;
 __host__ __device__ inline int step_mode(int64_t fused_vt, int64_t tiled_vt, int64_t split_below, int policy = 0)
 {
     const bool tiles = policy == 2 || (policy == 0 && tiled_vt / 32 >= kTileRounds * split_below);
-    return fuse_step(fused_vt, split_below) | (tiles ? kTileBlocks : 0);
+    return fuse_step(fused_vt, split_below) | (tiles ? kWideStep : 0);
 }
 
 // An epoch of the serving runtime: for each resident slot, the range of its

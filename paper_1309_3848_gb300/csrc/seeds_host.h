@@ -315,7 +315,7 @@ inline void build_steps(const std::vector<DevImage> &imgs, const std::vector<int
         for (int pass = 0; pass < 3; ++pass) {
             int64_t v = 0;
             const int mode =
-                pass == 0 ? 2 : pass == 1 ? 2 | kTileBlocks : step_mode(sized[0], sized[1], split_below, tile_policy);
+                pass == 0 ? 2 : pass == 1 ? 2 | kWideStep : step_mode(sized[0], sized[1], split_below, tile_policy);
             for (int i = 0; i < n; ++i) {
                 const DevImage &im = imgs[i];
                 const int o = b[i] + s;

@@ -1402,10 +1402,14 @@ __device__ __forceinline__ void op_block_tile(const DevImage &im, int o, int lev
 // catch-up: replay op o-1's moves into the buffer that op read
 // ---------------------------------------------------------------------------
 
-// A catch-up entry of its own (before a descent or the output): replay op
-// o-1's moves into the buffer that op read.
-__device__ void op_catchup(const DevImage &im, int o, int level, int phase, int units, int group, int off, int lane,
-                           int32_t *wsh, int max_nbins)
+// A catch-up entry of its own (before a descent, or beside a phase of a step
+// that does not fuse replays): replay op o-1's moves into the buffer that op
+// read.  `units`: the phase's units; `lanes`: the entry's units.  group 32:
+// warp w replays unit w.  Otherwise lane l of warp w reads the decisions of
+// units per * 32 * w + 32 * r + l (r < per, coalesced), per = kCatchupPerLane
+// when the entry has fewer lanes than units, else 1.
+__device__ void op_catchup(const DevImage &im, int o, int level, int phase, int units, int lanes, int group, int off,
+                           int lane, int32_t *wsh, int max_nbins)
 {
     const int nb = (o & 1) ^ 1;  // = (o-1) & 1: the buffer op o-1 read and decided into
     const int nx = im.nbx[level];
@@ -1419,20 +1423,21 @@ __device__ void op_catchup(const DevImage &im, int o, int level, int phase, int 
         replay_large_block(im, nb, level, bx, by, d, lane, wsh, max_nbins);
         return;
     }
-    if (level == 0) {  // pixels: kCatchupPerLane units per lane, coalesced rows
-        const int chunk = off >> 5;
-        uint32_t d[kCatchupPerLane];
+    const int per = lanes < units ? kCatchupPerLane : 1;
+    const int u0 = (off >> 5) * 32 * per + lane;
+    uint32_t d[kCatchupPerLane];
 #pragma unroll
-        for (int r = 0; r < kCatchupPerLane; ++r) {
-            const int u = chunk * 32 * kCatchupPerLane + 32 * r + lane;
-            d[r] = u < units ? im.dec[nb][SEEDS_IDX(im, u, im.units_cap)] : kNoMove;
-        }
+    for (int r = 0; r < kCatchupPerLane; ++r) {
+        const int u = u0 + 32 * r;
+        d[r] = r < per && u < units ? im.dec[nb][SEEDS_IDX(im, u, im.units_cap)] : kNoMove;
+    }
+    if (level == 0) {  // pixels
         const bool means = op_at(im.L, im.iters, im.means_iters, o - 1).kind == OP_MPHASE;
 #pragma unroll
         for (int r = 0; r < kCatchupPerLane; ++r) {
             if (d[r] == kNoMove) continue;
             int x, y;
-            unit_pos(chunk * 32 * kCatchupPerLane + 32 * r + lane, phase, im.W, &x, &y);
+            unit_pos(u0 + 32 * r, phase, im.W, &x, &y);
             replay_pixel(im, nb, y * im.W + x, d[r]);
             if (means)
                 move_sums(im, nb, (int)(d[r] >> 16), (int)(d[r] & 0xFFFFu), x, y);
@@ -1441,13 +1446,25 @@ __device__ void op_catchup(const DevImage &im, int o, int level, int phase, int 
         }
         return;
     }
-    const int u = off + lane;  // small blocks: one thread per unit
-    if (u >= units) return;
-    const uint32_t d = im.dec[nb][SEEDS_IDX(im, u, im.units_cap)];
-    if (d == kNoMove) return;
-    int bx, by;
-    unit_pos(u, phase, nx, &bx, &by);
-    replay_small_block(im, nb, level, bx, by, d);
+    if (level_group(im, level) == 32) {  // blocks a warp judges: the warp replays each move (per is 1)
+        unsigned m = __ballot_sync(0xffffffffu, d[0] != kNoMove);
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t dl = __shfl_sync(0xffffffffu, d[0], l);
+            int bx, by;
+            unit_pos(u0 - lane + l, phase, nx, &bx, &by);
+            replay_large_block(im, nb, level, bx, by, dl, lane, wsh, max_nbins);
+        }
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < kCatchupPerLane; ++r) {  // small blocks: a lane each
+        if (d[r] == kNoMove) continue;
+        int bx, by;
+        unit_pos(u0 + 32 * r, phase, nx, &bx, &by);
+        replay_small_block(im, nb, level, bx, by, d[r]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1652,8 +1669,8 @@ __global__ void __launch_bounds__(1024, 1) seeds_persistent(const DevImage *__re
                 op_means_init(im, E.opidx, E.units, off + lane, lane);
                 break;
             case OP_CATCHUP:
-                op_catchup(im, E.opidx, E.level, E.phase, (int)phase_units(im, E.level, E.phase), E.group, off,
-                           lane, wsh, S.max_nbins);
+                op_catchup(im, E.opidx, E.level, E.phase, (int)phase_units(im, E.level, E.phase), E.units, E.group,
+                           off, lane, wsh, S.max_nbins);
                 break;
             case OP_DESCEND:
                 op_descend(im, E.opidx, E.level, E.units, off + lane);
@@ -1771,7 +1788,7 @@ __global__ void epoch_schedule_kernel(const DevImage *imgs, EpochPlan plan, Step
         int64_t sized[2] = {0, 0};  // the step's size with fused per-unit entries, with fused tiles
         for (int pass = 0; pass < 3; ++pass) {
             int64_t v = 0;
-            const int mode = pass == 0 ? 2 : pass == 1 ? 2 | kTileBlocks : fuse;
+            const int mode = pass == 0 ? 2 : pass == 1 ? 2 | kWideStep : fuse;
             for (int i = 0; i < plan.n; ++i) {
                 const EpochSlot &q = plan.s[i];
                 const int o = q.begin + s;
@@ -1977,7 +1994,7 @@ __global__ void static_setup_kernel(StaticSetup S)
         StepEntry tmp[2];
         int64_t vf = 0, vtile = 0;
         emit_entries(im, 0, o, catchup, 2, tmp, &vf);
-        emit_entries(im, 0, o, catchup, 2 | kTileBlocks, tmp, &vtile);
+        emit_entries(im, 0, o, catchup, 2 | kWideStep, tmp, &vtile);
         ne += emit_entries(im, 0, o, catchup, step_mode(vf, vtile, S.split_below), S.ent + ne, &vt);
         S.vt[o] = vt;
     }

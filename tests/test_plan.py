@@ -101,7 +101,10 @@ def test_every_op_runs_once_in_order_and_every_phase_is_replayed_once(case, sms)
             seen[i].append(s)
     for i, o in enumerate(ops):
         assert seen[i] == list(range(len(o)))
-        phases = {s for s, (kind, _, _) in enumerate(o) if kind in (PHASE, MPHASE)}
+        # the output reads the buffer the last phase wrote its moves into:
+        # that phase is not replayed
+        phases = {s for s, (kind, _, _) in enumerate(o[:-2]) if kind in (PHASE, MPHASE)}
+        assert o[-1][0] == OUTPUT and o[-2][0] in (PHASE, MPHASE)
         assert replayed[i] == phases, "phases never replayed: %s" % sorted(phases - replayed[i])
 
 
@@ -127,7 +130,7 @@ def test_units_follow_the_lattices():
             if e["cphase"] >= 0:  # the union of both phases' lattices
                 c2, r2 = lattice(nx, ny, e["cphase"])
                 cols, rows = max(cols, c2), max(rows, r2)
-            assert e["units"] == cols * rows
+            assert e["units"] == cols * rows  # 1080p has no wide step with 152 SMs
     # pixel phases: warp tiles of 32 x 4 (or 32 x 2) units; block phases of
     # warp-judged levels, in steps with at least two tiles per warp slot:
     # warp tiles of 32 x 1 units
@@ -205,8 +208,49 @@ def test_small_blocks_take_a_thread_each():
         t = b.seeds_tuning(0, 0, 0, area, 4)
         for _, ents in b.plan([p], 152, t):
             for e in ents:
-                if e["op"] in (PHASE, CATCHUP) and e["level"] > 0:
+                if e["op"] == PHASE and e["level"] > 0:
                     assert e["group"] == (1 if maxarea(e["level"]) <= area else 32)
+                elif e["op"] == CATCHUP and e["level"] > 0:  # the 481x321 image has no wide step
+                    assert e["group"] == (1 if maxarea(e["level"]) <= area else 32)
+
+
+def test_catchup_entries_are_wide_only_in_wide_steps():
+    """A catch-up gives a lane four pixels, a small block a lane each and a
+    block a warp judges a warp each; in a wide step (block_tiles = 2: every
+    step) a lane takes four small blocks, and blocks a warp judges of at
+    most 64 pixels a lane each (the warp replays their moves)."""
+    ps = [params_of(j) for j in synth.batch_4k(2)]
+    g = grid(ps[0])
+    W, H = ps[0].width, ps[0].height
+
+    def maxarea(level):
+        nx, ny = g[level]
+        w = max((i + 1) * W // nx - i * W // nx for i in range(nx))
+        h = max((i + 1) * H // ny - i * H // ny for i in range(ny))
+        return w * h
+
+    for policy in (1, 2):
+        seen = set()
+        for sms in (1 << 12, 1 << 16):  # many SMs: block replays in catch-up entries
+            for _, ents in b.plan(ps, sms, b.seeds_tuning(0, 0, 0, 16, 4, policy)):
+                for e in ents:
+                    if e["op"] != CATCHUP:
+                        continue
+                    cols, rows = lattice(*g[e["level"]], e["phase"])
+                    pu = cols * rows
+                    area = maxarea(e["level"]) if e["level"] else 1
+                    if e["level"] == 0:
+                        want = (1, -(-pu // 4))
+                    elif area > 16:
+                        want = (32, pu) if policy == 1 or area > 64 else (1, pu)
+                    else:
+                        want = (1, pu) if policy == 1 else (1, -(-pu // 4))
+                    assert (e["group"], e["units"]) == want, (policy, e, pu, area)
+                    seen.add((e["level"], want[0], want[1] != pu))
+        if policy == 1:
+            assert {(1, 1, False), (2, 1, False), (3, 32, False), (4, 32, False), (5, 32, False)} <= seen, seen
+        else:
+            assert {(1, 1, True), (2, 1, True), (3, 1, False), (4, 32, False), (5, 32, False)} <= seen, seen
 
 
 def test_block_steps_run_in_tiles_when_they_fill_the_machine_twice():
@@ -302,4 +346,4 @@ def test_a_run_split_into_launches_runs_every_op_once(case):
                 seen[i].append(e["opidx"])
     for i, o in enumerate(ops):
         assert seen[i] == list(range(len(o)))
-        assert replayed[i] == {s for s, (kind, _, _) in enumerate(o) if kind in (PHASE, MPHASE)}
+        assert replayed[i] == {s for s, (kind, _, _) in enumerate(o[:-2]) if kind in (PHASE, MPHASE)}
