@@ -48,11 +48,17 @@ def run_stream(requests: Sequence[Tuple[float, synth.JobSpec]], images: Sequence
                pinned: bool = True) -> StreamResult:
     """Serve `requests` (arrival time in s, job) whose host images are
     `images` (uint8 HxWx3, one per request).  Arrivals are released in real
-    time on the server's clock."""
+    time on the server's clock.
+
+    Python's cyclic garbage collector is off while the stream runs (one
+    collection first, the previous state restored after): a full collection
+    stopped this loop for 35-75 ms, and every request that arrived in that
+    window waited for it (p99 at 1000 req/s: 46-85 ms with it, 8-12 ms
+    without)."""
+    import gc
     import torch  # pinned host buffers
 
     srv = binding.Server(arena_bytes, max_slots, epoch_steps, max_bins_per_channel)
-    n = len(requests)
     outs, srcs = [], []
     for (_, job), img in zip(requests, images):
         t = torch.from_numpy(np.ascontiguousarray(img))
@@ -62,6 +68,20 @@ def run_stream(requests: Sequence[Tuple[float, synth.JobSpec]], images: Sequence
         srcs.append(t)
         outs.append(o)
     params = [job_params(job) for _, job in requests]
+    gc_was_on = gc.isenabled()
+    gc.collect()
+    gc.disable()
+    try:
+        return _serve(srv, requests, params, srcs, outs)
+    finally:
+        if gc_was_on:
+            gc.enable()
+        srv.close()
+
+
+def _serve(srv, requests, params, srcs, outs) -> StreamResult:
+    """run_stream's loop: release, step, poll until every request is done."""
+    n = len(requests)
     start = srv.stats().host_ms
     arrival = np.array([start + 1e3 * a for a, _ in requests])
     id_to_req: Dict[int, int] = {}
@@ -86,7 +106,6 @@ def run_stream(requests: Sequence[Tuple[float, synth.JobSpec]], images: Sequence
                 time.sleep(min(wait, 0.002))
     srv.drain()
     st = srv.stats()
-    srv.close()
     lat = done_ms - arrival
     return StreamResult(latency_ms=lat, makespan_ms=float(np.nanmax(done_ms) - arrival[0]),
                         pixels=sum(job.pixels for _, job in requests), labels=[o.numpy() for o in outs],

@@ -45,7 +45,10 @@ def test_served_labels_equal_alone_and_oracle(torch, serve):
     reqs = mixed_requests(5, 24, rate=2000.0)
     imgs = [synth.make_image(j.image) for _, j in reqs]
     # a small arena and few slots: requests queue, overlap and reuse memory
+    import gc as pygc
+    assert pygc.isenabled()
     res = serve.run_stream(reqs, imgs, arena_bytes=8 << 20, max_slots=4, epoch_steps=4)
+    assert pygc.isenabled()  # the collector, off while the stream runs, is back on
     assert res.max_resident > 1
     assert res.epochs > 1
     want = gc.oracle_many([j for _, j in reqs], imgs)
