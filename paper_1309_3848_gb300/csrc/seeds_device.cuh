@@ -161,7 +161,7 @@ constexpr int kTileBytes = (kTileW * kTileH * 2 + kTileUY * kTileUX * 2 + kTileU
 // kCatchupLaneArea pixels take a lane each to read their decisions; the
 // warp then replays the moved ones one after another.
 constexpr int kCatchupPerLane = 4;
-constexpr int kCatchupLaneArea = 64;
+constexpr int kCatchupLaneArea = 128;
 // descents and the output: cells (pixels) of a row per thread
 constexpr int kRowChunk = 8;
 

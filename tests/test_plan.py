@@ -218,7 +218,7 @@ def test_catchup_entries_are_wide_only_in_wide_steps():
     """A catch-up gives a lane four pixels, a small block a lane each and a
     block a warp judges a warp each; in a wide step (block_tiles = 2: every
     step) a lane takes four small blocks, and blocks a warp judges of at
-    most 64 pixels a lane each (the warp replays their moves)."""
+    most 128 pixels a lane each (the warp replays their moves)."""
     ps = [params_of(j) for j in synth.batch_4k(2)]
     g = grid(ps[0])
     W, H = ps[0].width, ps[0].height
@@ -242,7 +242,7 @@ def test_catchup_entries_are_wide_only_in_wide_steps():
                     if e["level"] == 0:
                         want = (1, -(-pu // 4))
                     elif area > 16:
-                        want = (32, pu) if policy == 1 or area > 64 else (1, pu)
+                        want = (32, pu) if policy == 1 or area > 128 else (1, pu)
                     else:
                         want = (1, pu) if policy == 1 else (1, -(-pu // 4))
                     assert (e["group"], e["units"]) == want, (policy, e, pu, area)
@@ -250,7 +250,7 @@ def test_catchup_entries_are_wide_only_in_wide_steps():
         if policy == 1:
             assert {(1, 1, False), (2, 1, False), (3, 32, False), (4, 32, False), (5, 32, False)} <= seen, seen
         else:
-            assert {(1, 1, True), (2, 1, True), (3, 1, False), (4, 32, False), (5, 32, False)} <= seen, seen
+            assert {(1, 1, True), (2, 1, True), (3, 1, False), (4, 1, False), (5, 32, False)} <= seen, seen
 
 
 def test_block_steps_run_in_tiles_when_they_fill_the_machine_twice():
