@@ -742,6 +742,31 @@ __device__ __forceinline__ void replay_pixel(const DevImage &im, int buf, int p,
     move_size(im, buf, k, n, 1);
 }
 
+// A histogram pixel phase's decision: the pixel's label k, the direction of
+// the 4-neighbour whose label it takes (0 left, 1 right, 2 up, 3 down) and
+// its bin j (k < 2^16, j < 2^12: below kNoMove).  A replay then needs no
+// load of the bin, and reads the new label from that neighbour, which no op
+// between the judge and the replay relabels: the neighbour has the other
+// parity, and the buffer the next op reads holds it as the judge saw it.
+__device__ __forceinline__ uint32_t pixel_dec(int k, int dir, int j)
+{
+    return ((uint32_t)k << 14) | ((uint32_t)dir << 12) | (uint32_t)j;
+}
+// the direction of a 4-neighbour of the staged cell T whose label is n
+__device__ __forceinline__ int pixel_dir(const uint16_t *T, int n)
+{
+    return T[-1] == n ? 0 : T[1] == n ? 1 : T[-kTileW] == n ? 2 : 3;
+}
+// replay the decided move d of pixel (x, y) into buffer `buf`, the new label n
+__device__ __forceinline__ void replay_pixel_dec(const DevImage &im, int buf, int x, int y, uint32_t d, int n)
+{
+    const int k = (int)(d >> 14), j = (int)(d & 0xFFFu);
+    im.lab[0][buf][y * im.W + x] = (uint16_t)n;
+    move_counts(im, buf, k, n, j, 1);
+    move_size(im, buf, k, n, 1);
+    if (im.prior) move_xy(im, buf, k, n, x, x + 1, y, y + 1);
+}
+
 // One warp-tile of a pixel phase: units (ux, uy) with ux in a 32-wide column
 // range (one per lane) and uy in a UY-row range.  The warp first
 // replays the moves of the previous phase (cphase >= 0) for the same unit
@@ -804,16 +829,22 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
 #pragma unroll
     for (int r = 0; r < UY; ++r) jsh[r * 32 + lane] = jv[r];
 
-    // replay the previous phase's moves into buffer nb
+    // replay the previous phase's moves into buffer nb (a histogram phase's
+    // new label from the staged neighbour it names)
+    __syncwarp();
 #pragma unroll
     for (int r = 0; r < UY; ++r)
         if (cd[r] != kNoMove) {
             const int cx = 2 * ux + cpx, cy = 2 * (uy0 + r) + cpy;
-            replay_pixel(im, nb, cy * W + cx, cd[r]);
-            if constexpr (MEANS)
+            if constexpr (MEANS) {
+                replay_pixel(im, nb, cy * W + cx, cd[r]);
                 move_sums(im, nb, (int)(cd[r] >> 16), (int)(cd[r] & 0xFFFFu), cx, cy);
-            else if (im.prior)
-                move_xy(im, nb, (int)(cd[r] >> 16), (int)(cd[r] & 0xFFFFu), cx, cx + 1, cy, cy + 1);
+            } else {
+                const uint16_t *C = tsh + (2 * r + cpy - py + 2) * kTileW + (2 * lane + cpx - px + 2);
+                const int dir = (int)(cd[r] >> 12) & 3;
+                const int n = dir == 0 ? C[-1] : dir == 1 ? C[1] : dir == 2 ? C[-kTileW] : C[kTileW];
+                replay_pixel_dec(im, nb, cx, cy, cd[r], n);
+            }
         }
     __syncwarp();
 
@@ -916,7 +947,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
                                           Kp, Gk);
             uint32_t dec = kNoMove;
             if (best != kNoLabel) {
-                dec = ((uint32_t)k << 16) | (uint32_t)best;
+                dec = pixel_dec(k, pixel_dir(T, best), j);
                 im.lab[0][nb][SEEDS_IDX(im, p, (int64_t)W * H)] = (uint16_t)SEEDS_IDX(im, best, im.K);
                 move_counts(im, nb, k, best, j, 1);
                 move_size(im, nb, k, best, 1);
@@ -958,7 +989,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
                              gn * (int64_t)(G_b + Kp - Gk) * s_b * (s_k - 1);
         uint32_t dec = kNoMove;
         if (gain > 0) {
-            dec = ((uint32_t)k << 16) | (uint32_t)best;
+            dec = pixel_dec(k, pixel_dir(T, best), j);
             im.lab[0][nb][SEEDS_IDX(im, p, (int64_t)W * H)] = (uint16_t)SEEDS_IDX(im, best, im.K);
             move_counts(im, nb, k, best, j, 1);
             move_size(im, nb, k, best, 1);
@@ -1438,11 +1469,14 @@ __device__ void op_catchup(const DevImage &im, int o, int level, int phase, int 
             if (d[r] == kNoMove) continue;
             int x, y;
             unit_pos(u0 + 32 * r, phase, im.W, &x, &y);
-            replay_pixel(im, nb, y * im.W + x, d[r]);
-            if (means)
+            if (means) {
+                replay_pixel(im, nb, y * im.W + x, d[r]);
                 move_sums(im, nb, (int)(d[r] >> 16), (int)(d[r] & 0xFFFFu), x, y);
-            else if (im.prior)
-                move_xy(im, nb, (int)(d[r] >> 16), (int)(d[r] & 0xFFFFu), x, x + 1, y, y + 1);
+            } else {  // the new label from the named neighbour in the buffer op o reads
+                const int dir = (int)(d[r] >> 12) & 3;
+                const int qx = x + (dir == 0 ? -1 : dir == 1 ? 1 : 0), qy = y + (dir == 2 ? -1 : dir == 3 ? 1 : 0);
+                replay_pixel_dec(im, nb, x, y, d[r], im.lab[0][nb ^ 1][SEEDS_IDX(im, qy * im.W + qx, (int64_t)im.W * im.H)]);
+            }
         }
         return;
     }
