@@ -428,9 +428,11 @@ int seeds_server_stats(const seeds_server *s, seeds_server_stats_t *out);
  * channel; a 1920x1080 image with 1000 superpixels needs about 17 MiB),
  * and the usual codes for bad parameters.  The first call on each device
  * looks up the array's device address (with that device current) and
- * caches it, and the first call with color_space = 1 on each device also
- * copies the 1 KB LAB tables into a static device array (a synchronous copy,
- * no allocation); make those first calls before any stream capture.  All calls
+ * caches it (calls outside a stream capture look it up again), and every
+ * call with color_space = 1 made outside a capture copies the 1 KB LAB
+ * tables into a static device array on `stream` (no allocation); make the
+ * first call on each device, and the first after a device reset, before any
+ * stream capture.  All calls
  * share the one array, which keeps the previous call's contents: each call
  * re-initialises everything it reads, but calls whose work overlaps on the
  * GPU (other streams, other host threads) race on it and must be serialised

@@ -414,9 +414,11 @@ cudaError_t launch_persistent(const DevImage *d_imgs, const Schedule &sch, GridB
                               int grid, int threads, size_t smem, cudaStream_t s);
 cudaError_t persistent_max_blocks_per_sm(int threads, size_t smem, int *n);
 cudaError_t prepare_persistent(size_t smem);
-// The LAB conversion tables on the current device (once per device; a
-// synchronous copy of 1 KB the first time).
-cudaError_t upload_lab_tables();
+// The LAB conversion tables (1 KB) on the current device, copied on stream
+// `s` on every call made while `s` is not being captured, so that a device
+// reset (which clears the module's static arrays) is followed by a fresh
+// copy; a call made during a capture relies on an earlier copy on the device.
+cudaError_t upload_lab_tables(cudaStream_t s);
 cudaError_t launch_recount(const DevImage *d_imgs, int img, int level, int64_t npix, cudaStream_t s);
 
 }  // namespace seeds

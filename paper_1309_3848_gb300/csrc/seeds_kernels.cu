@@ -1909,30 +1909,37 @@ cudaError_t persistent_max_blocks_per_sm(int threads, size_t smem, int *n)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, seeds_persistent, threads, smem);
 }
 
-cudaError_t upload_lab_tables()
+cudaError_t upload_lab_tables(cudaStream_t s)
 {
     static std::mutex mu;
     static bool done[64] = {};
+    static bool built = false;
+    static int32_t lin[256], mq[9];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
-    if (done[dev]) return cudaSuccess;
-    // sRGB decoding curve (IEC 61966-2-1) and the sRGB -> XYZ (D65) matrix
-    static const double m[3][3] = {{0.4124, 0.3576, 0.1805}, {0.2126, 0.7152, 0.0722}, {0.0193, 0.1192, 0.9505}};
-    int32_t lin[256], mq[9];
-    for (int v = 0; v < 256; ++v) {
-        const double c = v / 255.0;
-        const double l = c <= 0.04045 ? c / 12.92 : std::pow((c + 0.055) / 1.055, 2.4);
-        lin[v] = (int32_t)std::llround(l * 16777216.0);
+    if (!built) {
+        // sRGB decoding curve (IEC 61966-2-1) and the sRGB -> XYZ (D65) matrix
+        static const double m[3][3] = {{0.4124, 0.3576, 0.1805}, {0.2126, 0.7152, 0.0722}, {0.0193, 0.1192, 0.9505}};
+        for (int v = 0; v < 256; ++v) {
+            const double c = v / 255.0;
+            const double l = c <= 0.04045 ? c / 12.92 : std::pow((c + 0.055) / 1.055, 2.4);
+            lin[v] = (int32_t)std::llround(l * 16777216.0);
+        }
+        for (int i = 0; i < 3; ++i) {
+            const double white = m[i][0] + m[i][1] + m[i][2];
+            for (int j = 0; j < 3; ++j) mq[3 * i + j] = (int32_t)std::llround(m[i][j] / white * 1048576.0);
+        }
+        built = true;
     }
-    for (int i = 0; i < 3; ++i) {
-        const double white = m[i][0] + m[i][1] + m[i][2];
-        for (int j = 0; j < 3; ++j) mq[3 * i + j] = (int32_t)std::llround(m[i][j] / white * 1048576.0);
-    }
-    e = cudaMemcpyToSymbol(g_lab_lin, lin, sizeof(lin));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_lab_m, mq, sizeof(mq));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusNone) return done[dev] ? cudaSuccess : cudaErrorStreamCaptureUnsupported;
+    e = cudaMemcpyToSymbolAsync(g_lab_lin, lin, sizeof(lin), 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_lab_m, mq, sizeof(mq), 0, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
@@ -2069,7 +2076,7 @@ extern "C" int seeds_run_static(const seeds_params *p, const uint8_t *d_rgb, int
     const size_t o_state = off;
     off += h.bytes;
     if (off > (size_t)SEEDS_STATIC_SCRATCH_BYTES) return SEEDS_ERR_STATIC_SIZE;
-    if (p->color_space == 1 && upload_lab_tables() != cudaSuccess) return SEEDS_ERR_CUDA;
+    if (p->color_space == 1 && upload_lab_tables((cudaStream_t)stream) != cudaSuccess) return SEEDS_ERR_CUDA;
 
     // ---- the scratch's device address on the current device
     int dev = 0;

@@ -309,7 +309,8 @@ int create_ctx(const seeds_params *p, int32_t n, seeds_ctx **out)
     if (!rc) rc = from_cuda(cudaEventCreate(&c->ev1));
     for (int i = 0; i < n && !rc; ++i)
         if (c->img[i].p.color_space == 1) {
-            rc = from_cuda(upload_lab_tables());
+            rc = from_cuda(upload_lab_tables(0));
+            if (!rc) rc = from_cuda(cudaStreamSynchronize(0));
             break;
         }
     if (!rc) {

@@ -220,7 +220,8 @@ int seeds_server_create(const seeds_server_config *cfg, seeds_server **out)
     if (!rc) rc = from_cuda(cudaMalloc((void **)&s->d_ent, sizeof(StepEntry) * max_ent));
     if (!rc) rc = from_cuda(cudaMalloc((void **)&s->d_first, sizeof(int32_t) * (cfg->epoch_steps + 1)));
     if (!rc) rc = from_cuda(cudaMalloc((void **)&s->d_vt, sizeof(int64_t) * cfg->epoch_steps));
-    if (!rc) rc = from_cuda(upload_lab_tables());
+    if (!rc) rc = from_cuda(upload_lab_tables(0));
+    if (!rc) rc = from_cuda(cudaStreamSynchronize(0));
     if (!rc) {
         // the largest CTA whose warps' shared scratch fits
         for (int threads : {1024, 512, 256, 128}) {
