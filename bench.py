@@ -535,7 +535,7 @@ def serve_sample(rates, seconds, per_size=3, arena_gib=8, epoch_steps=SERVE_EPOC
         if not reqs:
             continue
         res = serve.run_stream(reqs, serve.stream_images(reqs, pool), arena_bytes=arena_gib << 30, max_slots=128,
-                               epoch_steps=epoch_steps, max_bins_per_channel=5)
+                               epoch_steps=epoch_steps, max_bins_per_channel=5, keep_labels=False)
         out.append({"rate_req_s": rate, "requests": len(reqs), "mpix_s": res.mpix_per_s,
                     "p50_ms": res.percentile(50), "p99_ms": res.percentile(99), "max_resident": res.max_resident,
                     "epochs": res.epochs, "epoch_steps": epoch_steps, "arrival_window_s": seconds,

@@ -72,6 +72,52 @@ def test_arena_bounds_residency(torch, serve):
         assert np.array_equal(lab, res.labels[0])
 
 
+def test_stats_count_the_arena_a_resident_request_holds(torch, serve):
+    """While a request is resident its footprint (state, image and label
+    staging) is out of the arena's free bytes; after it completes and is
+    polled the whole arena is free again."""
+    from paper_1309_3848_gb300 import binding
+    arena = 64 << 20
+    job = synth.JobSpec(synth.ImageSpec(640, 480, seed=3, cells=40, sigma=8.0), 300, 5, 3, 1)
+    img = synth.make_image(job.image)
+    out = np.zeros((480, 640), np.int32)
+    srv = binding.Server(arena, 4, 2, 5)
+    try:
+        st = srv.stats()
+        assert st.arena_free_bytes == arena and st.resident == 0
+        srv.submit(serve.job_params(job), img, out)
+        assert srv.stats().queued == 1
+        assert srv.step() == 1  # admitted, first epoch launched
+        st = srv.stats()
+        # the image and label staging (7 B/px) plus the state, which the
+        # context footprint gives to within its alignment padding
+        need = binding.footprint([serve.job_params(job)]) + 640 * 480 * 7
+        assert st.resident == 1 and st.queued == 0
+        assert 640 * 480 * 7 < arena - st.arena_free_bytes and abs(arena - st.arena_free_bytes - need) <= 4096
+        done = []
+        while not done:
+            srv.step()
+            done += srv.poll()
+        srv.drain()
+        st = srv.stats()
+        assert st.resident == 0 and st.arena_free_bytes == arena
+    finally:
+        srv.close()
+    assert gc.first_mismatch(out, gc.oracle_run(job, img)) is None
+
+
+def test_stream_without_kept_labels_reuses_label_buffers(torch, serve):
+    """keep_labels=False (the bench's serving sample): every request still
+    completes, label buffers of completed requests go to later requests of
+    the same size, and the result carries no labels."""
+    reqs = mixed_requests(7, 16, rate=4000.0)
+    imgs = [synth.make_image(j.image) for _, j in reqs]
+    res = serve.run_stream(reqs, imgs, arena_bytes=16 << 20, max_slots=4, epoch_steps=8, keep_labels=False)
+    assert res.labels == []
+    assert np.all(np.isfinite(res.latency_ms)) and np.all(res.latency_ms >= 0)
+    assert res.pixels == sum(j.pixels for _, j in reqs)
+
+
 def test_request_too_large_for_the_arena_is_refused(torch, serve):
     from paper_1309_3848_gb300 import binding
     srv = binding.Server(1 << 20, 2, 4, 5)
