@@ -703,11 +703,16 @@ def run_gpu(args):
         if len(jobs) > 1:  # the same images, one context and one launch per image
             line["plain"] = plain_per_image(torch, binding, params, d, outs, flush, px)
             line["batched_over_plain"] = value / line["plain"]["mpix_s"]
+        # the batch's labels to the host, then its context and buffers freed:
+        # the samples below time other runs, each with memory of its own
+        gpu_labels = [o.cpu().numpy() for o in outs]
+        ctx.close()
+        del step, host_step, ctx, d, outs, h_imgs, h_outs
+        torch.cuda.empty_cache()
         if args.workload != "batch64_mixed":
             line["batch64_mixed"] = batched_vs_plain(torch, binding, flush)
         line["served"] = serve_sample(rates=SERVE_RATES, seconds=2.0)
         line["next_rows"] = next_rows(torch, binding, flush, jobs, imgs, value)
-        gpu_labels = [o.cpu().numpy() for o in outs]
         v, cores, sample = cpu_sample(jobs, imgs)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu(),
                                 "sample": sample}
