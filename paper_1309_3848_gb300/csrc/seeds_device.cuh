@@ -161,6 +161,12 @@ constexpr int kTileBytes = (kTileW * kTileH * 2 + kTileUY * kTileUX * 2 + kTileU
 // kCatchupLaneArea pixels take a lane each to read their decisions; the
 // warp then replays the moved ones one after another.
 constexpr int kCatchupPerLane = 4;
+// A warp of a small-block phase takes 32 units of a lattice row, or, on a
+// level whose superpixels span at least kSmallTileSpan units per side, a
+// kSmallTileX x kSmallTileY block of units: such warps often lie inside
+// one superpixel and finish after their ring tests, where a row of 32 units
+// always crosses a boundary and runs the judge for its few boundary lanes.
+constexpr int kSmallTileX = 8, kSmallTileY = 4, kSmallTileSpan = 16;
 constexpr int kCatchupLaneArea = 128;
 // descents and the output: cells (pixels) of a row per thread
 constexpr int kRowChunk = 8;
@@ -226,6 +232,15 @@ __host__ __device__ inline int level_group(const DevImage &im, int level)
     if (level == 0) return 1;
     const bool thread = im.maxarea[level] <= im.small_area && (int64_t)im.W * im.H * kSmallMax < (1ll << 31);
     return thread ? 1 : 32;
+}
+
+// whether the warps of a small-block phase take 2D blocks of units: the
+// superpixels of a level span 2^(L - level) lattice units per side (the
+// grid of Sec. 5.1 halves the blocks at each level, the parity lattice takes
+// every other block)
+__host__ __device__ inline bool small_tiles_2d(const DevImage &im, int level)
+{
+    return (1 << (im.L - level)) >= kSmallTileSpan;
 }
 
 // threads per unit of a catch-up entry, and units per lane where that is 1
@@ -312,7 +327,7 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
             }
         }
     }
-    int64_t units = 0;
+    int64_t units = 0, threads = -1;  // threads: the entry's count when it is not units * group
     int group = 1;
     int kind = op.kind;
     switch (op.kind) {
@@ -334,6 +349,8 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
             lattice(im.nbx[op.level], im.nby[op.level], op.phase, cphase, &cols, &rows);
             units = (int64_t)cols * rows;
             group = level_group(im, op.level);
+            if (group == 1 && small_tiles_2d(im, op.level))
+                threads = (int64_t)((cols + kSmallTileX - 1) / kSmallTileX) * ((rows + kSmallTileY - 1) / kSmallTileY) * 32;
         }
         break;
     case OP_MINIT:  // a thread per pixel
@@ -346,7 +363,7 @@ __host__ __device__ inline int emit_entries(const DevImage &im, int img, int o, 
         units = (int64_t)im.H * ((im.W + kRowChunk - 1) / kRowChunk);
         break;
     }
-    const int64_t count = (units * group + 31) / 32 * 32;
+    const int64_t count = threads >= 0 ? threads : (units * group + 31) / 32 * 32;
     if (count > 0) {
         StepEntry e{img, kind, op.level, op.phase, o, (int32_t)units, *vt, group, cphase};
         out[n++] = e;

@@ -1155,17 +1155,30 @@ __device__ uint32_t judge_small_block(const DevImage &im, int b, int nb, int lev
     return judge_small_block_c<SM>(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1);
 }
 
-// Unit (ux,uy) of the union lattice: replay the previous phase's move of that
-// unit (cphase >= 0), then judge this phase's unit.
-__device__ void op_block_phase_thread(const DevImage &im, int o, int level, int phase, int cphase, int units, int u)
+// Thread t of the entry takes unit (ux,uy) of the union lattice (the t-th
+// unit, or lane t%32 of the t/32-th block of kSmallTileX x kSmallTileY
+// units, small_tiles_2d): replay the previous phase's move of that unit
+// (cphase >= 0), then judge this phase's unit.
+__device__ void op_block_phase_thread(const DevImage &im, int o, int level, int phase, int cphase, int units, int t)
 {
-    if (u >= units) return;
     const int b = o & 1, nb = b ^ 1;
     const int nx = im.nbx[level], ny = im.nby[level];
     int mcols, mrows, ncols, nrows;
     lattice(nx, ny, phase, cphase, &mcols, &mrows);
     lattice(nx, ny, phase, -1, &ncols, &nrows);
-    const int uy = u / mcols, ux = u - uy * mcols;
+    int ux, uy;
+    if (small_tiles_2d(im, level)) {
+        const int w = t >> 5, l = t & 31;
+        const int tiles_x = (mcols + kSmallTileX - 1) / kSmallTileX;
+        const int ty = w / tiles_x, tx = w - ty * tiles_x;
+        ux = tx * kSmallTileX + l % kSmallTileX;
+        uy = ty * kSmallTileY + l / kSmallTileX;
+        if (ux >= mcols || uy >= mrows) return;
+    } else {
+        if (t >= units) return;
+        uy = t / mcols;
+        ux = t - uy * mcols;
+    }
     if (cphase >= 0) {
         int ccols, crows;
         lattice(nx, ny, cphase, -1, &ccols, &crows);

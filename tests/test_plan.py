@@ -289,6 +289,36 @@ def test_block_steps_run_in_tiles_when_they_fill_the_machine_twice():
     assert seen == {(False, False), (True, False), (True, True)}
 
 
+def test_small_block_warps_take_2d_blocks_where_superpixels_are_wide():
+    """A small-block phase gives each warp 32 units of a row, or, on a level
+    whose superpixels span at least 16 lattice units per side (2^(L - level):
+    level 1 of L = 5), a block of 8 x 4 units; its entry then counts
+    ceil(cols/8) * ceil(rows/4) warps."""
+    for jobs, L2d in ((synth.batch_4k(2), {1}), (synth.plain_1080(), set())):
+        ps = [params_of(j) for j in jobs]
+        g = grid(ps[0])
+        L = ps[0].block_levels
+        seen = set()
+        for sms in (1, 152):
+            for threads, ents in b.plan(ps, sms):
+                ends = [e["vt_begin"] for e in ents[1:]] + [threads]
+                for e, end in zip(ents, ends):
+                    if e["op"] != PHASE or e["level"] == 0 or e["group"] != 1:
+                        continue
+                    cols, rows = lattice(*g[e["level"]], e["phase"])
+                    if e["cphase"] >= 0:
+                        c2, r2 = lattice(*g[e["level"]], e["cphase"])
+                        cols, rows = max(cols, c2), max(rows, r2)
+                    assert e["units"] == cols * rows
+                    if (1 << (L - e["level"])) >= 16:
+                        want = -(-cols // 8) * -(-rows // 4) * 32
+                    else:
+                        want = -(-cols * rows // 32) * 32
+                    assert end - e["vt_begin"] == want, (e, want)
+                    seen.add(e["level"] if (1 << (L - e["level"])) >= 16 else -e["level"])
+        assert {l for l in seen if l > 0} == L2d
+
+
 def test_a_batch_shares_every_step():
     ps = CASES["batch"]
     steps = b.plan(ps, 152)
