@@ -35,11 +35,14 @@ STEP_CASES = [
     synth.JobSpec(synth.ImageSpec(64, 48, seed=5, cells=7, sigma=12.0), 12, 4, 2, 2),
     synth.JobSpec(synth.ImageSpec(97, 61, seed=6, cells=9, sigma=10.0, gradient=True), 30, 8, 3, 2, 3, (2, 1)),
     synth.JobSpec(synth.ImageSpec(50, 37, seed=7, cells=5, sigma=15.0), 20, 3, 0, 3, 0, (1, 1)),
+    # five block levels: level 1's superpixels span 16 lattice units per
+    # side, so its small-block warps take 8 x 4 blocks of units
+    synth.JobSpec(synth.ImageSpec(481, 321, seed=8, cells=12, sigma=8.0, gradient=True), 60, 5, 5, 2),
 ]
 
 
 @pytest.mark.parametrize("tiles", [1, 2], ids=["per-unit", "tiled"])
-@pytest.mark.parametrize("job", STEP_CASES, ids=["481x321", "64x48", "97x61_B8", "50x37_L0"])
+@pytest.mark.parametrize("job", STEP_CASES, ids=["481x321", "64x48", "97x61_B8", "50x37_L0", "481x321_L5"])
 def test_state_matches_after_every_op(torch, binding, job, tiles):
     W, H = job.image.width, job.image.height
     img = synth.make_image(job.image)
