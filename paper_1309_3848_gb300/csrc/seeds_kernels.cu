@@ -808,26 +808,34 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         cd[r] = (ux < ccols && uy < crows) ? im.dec[nb][SEEDS_IDX(im, uy * ccols + ux, im.units_cap)] : kNoMove;
     }
 
-    // stage the labels of buffer b and the units' bins.  Every load is
-    // issued before the first shared-memory store: a warp issues in order,
-    // and a store waits for its load, so interleaving them would serialise
-    // one L2 round trip per store.  Lane l loads columns l, l+32 (packed in
-    // one register) and, for l < 4, l+64 of each row.
+    // stage the labels of buffer b (and, in a means phase, the units' bins).
+    // Every load is issued before the first shared-memory store: a warp
+    // issues in order, and a store waits for its load, so interleaving them
+    // would serialise one L2 round trip per store.  Lane l loads columns l,
+    // l+32 (packed in one register) and, for l < 4, l+64 of each row.  A
+    // histogram phase loads a unit's bin only when it judges the unit: the
+    // boundary units are a tenth of the tile at 4K, and loading every
+    // unit's bin read half of the bin map each phase, most of it unused
+    // (4K batch: pixel phase 697 -> 651 us per step).
     constexpr int TH = tile_h(UY);
     TileRegs<TH> stage;
     tile_load<TH>(stage, im.lab[0][b], W, H, 2 * tx * kTileUX + px - 2, 2 * uy0 + py - 2, lane);
     uint16_t jv[UY];
+    if constexpr (MEANS) {
 #pragma unroll
-    for (int r = 0; r < UY; ++r) {
-        const int uy = uy0 + r;
-        jv[r] = (ux < ncols && uy < nrows) ? bin_at(im, (2 * uy + py) * W + 2 * ux + px) : 0;
+        for (int r = 0; r < UY; ++r) {
+            const int uy = uy0 + r;
+            jv[r] = (ux < ncols && uy < nrows) ? bin_at(im, (2 * uy + py) * W + 2 * ux + px) : 0;
+        }
     }
     __syncwarp();  // keeps the loads above the stores
     uint16_t *jsh = tsh + kTileW * TH;
     uint8_t *lst = (uint8_t *)(jsh + UY * kTileUX);
     tile_store<TH>(stage, tsh, lane);
+    if constexpr (MEANS) {
 #pragma unroll
-    for (int r = 0; r < UY; ++r) jsh[r * 32 + lane] = jv[r];
+        for (int r = 0; r < UY; ++r) jsh[r * 32 + lane] = jv[r];
+    }
 
     // replay the previous phase's moves into buffer nb (a histogram phase's
     // new label from the staged neighbour it names)
@@ -888,7 +896,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         int cand[4];
         // pass 1 found that it may leave
         const int nc = sorted_candidates(T[-1], T[1], T[-kTileW], T[kTileW], k, cand);
-        const int j = jsh[r * 32 + l];
+        const int j = MEANS ? (int)jsh[r * 32 + l] : bin_at(im, p);
         if constexpr (MEANS) {
             im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = means_pixel(im, b, nb, x, y, k, j, cand);
             continue;
