@@ -70,7 +70,8 @@ struct DevImage {
     uint16_t *lab[kMaxLevels + 1][2];   // [0]: pixel labels, [l]: level-l block grid; 2 buffers
     int32_t *hist[2];                   // K x nbins counts, 2 buffers
     int32_t *size[2];                   // |A_k|, 2 buffers
-    uint32_t *dec[2];                   // per unit of a phase: a move (block: k << 16 | n; histogram pixel phase: pixel_dec) or kNoMove
+    uint32_t *dec[2];                   // per unit of a phase: a move (block: k << 16 | n; histogram pixel phase:
+                                        // pixel_dec) or kNoMove; only moves are written, replays reset them
     unsigned long long *msum[2];        // K x 5: sums of the 3 colour codes, of x, of y (means iterations;
                                         // x and y through every move with the compactness prior)
     uint8_t *edges;                     // per pixel, edge snapping: bit 0 across to the right, bit 1 down

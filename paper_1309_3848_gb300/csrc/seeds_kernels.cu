@@ -502,6 +502,11 @@ __device__ void op_init(const DevImage &im, int k, int lane, int32_t *wsh)
         if (im.prior && q == 4) v = range_sum(y0, y1) * (unsigned long long)(x1 - x0);
         im.msum[lane / 5][(int64_t)k * 5 + q] = v;
     }
+    {  // every decision "no move": the judges write moves only, and replays reset what they read
+        const int64_t chunk = (im.units_cap + im.K - 1) / im.K;
+        const int64_t e0 = (int64_t)k * chunk, e1 = min(e0 + chunk, (int64_t)im.units_cap);
+        for (int64_t e = e0 + lane; e < e1; e += 32) im.dec[0][e] = im.dec[1][e] = kNoMove;
+    }
     if (im.L >= 1 && lane < 4) {
         const int L = im.L;
         const int bx = 2 * sx + (lane & 1), by = 2 * sy + (lane >> 1);
@@ -853,6 +858,7 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
                 const int n = dir == 0 ? C[-1] : dir == 1 ? C[1] : dir == 2 ? C[-kTileW] : C[kTileW];
                 replay_pixel_dec(im, nb, cx, cy, cd[r], n);
             }
+            im.dec[nb][SEEDS_IDX(im, (uy0 + r) * ccols + ux, im.units_cap)] = kNoMove;
         }
     __syncwarp();
 
@@ -865,8 +871,6 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
             const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * lane + 2);
             if (may_leave([&](int dx, int dy) { return (int)T[dy * kTileW + dx]; }, (int)T[0]))
                 mine |= 1u << r;
-            else
-                im.dec[b][SEEDS_IDX(im, uy * ncols + ux, im.units_cap)] = kNoMove;
         }
     }
     int nbd = 0;
@@ -889,16 +893,14 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
         const int x = 2 * uxe + px, y = 2 * uy + py, p = y * W + x;
         const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * l + 2);  // the unit's cell in the tile
         const int k = T[0];
-        if (im.edges && edge_frozen(im, p, k, T[-1], T[1], T[-kTileW], T[kTileW])) {
-            im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = kNoMove;
-            continue;
-        }
+        if (im.edges && edge_frozen(im, p, k, T[-1], T[1], T[-kTileW], T[kTileW])) continue;
         int cand[4];
         // pass 1 found that it may leave
         const int nc = sorted_candidates(T[-1], T[1], T[-kTileW], T[kTileW], k, cand);
         const int j = MEANS ? (int)jsh[r * 32 + l] : bin_at(im, p);
         if constexpr (MEANS) {
-            im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = means_pixel(im, b, nb, x, y, k, j, cand);
+            const uint32_t dm = means_pixel(im, b, nb, x, y, k, j, cand);
+            if (dm != kNoMove) im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = dm;
             continue;
         }
         // Prop. 2 sums G_x = sum_{i in K_p} b_{N_i}(x) as a weighted count
@@ -960,8 +962,8 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
                 move_counts(im, nb, k, best, j, 1);
                 move_size(im, nb, k, best, 1);
                 move_xy(im, nb, k, best, x, x + 1, y, y + 1);
+                im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = dec;
             }
-            im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = dec;
             continue;
         }
         // the histogram and size lookups of every candidate and of k, all
@@ -1001,8 +1003,8 @@ __device__ void op_pixel_tile(const DevImage &im, int o, int phase, int cphase, 
             im.lab[0][nb][SEEDS_IDX(im, p, (int64_t)W * H)] = (uint16_t)SEEDS_IDX(im, best, im.K);
             move_counts(im, nb, k, best, j, 1);
             move_size(im, nb, k, best, 1);
+            im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = dec;
         }
-        im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = dec;
     }
     __syncwarp();
 }
@@ -1192,7 +1194,10 @@ __device__ void op_block_phase_thread(const DevImage &im, int o, int level, int 
         lattice(nx, ny, cphase, -1, &ccols, &crows);
         if (ux < ccols && uy < crows) {
             const uint32_t d = im.dec[nb][SEEDS_IDX(im, uy * ccols + ux, im.units_cap)];
-            if (d != kNoMove) replay_small_block(im, nb, level, 2 * ux + (cphase & 1), 2 * uy + (cphase >> 1), d);
+            if (d != kNoMove) {
+                replay_small_block(im, nb, level, 2 * ux + (cphase & 1), 2 * uy + (cphase >> 1), d);
+                im.dec[nb][SEEDS_IDX(im, uy * ccols + ux, im.units_cap)] = kNoMove;
+            }
         }
     }
     if (ux >= ncols || uy >= nrows) return;
@@ -1201,7 +1206,7 @@ __device__ void op_block_phase_thread(const DevImage &im, int o, int level, int 
     const uint32_t dec = ma <= 4   ? judge_small_block<4>(im, b, nb, level, bx, by)
                          : ma <= 9 ? judge_small_block<9>(im, b, nb, level, bx, by)
                                    : judge_small_block<kSmallMax>(im, b, nb, level, bx, by);
-    im.dec[b][SEEDS_IDX(im, uy * ncols + ux, im.units_cap)] = dec;
+    if (dec != kNoMove) im.dec[b][SEEDS_IDX(im, uy * ncols + ux, im.units_cap)] = dec;
 }
 
 // ---------------------------------------------------------------------------
@@ -1284,9 +1289,11 @@ __device__ void op_block_phase_warp(const DevImage &im, int o, int level, int ph
         lattice(nx, ny, cphase, -1, &ccols, &crows);
         if (ux < ccols && uy < crows) {
             const uint32_t d = im.dec[nb][SEEDS_IDX(im, uy * ccols + ux, im.units_cap)];
-            if (d != kNoMove)
+            if (d != kNoMove) {
                 replay_large_block(im, nb, level, 2 * ux + (cphase & 1), 2 * uy + (cphase >> 1), d, lane, wsh,
                                    max_nbins);
+                if (lane == 0) im.dec[nb][SEEDS_IDX(im, uy * ccols + ux, im.units_cap)] = kNoMove;
+            }
         }
     }
     if (ux >= ncols || uy >= nrows) return;
@@ -1302,7 +1309,7 @@ __device__ void op_block_phase_warp(const DevImage &im, int o, int level, int ph
     const uint32_t d = nc == 0 ? kNoMove
                                : judge_large_block_c(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1, lane, wsh,
                                                      max_nbins);
-    if (lane == 0) im.dec[b][SEEDS_IDX(im, uu, im.units_cap)] = d;
+    if (lane == 0 && d != kNoMove) im.dec[b][SEEDS_IDX(im, uu, im.units_cap)] = d;
 }
 
 // Judge large block (bx,by) of label k that may leave, with candidates cand
@@ -1410,6 +1417,7 @@ __device__ __forceinline__ void op_block_tile(const DevImage &im, int o, int lev
             replay_large_block(im, nb, level, 2 * (tx * kTileUX + l) + cpx, 2 * (uy0 + r) + cpy, d, lane, wsh,
                                max_nbins);
         }
+        if (cd[r] != kNoMove) im.dec[nb][SEEDS_IDX(im, (uy0 + r) * ccols + ux, im.units_cap)] = kNoMove;
     }
     __syncwarp();
 
@@ -1422,8 +1430,6 @@ __device__ __forceinline__ void op_block_tile(const DevImage &im, int o, int lev
             const uint16_t *T = tsh + (2 * r + 2) * kTileW + (2 * lane + 2);
             if (may_leave([&](int dx, int dy) { return (int)T[dy * kTileW + dx]; }, (int)T[0]))
                 mine |= 1u << r;
-            else
-                im.dec[b][SEEDS_IDX(im, uy * ncols + ux, im.units_cap)] = kNoMove;
         }
     }
 
@@ -1444,7 +1450,7 @@ __device__ __forceinline__ void op_block_tile(const DevImage &im, int o, int lev
             sorted_candidates(T[-1], T[1], T[-kTileW], T[kTileW], k, cand);
             const uint32_t d =
                 judge_large_block_c(im, b, nb, level, bx, by, k, cand, x0, x1, y0, y1, lane, wsh, max_nbins);
-            if (lane == 0) im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = d;
+            if (lane == 0 && d != kNoMove) im.dec[b][SEEDS_IDX(im, uy * ncols + uxe, im.units_cap)] = d;
         }
     }
     __syncwarp();
@@ -1473,6 +1479,7 @@ __device__ void op_catchup(const DevImage &im, int o, int level, int phase, int 
         int bx, by;
         unit_pos(u, phase, nx, &bx, &by);
         replay_large_block(im, nb, level, bx, by, d, lane, wsh, max_nbins);
+        if (lane == 0) im.dec[nb][SEEDS_IDX(im, u, im.units_cap)] = kNoMove;
         return;
     }
     const int per = lanes < units ? kCatchupPerLane : 1;
@@ -1482,6 +1489,7 @@ __device__ void op_catchup(const DevImage &im, int o, int level, int phase, int 
     for (int r = 0; r < kCatchupPerLane; ++r) {
         const int u = u0 + 32 * r;
         d[r] = r < per && u < units ? im.dec[nb][SEEDS_IDX(im, u, im.units_cap)] : kNoMove;
+        if (d[r] != kNoMove) im.dec[nb][SEEDS_IDX(im, u, im.units_cap)] = kNoMove;
     }
     if (level == 0) {  // pixels
         const bool means = op_at(im.L, im.iters, im.means_iters, o - 1).kind == OP_MPHASE;
