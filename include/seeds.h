@@ -314,6 +314,23 @@ int seeds_anytime_steps(seeds_ctx *c, int32_t *steps);
 int seeds_run_host(seeds_ctx *c, const uint8_t *const *h_rgb, const int64_t *h_row_strides, int32_t *const *h_labels,
                    void *stream);
 
+/* seeds_run_host over a stream of n_batches batches of the context's shape
+ * (Sec. 5.1-5.3 for each), with the copies of one batch overlapping the
+ * launch of another: batch b's host->device copies run while batch b-1 is
+ * segmented, and its labels go back while batch b+1 is.  Two sets of
+ * staging buffers alternate; the copies run on two streams of the
+ * context's own, and `stream` waits for all of them before the call's work
+ * counts as done, so stream order holds for the whole sequence.
+ * h_rgb, h_row_strides, h_labels: n_batches * n pointers (n the batch
+ * size), batch-major (entry b*n + i is image i of batch b), as in
+ * seeds_run_host; the same host buffer may serve several batches.
+ * Asynchronous on `stream`; host buffers must stay valid until it completes
+ * (pinned buffers make the copies asynchronous).  Errors:
+ * SEEDS_ERR_INVALID for n_batches < 1, a null pointer, a row stride below
+ * 3*W, or `stream` under capture into a CUDA graph. */
+int seeds_run_host_stream(seeds_ctx *c, int32_t n_batches, const uint8_t *const *h_rgb,
+                          const int64_t *h_row_strides, int32_t *const *h_labels, void *stream);
+
 /* Launch knobs; see seeds_tuning.  They change no label, so the paper has
  * no counterpart. */
 int seeds_set_tuning(seeds_ctx *c, const seeds_tuning *t);

@@ -38,7 +38,7 @@ EXPORTS = [
     "seeds_create",
     "seeds_iterate", "seeds_labels", "seeds_num_superpixels", "seeds_status", "seeds_destroy",
     "seeds_batch_create", "seeds_batch_size", "seeds_batch_num_superpixels", "seeds_batch_iterate",
-    "seeds_batch_labels", "seeds_batch_run", "seeds_batch_run_anytime", "seeds_anytime_steps", "seeds_run_host", "seeds_set_tuning", "seeds_get_tuning",
+    "seeds_batch_labels", "seeds_batch_run", "seeds_batch_run_anytime", "seeds_anytime_steps", "seeds_run_host", "seeds_run_host_stream", "seeds_set_tuning", "seeds_get_tuning",
     "seeds_tune_search",
     "seeds_debug_num_ops", "seeds_debug_op_info", "seeds_debug_run_ops", "seeds_debug_read_state",
     "seeds_debug_set_labels", "seeds_debug_inject_error", "seeds_debug_barrier_test", "seeds_debug_launch_count", "seeds_profile_enable",
@@ -117,6 +117,7 @@ def _load():
         "seeds_batch_run_anytime": [vp, P(vp), P(i64), P(vp), i32, i64, vp],
         "seeds_anytime_steps": [vp, P(i32)],
         "seeds_run_host": [vp, P(vp), P(i64), P(vp), vp],
+        "seeds_run_host_stream": [vp, i32, P(vp), P(i64), P(vp), vp],
         "seeds_set_tuning": [vp, P(seeds_tuning)],
         "seeds_get_tuning": [vp, P(seeds_tuning)],
         "seeds_tune_search": [P(seeds_tuning), TUNE_COST_FN, vp, P(seeds_tuning)],
@@ -401,8 +402,8 @@ class SeedsContext:
         check(lib.seeds_anytime_steps(self._h, ctypes.byref(n)), "seeds_anytime_steps")
         return n.value
 
-    def run_host(self, images, outs, stream=None):
-        """images: host uint8 (H, W, 3) tensors; outs: host int32 (H, W)."""
+    @staticmethod
+    def _host_io(images, outs):
         ptrs, strides = [], []
         for t in images:
             assert not t.is_cuda and t.stride(2) == 1 and t.stride(1) == 3
@@ -410,8 +411,28 @@ class SeedsContext:
             strides.append(t.stride(0))
         for t in outs:
             assert not t.is_cuda and t.is_contiguous() and t.element_size() == 4
-        check(lib.seeds_run_host(self._h, _ptrs(ptrs), _ptrs(strides, ctypes.c_int64),
-                                 _ptrs([t.data_ptr() for t in outs]), _stream_handle(stream)), "seeds_run_host")
+        return ptrs, strides, [t.data_ptr() for t in outs]
+
+    def run_host(self, images, outs, stream=None):
+        """images: host uint8 (H, W, 3) tensors; outs: host int32 (H, W)."""
+        ptrs, strides, optrs = self._host_io(images, outs)
+        check(lib.seeds_run_host(self._h, _ptrs(ptrs), _ptrs(strides, ctypes.c_int64), _ptrs(optrs),
+                                 _stream_handle(stream)), "seeds_run_host")
+
+    def run_host_stream(self, batches, outs, stream=None):
+        """batches[b]: the batch's host uint8 (H, W, 3) tensors; outs[b]: its
+        host int32 (H, W) label tensors.  One call for the whole sequence,
+        copies of one batch overlapping the launch of another."""
+        assert len(batches) == len(outs)
+        ptrs, strides, optrs = [], [], []
+        for imgs, labs in zip(batches, outs):
+            assert len(imgs) == len(labs) == self.n
+            p, st, o = self._host_io(imgs, labs)
+            ptrs += p
+            strides += st
+            optrs += o
+        check(lib.seeds_run_host_stream(self._h, len(batches), _ptrs(ptrs), _ptrs(strides, ctypes.c_int64),
+                                        _ptrs(optrs), _stream_handle(stream)), "seeds_run_host_stream")
 
     def status(self) -> int:
         return lib.seeds_status(self._h)

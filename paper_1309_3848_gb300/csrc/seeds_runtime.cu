@@ -60,9 +60,12 @@ struct seeds_ctx {
     int64_t launches = 0;
     unsigned long long dbg_timeout_ns = 0;  // failure tests: barrier limit, withheld arrival
     int32_t dbg_withhold = 0;
-    unsigned char *stage = nullptr;
-    size_t stage_bytes = 0;
+    unsigned char *stage[2] = {};  // host-run staging: slot 0 (seeds_run_host), slot 1 (streams)
+    size_t stage_bytes = 0;        // per slot
     std::vector<size_t> stage_rgb, stage_out;
+    // seeds_run_host_stream: copy streams and the events that order them
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_entry = nullptr, ev_in[2] = {}, ev_k[2] = {}, ev_out[2] = {};
 };
 
 namespace {
@@ -268,7 +271,16 @@ void destroy_ctx(seeds_ctx *c)
     cudaFree(c->d_bar);
     cudaFree(c->d_err);
     cudaFree(c->d_steps);
-    cudaFree(c->stage);
+    cudaFree(c->stage[0]);
+    cudaFree(c->stage[1]);
+    if (c->s_in) {
+        cudaStreamSynchronize(c->s_in);
+        cudaStreamSynchronize(c->s_out);
+        cudaStreamDestroy(c->s_in);
+        cudaStreamDestroy(c->s_out);
+    }
+    for (cudaEvent_t e : {c->ev_entry, c->ev_in[0], c->ev_in[1], c->ev_k[0], c->ev_k[1], c->ev_out[0], c->ev_out[1]})
+        if (e) cudaEventDestroy(e);
     cudaFree(c->d_trace);
     if (c->done) cudaEventDestroy(c->done);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -588,14 +600,24 @@ int seeds_anytime_steps(seeds_ctx *c, int32_t *steps)
     return from_cuda(cudaMemcpy(steps, c->d_steps, sizeof(int32_t), cudaMemcpyDeviceToHost));
 }
 
-int seeds_run_host(seeds_ctx *c, const uint8_t *const *h_rgb, const int64_t *h_row_strides, int32_t *const *h_labels,
-                   void *stream)
+}  // extern "C"
+
+namespace {
+
+bool host_io_valid(const seeds_ctx *c, const uint8_t *const *h_rgb, const int64_t *h_row_strides,
+                   int32_t *const *h_labels, size_t count)
 {
-    if (!c || !h_rgb || !h_row_strides || !h_labels) return SEEDS_ERR_INVALID;
     const size_t n = c->img.size();
-    for (size_t i = 0; i < n; ++i)
-        if (!h_rgb[i] || !h_labels[i] || h_row_strides[i] < 3 * (int64_t)c->img[i].p.width) return SEEDS_ERR_INVALID;
-    if (!c->stage) {
+    for (size_t j = 0; j < count; ++j)
+        if (!h_rgb[j] || !h_labels[j] || h_row_strides[j] < 3 * (int64_t)c->img[j % n].p.width) return false;
+    return true;
+}
+
+// Staging slot `slot` (each slot: every image's RGB, then its int32 labels)
+int ensure_stage(seeds_ctx *c, int slot)
+{
+    const size_t n = c->img.size();
+    if (c->stage_rgb.empty()) {
         size_t off = 0;
         c->stage_rgb.resize(n);
         c->stage_out.resize(n);
@@ -605,29 +627,111 @@ int seeds_run_host(seeds_ctx *c, const uint8_t *const *h_rgb, const int64_t *h_r
             c->stage_out[i] = off;
             off = align_up(off + (size_t)c->img[i].N * 4);
         }
-        int rc = from_cuda(cudaMalloc((void **)&c->stage, off));
-        if (rc) return rc;
         c->stage_bytes = off;
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    for (size_t i = 0; i < n; ++i) {
+    if (c->stage[slot]) return SEEDS_OK;
+    return from_cuda(cudaMalloc((void **)&c->stage[slot], c->stage_bytes));
+}
+
+// batch `h_*[0..n)` host -> staging slot, on stream s; points the io records at the slot
+int stage_in(seeds_ctx *c, int slot, const uint8_t *const *h_rgb, const int64_t *h_row_strides, cudaStream_t s)
+{
+    for (size_t i = 0; i < c->img.size(); ++i) {
         const ImageHost &h = c->img[i];
         const size_t row = (size_t)h.p.width * 3;
-        int rc = from_cuda(cudaMemcpy2DAsync(c->stage + c->stage_rgb[i], row, h_rgb[i], (size_t)h_row_strides[i], row,
-                                             (size_t)h.p.height, cudaMemcpyHostToDevice, s));
+        int rc = from_cuda(cudaMemcpy2DAsync(c->stage[slot] + c->stage_rgb[i], row, h_rgb[i], (size_t)h_row_strides[i],
+                                             row, (size_t)h.p.height, cudaMemcpyHostToDevice, s));
         if (rc) return rc;
-        c->io[i].rgb = c->stage + c->stage_rgb[i];
+        c->io[i].rgb = c->stage[slot] + c->stage_rgb[i];
         c->io[i].stride = (int64_t)row;
-        c->io[i].out = (int32_t *)(c->stage + c->stage_out[i]);
+        c->io[i].out = (int32_t *)(c->stage[slot] + c->stage_out[i]);
     }
-    int rc = launch(c, SCHED_FULL, 0, 0, s);
-    if (rc) return rc;
-    for (size_t i = 0; i < n; ++i) {
-        rc = from_cuda(cudaMemcpyAsync(h_labels[i], c->stage + c->stage_out[i], (size_t)c->img[i].N * 4,
-                                       cudaMemcpyDeviceToHost, s));
+    return SEEDS_OK;
+}
+
+int stage_out(seeds_ctx *c, int slot, int32_t *const *h_labels, cudaStream_t s)
+{
+    for (size_t i = 0; i < c->img.size(); ++i) {
+        int rc = from_cuda(cudaMemcpyAsync(h_labels[i], c->stage[slot] + c->stage_out[i], (size_t)c->img[i].N * 4,
+                                           cudaMemcpyDeviceToHost, s));
         if (rc) return rc;
     }
-    return from_cuda(cudaEventRecord(c->done, s));
+    return SEEDS_OK;
+}
+
+int ensure_pipe(seeds_ctx *c)
+{
+    if (c->s_in) return SEEDS_OK;
+    int rc = from_cuda(cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking));
+    if (!rc) rc = from_cuda(cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&c->ev_entry, &c->ev_in[0], &c->ev_in[1], &c->ev_k[0], &c->ev_k[1], &c->ev_out[0],
+                           &c->ev_out[1]})
+        if (!rc) rc = from_cuda(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int seeds_run_host(seeds_ctx *c, const uint8_t *const *h_rgb, const int64_t *h_row_strides, int32_t *const *h_labels,
+                   void *stream)
+{
+    if (!c || !h_rgb || !h_row_strides || !h_labels) return SEEDS_ERR_INVALID;
+    if (!host_io_valid(c, h_rgb, h_row_strides, h_labels, c->img.size())) return SEEDS_ERR_INVALID;
+    int rc = ensure_stage(c, 0);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = stage_in(c, 0, h_rgb, h_row_strides, s);
+    if (!rc) rc = launch(c, SCHED_FULL, 0, 0, s);
+    if (!rc) rc = stage_out(c, 0, h_labels, s);
+    return rc ? rc : from_cuda(cudaEventRecord(c->done, s));
+}
+
+// Batch b uses staging slot b & 1.  Its copies in (stream s_in) wait for the
+// launch of batch b-2, the last reader of that slot's RGB; its launch (the
+// caller's stream) waits for them and for the copies out of batch b-2, the
+// last readers of the slot's labels; its copies out (s_out) wait for the
+// launch.  Each wait names the event's latest record, made one or two
+// batches earlier, before the event is recorded again.
+int seeds_run_host_stream(seeds_ctx *c, int32_t n_batches, const uint8_t *const *h_rgb,
+                          const int64_t *h_row_strides, int32_t *const *h_labels, void *stream)
+{
+    if (!c || n_batches < 1 || !h_rgb || !h_row_strides || !h_labels) return SEEDS_ERR_INVALID;
+    const size_t n = c->img.size();
+    if (!host_io_valid(c, h_rgb, h_row_strides, h_labels, n * (size_t)n_batches)) return SEEDS_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    int rc = from_cuda(cudaStreamIsCapturing(s, &cap));
+    if (rc) return rc;
+    if (cap != cudaStreamCaptureStatusNone) return SEEDS_ERR_INVALID;
+    rc = ensure_stage(c, 0);
+    if (!rc) rc = ensure_stage(c, 1);
+    if (!rc) rc = ensure_pipe(c);
+    if (rc) return rc;
+    // the copy streams start after the caller's earlier work (an earlier
+    // host run may still be reading slot 0)
+    rc = from_cuda(cudaEventRecord(c->ev_entry, s));
+    if (!rc) rc = from_cuda(cudaStreamWaitEvent(c->s_in, c->ev_entry, 0));
+    if (!rc) rc = from_cuda(cudaStreamWaitEvent(c->s_out, c->ev_entry, 0));
+    for (int32_t b = 0; b < n_batches && !rc; ++b) {
+        const int slot = b & 1;
+        const size_t at = (size_t)b * n;
+        if (b >= 2) rc = from_cuda(cudaStreamWaitEvent(c->s_in, c->ev_k[slot], 0));
+        if (!rc) rc = stage_in(c, slot, h_rgb + at, h_row_strides + at, c->s_in);
+        if (!rc) rc = from_cuda(cudaEventRecord(c->ev_in[slot], c->s_in));
+        if (!rc) rc = from_cuda(cudaStreamWaitEvent(s, c->ev_in[slot], 0));
+        if (!rc && b >= 2) rc = from_cuda(cudaStreamWaitEvent(s, c->ev_out[slot], 0));
+        if (!rc) rc = launch(c, SCHED_FULL, 0, 0, s);
+        if (!rc) rc = from_cuda(cudaEventRecord(c->ev_k[slot], s));
+        if (!rc) rc = from_cuda(cudaStreamWaitEvent(c->s_out, c->ev_k[slot], 0));
+        if (!rc) rc = stage_out(c, slot, h_labels + at, c->s_out);
+        if (!rc) rc = from_cuda(cudaEventRecord(c->ev_out[slot], c->s_out));
+    }
+    // the caller's stream ends after the last copies out (s_out runs them in order)
+    const int last = (n_batches - 1) & 1;
+    if (!rc) rc = from_cuda(cudaStreamWaitEvent(s, c->ev_out[last], 0));
+    return rc ? rc : from_cuda(cudaEventRecord(c->done, s));
 }
 
 int seeds_status(seeds_ctx *c)

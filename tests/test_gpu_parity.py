@@ -1,5 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the oracle, bit for
 bit (labels, bins, histograms and sizes are integers: tolerance 0)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -246,6 +248,51 @@ def test_iterate_then_labels_and_host_path(torch, binding):
         torch.cuda.synchronize()
         ctx.check_status()
         assert np.array_equal(dst.numpy(), want)
+
+
+def test_streamed_host_runs_match_the_oracle_batch_by_batch(torch, binding):
+    """seeds_run_host_stream: five batches of two images (three distinct
+    image sets, one of them pageable with padded rows), copies overlapping
+    the launches through two staging slots; every batch's labels equal the
+    oracle's, and host runs before and after on the same context still do."""
+    jobs = [synth.JobSpec(synth.ImageSpec(97, 61, seed=6, cells=9, sigma=10.0, gradient=True), 30, 8, 3, 2, 3),
+            synth.JobSpec(synth.ImageSpec(64, 48, seed=5, cells=7, sigma=12.0), 12, 4, 2, 2)]
+    ctx = binding.SeedsContext([gc.params_for(binding, j) for j in jobs])
+    sets, wants = [], []
+    for s in range(3):
+        imgs = [synth.make_image(dataclasses.replace(j.image, seed=j.image.seed + 10 * s)) for j in jobs]
+        wants.append([gc.oracle_run(j, im) for j, im in zip(jobs, imgs)])
+        if s == 2:  # pageable, rows 5 bytes apart beyond 3*W
+            host = []
+            for im in imgs:
+                H, W = im.shape[:2]
+                pad = np.zeros((H, W * 3 + 5), np.uint8)
+                pad[:, :W * 3] = im.reshape(H, W * 3)
+                host.append(torch.from_numpy(pad)[:, :W * 3].reshape(H, W, 3))
+        else:
+            host = [torch.from_numpy(im).pin_memory() for im in imgs]
+        sets.append(host)
+    order = [0, 1, 2, 0, 1]
+    outs = [[torch.full((j.image.height, j.image.width), -1, dtype=torch.int32).pin_memory() for j in jobs]
+            for _ in order]
+    single = [torch.empty((j.image.height, j.image.width), dtype=torch.int32).pin_memory() for j in jobs]
+    ctx.run_host(sets[1], single)
+    ctx.run_host_stream([sets[s] for s in order], outs)
+    ctx.run_host(sets[2], single)
+    torch.cuda.synchronize()
+    ctx.check_status()
+    for s, o in zip(order, outs):
+        for w, t in zip(wants[s], o):
+            assert np.array_equal(t.numpy(), w)
+    for w, t in zip(wants[2], single):
+        assert np.array_equal(t.numpy(), w)
+    one = [torch.empty_like(t) for t in outs[0]]  # a stream of one batch
+    ctx.run_host_stream([sets[1]], [one])
+    torch.cuda.synchronize()
+    for w, t in zip(wants[1], one):
+        assert np.array_equal(t.numpy(), w)
+    bad = binding.lib.seeds_run_host_stream(ctx._h, 0, None, None, None, None)
+    assert bad == binding.SEEDS_ERR_INVALID
 
 
 def test_strided_device_image(torch, binding):
