@@ -141,3 +141,17 @@ def test_every_declaration_cites_the_paper_or_says_it_has_no_counterpart():
     for name, comment in declaration_comments().items():
         flat = " ".join(re.sub(r"\n\s*\*(?!/)", " ", comment).split())
         assert re.search(r"\b(Sec\.|Prop\.|Eq\.)", flat) or "no counterpart" in flat.lower(), name
+
+
+def test_entry_points_refuse_a_null_context_or_server(binding):
+    """Every call on a context or a server checks its handle before anything
+    else: a null one returns SEEDS_ERR_INVALID (no device is touched)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    sigs = re.findall(r"\bint\s+(seeds_\w+)\s*\(\s*(?:const\s+)?(seeds_ctx|seeds_server)\s*\*", text)
+    assert len(sigs) >= 30
+    for name, _ in sigs:
+        fn = getattr(binding.lib, name)
+        args = [None if t is ctypes.c_void_p or hasattr(t, "contents") or t is None else t(1)
+                for t in fn.argtypes]
+        args[0] = None
+        assert fn(*args) == binding.SEEDS_ERR_INVALID, name
