@@ -45,7 +45,7 @@ def job_params(job: synth.JobSpec) -> binding.seeds_params:
 
 def run_stream(requests: Sequence[Tuple[float, synth.JobSpec]], images: Sequence, arena_bytes: int,
                max_slots: int = 64, epoch_steps: int = 8, max_bins_per_channel: int = 8,
-               pinned: bool = True, keep_labels: bool = True) -> StreamResult:
+               pinned: bool = True, keep_labels: bool = True, prepin: int = 8) -> StreamResult:
     """Serve `requests` (arrival time in s, job) whose host images are
     `images` (uint8 HxWx3, one per request).  Arrivals are released in real
     time on the server's clock.
@@ -53,7 +53,12 @@ def run_stream(requests: Sequence[Tuple[float, synth.JobSpec]], images: Sequence
     Requests that name the same image object share one (pinned) copy of it.
     With keep_labels=False a request's label buffer goes back to a pool of
     its size once the request completes, for a later request to reuse, and
-    the result carries no labels.  Pinning a separate copy of every image and
+    the result carries no labels; each size's pool starts with up to
+    `prepin` buffers made before the first arrival, and grows only when
+    more requests of that size are resident at once.  A buffer made during
+    the stream pins host memory on the release loop's time (~10 ms for a
+    3840x2160 label map), so a backlog that needs new buffers grows while
+    they are made.  Pinning a separate copy of every image and
     every label map (tens of GB for a 2 s stream at 2000 req/s) made the
     host stall more and more as it pinned and released them: p99 at 1000
     req/s grew from 8 to 47 ms over three streams, against 8-9 ms with shared
@@ -80,30 +85,39 @@ def run_stream(requests: Sequence[Tuple[float, synth.JobSpec]], images: Sequence
     gc.collect()
     gc.disable()
     try:
-        return _serve(srv, requests, params, srcs, pinned, keep_labels)
+        return _serve(srv, requests, params, srcs, pinned, keep_labels, prepin)
     finally:
         if gc_was_on:
             gc.enable()
         srv.close()
 
 
-def _serve(srv, requests, params, srcs, pinned, keep_labels) -> StreamResult:
+def _serve(srv, requests, params, srcs, pinned, keep_labels, prepin) -> StreamResult:
     """run_stream's loop: release, step, poll until every request is done."""
     import torch
 
     n = len(requests)
     spare: Dict[Tuple[int, int], List[object]] = {}
 
-    def label_buffer(job):
-        shape = (job.image.height, job.image.width)
-        pool = spare.get(shape)
-        if pool:
-            return pool.pop()
+    def new_buffer(shape):
         o = torch.empty(shape, dtype=torch.int32)
         return o.pin_memory() if pinned else o
 
-    # kept labels: every request's buffer exists before the first arrival
-    outs: List[object] = [label_buffer(job) for _, job in requests] if keep_labels else [None] * n
+    def label_buffer(job):
+        shape = (job.image.height, job.image.width)
+        pool = spare.get(shape)
+        return pool.pop() if pool else new_buffer(shape)
+
+    if keep_labels:  # every request's buffer exists before the first arrival
+        outs: List[object] = [label_buffer(job) for _, job in requests]
+    else:
+        outs = [None] * n
+        count: Dict[Tuple[int, int], int] = {}
+        for _, job in requests:
+            shape = (job.image.height, job.image.width)
+            count[shape] = count.get(shape, 0) + 1
+        for shape, c in count.items():
+            spare[shape] = [new_buffer(shape) for _ in range(min(c, prepin))]
 
     start = srv.stats().host_ms
     arrival = np.array([start + 1e3 * a for a, _ in requests])

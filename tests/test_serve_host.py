@@ -118,3 +118,29 @@ def test_garbage_collector_is_off_during_the_stream_and_restored(fake, was_on):
         assert fake.last.gc_on == [False] * len(reqs)
     finally:
         gc.enable()
+
+
+@pytest.mark.parametrize("prepin", [0, 8])
+def test_label_pools_are_made_before_the_first_arrival(fake, monkeypatch, prepin):
+    """Without kept labels each size's pool is filled before the stream
+    starts (up to `prepin` buffers), so no buffer is made on the release
+    loop's time while no more than that many requests of a size are
+    resident; with prepin=0 they are made as requests arrive."""
+    import torch
+    made_at = []  # submits done when each label buffer was made
+    real_empty = torch.empty
+
+    def counting_empty(*a, **k):
+        t = real_empty(*a, **k)
+        if k.get("dtype") is torch.int32:
+            made_at.append(len(FakeServer.last.srcs))
+        return t
+
+    monkeypatch.setattr(torch, "empty", counting_empty)
+    reqs, imgs = stream(n=30, gap_s=0.002)
+    serve.run_stream(reqs, imgs, arena_bytes=1 << 20, pinned=False, keep_labels=False, prepin=prepin)
+    assert made_at
+    if prepin:
+        assert max(made_at) == 0 and len(made_at) == 3 * min(10, prepin)
+    else:
+        assert max(made_at) > 0 and len(made_at) < len(reqs)
