@@ -367,7 +367,10 @@ int seeds_autotune(seeds_ctx *c, const uint8_t *const *h_rgb_ptrs, const int64_t
  * at the next epoch.  Requests are admitted first come first served when a
  * slot is free and their footprint (seeds_footprint plus 7 bytes per pixel
  * of image and label staging) fits the arena.  Each image's labels are the
- * same alone or in any mix.  All work runs on the server's own stream. */
+ * same alone or in any mix.  All work runs on the server's own streams:
+ * one for the launches and one each for the copies in and out, which
+ * overlap the launches; a finished image's arena space is reused only once
+ * its labels have reached the host. */
 typedef struct seeds_server seeds_server;
 
 typedef struct {

@@ -7,9 +7,12 @@
 // call to seeds_server_step launches one epoch: one persistent-kernel launch
 // that advances every resident image by up to `epoch_steps` of its ops, so
 // images admitted while others are on the device start at the next epoch
-// and run side by side with them.  A finished image's labels are copied to
-// its host buffer and its arena space is reused by later epochs (the stream
-// orders the reuse after the copy).
+// and run side by side with them.  The copies run on two streams beside
+// the launches: an admitted image's RGB goes in while the previous epoch
+// runs, and a finished image's labels go out while the next one does.  A
+// finished image's arena space returns to the allocator only once its
+// epoch's copies out have completed, so a later admission's copy in, which
+// waits for nothing, never overwrites state still in use.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -86,8 +89,9 @@ struct Request {
 };
 
 struct Epoch {
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr;   // recorded after the epoch's copies out
     std::vector<int64_t> done;  // requests whose labels this epoch delivers
+    std::vector<std::pair<size_t, size_t>> freed;  // their arena space (offset, bytes)
 };
 
 // bytes a request occupies in the arena: its state, its image, its labels
@@ -121,7 +125,9 @@ struct seeds_server {
     StepEntry *d_ent = nullptr;
     int32_t *d_first = nullptr;
     int64_t *d_vt = nullptr;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;            // the epochs' launches
+    cudaStream_t s_in = nullptr, s_out = nullptr;  // copies in and out
+    cudaEvent_t ev_in = nullptr, ev_k = nullptr;   // copies in done; launch done
     int grid = 0;
     size_t smem = 0;
     std::deque<Request *> queue;
@@ -163,6 +169,7 @@ int reap(seeds_server *s, size_t keep)
         float ms = 0.f;
         cudaEventElapsedTime(&ms, s->t0, ep.ev);
         for (int64_t id : ep.done) s->completed.emplace_back(id, ms);
+        for (auto &f : ep.freed) s->alloc.release(f.first, f.second);
         s->spare_events.push_back(ep.ev);
         s->inflight.pop_front();
     }
@@ -172,7 +179,8 @@ int reap(seeds_server *s, size_t keep)
 void destroy_server(seeds_server *s)
 {
     if (!s) return;
-    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (cudaStream_t st : {s->stream, s->s_in, s->s_out})
+        if (st) cudaStreamSynchronize(st);
     for (auto *r : s->queue) delete r;
     for (auto *r : s->slots) delete r;
     for (auto &ep : s->inflight) cudaEventDestroy(ep.ev);
@@ -185,7 +193,10 @@ void destroy_server(seeds_server *s)
     cudaFree(s->d_ent);
     cudaFree(s->d_first);
     cudaFree(s->d_vt);
-    if (s->stream) cudaStreamDestroy(s->stream);
+    for (cudaStream_t st : {s->stream, s->s_in, s->s_out})
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : {s->ev_in, s->ev_k})
+        if (e) cudaEventDestroy(e);
     delete s;
 }
 
@@ -212,6 +223,10 @@ int seeds_server_create(const seeds_server_config *cfg, seeds_server **out)
     int rc = from_cuda(cudaGetDevice(&s->device));
     if (!rc) rc = from_cuda(cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device));
     if (!rc) rc = from_cuda(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    if (!rc) rc = from_cuda(cudaStreamCreateWithFlags(&s->s_in, cudaStreamNonBlocking));
+    if (!rc) rc = from_cuda(cudaStreamCreateWithFlags(&s->s_out, cudaStreamNonBlocking));
+    if (!rc) rc = from_cuda(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
+    if (!rc) rc = from_cuda(cudaEventCreateWithFlags(&s->ev_k, cudaEventDisableTiming));
     if (!rc) rc = from_cuda(cudaMalloc((void **)&s->arena, (size_t)cfg->arena_bytes));
     if (!rc) rc = from_cuda(cudaMalloc((void **)&s->d_imgs, sizeof(DevImage) * cfg->max_slots));
     if (!rc) rc = from_cuda(cudaMalloc((void **)&s->d_bar, sizeof(GridBarrier)));
@@ -291,6 +306,7 @@ int seeds_server_step(seeds_server *s, int32_t *resident_out)
     cudaStream_t st = s->stream;
 
     // admit from the head of the queue while a slot and arena space are free
+    int admitted_now = 0;
     while (!s->queue.empty()) {
         Request *r = s->queue.front();
         int slot = -1;
@@ -304,7 +320,7 @@ int seeds_server_step(seeds_server *s, int32_t *resident_out)
         unsigned char *base = s->arena + r->off;
         const size_t row = (size_t)r->h.p.width * 3;
         rc = from_cuda(cudaMemcpy2DAsync(base + r->rgb_off, row, r->h_rgb, (size_t)r->stride, row,
-                                         (size_t)r->h.p.height, cudaMemcpyHostToDevice, st));
+                                         (size_t)r->h.p.height, cudaMemcpyHostToDevice, s->s_in));
         const DevImage rec =
             make_dev_image(r->h, base, s->tune, IoEntry{base + r->rgb_off, (int64_t)row, (int32_t *)(base + r->out_off)},
                            s->d_err);
@@ -318,6 +334,13 @@ int seeds_server_step(seeds_server *s, int32_t *resident_out)
         r->slot = slot;
         s->slots[slot] = r;
         ++s->admitted;
+        ++admitted_now;
+    }
+    // the epoch reads the admitted images' RGB
+    if (admitted_now) {
+        rc = from_cuda(cudaEventRecord(s->ev_in, s->s_in));
+        if (!rc) rc = from_cuda(cudaStreamWaitEvent(st, s->ev_in, 0));
+        if (rc) return rc;
     }
 
     // plan the epoch: every resident image advances by up to epoch_steps ops
@@ -348,6 +371,8 @@ int seeds_server_step(seeds_server *s, int32_t *resident_out)
     if (!rc)
         rc = from_cuda(
             launch_persistent(s->d_imgs, sch, s->d_bar, s->d_err, s->grid, s->tune.threads_per_block, s->smem, st));
+    if (!rc) rc = from_cuda(cudaEventRecord(s->ev_k, st));
+    if (!rc) rc = from_cuda(cudaStreamWaitEvent(s->s_out, s->ev_k, 0));
     if (rc) return rc;
     s->launches += 2;
     ++s->epochs;
@@ -360,15 +385,15 @@ int seeds_server_step(seeds_server *s, int32_t *resident_out)
         r->pending = is_phase(r->h.ops[r->progress - 1].kind) ? r->progress - 1 : -1;
         if (r->progress < r->nops) continue;
         rc = from_cuda(cudaMemcpyAsync(r->h_out, s->arena + r->off + r->out_off, (size_t)r->h.N * 4,
-                                       cudaMemcpyDeviceToHost, st));
+                                       cudaMemcpyDeviceToHost, s->s_out));
         if (rc) return rc;
         ep.done.push_back(r->id);
+        ep.freed.emplace_back(r->off, r->bytes);
         s->slots[r->slot] = nullptr;
-        s->alloc.release(r->off, r->bytes);
         delete r;
     }
     ep.ev = take_event(s);
-    rc = from_cuda(cudaEventRecord(ep.ev, st));
+    rc = from_cuda(cudaEventRecord(ep.ev, s->s_out));
     if (rc) return rc;
     s->inflight.push_back(ep);
     return SEEDS_OK;
@@ -392,7 +417,9 @@ int seeds_server_poll(seeds_server *s, int64_t *ids, float *done_ms, int32_t cap
 int seeds_server_drain(seeds_server *s)
 {
     if (!s) return SEEDS_ERR_INVALID;
-    int rc = from_cuda(cudaStreamSynchronize(s->stream));
+    int rc = SEEDS_OK;
+    for (cudaStream_t st : {s->stream, s->s_in, s->s_out})
+        if (!rc) rc = from_cuda(cudaStreamSynchronize(st));
     if (rc) return rc;
     rc = reap(s, 0);
     if (rc) return rc;
