@@ -326,9 +326,10 @@ int seeds_server_step(seeds_server *s, int32_t *resident_out)
                            s->d_err);
         if (!rc) rc = from_cuda(launch_admit(s->d_imgs, slot, rec, st));
         if (rc) {
+            cudaStreamSynchronize(s->s_in);  // its copy in may be under way
             s->alloc.release(r->off, r->bytes);
             delete r;
-            return rc;
+            break;
         }
         ++s->launches;
         r->slot = slot;
@@ -336,12 +337,14 @@ int seeds_server_step(seeds_server *s, int32_t *resident_out)
         ++s->admitted;
         ++admitted_now;
     }
-    // the epoch reads the admitted images' RGB
+    // the epoch reads the admitted images' RGB (also after a failed
+    // admission: the ones admitted before it stay resident)
     if (admitted_now) {
-        rc = from_cuda(cudaEventRecord(s->ev_in, s->s_in));
-        if (!rc) rc = from_cuda(cudaStreamWaitEvent(st, s->ev_in, 0));
-        if (rc) return rc;
+        int rw = from_cuda(cudaEventRecord(s->ev_in, s->s_in));
+        if (!rw) rw = from_cuda(cudaStreamWaitEvent(st, s->ev_in, 0));
+        if (!rc) rc = rw;
     }
+    if (rc) return rc;
 
     // plan the epoch: every resident image advances by up to epoch_steps ops
     EpochPlan plan;
