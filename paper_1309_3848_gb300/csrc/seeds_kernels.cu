@@ -443,46 +443,61 @@ __device__ void op_init(const DevImage &im, int k, int lane, int32_t *wsh)
     const int sx = k % im.gx, sy = k / im.gx;
     const int x0 = (int)((int64_t)sx * im.W / im.gx), x1 = (int)((int64_t)(sx + 1) * im.W / im.gx);
     const int y0 = (int)((int64_t)sy * im.H / im.gy), y1 = (int)((int64_t)(sy + 1) * im.H / im.gy);
-    const int area = (x1 - x0) * (y1 - y0);
+    const int w = x1 - x0, area = w * (y1 - y0);
     const int B = im.B;
-    // rounds of 8 rows x 32 columns: lanes walk a row, rows are unrolled
-    for (int yb = y0; yb < y1; yb += 8)
-        for (int xb = x0; xb < x1; xb += 32) {
-        int j[8], p[8];
-        const int x = xb + lane;
+    // The rectangle's pixels in row-major order, 256 per round: lane l takes
+    // pixels l, l + 32, ..., l + 224 of the round, so every lane has work in
+    // every round but the last whatever the rectangle's width.  A position
+    // (x, y) steps 32 pixels on by (32 % w, 32 / w) and at most one wrap.
+    const int step_y = 32 / w, step_x = 32 - step_y * w;
+    int x = lane % w, y = lane / w;  // relative to (x0, y0)
+    for (int i0 = 0; i0 < area; i0 += 256) {
+        int j[8];
+        const int rx = x, ry = y;  // the round's first position, walked again for the stores
         // the round's 24 byte loads first, then the arithmetic on them
         uint32_t rgb[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int y = yb + q;
             rgb[q] = 0xFFFFFFFFu;
-            if (y < y1 && x < x1) {
-                const uint8_t *px = im.rgb + (int64_t)y * im.stride + 3 * (int64_t)x;
+            if (y0 + y < y1) {
+                const uint8_t *px = im.rgb + (int64_t)(y0 + y) * im.stride + 3 * (int64_t)(x0 + x);
                 rgb[q] = (uint32_t)px[0] | ((uint32_t)px[1] << 8) | ((uint32_t)px[2] << 16);
+            }
+            x += step_x;
+            y += step_y;
+            if (x >= w) {
+                x -= w;
+                ++y;
             }
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             j[q] = -1;
-            p[q] = 0;
             if (rgb[q] != 0xFFFFFFFFu) {
                 int r = rgb[q] & 255, g = (rgb[q] >> 8) & 255, b = (rgb[q] >> 16) & 255;
                 if (im.color) lab8(r, g, b, r, g, b);
                 j[q] = ((r * B) >> 8) * B * B + ((g * B) >> 8) * B + ((b * B) >> 8);
-                p[q] = (yb + q) * im.W + x;
             }
         }
+        int cx = rx, cy = ry;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            if (j[q] >= 0) {
+            if (j[q] >= 0) {  // a pixel of the rectangle
+                const int p = (y0 + cy) * im.W + x0 + cx;
                 if (im.bins16)
-                    ((uint16_t *)im.bins)[p[q]] = (uint16_t)j[q];
+                    ((uint16_t *)im.bins)[p] = (uint16_t)j[q];
                 else
-                    ((uint8_t *)im.bins)[p[q]] = (uint8_t)j[q];
-                if (im.L == 0) im.lab[0][0][p[q]] = im.lab[0][1][p[q]] = (uint16_t)k;
+                    ((uint8_t *)im.bins)[p] = (uint8_t)j[q];
+                if (im.L == 0) im.lab[0][0][p] = im.lab[0][1][p] = (uint16_t)k;
             }
             const unsigned peers = __match_any_sync(0xffffffffu, j[q]);
             if (j[q] >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hsh[j[q]], __popc(peers));
+            cx += step_x;
+            cy += step_y;
+            if (cx >= w) {
+                cx -= w;
+                ++cy;
+            }
         }
     }
     if (im.edges) edge_mask_rect(im, x0, x1, y0, y1, lane);
