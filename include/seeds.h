@@ -382,7 +382,7 @@ typedef struct {
 
 typedef struct {
     int32_t queued, resident;
-    int64_t arena_free_bytes;
+    int64_t arena_free_bytes;  /* free now: a finished request's space counts once its labels have reached the host */
     int64_t epochs, launches, admitted;
     double host_ms;  /* host time since creation, on the clock done_ms uses */
 } seeds_server_stats_t;
