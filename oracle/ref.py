@@ -80,6 +80,10 @@ def lib():
             L.ref_decide.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.ref_run_sequential.argtypes = [vp, vp, i64, u64, ctypes.c_int, vp, i64]
             L.ref_run_sequential.restype = i64
+            L.ref_splitmix64_draws.argtypes = [u64, i32, vp]
+            L.ref_splitmix64_draws.restype = None
+            L.ref_unit_order.argtypes = [u64, i32, vp]
+            L.ref_unit_order.restype = None
             _lib = L
     return _lib
 
@@ -105,6 +109,21 @@ def grid(width, height, num_superpixels, block_levels=0, bins_per_channel=5, ite
     gx, gy = ctypes.c_int32(0), ctypes.c_int32(0)
     rc = lib().ref_grid(ctypes.byref(p), ctypes.byref(gx), ctypes.byref(gy))
     return rc, gx.value, gy.value
+
+
+def splitmix64_draws(seed, n):
+    """The first n 64-bit draws of the sequential mode's generator from
+    state `seed`."""
+    out = np.zeros(n, np.uint64)
+    lib().ref_splitmix64_draws(ctypes.c_uint64(seed), n, out.ctypes.data)
+    return [int(v) for v in out]
+
+
+def unit_order(seed, nu):
+    """The sequential mode's first-sweep visiting order of nu units."""
+    out = np.zeros(nu, np.int32)
+    lib().ref_unit_order(ctypes.c_uint64(seed), nu, out.ctypes.data)
+    return out
 
 
 def _rgb_arg(rgb):

@@ -103,7 +103,9 @@
  *   R14 sequential mode (quality reference only): per iteration the units
  *       are visited in a random permutation (SplitMix64 + Fisher-Yates),
  *       each boundary unit proposes one uniformly drawn candidate, and an
- *       accepted move is applied at once.
+ *       accepted move is applied at once.  The generator and the visiting
+ *       order are pinned (published SplitMix64 outputs; uniformity over all
+ *       orders); the candidate draw is parity unpinned.
  */
 #include <math.h>
 #include <stdint.h>
@@ -996,6 +998,35 @@ static uint64_t splitmix64(uint64_t *s)
     return z ^ (z >> 31);
 }
 
+/* One sweep's visiting order of nu units: the identity shuffled by Fisher
+ * and Yates' method in Durstenfeld's form (Knuth, TAOCP vol. 2, 3.4.2,
+ * Algorithm P): for u = nu-1 down to 1, swap entry u with a uniformly drawn
+ * entry v in [0, u]. */
+static void shuffle_units(uint64_t *rng, int32_t *order, int64_t nu)
+{
+    for (int64_t u = 0; u < nu; ++u) order[u] = (int32_t)u;
+    for (int64_t u = nu - 1; u > 0; --u) {
+        int64_t v = (int64_t)(splitmix64(rng) % (uint64_t)(u + 1));
+        int32_t t = order[u];
+        order[u] = order[v];
+        order[v] = t;
+    }
+}
+
+/* test hooks: the first n draws from state `seed`, and the first sweep's
+ * visiting order of nu units, as the sequential mode makes them */
+void ref_splitmix64_draws(uint64_t seed, int32_t n, uint64_t *out)
+{
+    uint64_t rng = seed;
+    for (int32_t i = 0; i < n; ++i) out[i] = splitmix64(&rng);
+}
+
+void ref_unit_order(uint64_t seed, int32_t nu, int32_t *out)
+{
+    uint64_t rng = seed;
+    shuffle_units(&rng, out, nu);
+}
+
 /* sum over labels of b^2 for the in-image 3x3 patch around (x,y), counts */
 static int64_t patch_sum_sq(const ref_state *st, int x, int y)
 {
@@ -1086,11 +1117,7 @@ int64_t ref_run_sequential(ref_state *st, const uint8_t *rgb, int64_t row_stride
         int nbx = st->nbx[level], nby = st->nby[level];
         int64_t nu = (int64_t)nbx * nby;
         for (int it = 0; it < st->p.iters_per_level; ++it) {
-            for (int64_t u = 0; u < nu; ++u) order[u] = (int32_t)u;
-            for (int64_t u = nu - 1; u > 0; --u) { /* Fisher-Yates */
-                int64_t v = (int64_t)(splitmix64(&rng) % (uint64_t)(u + 1));
-                int32_t t = order[u]; order[u] = order[v]; order[v] = t;
-            }
+            shuffle_units(&rng, order, nu);
             for (int64_t t = 0; t < nu; ++t) {
                 int bx = order[t] % nbx, by = order[t] / nbx;
                 int k = unit_label(st, level, bx, by);

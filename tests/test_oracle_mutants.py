@@ -51,6 +51,8 @@ MUTANTS = {
     "compact prior centres taken once, not at every phase start": (
         "    if (level == 0 && st->p.compact_prior > 0) means_recount(st); /* R19: centres at phase start */\n",
         "    if (level == 0 && st->p.compact_prior > 0 && phase == 0 && 0) means_recount(st);\n"),
+    "sequential visiting order by Sattolo's shuffle": ("splitmix64(rng) % (uint64_t)(u + 1)", "splitmix64(rng) % (uint64_t)u"),
+    "sequential generator loses its second mix": ("z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;", "z = z ^ (z >> 27);"),
     "SPM alone runs one histogram iteration": (
         "        for (int it = 0; it < st->p.iters_per_level; ++it)\n            for (int phase = 0; phase < 4; ++phase) total += ref_run_phase(st, level, phase);",
         "        for (int it = 0; it < (st->p.iters_per_level ? st->p.iters_per_level : 1); ++it)\n            for (int phase = 0; phase < 4; ++phase) total += ref_run_phase(st, level, phase);"),

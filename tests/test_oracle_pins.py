@@ -404,6 +404,34 @@ def test_proxy_sequential_with_one_bin_climbs_the_boundary_term():
     assert np.array_equal(lab, final)
 
 
+def test_sequential_draws_are_the_published_splitmix64_outputs():
+    """R14's generator against the published outputs of SplitMix64 from
+    state 0 (tests/golden/splitmix64_state0.txt)."""
+    want = [int(l.split()[0], 16) for l in open(os.path.join(GOLDEN, "splitmix64_state0.txt"))
+            if l.strip() and l[0] != "#"]
+    assert len(want) == 5 and ref.splitmix64_draws(0, len(want)) == want
+
+
+def test_sequential_visiting_order_is_a_uniform_permutation():
+    """R14 visits the units of a sweep in a uniformly random order: over
+    many seeds every one of the n! orders of n units occurs, at frequencies
+    a chi-square test accepts (Sattolo's variant, a draw below u instead of
+    up to u, makes only the cyclic orders; a skipped swap or a biased index
+    leaves orders out or skews them)."""
+    trials = 24000
+    for n in (1, 2, 3, 4):
+        counts = {}
+        for seed in range(trials):
+            o = tuple(ref.unit_order(seed, n).tolist())
+            counts[o] = counts.get(o, 0) + 1
+        assert set(counts) == set(itertools.permutations(range(n))), n
+        fact = len(counts)
+        e = trials / fact
+        chi2 = sum((c - e) ** 2 / e for c in counts.values())
+        # upper 0.01% points of chi-square with fact-1 = 0, 1, 5, 23 degrees of freedom
+        assert chi2 <= {1: 0.0, 2: 15.2, 6: 25.8, 24: 57.1}[fact], (n, chi2)
+
+
 def test_prop1_agreement_rate_is_high():
     """Diagnostic for Prop. 1 (an approximation; the paper reports agreement
     of 89-97%): over the parity schedule's pixel moves on a few noisy
