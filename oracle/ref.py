@@ -84,6 +84,8 @@ def lib():
             L.ref_splitmix64_draws.restype = None
             L.ref_unit_order.argtypes = [u64, i32, vp]
             L.ref_unit_order.restype = None
+            L.ref_candidate_picks.argtypes = [u64, i32, i32, vp]
+            L.ref_candidate_picks.restype = None
             _lib = L
     return _lib
 
@@ -123,6 +125,14 @@ def unit_order(seed, nu):
     """The sequential mode's first-sweep visiting order of nu units."""
     out = np.zeros(nu, np.int32)
     lib().ref_unit_order(ctypes.c_uint64(seed), nu, out.ctypes.data)
+    return out
+
+
+def candidate_picks(seed, nc, n):
+    """n successive candidate picks among nc, as the sequential mode draws
+    them from state `seed`."""
+    out = np.zeros(n, np.int32)
+    lib().ref_candidate_picks(ctypes.c_uint64(seed), nc, n, out.ctypes.data)
     return out
 
 

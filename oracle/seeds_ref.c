@@ -103,9 +103,9 @@
  *   R14 sequential mode (quality reference only): per iteration the units
  *       are visited in a random permutation (SplitMix64 + Fisher-Yates),
  *       each boundary unit proposes one uniformly drawn candidate, and an
- *       accepted move is applied at once.  The generator and the visiting
- *       order are pinned (published SplitMix64 outputs; uniformity over all
- *       orders); the candidate draw is parity unpinned.
+ *       accepted move is applied at once.  The generator, the visiting
+ *       order and the candidate pick are pinned (published SplitMix64
+ *       outputs; uniformity over all orders and over the candidates).
  */
 #include <math.h>
 #include <stdint.h>
@@ -1013,8 +1013,15 @@ static void shuffle_units(uint64_t *rng, int32_t *order, int64_t nu)
     }
 }
 
-/* test hooks: the first n draws from state `seed`, and the first sweep's
- * visiting order of nu units, as the sequential mode makes them */
+/* the candidate a unit proposes: one of its nc candidates, uniformly */
+static int draw_candidate(uint64_t *rng, int nc)
+{
+    return (int)(splitmix64(rng) % (uint64_t)nc);
+}
+
+/* test hooks: the first n draws from state `seed`, the first sweep's
+ * visiting order of nu units, and n successive candidate picks among nc,
+ * as the sequential mode makes them */
 void ref_splitmix64_draws(uint64_t seed, int32_t n, uint64_t *out)
 {
     uint64_t rng = seed;
@@ -1025,6 +1032,12 @@ void ref_unit_order(uint64_t seed, int32_t nu, int32_t *out)
 {
     uint64_t rng = seed;
     shuffle_units(&rng, out, nu);
+}
+
+void ref_candidate_picks(uint64_t seed, int32_t nc, int32_t n, int32_t *out)
+{
+    uint64_t rng = seed;
+    for (int32_t i = 0; i < n; ++i) out[i] = draw_candidate(&rng, nc);
 }
 
 /* sum over labels of b^2 for the in-image 3x3 patch around (x,y), counts */
@@ -1124,7 +1137,7 @@ int64_t ref_run_sequential(ref_state *st, const uint8_t *rgb, int64_t row_stride
                 int cand[4];
                 int nc = candidates(st, level, bx, by, k, cand);
                 if (nc == 0) continue;
-                int n = cand[splitmix64(&rng) % (uint64_t)nc];
+                int n = cand[draw_candidate(&rng, nc)];
                 if (!leaving_keeps_connected(st, level, bx, by, k)) continue;
                 int ok;
                 if (accept_mode == 1) {

@@ -53,6 +53,8 @@ MUTANTS = {
         "    if (level == 0 && st->p.compact_prior > 0 && phase == 0 && 0) means_recount(st);\n"),
     "sequential visiting order by Sattolo's shuffle": ("splitmix64(rng) % (uint64_t)(u + 1)", "splitmix64(rng) % (uint64_t)u"),
     "sequential generator loses its second mix": ("z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;", "z = z ^ (z >> 27);"),
+    "sequential candidate pick never takes the last candidate": (
+        "return (int)(splitmix64(rng) % (uint64_t)nc);", "return (int)(splitmix64(rng) % (uint64_t)(nc > 1 ? nc - 1 : 1));"),
     "SPM alone runs one histogram iteration": (
         "        for (int it = 0; it < st->p.iters_per_level; ++it)\n            for (int phase = 0; phase < 4; ++phase) total += ref_run_phase(st, level, phase);",
         "        for (int it = 0; it < (st->p.iters_per_level ? st->p.iters_per_level : 1); ++it)\n            for (int phase = 0; phase < 4; ++phase) total += ref_run_phase(st, level, phase);"),

@@ -432,6 +432,22 @@ def test_sequential_visiting_order_is_a_uniform_permutation():
         assert chi2 <= {1: 0.0, 2: 15.2, 6: 25.8, 24: 57.1}[fact], (n, chi2)
 
 
+def test_sequential_candidate_pick_is_uniform():
+    """R14's proposal: one of a unit's nc candidates, each equally likely
+    (chi-square over 60,000 picks), taken from the generator's draws."""
+    want = [int(l.split()[0], 16) for l in open(os.path.join(GOLDEN, "splitmix64_state0.txt"))
+            if l.strip() and l[0] != "#"]
+    for nc in (1, 2, 3, 4):
+        picks = ref.candidate_picks(0, nc, 60000)
+        assert [int(v) for v in picks[:5]] == [w % nc for w in want]
+        counts = np.bincount(picks, minlength=nc)
+        assert len(counts) == nc and counts.min() > 0
+        e = len(picks) / nc
+        chi2 = float(((counts - e) ** 2 / e).sum())
+        # upper 0.01% points of chi-square with nc-1 = 0..3 degrees of freedom
+        assert chi2 <= {1: 0.0, 2: 15.2, 3: 18.5, 4: 21.2}[nc], (nc, chi2)
+
+
 def test_prop1_agreement_rate_is_high():
     """Diagnostic for Prop. 1 (an approximation; the paper reports agreement
     of 89-97%): over the parity schedule's pixel moves on a few noisy
